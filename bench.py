@@ -1,0 +1,394 @@
+"""Benchmark: batched BP-SF on the [[144,12,12]] code-capacity workload.
+
+Workload (one step): 4 x 10^6 syndromes of the [[144,12,12]] BB code under
+i.i.d. Z errors at p in {0.02, 0.04, 0.06, 0.08} (10^6 per p, fixed seeds),
+decoded with normalised min-sum (alpha 0.625, max_iter 100), |Phi| = 6
+(63 trials per failed shot, short_iter 20), minimum-weight selection.  All
+four batches and all trials run in ONE persistent launch per step.
+
+Prints one JSON line.  ``--impl reference`` times the CPU oracle instead (the
+reference arm: a plain C implementation run on the host cores).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import multiprocessing as mp
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+P_LIST = (0.02, 0.04, 0.06, 0.08)
+SHOTS_PER_P = 1_000_000
+CODE = "bb144"
+N_BITS, M_CHECKS, NNZ = 144, 72, 432
+PARAMS = dict(max_iter=100, alpha=0.625, w=6, w_max=0, short_iter=20, select=0)
+METRIC = "BP-SF shots/sec and p50/p99 latency, [[144,12,12]], batched/served vs plain, equal LER"
+WORKLOAD = ("[[144,12,12]] BB code capacity, p in {0.02,0.04,0.06,0.08}, 10^6 shots per p, "
+            "max_iter 100, w 6 (63 trials) x short_iter 20, alpha 0.625, min-weight selection")
+
+
+def _gen_chunk(args):
+    import synth
+    seed, shot0, n, p = args
+    bits = synth.bernoulli_bits(seed, 0, shot0, n, N_BITS, p)
+    pad = np.zeros((n, 160), dtype=np.uint8)
+    pad[:, :N_BITS] = bits
+    return np.packbits(pad.reshape(n, 20, 8), axis=-1, bitorder="little").reshape(n, 20).view(np.uint32)
+
+
+def gen_errors(pool, p_idx, shot0, n, chunk=1 << 16):
+    import synth
+    seed = synth.SEEDS["bb144_cc"][p_idx]
+    jobs = [(seed, shot0 + a, min(chunk, n - a), P_LIST[p_idx]) for a in range(0, n, chunk)]
+    parts = pool.map(_gen_chunk, jobs) if pool else list(map(_gen_chunk, jobs))
+    return np.concatenate(parts, axis=0)
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index=0):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+def roofline_peak_edge_updates(sm_count, sm_mhz):
+    """Peak edge-updates/s of the SM-bound kernel (shared-memory bound: 16 B per
+    edge-update against 128 B/clk/SM; the ALU bound of ~10 lane-ops per
+    edge-update against 128 lanes/clk/SM is looser)."""
+    smem = sm_count * 128.0 * sm_mhz * 1e6 / 16.0
+    alu = sm_count * 128.0 * sm_mhz * 1e6 / 10.0
+    return min(smem, alu)
+
+
+# --------------------------------------------------------------------------
+# CPU oracle (the reference arm and the cpu_baseline)
+# --------------------------------------------------------------------------
+
+def oracle_sample(n_per_p, shot0=0):
+    import oracle
+    import synth
+    hx, _ = oracle.named_code(CODE)
+    oc = oracle.Code(hx)
+    threads = oracle.max_threads()
+    P = oracle.Params(PARAMS["max_iter"], PARAMS["alpha"], PARAMS["w"], PARAMS["w_max"], PARAMS["short_iter"],
+                      PARAMS["select"])
+    inputs = []
+    for k, p in enumerate(P_LIST):
+        e = synth.bernoulli_bits(synth.SEEDS["bb144_cc"][k], 0, shot0, n_per_p, N_BITS, p)
+        inputs.append((p, oc.syndrome(e)))
+    t0 = time.perf_counter()
+    for p, s in inputs:
+        oc.bpsf_batch(s, p, P, fp32=True, threads=threads)
+    dt = time.perf_counter() - t0
+    return dict(value=len(P_LIST) * n_per_p / dt, unit="shots/s", cores=threads, kind="oracle",
+                sample="%d shots per p (first shots of each p's stream), FP32 oracle, %d host threads"
+                       % (n_per_p, threads), seconds=dt)
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    n_per_p = args.ref_shots
+    oracle_sample(max(n_per_p // 20, 10))  # warm-up: load and page in the oracle
+    times, cb = [], None
+    for _ in range(args.steps):
+        cb = oracle_sample(n_per_p)
+        times.append(cb["seconds"])
+    shots = len(P_LIST) * n_per_p
+    v = shots * len(times) / sum(times)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "shots/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample_shots_per_p": n_per_p},
+            "cpu_baseline": {"value": v, "unit": "shots/s", "cores": cb["cores"], "kind": "oracle",
+                             "sample": cb["sample"]},
+            "e2e": {"value": v, "unit": "shots/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------------
+# GPU arm
+# --------------------------------------------------------------------------
+
+def run_gpu(args, rank, world, pool):
+    import torch
+    from paper_2507_00254_gb300 import build as libbuild
+    libbuild.build()
+    from paper_2507_00254_gb300 import bpsf as B
+    from paper_2507_00254_gb300 import codes, harness
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    n = args.shots_per_p
+    shot0 = rank * n  # weak scaling: each rank decodes its own 10^6 shots per p
+    c = codes.bb(CODE)
+    Pm = B.Params(**PARAMS)
+    decs = [B.Decoder(c.ptr, c.idx, c.M, c.N, np.full(c.N, p), Pm) for p in P_LIST]
+    stream = torch.cuda.current_stream()
+    # Inputs: errors from the seeded generator, syndromes by the library's kernel.
+    t_gen = time.perf_counter()
+    errs, synds = [], []
+    for k in range(len(P_LIST)):
+        e_np = gen_errors(pool, k, shot0, n)
+        e_d = torch.from_numpy(e_np.view(np.int32)).cuda()
+        errs.append(e_d)
+        synds.append(decs[k].syndrome(e_d))
+    torch.cuda.synchronize()
+    t_gen = time.perf_counter() - t_gen
+    # Launch shape: the autotuner's pick for this code.
+    tuned = decs[0].autotune(p_sample=0.06, n_sample=1 << 16) if args.autotune else decs[0].tuning
+    for d in decs:
+        d.tuning = tuned
+    outs = [d.outputs(n) for d in decs]
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.int32, device="cuda")  # 512 MB > L2
+
+    def step():
+        B.decode_multi(decs, synds, outs=outs, sync=False)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    for d in decs:
+        B.bpsf_sync(d.handle, stream.cuda_stream)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = ClockSampler(torch.cuda.current_device())
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    t_wall = time.perf_counter()
+    work = []
+    for k in range(args.steps):
+        flush.zero_()
+        ev[k][0].record(stream)
+        step()
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall
+    clk = clocks.stop()
+    if dist:
+        dist.barrier()
+    for d in decs:
+        B.bpsf_sync(d.handle, stream.cuda_stream)
+        work.append(d.last_work())
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    ms = float(np.mean(step_ms))
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    shots_step = n * len(P_LIST)
+    value = shots_step * world / (ms / 1e3)
+
+    # Roofline of the persistent kernel (the one launch per step).
+    edge_updates = sum(w["edge_updates"] for w in work)
+    props = torch.cuda.get_device_properties(0)
+    peaks = measured_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    peak = roofline_peak_edge_updates(props.multi_processor_count, sm_max)
+    achieved = edge_updates / (ms / 1e3)
+
+    # LER per p (harness, on the device) and the plain per-shot form on a sample.
+    hx = codes.bb(CODE, 0).dense()
+    hz = codes.bb(CODE, 1).dense()
+    lx = harness.x_logicals(hx, hz)
+    G = torch.from_numpy(np.vstack([hx, lx]).astype(np.float32)).cuda()
+
+    def unpack_dev(words, nb):
+        w = words.view(torch.int32)
+        bits = (w.unsqueeze(-1) >> torch.arange(32, device=w.device, dtype=torch.int32)) & 1
+        return bits.reshape(w.shape[0], -1)[:, :nb]
+
+    def fails(e_words, corr_words, conv):
+        out = torch.zeros(e_words.shape[0], dtype=torch.bool, device="cuda")
+        for a in range(0, e_words.shape[0], 1 << 18):
+            b = min(e_words.shape[0], a + (1 << 18))
+            r = unpack_dev(e_words[a:b] ^ corr_words[a:b], N_BITS).float()
+            par = torch.remainder(r @ G.T, 2.0) > 0.5
+            out[a:b] = par.any(dim=1) | (conv[a:b] == 0)
+        return out
+
+    ler, plain = {}, {}
+    n_plain = min(args.plain_shots, n)
+    for k, p in enumerate(P_LIST):
+        f = fails(errs[k], outs[k]["corr"], outs[k]["conv"])
+        L = float(f.float().mean().item())
+        ler[str(p)] = {"ler": L, "sigma": (L * (1 - L) / n) ** 0.5,
+                       "stage_counts": np.bincount(outs[k]["stage"].cpu().numpy(), minlength=3).tolist()}
+        # Plain form on the first n_plain shots: per-shot latency and equality with batched.
+        po = decs[k].outputs(n_plain)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        decs[k].decode(synds[k][:n_plain].contiguous(), out=po, plain=True)
+        dt = time.perf_counter() - t0
+        same = all(bool((po[key] == outs[k][key][:n_plain]).all()) for key in ("corr", "conv", "iters", "stage"))
+        plain[str(p)] = {"shots": n_plain, "shots_per_s": n_plain / dt, "identical_to_batched": same}
+    # Per-shot latency of the plain form (launch to flag readback), all p pooled, on a small sample.
+    lat = []
+    for k in range(len(P_LIST)):
+        po = decs[k].outputs(1)
+        for i in range(min(200, n_plain)):
+            t0 = time.perf_counter()
+            decs[k].decode(synds[k][i:i + 1].contiguous(), out=po, plain=True)
+            lat.append(time.perf_counter() - t0)
+    lat_ms = np.array(lat) * 1e3
+    plain_total = sum(v["shots"] for v in plain.values())
+    plain_time = sum(v["shots"] / v["shots_per_s"] for v in plain.values())
+
+    # End-to-end: host (pinned) syndromes in, host results out, through the C ABI.
+    h_synd = [torch.empty((n, 3), dtype=torch.int32, pin_memory=True) for _ in P_LIST]
+    for k in range(len(P_LIST)):
+        h_synd[k].copy_(synds[k].cpu())
+    h_corr = torch.empty((n, 5), dtype=torch.int32, pin_memory=True)
+    h_conv = torch.empty(n, dtype=torch.uint8, pin_memory=True)
+    h_it = torch.empty(n, dtype=torch.int16, pin_memory=True)
+    h_st = torch.empty(n, dtype=torch.uint8, pin_memory=True)
+    e2e_steps = max(1, min(args.steps, 3))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        for k in range(len(P_LIST)):
+            B.bpsf_decode_host(decs[k].handle, n, h_synd[k].data_ptr(), 3, h_corr.data_ptr(), 5,
+                               h_conv.data_ptr(), h_it.data_ptr(), h_st.data_ptr(), stream.cuda_stream)
+    e2e_dt = (time.perf_counter() - t0) / e2e_steps
+    h2d = len(P_LIST) * n * 3 * 4
+    d2h = len(P_LIST) * n * (5 * 4 + 1 + 2 + 1)
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = pool.apply(oracle_sample, (args.cpu_shots,)) if pool else oracle_sample(args.cpu_shots)
+        cpu.pop("seconds", None)
+
+    if rank == 0:
+        traffic = args.traffic_bytes if args.traffic_bytes > 0 else None
+        line = {
+            "metric": METRIC, "value": value, "unit": "shots/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "shots_per_step": shots_step * world, "form": "batched",
+                       "launch": "one persistent decode_multi launch per step (4 batches)",
+                       "tuning": list(tuned), "l2": "flushed between steps (512 MB write)",
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "roofline": {"bound": "alu", "achieved": achieved / 1e9, "peak": peak / 1e9, "unit": "Gedge-updates/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "note": "peak = SMs x 128 B/clk shared memory / 16 B per edge-update at the max SM clock"},
+            "cpu_baseline": cpu,
+            "e2e": {"value": shots_step / e2e_dt, "unit": "shots/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h},
+            "gpu_launches": args.steps,
+            "clocks": clk,
+            "latency_ms": {"batched_step_p50": float(np.percentile(step_ms, 50)),
+                           "batched_step_p99": float(np.percentile(step_ms, 99)),
+                           "plain_per_shot_p50": float(np.percentile(lat_ms, 50)),
+                           "plain_per_shot_p99": float(np.percentile(lat_ms, 99))},
+            "forms": {"batched_shots_per_s": value, "plain_shots_per_s": plain_total / plain_time,
+                      "plain": plain},
+            "ler": ler,
+            "work": {"edge_updates_per_step": edge_updates, "failed_shots_per_step": sum(w["failed_shots"] for w in work),
+                     "trial_runs_per_step": sum(w["trial_runs"] for w in work)},
+            "input_gen_s": t_gen, "wall_timed_s": t_wall,
+        }
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--shots-per-p", type=int, default=SHOTS_PER_P)
+    ap.add_argument("--plain-shots", type=int, default=2000)
+    ap.add_argument("--cpu-shots", type=int, default=15000)
+    ap.add_argument("--ref-shots", type=int, default=3000)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--autotune", type=int, default=1)
+    ap.add_argument("--traffic-bytes", type=float, default=0.0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    # Input generation and the oracle baseline use a spawn pool created before CUDA starts.
+    ctx = mp.get_context("spawn")
+    pool = ctx.Pool(processes=max(1, min(16, os.cpu_count() or 1)))
+    try:
+        run_gpu(args, rank, world, pool)
+    finally:
+        pool.close()
+        pool.join()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,312 @@
+/*
+ * bpsf.h — C ABI of libbpsf, a GB300 (sm_103a) decoder for quantum LDPC codes
+ * implementing BP-SF: normalised min-sum belief propagation with oscillation
+ * tracking, followed by speculative syndrome-flip trials, from
+ * "Fully Parallelized BP Decoding for Quantum LDPC Codes Can Outperform
+ * BP-OSD" (Wang, Li, Mueller; arXiv 2507.00254).
+ *
+ * The problem (Section II-B, "Decoding Problem"): given a parity-check matrix
+ * H in F_2^{M x N} and a syndrome s in F_2^M, find e in F_2^N with
+ * e H^T = s.  The decoder is Algorithm 1 (BP-SF): an initial min-sum run
+ * (Section II-B, Eq. c2v) with per-bit flip counters; if it does not
+ * converge, Phi = the |Phi| = w most-flipped bits, every non-empty subset t
+ * of Phi with |t| <= w_max gives a trial syndrome s' = s xor t H^T, each
+ * trial is decoded by a fresh short BP, and a converged trial returns e' xor t.
+ *
+ * Conventions used by every entry point:
+ *   - Bit vectors are packed into uint32 words, least significant bit first:
+ *     bit i of a vector lives in word i / 32 at position i % 32.  A syndrome
+ *     takes Ws = ceil(M / 32) words, a correction Wn = ceil(N / 32) words.
+ *     Rows of a batch are `stride` words apart (stride >= Ws or Wn).
+ *   - Pointers named d_* are device pointers on the current CUDA device;
+ *     h_* are host pointers.  The caller owns every input and output buffer.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default).
+ *     Device calls are asynchronous on that stream; bpsf_sync() waits and
+ *     reports errors the device found (timeouts, record overflow).
+ *   - Every function returns a bpsf_status and never aborts or throws; on
+ *     failure bpsf_last_error() gives a message for the calling thread.
+ *   - Messages are FP32.  Each add and multiply is rounded on its own, in
+ *     one fixed order (V2C and posterior sums fold from the channel LLR over
+ *     the checks of a column in ascending check index), so results do not
+ *     depend on the launch shape.
+ */
+#ifndef BPSF_H
+#define BPSF_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    BPSF_OK = 0,
+    BPSF_EINVAL = 1,    /* invalid argument (message in bpsf_last_error) */
+    BPSF_ENOMEM = 2,    /* device or pinned allocation failed, or a cap was hit */
+    BPSF_ECUDA = 3,     /* a CUDA runtime call failed */
+    BPSF_ETIMEOUT = 4,  /* a bounded wait ran out (device spin or host poll) */
+    BPSF_EBUSY = 5,     /* no room right now (serving admission) */
+    BPSF_ECLOSED = 6,   /* the server was stopped */
+    BPSF_EDEVICE = 7    /* the device reported an internal error */
+} bpsf_status;
+
+typedef enum { BPSF_CSR = 0, BPSF_CSC = 1 } bpsf_layout;
+
+enum { BPSF_SELECT_MIN_WEIGHT = 0, BPSF_SELECT_FIRST = 1 };
+
+/*
+ * Decoder parameters (Algorithm 1 inputs plus the min-sum settings of
+ * Section II-B).
+ *   max_iter   iterations of the initial run (i_max of Algorithm 1), 1..32767.
+ *   alpha      normalisation factor of Eq. (c2v), finite and > 0.
+ *   w          |Phi|, the number of oscillating bits used for trials,
+ *              0..16; 0 means plain BP with no post-processing.
+ *   w_max      largest trial weight, 1..w; 0 means w (all 2^w - 1 subsets).
+ *   short_iter iterations of each trial run, 1..max_iter.
+ *   select     BPSF_SELECT_MIN_WEIGHT: the converged trial whose e' xor t has
+ *              the smallest Hamming weight, ties to the smaller subset mask;
+ *              BPSF_SELECT_FIRST: the converged trial with the smallest mask
+ *              (the paper's "first valid" rule made deterministic).
+ *   flags      reserved, must be 0.
+ */
+typedef struct {
+    int32_t max_iter;
+    float alpha;
+    int32_t w;
+    int32_t w_max;
+    int32_t short_iter;
+    int32_t select;
+    uint32_t flags;
+} bpsf_params;
+
+typedef struct bpsf_ctx bpsf_ctx;
+
+/*
+ * Create a decoder for one code (H) and one prior vector.
+ *   M, N       rows (checks) and columns (variables) of H, 1..65535.
+ *   nnz        ones in H, 1..65535.
+ *   layout     BPSF_CSR: ptr has M+1 entries and idx holds column indices;
+ *              BPSF_CSC: ptr has N+1 entries and idx holds row indices.
+ *   ptr, idx   host arrays, copied; indices in range, no duplicates.  Every
+ *              row needs at least two ones (a check of degree one has no
+ *              "other" variable in Eq. c2v); rows of degree > 32 or columns
+ *              of degree > 16 are rejected.
+ *   priors     host array of N error probabilities p_i in (0, 0.5); the
+ *              channel LLR log((1 - p_i) / p_i) (Section II-B, step 1) is
+ *              computed in double and rounded once to float.
+ *   params     decoder parameters (see bpsf_params).
+ * The context allocates device memory on the current device and owns it.
+ */
+bpsf_status bpsf_create(bpsf_ctx **out, int32_t M, int32_t N, int64_t nnz, int32_t layout, const int32_t *ptr,
+                        const int32_t *idx, const double *priors, const bpsf_params *params);
+
+/* Release a context and its device memory (NULL is ignored).  Wait for the
+ * context's work to finish first. */
+void bpsf_destroy(bpsf_ctx *ctx);
+
+/*
+ * Batched BP-SF (Algorithm 1 on every shot): one persistent launch decodes
+ * all n_shots syndromes and all of their trial runs.  Work items are the
+ * initial runs and the trials of failed shots; thread teams take items from
+ * a device-wide queue, retire converged runs early and refill free slots.
+ *   d_synd       n_shots rows of Ws words (padding bits beyond M ignored).
+ *   d_corr       n_shots rows of Wn words: the returned correction e.
+ *   d_converged  n_shots bytes: 1 if e H^T = s holds for the returned e.
+ *   d_iters      n_shots int16: iterations of the run whose e is returned.
+ *   d_stage      n_shots bytes (nullable): 0 initial run converged, 1 a
+ *                trial converged, 2 failure (the initial run's e is returned).
+ * Results depend only on the inputs (not on timing or launch shape).  The
+ * first call with a larger n_shots than before allocates device workspace,
+ * so capture such calls in a CUDA graph only after a warm-up call.
+ */
+bpsf_status bpsf_decode(bpsf_ctx *ctx, int64_t n_shots, const uint32_t *d_synd, int32_t synd_stride_words,
+                        uint32_t *d_corr, int32_t corr_stride_words, uint8_t *d_converged, int16_t *d_iters,
+                        uint8_t *d_stage, void *stream);
+
+/*
+ * Plain per-shot form (the baseline the batched form is compared with):
+ * for each shot, launch the initial run alone, synchronise and read its
+ * stage; on failure launch that shot's trial sweep and synchronise again.
+ * Same arguments and results as bpsf_decode; returns after the last shot.
+ */
+bpsf_status bpsf_decode_plain(bpsf_ctx *ctx, int64_t n_shots, const uint32_t *d_synd, int32_t synd_stride_words,
+                              uint32_t *d_corr, int32_t corr_stride_words, uint8_t *d_converged, int16_t *d_iters,
+                              uint8_t *d_stage, void *stream);
+
+/*
+ * End-to-end form with HOST buffers: copies the syndromes to the device,
+ * runs bpsf_decode and copies the results back, all on `stream`, and
+ * returns when the results are in the host buffers.  Pinned buffers give
+ * full copy bandwidth.  h_stage is nullable.
+ */
+bpsf_status bpsf_decode_host(bpsf_ctx *ctx, int64_t n_shots, const uint32_t *h_synd, int32_t synd_stride_words,
+                             uint32_t *h_corr, int32_t corr_stride_words, uint8_t *h_converged, int16_t *h_iters,
+                             uint8_t *h_stage, void *stream);
+
+/* One batch of one code for bpsf_decode_multi (fields as in bpsf_decode). */
+typedef struct {
+    bpsf_ctx *ctx;
+    int64_t n_shots;
+    const uint32_t *d_synd;
+    int32_t synd_stride_words;
+    uint32_t *d_corr;
+    int32_t corr_stride_words;
+    uint8_t *d_converged;
+    int16_t *d_iters;
+    uint8_t *d_stage;
+} bpsf_job;
+
+/*
+ * Mixed-code batch: all jobs (codes of different sizes) decode in ONE
+ * persistent launch; thread blocks move to another code when theirs runs
+ * out of work.  At most 16 jobs; all contexts on the current device.
+ */
+bpsf_status bpsf_decode_multi(int32_t n_jobs, const bpsf_job *jobs, void *stream);
+
+/* Wait for `stream` and report device-side errors of ctx's last launches
+ * (BPSF_ETIMEOUT for a bounded device wait that ran out, BPSF_EDEVICE for an
+ * internal error).  Clears the device error word. */
+bpsf_status bpsf_sync(bpsf_ctx *ctx, void *stream);
+
+/*
+ * Launch shape of the batched kernel for one context (the autotuner's
+ * search space).  A team of warps_per_team warps decodes slots_per_team work
+ * items in lock step; warps_per_block / warps_per_team teams share a block;
+ * blocks_per_sm blocks per SM (0 = as many as fit).
+ */
+typedef struct {
+    int32_t warps_per_team;  /* 1, 2, 4 or 8 */
+    int32_t slots_per_team;  /* 1..32 */
+    int32_t warps_per_block; /* multiple of warps_per_team, <= 16 */
+    int32_t blocks_per_sm;   /* 0 = occupancy limit */
+} bpsf_tuning;
+
+bpsf_status bpsf_get_tuning(const bpsf_ctx *ctx, bpsf_tuning *out);
+bpsf_status bpsf_set_tuning(bpsf_ctx *ctx, const bpsf_tuning *t);
+
+/*
+ * Autotuner: times bpsf_decode over candidate launch shapes on n_sample
+ * syndromes of random errors drawn at rate p_sample (device generator),
+ * keeps the fastest, and caches it per code shape (M, N, nnz, degrees) for
+ * the process.  Synchronises `stream`.  chosen is nullable.
+ */
+bpsf_status bpsf_autotune(bpsf_ctx *ctx, double p_sample, int64_t n_sample, void *stream, bpsf_tuning *chosen);
+
+/* ---------------------------------------------------------------------- */
+/* Serving: continuous batching of a request stream (mixed codes).        */
+/* ---------------------------------------------------------------------- */
+
+typedef struct bpsf_server bpsf_server;
+
+/*
+ * Serving configuration.
+ *   max_inflight_shots  device slots for admitted shots, per code (admission
+ *                       limit; a request that does not fit waits or gets
+ *                       BPSF_EBUSY).
+ *   blocks              persistent blocks of the serving kernel (0 = all SMs).
+ *   idle_exit_us        the device loop exits after this long without work
+ *                       (bounded wait; the next submit relaunches it).
+ *   max_requests        request slots in flight (tickets not yet polled).
+ */
+typedef struct {
+    int64_t max_inflight_shots;
+    int32_t blocks;
+    int32_t idle_exit_us;
+    int32_t max_requests;
+    uint32_t flags;
+} bpsf_serve_cfg;
+
+/* Start a server over n_codes contexts (not owned; they must outlive it). */
+bpsf_status bpsf_serve_start(bpsf_server **out, bpsf_ctx *const *codes, int32_t n_codes, const bpsf_serve_cfg *cfg);
+
+/*
+ * Submit n shots of code index `code` (h_synd: n rows of that code's Ws
+ * words, host memory, copied before return).  Blocks while the code's
+ * device slots are full, up to timeout_us (0 = do not wait: BPSF_EBUSY).
+ * On success *ticket identifies the request.  Thread-safe.
+ */
+bpsf_status bpsf_serve_submit(bpsf_server *s, int32_t code, int64_t n, const uint32_t *h_synd, int64_t timeout_us,
+                              uint64_t *ticket);
+
+/*
+ * Wait up to timeout_us for a request (BPSF_ETIMEOUT if not done), then copy
+ * its results (Wn words per shot, converged bytes, int16 iterations; h_stage
+ * nullable) and release the ticket.  Thread-safe.
+ */
+bpsf_status bpsf_serve_poll(bpsf_server *s, uint64_t ticket, int64_t timeout_us, uint32_t *h_corr,
+                            uint8_t *h_converged, int16_t *h_iters, uint8_t *h_stage);
+
+/* Stop accepting requests, let admitted ones finish, stop the device loop
+ * and free the server.  Tickets not yet polled are lost. */
+bpsf_status bpsf_serve_stop(bpsf_server *s);
+
+/* ---------------------------------------------------------------------- */
+/* Code builders and helpers                                              */
+/* ---------------------------------------------------------------------- */
+
+/*
+ * Bivariate bicycle code (Appendix "Code Construction", BB codes):
+ * x = S_l (x) I_m, y = I_l (x) S_m with S_l the cyclic shift, A = a(x, y),
+ * B = b(x, y), H_X = [A | B] (which = 0) or H_Z = [B^T | A^T] (which = 1).
+ * Terms are monomials x^{a_x[t]} y^{a_y[t]}; repeated terms cancel mod 2.
+ * m = 1 gives the generalised bicycle codes of the same appendix.
+ * Output in CSR: ptr_out has l*m + 1 entries, idx_out room for idx_cap
+ * column indices (ascending per row); *nnz_out = ones written.
+ */
+bpsf_status bpsf_bb_code(int32_t l, int32_t m, int32_t n_a, const int32_t *a_x, const int32_t *a_y, int32_t n_b,
+                         const int32_t *b_x, const int32_t *b_y, int32_t which, int32_t *ptr_out, int32_t *idx_out,
+                         int64_t idx_cap, int64_t *nnz_out);
+
+/*
+ * R-round phenomenological detector matrix built from one round's H0
+ * (M0 x N0, CSR): H = [I_R (x) H0 | B_R (x) I_M0] with B_R lower bidiagonal;
+ * detector row t*M0 + j compares rounds t and t-1 of check j; columns are
+ * R*N0 data errors (round-major) then R*M0 measurement errors.  The
+ * phenomenological model is not in the paper; see the project notes.
+ * Output CSR with R*M0 rows; idx_cap bounds idx_out.
+ */
+bpsf_status bpsf_phenom_code(int32_t M0, int32_t N0, const int32_t *ptr0, const int32_t *idx0, int32_t rounds,
+                             int32_t *ptr_out, int32_t *idx_out, int64_t idx_cap, int64_t *nnz_out);
+
+/* s = H e (mod 2) for n packed error vectors on the device (harness). */
+bpsf_status bpsf_syndrome(const bpsf_ctx *ctx, int64_t n, const uint32_t *d_err, int32_t err_stride_words,
+                          uint32_t *d_synd, int32_t synd_stride_words, void *stream);
+
+/*
+ * Debug/test hook: batched decode that also dumps internal values.  All
+ * outputs are device arrays indexed by shot (nullable):
+ *   d_lout        n x N float: posterior LLRs of the initial run's last iteration.
+ *   d_flips       n x N uint16: flip counters of the initial run.
+ *   d_phi         n x w int32: Phi of failed shots (untouched otherwise).
+ *   d_trial_synd  n x T x Ws uint32: trial syndromes s' (T = trials per shot).
+ *   d_trial_conv  n x T bytes: trial converged flags (failed shots only).
+ *   d_trial_iters n x T int16: trial iterations (failed shots only).
+ * It runs the same kernels as bpsf_decode with the dump stores enabled.
+ */
+bpsf_status bpsf_decode_debug(bpsf_ctx *ctx, int64_t n_shots, const uint32_t *d_synd, int32_t synd_stride_words,
+                              uint32_t *d_corr, int32_t corr_stride_words, uint8_t *d_converged, int16_t *d_iters,
+                              uint8_t *d_stage, float *d_lout, uint16_t *d_flips, int32_t *d_phi,
+                              uint32_t *d_trial_synd, uint8_t *d_trial_conv, int16_t *d_trial_iters, void *stream);
+
+/* Number of trials per failed shot (masks with popcount <= w_max). */
+int32_t bpsf_num_trials(const bpsf_ctx *ctx);
+
+/* Work counters of the last decode on ctx (after bpsf_sync): runs started,
+ * failed shots (records) and edge-updates (iterations x nnz summed over runs). */
+typedef struct {
+    int64_t initial_runs;
+    int64_t failed_shots;
+    int64_t trial_runs;
+    int64_t iterations;
+    int64_t edge_updates;
+} bpsf_work;
+bpsf_status bpsf_last_work(bpsf_ctx *ctx, bpsf_work *out);
+
+const char *bpsf_status_str(bpsf_status s);
+const char *bpsf_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BPSF_H */

@@ -310,10 +310,11 @@ void oracle_syndrome(const oracle_code *c, const uint8_t *e, uint8_t *s) {
     }
 }
 
+/* e H^T = s, row by row over the ones of each row. */
 static int satisfies(const oracle_code *c, const uint8_t *e, const uint8_t *s) {
     for (int j = 0; j < c->M; j++) {
         int acc = 0;
-        for (int i = 0; i < c->N; i++) acc ^= (c->H[j * c->N + i] & e[i]);
+        for (int g = c->row_ptr[j]; g < c->row_ptr[j + 1]; g++) acc ^= e[c->row_var[g]];
         if (acc != s[j]) return 0;
     }
     return 1;

@@ -1,0 +1,760 @@
+// Host side of libbpsf: argument checking, Tanner-graph layout, device
+// workspace, the batched / plain / host-buffer / mixed-code decode forms,
+// launch-shape tuning and the code builders.  See include/bpsf.h.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "bpsf.h"
+#include "bpsf_api_internal.h"
+#include "bpsf_internal.h"
+
+using namespace bpsf;
+
+static thread_local std::string g_err;
+
+bpsf_status bpsf_fail(bpsf_status s, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return s;
+}
+
+extern "C" const char *bpsf_last_error(void) { return g_err.c_str(); }
+
+extern "C" const char *bpsf_status_str(bpsf_status s) {
+    switch (s) {
+        case BPSF_OK: return "ok";
+        case BPSF_EINVAL: return "invalid argument";
+        case BPSF_ENOMEM: return "out of memory";
+        case BPSF_ECUDA: return "CUDA error";
+        case BPSF_ETIMEOUT: return "timeout";
+        case BPSF_EBUSY: return "busy";
+        case BPSF_ECLOSED: return "closed";
+        case BPSF_EDEVICE: return "device error";
+    }
+    return "unknown status";
+}
+
+// Bound on any device-side wait (a trial waiting for its record, a block
+// waiting for other blocks to publish trials).
+static const unsigned long long kWaitNs = 5ull * 1000 * 1000 * 1000;
+
+// ---------------------------------------------------------------------------
+// Context creation
+// ---------------------------------------------------------------------------
+
+static size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
+
+static void free_workspace(bpsf_ctx *c) {
+    if (c->d_rec) cudaFree(c->d_rec);
+    c->d_rec = nullptr;
+    c->rec = Records{};
+    c->rec_cap = 0;
+}
+
+extern "C" void bpsf_destroy(bpsf_ctx *c) {
+    if (!c) return;
+    int prev = -1;
+    cudaGetDevice(&prev);
+    cudaSetDevice(c->device);
+    free_workspace(c);
+    if (c->d_code) cudaFree(c->d_code);
+    if (c->d_ctr) cudaFree(c->d_ctr);
+    if (c->h_ctr) cudaFreeHost(c->h_ctr);
+    if (c->h_flag) cudaFreeHost(c->h_flag);
+    if (c->h_preset) cudaFreeHost(c->h_preset);
+    if (c->d_host_stage) cudaFree(c->d_host_stage);
+    if (prev >= 0) cudaSetDevice(prev);
+    delete c;
+}
+
+int bpsf_ctx_team_smem(const bpsf_ctx *c, int S, int teams) {
+    return block_smem_bytes(c->M, c->N, c->nnz, c->Ws, S, teams);
+}
+
+// Largest S (<= S0) whose block fits in shared memory; 0 if none.
+static int fit_slots(const bpsf_ctx *c, int S0, int teams) {
+    for (int S = S0; S >= 1; --S)
+        if (bpsf_ctx_team_smem(c, S, teams) <= c->smem_optin) return S;
+    return 0;
+}
+
+static bpsf_tuning default_tuning(const bpsf_ctx *c) {
+    bpsf_tuning t{};
+    if (c->nnz <= 1024) {
+        t.warps_per_team = 1;
+        t.slots_per_team = 4;
+        t.warps_per_block = 8;
+    } else if (c->nnz <= 4096) {
+        t.warps_per_team = 2;
+        t.slots_per_team = 2;
+        t.warps_per_block = 8;
+    } else {
+        t.warps_per_team = 8;
+        t.slots_per_team = 1;
+        t.warps_per_block = 16;
+    }
+    const int teams = t.warps_per_block / t.warps_per_team;
+    int S = fit_slots(c, t.slots_per_team, teams);
+    while (S == 0 && t.warps_per_block > t.warps_per_team) {
+        t.warps_per_block /= 2;
+        S = fit_slots(c, t.slots_per_team, t.warps_per_block / t.warps_per_team);
+    }
+    t.slots_per_team = S > 0 ? S : 1;
+    t.blocks_per_sm = 0;
+    return t;
+}
+
+static bpsf_status check_tuning(const bpsf_ctx *c, const bpsf_tuning &t) {
+    const int W = t.warps_per_team, S = t.slots_per_team, B = t.warps_per_block;
+    if (!(W == 1 || W == 2 || W == 4 || W == 8)) return bpsf_fail(BPSF_EINVAL, "warps_per_team must be 1, 2, 4 or 8");
+    if (S < 1 || S > kMaxSlots) return bpsf_fail(BPSF_EINVAL, "slots_per_team must be in 1..%d", kMaxSlots);
+    if (B < W || B > 16 || B % W) return bpsf_fail(BPSF_EINVAL, "warps_per_block must be a multiple of warps_per_team, <= 16");
+    if (W > 1 && B / W > kMaxNamedTeams) return bpsf_fail(BPSF_EINVAL, "at most %d multi-warp teams per block", kMaxNamedTeams);
+    if (t.blocks_per_sm < 0) return bpsf_fail(BPSF_EINVAL, "blocks_per_sm must be >= 0");
+    const int smem = bpsf_ctx_team_smem(c, S, B / W);
+    if (smem > c->smem_optin)
+        return bpsf_fail(BPSF_EINVAL, "launch shape needs %d bytes of shared memory (limit %d)", smem, c->smem_optin);
+    return BPSF_OK;
+}
+
+bpsf_status bpsf_ensure_kernel_attrs(int variant, int smem_optin) {
+    static std::mutex mu;
+    static bool done[8] = {false};
+    std::lock_guard<std::mutex> lk(mu);
+    for (int dbg = 0; dbg < 2; ++dbg) {
+        const int k = variant * 2 + dbg;
+        if (done[k]) continue;
+        cudaError_t e = cudaFuncSetAttribute(persistent_kernel_ptr(variant, dbg != 0),
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin);
+        if (e != cudaSuccess)
+            return bpsf_fail(BPSF_ECUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(e));
+        done[k] = true;
+    }
+    return BPSF_OK;
+}
+
+extern "C" bpsf_status bpsf_create(bpsf_ctx **out, int32_t M, int32_t N, int64_t nnz, int32_t layout,
+                                   const int32_t *ptr, const int32_t *idx, const double *priors,
+                                   const bpsf_params *params) {
+    if (!out) return bpsf_fail(BPSF_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!ptr || !idx || !priors || !params) return bpsf_fail(BPSF_EINVAL, "NULL array or params");
+    if (M < 1 || M > 65535 || N < 1 || N > 65535) return bpsf_fail(BPSF_EINVAL, "M and N must be in 1..65535");
+    if (nnz < 1 || nnz > 65535) return bpsf_fail(BPSF_EINVAL, "nnz must be in 1..65535");
+    if (layout != BPSF_CSR && layout != BPSF_CSC) return bpsf_fail(BPSF_EINVAL, "layout must be BPSF_CSR or BPSF_CSC");
+    const bpsf_params p = *params;
+    if (p.flags != 0) return bpsf_fail(BPSF_EINVAL, "params.flags must be 0");
+    if (p.max_iter < 1 || p.max_iter > 32767) return bpsf_fail(BPSF_EINVAL, "max_iter must be in 1..32767");
+    if (!(p.alpha > 0.f) || !std::isfinite(p.alpha)) return bpsf_fail(BPSF_EINVAL, "alpha must be finite and > 0");
+    if (p.w < 0 || p.w > kMaxW) return bpsf_fail(BPSF_EINVAL, "w must be in 0..%d", kMaxW);
+    if (p.w > N) return bpsf_fail(BPSF_EINVAL, "w must not exceed N");
+    if (p.w > 0) {
+        if (p.w_max < 0 || p.w_max > p.w) return bpsf_fail(BPSF_EINVAL, "w_max must be in 0..w");
+        if (p.short_iter < 1 || p.short_iter > p.max_iter)
+            return bpsf_fail(BPSF_EINVAL, "short_iter must be in 1..max_iter");
+    }
+    if (p.select != BPSF_SELECT_MIN_WEIGHT && p.select != BPSF_SELECT_FIRST)
+        return bpsf_fail(BPSF_EINVAL, "select must be 0 or 1");
+    const int outer = layout == BPSF_CSR ? M : N, inner = layout == BPSF_CSR ? N : M;
+    if (ptr[0] != 0 || ptr[outer] != nnz) return bpsf_fail(BPSF_EINVAL, "ptr[0] must be 0 and ptr[last] must be nnz");
+    std::vector<std::vector<int>> rows(M);
+    for (int a = 0; a < outer; ++a) {
+        if (ptr[a + 1] < ptr[a]) return bpsf_fail(BPSF_EINVAL, "ptr must be non-decreasing");
+        for (int k = ptr[a]; k < ptr[a + 1]; ++k) {
+            const int b = idx[k];
+            if (b < 0 || b >= inner) return bpsf_fail(BPSF_EINVAL, "index %d out of range at position %d", b, k);
+            if (layout == BPSF_CSR)
+                rows[a].push_back(b);
+            else
+                rows[b].push_back(a);
+        }
+    }
+    for (int i = 0; i < N; ++i) {
+        const double pi = priors[i];
+        if (!(pi > 0.0 && pi < 0.5)) return bpsf_fail(BPSF_EINVAL, "prior %d = %g is not in (0, 0.5)", i, pi);
+    }
+    bpsf_ctx *c = new bpsf_ctx();
+    c->M = M;
+    c->N = N;
+    c->nnz = (int)nnz;
+    c->Ws = (M + 31) / 32;
+    c->Wn = (N + 31) / 32;
+    c->p = p;
+    if (c->p.w > 0 && c->p.w_max == 0) c->p.w_max = c->p.w;
+    c->csr_ptr.assign(M + 1, 0);
+    c->csr_col.reserve(nnz);
+    int dc = 0;
+    for (int j = 0; j < M; ++j) {
+        std::sort(rows[j].begin(), rows[j].end());
+        for (size_t k = 1; k < rows[j].size(); ++k)
+            if (rows[j][k] == rows[j][k - 1]) {
+                delete c;
+                return bpsf_fail(BPSF_EINVAL, "duplicate entry (%d, %d)", j, rows[j][k]);
+            }
+        if (rows[j].size() < 2) {
+            delete c;
+            return bpsf_fail(BPSF_EINVAL, "row %d has degree %d; every check needs degree >= 2", j, (int)rows[j].size());
+        }
+        dc = std::max(dc, (int)rows[j].size());
+        for (int v : rows[j]) c->csr_col.push_back(v);
+        c->csr_ptr[j + 1] = (int)c->csr_col.size();
+    }
+    // CSC: columns list their checks in ascending order (rows are visited in order).
+    std::vector<std::vector<std::pair<int, int>>> cols(N);  // (check, csr edge)
+    for (int j = 0; j < M; ++j)
+        for (int e = c->csr_ptr[j]; e < c->csr_ptr[j + 1]; ++e) cols[c->csr_col[e]].push_back({j, e});
+    int dv = 0;
+    for (int i = 0; i < N; ++i) dv = std::max(dv, (int)cols[i].size());
+    c->dc_max = dc;
+    c->dv_max = dv;
+    c->variant = kernel_variant(dc, std::max(dv, 1));
+    if (c->variant < 0) {
+        delete c;
+        return bpsf_fail(BPSF_EINVAL, "row degree %d or column degree %d too large (limits 32, 16)", dc, dv);
+    }
+    std::vector<uint16_t> row_ptr(M + 1), csr_to_csc(nnz), col_ptr(N + 1), csc_to_csr(nnz), csc_chk(nnz), csr_col(nnz);
+    std::vector<float> lch(N), lch_csr(nnz);
+    for (int j = 0; j <= M; ++j) row_ptr[j] = (uint16_t)c->csr_ptr[j];
+    for (int e = 0; e < nnz; ++e) csr_col[e] = (uint16_t)c->csr_col[e];
+    int f = 0;
+    for (int i = 0; i < N; ++i) {
+        col_ptr[i] = (uint16_t)f;
+        for (auto &ce : cols[i]) {
+            csc_chk[f] = (uint16_t)ce.first;
+            csc_to_csr[f] = (uint16_t)ce.second;
+            csr_to_csc[ce.second] = (uint16_t)f;
+            ++f;
+        }
+    }
+    col_ptr[N] = (uint16_t)f;
+    // Channel LLR (Section II-B, step 1) in double, rounded once to float.
+    for (int i = 0; i < N; ++i) lch[i] = (float)std::log((1.0 - priors[i]) / priors[i]);
+    for (int e = 0; e < nnz; ++e) lch_csr[e] = lch[c->csr_col[e]];
+    std::vector<uint32_t> masks;
+    for (uint32_t k = 1; c->p.w > 0 && k < (1u << c->p.w); ++k)
+        if (__builtin_popcount(k) <= c->p.w_max) masks.push_back(k);
+    c->n_trials = (int)masks.size();
+    if (masks.empty()) masks.push_back(0);
+
+    cudaGetDevice(&c->device);
+    cudaDeviceProp prop;
+    cudaError_t e = cudaGetDeviceProperties(&prop, c->device);
+    if (e != cudaSuccess) {
+        delete c;
+        return bpsf_fail(BPSF_ECUDA, "cudaGetDeviceProperties: %s", cudaGetErrorString(e));
+    }
+    c->sm_count = prop.multiProcessorCount;
+    c->smem_optin = (int)prop.sharedMemPerBlockOptin;
+
+    // One allocation for all code arrays.
+    size_t off[10], sz = 0;
+    const size_t n16 = 2 * (size_t)nnz;
+    size_t sizes[10] = {2 * (size_t)(M + 1), n16, 2 * (size_t)(N + 1), n16, n16, n16,
+                        4 * (size_t)N,       4 * (size_t)nnz, 4 * masks.size(), 0};
+    for (int k = 0; k < 9; ++k) {
+        off[k] = sz;
+        sz += align16(sizes[k]);
+    }
+    e = cudaMalloc(&c->d_code, sz);
+    if (e != cudaSuccess) {
+        delete c;
+        return bpsf_fail(BPSF_ENOMEM, "cudaMalloc(code): %s", cudaGetErrorString(e));
+    }
+    std::vector<unsigned char> hbuf(sz, 0);
+    const void *srcs[9] = {row_ptr.data(), csr_to_csc.data(), col_ptr.data(), csc_to_csr.data(), csc_chk.data(),
+                           csr_col.data(), lch.data(),        lch_csr.data(),    masks.data()};
+    for (int k = 0; k < 9; ++k) std::memcpy(hbuf.data() + off[k], srcs[k], sizes[k]);
+    e = cudaMemcpy(c->d_code, hbuf.data(), sz, cudaMemcpyHostToDevice);
+    unsigned char *base = (unsigned char *)c->d_code;
+    CodeDev &cd = c->code;
+    cd.M = M;
+    cd.N = N;
+    cd.nnz = (int)nnz;
+    cd.Ws = c->Ws;
+    cd.Wn = c->Wn;
+    cd.dc_max = dc;
+    cd.dv_max = dv;
+    cd.max_iter = p.max_iter;
+    cd.short_iter = c->p.w > 0 ? p.short_iter : 1;
+    cd.w = c->p.w;
+    cd.n_trials = c->n_trials;
+    cd.select = p.select;
+    cd.alpha = p.alpha;
+    cd.row_ptr = (const uint16_t *)(base + off[0]);
+    cd.csr_to_csc = (const uint16_t *)(base + off[1]);
+    cd.col_ptr = (const uint16_t *)(base + off[2]);
+    cd.csc_to_csr = (const uint16_t *)(base + off[3]);
+    cd.csc_chk = (const uint16_t *)(base + off[4]);
+    cd.csr_col = (const uint16_t *)(base + off[5]);
+    cd.lch = (const float *)(base + off[6]);
+    cd.lch_csr = (const float *)(base + off[7]);
+    cd.trial_mask = (const uint32_t *)(base + off[8]);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&c->d_ctr, sizeof(StreamCounters));
+    if (e == cudaSuccess) e = cudaMemset(c->d_ctr, 0, sizeof(StreamCounters));
+    if (e == cudaSuccess) e = cudaMallocHost((void **)&c->h_ctr, sizeof(StreamCounters));
+    if (e == cudaSuccess) e = cudaMallocHost((void **)&c->h_flag, 64);
+    if (e == cudaSuccess) e = cudaMallocHost((void **)&c->h_preset, sizeof(StreamCounters));
+    if (e != cudaSuccess) {
+        bpsf_destroy(c);
+        return bpsf_fail(BPSF_ECUDA, "context allocation: %s", cudaGetErrorString(e));
+    }
+    std::memset(c->h_ctr, 0, sizeof(StreamCounters));
+    c->tune = default_tuning(c);
+    bpsf_status st = bpsf_ensure_kernel_attrs(c->variant, c->smem_optin);
+    if (st != BPSF_OK) {
+        bpsf_destroy(c);
+        return st;
+    }
+    bpsf_tuning cached;
+    if (bpsf_tuning_cache_lookup(c, &cached)) c->tune = cached;
+    *out = c;
+    return BPSF_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Workspace: failed-shot records, capacity = shots of the largest batch.
+// ---------------------------------------------------------------------------
+
+bpsf_status bpsf_ensure_workspace(bpsf_ctx *c, long long n) {
+    if (n <= c->rec_cap) return BPSF_OK;
+    const long long cap = std::max<long long>(n, 1);
+    const int w = std::max(c->p.w, 1), T = std::max(c->n_trials, 1);
+    const size_t sz_shot = align16(8 * (size_t)cap), sz_ready = align16(4 * (size_t)cap),
+                 sz_done = align16(4 * (size_t)cap), sz_best = align16(8 * (size_t)cap),
+                 sz_phi = align16(4 * (size_t)cap * w), sz_synd = align16(4 * (size_t)cap * c->Ws),
+                 sz_corr = align16(4 * (size_t)cap * T * c->Wn), sz_iters = align16(2 * (size_t)cap * T);
+    const size_t total = sz_shot + sz_ready + sz_done + sz_best + sz_phi + sz_synd + sz_corr + sz_iters;
+    free_workspace(c);
+    void *mem = nullptr;
+    cudaError_t e = cudaMalloc(&mem, total);
+    if (e != cudaSuccess) return bpsf_fail(BPSF_ENOMEM, "workspace of %zu bytes: %s", total, cudaGetErrorString(e));
+    unsigned char *p = (unsigned char *)mem;
+    c->d_rec = mem;
+    c->rec.shot = (long long *)p;
+    p += sz_shot;
+    c->rec.ready = (unsigned *)p;
+    p += sz_ready;
+    c->rec.done = (unsigned *)p;
+    p += sz_done;
+    c->rec.best = (unsigned long long *)p;
+    p += sz_best;
+    c->rec.phi = (int32_t *)p;
+    p += sz_phi;
+    c->rec.synd = (uint32_t *)p;
+    p += sz_synd;
+    c->rec.corr = (uint32_t *)p;
+    p += sz_corr;
+    c->rec.iters = (int16_t *)p;
+    c->rec.cap = cap;
+    c->rec_cap = cap;
+    return BPSF_OK;
+}
+
+// Records must read "not ready" before a launch: clear the ready flags of
+// the first n slots on the stream.
+static bpsf_status clear_ready(bpsf_ctx *c, long long n, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(c->rec.ready, 0, 4 * (size_t)std::max<long long>(n, 1), s);
+    if (e != cudaSuccess) return bpsf_fail(BPSF_ECUDA, "cudaMemsetAsync: %s", cudaGetErrorString(e));
+    return BPSF_OK;
+}
+
+StreamDev bpsf_make_stream(const bpsf_ctx *c, const JobDev &job, const DebugDev *dbg, int W, int S, unsigned flags) {
+    StreamDev sd;
+    std::memset(&sd, 0, sizeof(sd));
+    sd.code = c->code;
+    sd.job = job;
+    sd.rec = c->rec;
+    sd.ctr = c->d_ctr;
+    if (dbg) sd.dbg = *dbg;
+    sd.W = W;
+    sd.S = S;
+    sd.flags = flags;
+    return sd;
+}
+
+int bpsf_grid_for(const bpsf_ctx *c, int variant, bool debug, int block, int smem, int blocks_per_sm) {
+    int occ = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, persistent_kernel_ptr(variant, debug), block, smem);
+    if (blocks_per_sm > 0) occ = std::min(occ, blocks_per_sm);
+    return occ * c->sm_count;
+}
+
+static bpsf_status check_io(const bpsf_ctx *c, int64_t n, const void *synd, int32_t ss, const void *corr, int32_t cs,
+                            const void *conv, const void *iters) {
+    if (!c) return bpsf_fail(BPSF_EINVAL, "ctx is NULL");
+    if (n < 0) return bpsf_fail(BPSF_EINVAL, "n_shots must be >= 0");
+    if (n > (1ll << 40)) return bpsf_fail(BPSF_EINVAL, "n_shots too large");
+    if (n == 0) return BPSF_OK;
+    if (!synd || !corr || !conv || !iters) return bpsf_fail(BPSF_EINVAL, "NULL input or output pointer");
+    if (ss < c->Ws) return bpsf_fail(BPSF_EINVAL, "synd_stride_words %d < Ws = %d", ss, c->Ws);
+    if (cs < c->Wn) return bpsf_fail(BPSF_EINVAL, "corr_stride_words %d < Wn = %d", cs, c->Wn);
+    return BPSF_OK;
+}
+
+static bpsf_status decode_impl(bpsf_ctx *c, int64_t n, const uint32_t *synd, int32_t ss, uint32_t *corr, int32_t cs,
+                               uint8_t *conv, int16_t *iters, uint8_t *stage, const DebugDev *dbg, void *stream) {
+    bpsf_status st = check_io(c, n, synd, ss, corr, cs, conv, iters);
+    if (st != BPSF_OK || n == 0) return st;
+    cudaSetDevice(c->device);
+    st = bpsf_ensure_workspace(c, n);
+    if (st != BPSF_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaMemsetAsync(c->d_ctr, 0, sizeof(StreamCounters), s);
+    if (e != cudaSuccess) return bpsf_fail(BPSF_ECUDA, "cudaMemsetAsync: %s", cudaGetErrorString(e));
+    st = clear_ready(c, n, s);
+    if (st != BPSF_OK) return st;
+    JobDev job{synd, corr, conv, iters, stage, n, ss, cs};
+    const bpsf_tuning &t = c->tune;
+    StreamDev sd = bpsf_make_stream(c, job, dbg, t.warps_per_team, t.slots_per_team, 0);
+    LaunchArgs la{&sd, 1, t.warps_per_block, kWaitNs};
+    const int block = 32 * t.warps_per_block;
+    const int smem = bpsf_ctx_team_smem(c, t.slots_per_team, t.warps_per_block / t.warps_per_team);
+    int grid = bpsf_grid_for(c, c->variant, dbg != nullptr, block, smem, t.blocks_per_sm);
+    if (grid <= 0) return bpsf_fail(BPSF_EINVAL, "launch shape does not fit on an SM");
+    launch_persistent(c->variant, dbg != nullptr, grid, block, smem, la, stream);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return bpsf_fail(BPSF_ECUDA, "kernel launch: %s", cudaGetErrorString(e));
+    c->last_launch_n = n;
+    return BPSF_OK;
+}
+
+extern "C" bpsf_status bpsf_decode(bpsf_ctx *c, int64_t n, const uint32_t *synd, int32_t ss, uint32_t *corr,
+                                   int32_t cs, uint8_t *conv, int16_t *iters, uint8_t *stage, void *stream) {
+    return decode_impl(c, n, synd, ss, corr, cs, conv, iters, stage, nullptr, stream);
+}
+
+extern "C" bpsf_status bpsf_decode_debug(bpsf_ctx *c, int64_t n, const uint32_t *synd, int32_t ss, uint32_t *corr,
+                                         int32_t cs, uint8_t *conv, int16_t *iters, uint8_t *stage, float *lout,
+                                         uint16_t *flips, int32_t *phi, uint32_t *tsynd, uint8_t *tconv,
+                                         int16_t *titers, void *stream) {
+    DebugDev d{lout, flips, phi, tsynd, tconv, titers};
+    return decode_impl(c, n, synd, ss, corr, cs, conv, iters, stage, &d, stream);
+}
+
+extern "C" bpsf_status bpsf_sync(bpsf_ctx *c, void *stream) {
+    if (!c) return bpsf_fail(BPSF_EINVAL, "ctx is NULL");
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) return bpsf_fail(BPSF_ECUDA, "cudaStreamSynchronize: %s", cudaGetErrorString(e));
+    e = cudaMemcpy(c->h_ctr, c->d_ctr, sizeof(StreamCounters), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return bpsf_fail(BPSF_ECUDA, "cudaMemcpy: %s", cudaGetErrorString(e));
+    const StreamCounters &k = *c->h_ctr;
+    c->last.initial_runs = (int64_t)k.init_done;
+    c->last.failed_shots = (int64_t)k.rec_count;
+    c->last.trial_runs = (int64_t)k.trial_runs;
+    c->last.iterations = (int64_t)k.iters_total;
+    c->last.edge_updates = (int64_t)k.iters_total * c->nnz;
+    if (k.status) {
+        const unsigned stv = k.status;
+        cudaMemsetAsync(&c->d_ctr->status, 0, sizeof(unsigned), (cudaStream_t)stream);
+        cudaStreamSynchronize((cudaStream_t)stream);
+        if (stv & (kDevReadyTimeout | kDevIdleTimeout))
+            return bpsf_fail(BPSF_ETIMEOUT, "a bounded device wait ran out (status 0x%x)", stv);
+        return bpsf_fail(BPSF_EDEVICE, "device error (status 0x%x)", stv);
+    }
+    return BPSF_OK;
+}
+
+extern "C" bpsf_status bpsf_last_work(bpsf_ctx *c, bpsf_work *out) {
+    if (!c || !out) return bpsf_fail(BPSF_EINVAL, "NULL argument");
+    *out = c->last;
+    return BPSF_OK;
+}
+
+extern "C" int32_t bpsf_num_trials(const bpsf_ctx *c) { return c ? c->n_trials : -1; }
+
+// ---------------------------------------------------------------------------
+// Plain per-shot form: launch, synchronise, read the flag, launch the trial
+// sweep on failure, synchronise.
+// ---------------------------------------------------------------------------
+
+extern "C" bpsf_status bpsf_decode_plain(bpsf_ctx *c, int64_t n, const uint32_t *synd, int32_t ss, uint32_t *corr,
+                                         int32_t cs, uint8_t *conv, int16_t *iters, uint8_t *stage, void *stream) {
+    bpsf_status st = check_io(c, n, synd, ss, corr, cs, conv, iters);
+    if (st != BPSF_OK || n == 0) return st;
+    cudaSetDevice(c->device);
+    st = bpsf_ensure_workspace(c, 1);
+    if (st != BPSF_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    const bpsf_tuning &t = c->tune;
+    const int W = t.warps_per_team;
+    // Launch A: one team, one slot, the initial run of one shot.
+    const int smemA = bpsf_ctx_team_smem(c, 1, 1);
+    // Launch B: the shot's trials spread over teams of the tuned shape.
+    const int S = t.slots_per_team, teams = t.warps_per_block / W;
+    const int smemB = bpsf_ctx_team_smem(c, S, teams);
+    const int trials = std::max(c->n_trials, 1);
+    const int gridB = std::max(1, (trials + S * teams - 1) / (S * teams));
+    StreamCounters preset;
+    std::memset(&preset, 0, sizeof(preset));
+    preset.shot_next = 1;
+    preset.init_done = 1;
+    preset.rec_count = 1;
+    *c->h_preset = preset;
+    long long iters_total = 0, trial_runs = 0, failed = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        JobDev job{synd + i * ss, corr + i * cs, conv + i, iters + i, stage ? stage + i : nullptr, 1, ss, cs};
+        cudaError_t e = cudaMemsetAsync(c->d_ctr, 0, sizeof(StreamCounters), s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(c->rec.ready, 0, 4, s);
+        if (e != cudaSuccess) return bpsf_fail(BPSF_ECUDA, "cudaMemsetAsync: %s", cudaGetErrorString(e));
+        StreamDev sdA = bpsf_make_stream(c, job, nullptr, W, 1, kNoTickets);
+        LaunchArgs laA{&sdA, 1, W, kWaitNs};
+        launch_persistent(c->variant, false, 1, 32 * W, smemA, laA, stream);
+        e = cudaMemcpyAsync(c->h_flag, conv + i, 1, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return bpsf_fail(BPSF_ECUDA, "plain initial run: %s", cudaGetErrorString(e));
+        if (c->h_flag[0] == 0 && c->p.w > 0) {
+            ++failed;
+            e = cudaMemcpyAsync(c->d_ctr, c->h_preset, sizeof(StreamCounters), cudaMemcpyHostToDevice, s);
+            if (e != cudaSuccess) return bpsf_fail(BPSF_ECUDA, "cudaMemcpyAsync: %s", cudaGetErrorString(e));
+            StreamDev sdB = bpsf_make_stream(c, job, nullptr, W, S, 0);
+            LaunchArgs laB{&sdB, 1, t.warps_per_block, kWaitNs};
+            launch_persistent(c->variant, false, gridB, 32 * t.warps_per_block, smemB, laB, stream);
+            e = cudaMemcpyAsync(c->h_ctr, c->d_ctr, sizeof(StreamCounters), cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+            if (e != cudaSuccess) return bpsf_fail(BPSF_ECUDA, "plain trial sweep: %s", cudaGetErrorString(e));
+            if (c->h_ctr->status)
+                return bpsf_fail(BPSF_ETIMEOUT, "device status 0x%x in the trial sweep", c->h_ctr->status);
+            trial_runs += (long long)c->h_ctr->trial_runs;
+            iters_total += (long long)c->h_ctr->iters_total;
+        }
+    }
+    c->last = bpsf_work{n, failed, trial_runs, iters_total, iters_total * c->nnz};
+    return BPSF_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Host-buffer form.
+// ---------------------------------------------------------------------------
+
+extern "C" bpsf_status bpsf_decode_host(bpsf_ctx *c, int64_t n, const uint32_t *h_synd, int32_t ss, uint32_t *h_corr,
+                                        int32_t cs, uint8_t *h_conv, int16_t *h_iters, uint8_t *h_stage,
+                                        void *stream) {
+    bpsf_status st = check_io(c, n, h_synd, ss, h_corr, cs, h_conv, h_iters);
+    if (st != BPSF_OK || n == 0) return st;
+    cudaSetDevice(c->device);
+    const size_t b_synd = 4 * (size_t)n * ss, b_corr = 4 * (size_t)n * cs, b_conv = (size_t)n, b_it = 2 * (size_t)n;
+    const size_t need = align16(b_synd) + align16(b_corr) + align16(b_conv) + align16(b_it) + align16(b_conv);
+    if (need > c->host_stage_bytes) {
+        if (c->d_host_stage) cudaFree(c->d_host_stage);
+        c->d_host_stage = nullptr;
+        c->host_stage_bytes = 0;
+        cudaError_t e = cudaMalloc(&c->d_host_stage, need);
+        if (e != cudaSuccess) return bpsf_fail(BPSF_ENOMEM, "staging buffers: %s", cudaGetErrorString(e));
+        c->host_stage_bytes = need;
+    }
+    unsigned char *p = (unsigned char *)c->d_host_stage;
+    uint32_t *d_synd = (uint32_t *)p;
+    p += align16(b_synd);
+    uint32_t *d_corr = (uint32_t *)p;
+    p += align16(b_corr);
+    uint8_t *d_conv = p;
+    p += align16(b_conv);
+    int16_t *d_it = (int16_t *)p;
+    p += align16(b_it);
+    uint8_t *d_stage = p;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaMemcpyAsync(d_synd, h_synd, b_synd, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return bpsf_fail(BPSF_ECUDA, "H2D: %s", cudaGetErrorString(e));
+    st = decode_impl(c, n, d_synd, ss, d_corr, cs, d_conv, d_it, d_stage, nullptr, stream);
+    if (st != BPSF_OK) return st;
+    e = cudaMemcpyAsync(h_corr, d_corr, b_corr, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h_conv, d_conv, b_conv, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h_iters, d_it, b_it, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && h_stage) e = cudaMemcpyAsync(h_stage, d_stage, b_conv, cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return bpsf_fail(BPSF_ECUDA, "D2H: %s", cudaGetErrorString(e));
+    return bpsf_sync(c, stream);
+}
+
+// ---------------------------------------------------------------------------
+// Mixed-code batch: one launch over up to kMaxStreams codes.
+// ---------------------------------------------------------------------------
+
+extern "C" bpsf_status bpsf_decode_multi(int32_t n_jobs, const bpsf_job *jobs, void *stream) {
+    if (n_jobs < 1 || n_jobs > kMaxStreams || !jobs) return bpsf_fail(BPSF_EINVAL, "n_jobs must be in 1..%d", kMaxStreams);
+    int dc = 0, dv = 0, wpb = 0;
+    for (int k = 0; k < n_jobs; ++k) {
+        const bpsf_job &j = jobs[k];
+        bpsf_status st = check_io(j.ctx, j.n_shots, j.d_synd, j.synd_stride_words, j.d_corr, j.corr_stride_words,
+                                  j.d_converged, j.d_iters);
+        if (st != BPSF_OK) return st;
+        for (int q = 0; q < k; ++q)
+            if (jobs[q].ctx == j.ctx) return bpsf_fail(BPSF_EINVAL, "a context appears twice in one launch");
+        if (j.ctx->device != jobs[0].ctx->device) return bpsf_fail(BPSF_EINVAL, "contexts on different devices");
+        dc = std::max(dc, j.ctx->dc_max);
+        dv = std::max(dv, j.ctx->dv_max);
+        wpb = std::max(wpb, j.ctx->tune.warps_per_block);
+    }
+    bpsf_ctx *c0 = jobs[0].ctx;
+    cudaSetDevice(c0->device);
+    const int variant = kernel_variant(dc, std::max(dv, 1));
+    cudaStream_t s = (cudaStream_t)stream;
+    std::vector<StreamDev> sds(n_jobs);
+    int smem = 0;
+    for (int k = 0; k < n_jobs; ++k) {
+        bpsf_ctx *c = jobs[k].ctx;
+        const bpsf_job &j = jobs[k];
+        int W = c->tune.warps_per_team;
+        if (wpb % W) W = 1;
+        int S = fit_slots(c, c->tune.slots_per_team, wpb / W);
+        if (S == 0) return bpsf_fail(BPSF_EINVAL, "code %d does not fit the shared block shape", k);
+        smem = std::max(smem, bpsf_ctx_team_smem(c, S, wpb / W));
+        bpsf_status st = bpsf_ensure_workspace(c, std::max<int64_t>(j.n_shots, 1));
+        if (st != BPSF_OK) return st;
+        cudaError_t e = cudaMemsetAsync(c->d_ctr, 0, sizeof(StreamCounters), s);
+        if (e != cudaSuccess) return bpsf_fail(BPSF_ECUDA, "cudaMemsetAsync: %s", cudaGetErrorString(e));
+        st = clear_ready(c, j.n_shots, s);
+        if (st != BPSF_OK) return st;
+        JobDev job{j.d_synd, j.d_corr, j.d_converged, j.d_iters, j.d_stage, j.n_shots, j.synd_stride_words,
+                   j.corr_stride_words};
+        sds[k] = bpsf_make_stream(c, job, nullptr, W, S, 0);
+        c->last_launch_n = j.n_shots;
+    }
+    {
+        bpsf_status st = bpsf_ensure_kernel_attrs(variant, c0->smem_optin);
+        if (st != BPSF_OK) return st;
+    }
+    const int block = 32 * wpb;
+    const int grid = bpsf_grid_for(c0, variant, false, block, smem, 0);
+    if (grid <= 0) return bpsf_fail(BPSF_EINVAL, "mixed launch shape does not fit on an SM");
+    LaunchArgs la{sds.data(), n_jobs, wpb, kWaitNs};
+    launch_persistent(variant, false, grid, block, smem, la, stream);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return bpsf_fail(BPSF_ECUDA, "kernel launch: %s", cudaGetErrorString(e));
+    return BPSF_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Tuning and autotuner.
+// ---------------------------------------------------------------------------
+
+extern "C" bpsf_status bpsf_get_tuning(const bpsf_ctx *c, bpsf_tuning *out) {
+    if (!c || !out) return bpsf_fail(BPSF_EINVAL, "NULL argument");
+    *out = c->tune;
+    return BPSF_OK;
+}
+
+extern "C" bpsf_status bpsf_set_tuning(bpsf_ctx *c, const bpsf_tuning *t) {
+    if (!c || !t) return bpsf_fail(BPSF_EINVAL, "NULL argument");
+    bpsf_status st = check_tuning(c, *t);
+    if (st != BPSF_OK) return st;
+    c->tune = *t;
+    return BPSF_OK;
+}
+
+typedef std::tuple<int, int, int, int, int> ShapeKey;  // M, N, nnz, dc, dv
+static std::mutex g_tune_mu;
+static std::map<ShapeKey, bpsf_tuning> g_tune_cache;
+
+static ShapeKey shape_key(const bpsf_ctx *c) { return ShapeKey(c->M, c->N, c->nnz, c->dc_max, c->dv_max); }
+
+bool bpsf_tuning_cache_lookup(const bpsf_ctx *c, bpsf_tuning *out) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune_cache.find(shape_key(c));
+    if (it == g_tune_cache.end()) return false;
+    if (check_tuning(c, it->second) != BPSF_OK) return false;
+    *out = it->second;
+    return true;
+}
+
+extern "C" bpsf_status bpsf_autotune(bpsf_ctx *c, double p_sample, int64_t n_sample, void *stream,
+                                     bpsf_tuning *chosen) {
+    if (!c) return bpsf_fail(BPSF_EINVAL, "ctx is NULL");
+    if (!(p_sample > 0.0 && p_sample < 0.5)) return bpsf_fail(BPSF_EINVAL, "p_sample must be in (0, 0.5)");
+    if (n_sample < 1 || n_sample > (1 << 24)) return bpsf_fail(BPSF_EINVAL, "n_sample must be in 1..2^24");
+    cudaSetDevice(c->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t b_err = 4 * (size_t)n_sample * c->Wn, b_synd = 4 * (size_t)n_sample * c->Ws;
+    const size_t b_corr = b_err, b_conv = (size_t)n_sample, b_it = 2 * (size_t)n_sample;
+    void *buf = nullptr;
+    const size_t total = align16(b_err) + align16(b_synd) + align16(b_corr) + align16(b_conv) + align16(b_it);
+    cudaError_t e = cudaMalloc(&buf, total);
+    if (e != cudaSuccess) return bpsf_fail(BPSF_ENOMEM, "autotune buffers: %s", cudaGetErrorString(e));
+    unsigned char *p = (unsigned char *)buf;
+    uint32_t *err = (uint32_t *)p;
+    p += align16(b_err);
+    uint32_t *synd = (uint32_t *)p;
+    p += align16(b_synd);
+    uint32_t *corr = (uint32_t *)p;
+    p += align16(b_corr);
+    uint8_t *conv = p;
+    p += align16(b_conv);
+    int16_t *it = (int16_t *)p;
+    launch_sample_errors(n_sample, c->N, p_sample, 0x5eed5eedull, err, c->Wn, stream);
+    launch_syndrome(c->code, n_sample, err, c->Wn, synd, c->Ws, stream);
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const bpsf_tuning saved = c->tune;
+    bpsf_tuning best = saved;
+    float best_ms = 1e30f;
+    bpsf_status st = BPSF_OK;
+    const int Ws_[] = {1, 2, 4, 8};
+    const int Ss_[] = {1, 2, 3, 4, 6, 8, 12, 16};
+    const int Bs_[] = {2, 4, 8, 16};
+    for (int W : Ws_)
+        for (int S : Ss_)
+            for (int B : Bs_) {
+                bpsf_tuning t{W, S, B, 0};
+                if (check_tuning(c, t) != BPSF_OK) continue;
+                if (W > 1 && S > 4) continue;
+                const int smem = bpsf_ctx_team_smem(c, S, B / W);
+                if (bpsf_grid_for(c, c->variant, false, 32 * B, smem, 0) <= 0) continue;
+                c->tune = t;
+                float ms_min = 1e30f;
+                for (int rep = 0; rep < 3 && st == BPSF_OK; ++rep) {
+                    cudaEventRecord(e0, s);
+                    st = bpsf_decode(c, n_sample, synd, c->Ws, corr, c->Wn, conv, it, nullptr, stream);
+                    cudaEventRecord(e1, s);
+                    if (st == BPSF_OK) st = bpsf_sync(c, stream);
+                    float ms = 0;
+                    cudaEventElapsedTime(&ms, e0, e1);
+                    if (rep > 0) ms_min = std::min(ms_min, ms);
+                }
+                if (st != BPSF_OK) break;
+                if (ms_min < best_ms) {
+                    best_ms = ms_min;
+                    best = t;
+                }
+            }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(buf);
+    c->tune = (st == BPSF_OK) ? best : saved;
+    if (st != BPSF_OK) return st;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune_cache[shape_key(c)] = best;
+    }
+    if (chosen) *chosen = best;
+    return BPSF_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Harness helper.
+// ---------------------------------------------------------------------------
+
+extern "C" bpsf_status bpsf_syndrome(const bpsf_ctx *c, int64_t n, const uint32_t *d_err, int32_t es,
+                                     uint32_t *d_synd, int32_t ss, void *stream) {
+    if (!c || n < 0) return bpsf_fail(BPSF_EINVAL, "bad ctx or n");
+    if (n == 0) return BPSF_OK;
+    if (!d_err || !d_synd) return bpsf_fail(BPSF_EINVAL, "NULL pointer");
+    if (es < c->Wn || ss < c->Ws) return bpsf_fail(BPSF_EINVAL, "stride too small");
+    launch_syndrome(c->code, n, d_err, es, d_synd, ss, stream);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return bpsf_fail(BPSF_ECUDA, "syndrome kernel: %s", cudaGetErrorString(e));
+    return BPSF_OK;
+}

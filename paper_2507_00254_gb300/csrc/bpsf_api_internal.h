@@ -1,0 +1,38 @@
+// Host-side context of libbpsf, shared by the decode and serving code.
+#pragma once
+
+#include <cstdint>
+#include <vector>
+
+#include "bpsf.h"
+#include "bpsf_internal.h"
+
+struct bpsf_ctx {
+    int device = 0, sm_count = 0, smem_optin = 0;
+    int M = 0, N = 0, nnz = 0, Ws = 0, Wn = 0, dc_max = 0, dv_max = 0, n_trials = 0, variant = 0;
+    bpsf_params p{};
+    std::vector<int32_t> csr_ptr, csr_col;  // host copy of H (CSR, ascending columns)
+    void *d_code = nullptr;                 // one allocation for all code arrays
+    bpsf::CodeDev code{};
+    bpsf::StreamCounters *d_ctr = nullptr;  // per-launch counters
+    bpsf::StreamCounters *h_ctr = nullptr;  // pinned copy read by bpsf_sync
+    bpsf::StreamCounters *h_preset = nullptr;
+    uint8_t *h_flag = nullptr;              // pinned flag read by the plain form
+    void *d_rec = nullptr;                  // failed-shot records
+    bpsf::Records rec{};
+    long long rec_cap = 0;
+    void *d_host_stage = nullptr;           // device buffers of bpsf_decode_host
+    size_t host_stage_bytes = 0;
+    bpsf_tuning tune{};
+    bpsf_work last{};
+    long long last_launch_n = 0;
+};
+
+bpsf_status bpsf_fail(bpsf_status s, const char *fmt, ...);
+bpsf_status bpsf_ensure_workspace(bpsf_ctx *c, long long n);
+bpsf_status bpsf_ensure_kernel_attrs(int variant, int smem_optin);
+int bpsf_ctx_team_smem(const bpsf_ctx *c, int S, int teams);
+int bpsf_grid_for(const bpsf_ctx *c, int variant, bool debug, int block, int smem, int blocks_per_sm);
+bool bpsf_tuning_cache_lookup(const bpsf_ctx *c, bpsf_tuning *out);
+bpsf::StreamDev bpsf_make_stream(const bpsf_ctx *c, const bpsf::JobDev &job, const bpsf::DebugDev *dbg, int W,
+                                 int S, unsigned flags);

@@ -1,0 +1,331 @@
+"""GPU parity: the CUDA BP-SF path (through the C ABI) against the CPU oracle.
+
+Same seeded inputs on both sides.  Integer work (syndromes, Phi, trial
+syndromes, flip counts, parity checks) must match bit for bit; posterior
+LLRs within |d| <= 1e-4 * max(1, |L|); corrections identical on >= 99.99% of
+shots; the logical error rate within the binomial 1-sigma of the FP64 oracle.
+"""
+import os
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle  # noqa: E402
+import synth  # noqa: E402
+from oracle import Code, Params as OParams  # noqa: E402
+from paper_2507_00254_gb300 import bpsf as B  # noqa: E402
+from paper_2507_00254_gb300 import build as libbuild  # noqa: E402
+from paper_2507_00254_gb300 import codes  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+THREADS = max(1, min(16, os.cpu_count() or 1))
+CORR_MATCH = 0.9999
+LLR_TOL = 1e-4
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib():
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    libbuild.build()
+    return B.lib()
+
+
+def pack(bits):
+    bits = np.ascontiguousarray(bits, dtype=np.uint8)
+    n, nb = bits.shape
+    w = (nb + 31) // 32
+    pad = np.zeros((n, 32 * w), dtype=np.uint8)
+    pad[:, :nb] = bits
+    return np.packbits(pad.reshape(n, w * 4, 8), axis=-1, bitorder="little").reshape(n, w * 4).view(np.uint32)
+
+
+def unpack(words, nb):
+    words = np.ascontiguousarray(words).view(np.uint8)
+    return np.unpackbits(words.reshape(words.shape[0], -1), axis=-1, bitorder="little")[:, :nb]
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a).view(np.int32)).cuda()
+
+
+def oracle_code(name):
+    if name.endswith("_phenom"):
+        hx, _ = oracle.named_code(name[: -len("_phenom")])
+        return Code(oracle.phenom_code(hx, 12))
+    hx, _ = oracle.named_code(name)
+    return Code(hx)
+
+
+def product_code(name):
+    return codes.phenom(name[: -len("_phenom")]) if name.endswith("_phenom") else codes.bb(name)
+
+
+def make_inputs(name, p, n, seed, stream=0):
+    oc = oracle_code(name)
+    if name.endswith("_phenom"):
+        e = synth.phenom_error_bits(seed, stream, 0, n, 144, 72, 12, p, p)
+    else:
+        e = synth.bernoulli_bits(seed, stream, 0, n, oc.N, p)
+    s = oc.syndrome(e)
+    return oc, e, s
+
+
+def decoder(name, p, params):
+    c = product_code(name)
+    return B.Decoder(c.ptr, c.idx, c.M, c.N, np.full(c.N, p), params)
+
+
+def oparams(P):
+    return OParams(P.max_iter, P.alpha, P.w, P.w_max, P.short_iter, P.select)
+
+
+def gpu_decode(dec, s_bits, **kw):
+    out = dec.decode(dev(pack(s_bits)), **kw)
+    return {k: v.cpu().numpy() for k, v in out.items()}
+
+
+def compare(oc, dec, s, p, P, e_bits=None, fp32=True):
+    eo, co, io, so = oc.bpsf_batch(s, p, oparams(P), fp32=fp32, threads=THREADS)
+    g = gpu_decode(dec, s)
+    eg = unpack(g["corr"], oc.N)
+    same = (eg == eo).all(axis=1)
+    frac = same.mean()
+    assert frac >= CORR_MATCH, "corrections match on %.6f of shots" % frac
+    assert ((g["conv"] != 0) == co)[same].all()
+    assert (g["iters"] == io)[same].all()
+    assert (g["stage"] == so)[same].all()
+    # Every converged correction satisfies the syndrome (checked by the oracle).
+    conv = g["conv"] != 0
+    if conv.any():
+        assert (oc.syndrome(eg[conv]) == s[conv]).all()
+    return g, (eo, co, io, so)
+
+
+# --------------------------------------------------------------------------
+# Workload parity
+# --------------------------------------------------------------------------
+
+def test_bb72_workload_matches_oracle():
+    """[[72,12,6]], p = 0.05, 10^4 shots, max_iter 50, w 4, short_iter 10."""
+    P = B.Params(max_iter=50, alpha=0.625, w=4, short_iter=10)
+    oc, e, s = make_inputs("bb72", 0.05, 10000, synth.SEEDS["bb72_cc"])
+    dec = decoder("bb72", 0.05, P)
+    g, (eo, co, io, so) = compare(oc, dec, s, 0.05, P)
+    assert (so == 2).sum() < (so == 1).sum() + (so == 0).sum()
+    assert (g["stage"] == 1).sum() > 0  # the trial path ran
+
+
+@pytest.mark.parametrize("p_idx", range(4))
+def test_bb144_workload_matches_oracle(p_idx):
+    """[[144,12,12]] at p in {0.02, 0.04, 0.06, 0.08}: max_iter 100, w 6, short_iter 20."""
+    p = (0.02, 0.04, 0.06, 0.08)[p_idx]
+    P = B.Params(max_iter=100, alpha=0.625, w=6, short_iter=20)
+    oc, e, s = make_inputs("bb144", p, 3000, synth.SEEDS["bb144_cc"][p_idx])
+    dec = decoder("bb144", p, P)
+    compare(oc, dec, s, p, P)
+
+
+def test_phenomenological_matches_oracle():
+    """12-round phenomenological [[144]] (864 x 2592), p = q = 0.004, max_iter 200, w 5, short_iter 30."""
+    P = B.Params(max_iter=200, alpha=0.625, w=5, short_iter=30)
+    oc, e, s = make_inputs("bb144_phenom", 0.004, 150, synth.SEEDS["bb144_phenom"][1])
+    dec = decoder("bb144_phenom", 0.004, P)
+    compare(oc, dec, s, 0.004, P)
+
+
+def test_mixed_codes_one_launch_match_oracle():
+    P = B.Params(max_iter=100, alpha=0.625, w=6, short_iter=20)
+    names = ["bb72", "bb90", "bb108", "bb144", "bb288"]
+    decs, synds, cases = [], [], []
+    for k, name in enumerate(names):
+        n = 300 + 97 * k
+        oc, e, s = make_inputs(name, 0.05, n, synth.SEEDS["mixed"][k])
+        decs.append(decoder(name, 0.05, P))
+        synds.append(dev(pack(s)))
+        cases.append((oc, s))
+    outs = B.decode_multi(decs, synds)
+    for (oc, s), o in zip(cases, outs):
+        eo, co, io, so = oc.bpsf_batch(s, 0.05, oparams(P), threads=THREADS)
+        eg = unpack(o["corr"].cpu().numpy(), oc.N)
+        assert (eg == eo).all(axis=1).mean() >= CORR_MATCH
+        assert (o["stage"].cpu().numpy() == so).mean() >= CORR_MATCH
+
+
+# --------------------------------------------------------------------------
+# Step-level parity through the debug dump
+# --------------------------------------------------------------------------
+
+def test_internal_values_match_oracle_bit_for_bit():
+    """LLRs, flip counts, Phi, trial syndromes and trial outcomes on a failure-heavy batch."""
+    P = B.Params(max_iter=50, alpha=0.625, w=4, short_iter=10)
+    oc, e, s = make_inputs("bb72", 0.09, 1500, 77)
+    dec = decoder("bb72", 0.09, P)
+    g = dec.decode_debug(dev(pack(s)))
+    g = {k: v.cpu().numpy() for k, v in g.items()}
+    n_failed = 0
+    for k in range(s.shape[0]):
+        r = oc.bp(s[k], 0.09, P.max_iter, P.alpha, fp32=True, track=True)
+        L = r["lout"].astype(np.float64)
+        d = np.abs(g["lout"][k].astype(np.float64) - L)
+        assert (d <= LLR_TOL * np.maximum(1.0, np.abs(L))).all()
+        assert (g["flips"][k].astype(np.uint16) == r["flips"]).all()
+        if r["converged"]:
+            continue
+        n_failed += 1
+        phi = oracle.top(r["flips"], P.w)
+        assert (g["phi"][k] == phi).all()
+        synd, conv, iters, es = oc.trials(s[k], 0.09, phi, oparams(P))
+        tsyn = unpack(g["trial_synd"][k].reshape(len(synd), -1), oc.M)
+        assert (tsyn == synd).all()
+        assert (g["trial_conv"][k] == conv).all()
+        assert (g["trial_iters"][k] == iters).all()
+    assert n_failed > 20
+
+
+# --------------------------------------------------------------------------
+# Forms and launch shapes give identical results
+# --------------------------------------------------------------------------
+
+def test_launch_shape_does_not_change_results():
+    P = B.Params(max_iter=100, alpha=0.625, w=6, short_iter=20)
+    oc, e, s = make_inputs("bb144", 0.07, 4000, 5)
+    dec = decoder("bb144", 0.07, P)
+    ref = gpu_decode(dec, s)
+    for t in [(1, 1, 4, 0), (1, 3, 8, 0), (2, 2, 8, 0), (4, 1, 8, 1), (1, 8, 16, 0), (8, 1, 16, 0)]:
+        dec.tuning = t
+        got = gpu_decode(dec, s)
+        for key in ("corr", "conv", "iters", "stage"):
+            assert (got[key] == ref[key]).all(), (t, key)
+
+
+def test_plain_form_equals_batched_form():
+    P = B.Params(max_iter=100, alpha=0.625, w=6, short_iter=20)
+    oc, e, s = make_inputs("bb144", 0.07, 300, 6)
+    dec = decoder("bb144", 0.07, P)
+    a = gpu_decode(dec, s)
+    b = gpu_decode(dec, s, plain=True)
+    for key in ("corr", "conv", "iters", "stage"):
+        assert (a[key] == b[key]).all(), key
+    assert (a["stage"] == 1).any()
+
+
+def test_host_buffer_form_equals_device_form():
+    P = B.Params(max_iter=50, alpha=0.625, w=4, short_iter=10)
+    oc, e, s = make_inputs("bb72", 0.06, 2000, 8)
+    dec = decoder("bb72", 0.06, P)
+    a = gpu_decode(dec, s)
+    h = dec.decode_host(pack(s))
+    assert (h["corr"].view(np.int32) == a["corr"]).all()
+    assert (h["conv"] == a["conv"]).all() and (h["iters"] == a["iters"]).all() and (h["stage"] == a["stage"]).all()
+
+
+# --------------------------------------------------------------------------
+# Variants and edge cases
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("variant", ["bp_only", "select_first", "w_max2", "ragged_bb90"])
+def test_variants_match_oracle(variant):
+    name, p = "bb72", 0.08
+    P = B.Params(max_iter=50, alpha=0.625, w=4, short_iter=10)
+    if variant == "bp_only":
+        P = B.Params(max_iter=50, alpha=0.625, w=0)
+    elif variant == "select_first":
+        P.select = B.BPSF_SELECT_FIRST
+    elif variant == "w_max2":
+        P = B.Params(max_iter=50, alpha=0.625, w=5, w_max=2, short_iter=10)
+    elif variant == "ragged_bb90":
+        name, p = "bb90", 0.06
+    oc, e, s = make_inputs(name, p, 2000, 9)
+    compare(oc, decoder(name, p, P), s, p, P)
+
+
+def test_edge_cases():
+    P = B.Params(max_iter=50, alpha=0.625, w=4, short_iter=10)
+    dec = decoder("bb90", 0.05, P)  # M = 45, N = 90: ragged words on both sides
+    oc = oracle_code("bb90")
+    # Empty batch.
+    out = dec.outputs(1)
+    B.bpsf_decode(dec.handle, 0, 0, 2, 0, 3, 0, 0, 0, 0)
+    # Zero syndromes converge at iteration 1 with e = 0.
+    g = gpu_decode(dec, np.zeros((5, 45), dtype=np.uint8))
+    assert (g["conv"] == 1).all() and (g["iters"] == 1).all() and (g["corr"] == 0).all() and (g["stage"] == 0).all()
+    # One shot; all-ones syndrome (maximum weight).
+    s1 = np.ones((1, 45), dtype=np.uint8)
+    compare(oc, dec, s1, 0.05, P)
+    # Padding bits beyond M are ignored; wide strides are honoured.
+    oc2, e, s = make_inputs("bb90", 0.06, 700, 10)
+    packed = pack(s)
+    wide = np.zeros((packed.shape[0], 4), dtype=np.uint32)
+    wide[:, :2] = packed
+    wide[:, 1] |= np.uint32(0xFFFFE000)  # bits 45..63 set
+    wide[:, 2:] = np.uint32(0xDEADBEEF)
+    o = dec.outputs(len(s))
+    o["corr"] = torch.zeros((len(s), 6), dtype=torch.int32, device="cuda")
+    dec.decode(dev(wide), out=o)
+    ref = gpu_decode(dec, s)
+    got = o["corr"].cpu().numpy()
+    assert (got[:, :3] == ref["corr"]).all() and (got[:, 3:] == 0).all()
+    assert (o["stage"].cpu().numpy() == ref["stage"]).all()
+    # Strides below the word count are rejected.
+    with pytest.raises(B.BpsfError) as ei:
+        B.bpsf_decode(dec.handle, 1, out["corr"].data_ptr(), 1, out["corr"].data_ptr(), 3,
+                      out["conv"].data_ptr(), out["iters"].data_ptr(), 0, 0)
+    assert ei.value.status == B.BPSF_EINVAL
+
+
+def test_work_counters_are_consistent():
+    P = B.Params(max_iter=100, alpha=0.625, w=6, short_iter=20)
+    oc, e, s = make_inputs("bb144", 0.08, 2000, 11)
+    dec = decoder("bb144", 0.08, P)
+    g = gpu_decode(dec, s)
+    w = dec.last_work()
+    assert w["initial_runs"] == 2000
+    assert w["failed_shots"] == int((g["stage"] != 0).sum())
+    assert w["trial_runs"] == w["failed_shots"] * 63
+    assert w["edge_updates"] == w["iterations"] * 432
+    assert w["iterations"] >= int(g["iters"][g["stage"] == 0].sum()) + 100 * w["failed_shots"]
+
+
+# --------------------------------------------------------------------------
+# Full-size configuration: sampled parity plus properties of every shot
+# --------------------------------------------------------------------------
+
+def test_full_size_bb144_p008_sampled_parity_and_ler():
+    """10^6 shots at p = 0.08 in the benchmark's launch shape; oracle on a random sample."""
+    p, n = 0.08, 1_000_000
+    P = B.Params(max_iter=100, alpha=0.625, w=6, short_iter=20)
+    c = product_code("bb144")
+    e = synth.bernoulli_bits(synth.SEEDS["bb144_cc"][3], 0, 0, n, c.N, p)
+    dec = decoder("bb144", p, P)
+    err = dev(pack(e))
+    synd = dec.syndrome(err)
+    torch.cuda.synchronize()
+    out = dec.decode(synd)
+    corr = out["corr"]
+    conv = out["conv"].bool()
+    # Property on every shot: converged corrections satisfy their syndrome.
+    resid = dec.syndrome(corr)
+    assert bool(((resid == synd).all(dim=1) | ~conv).all())
+    stage = out["stage"].cpu().numpy()
+    assert set(np.unique(stage)).issubset({0, 1, 2})
+    assert ((stage < 2) == conv.cpu().numpy()).all()
+    # Oracle on a random sample of shots.
+    rng = np.random.default_rng(123)
+    idx = np.sort(rng.choice(n, size=1500, replace=False))
+    oc = oracle_code("bb144")
+    s_np = unpack(synd.cpu().numpy()[idx], 72)
+    assert (s_np == oc.syndrome(e[idx])).all()
+    eo, co, io, so = oc.bpsf_batch(s_np, p, oparams(P), threads=THREADS)
+    eg = unpack(corr.cpu().numpy()[idx], 144)
+    assert (eg == eo).all(axis=1).mean() >= CORR_MATCH
+    # Logical error rate within the binomial 1-sigma of the FP64 oracle on the same shots.
+    hx, hz = oracle.named_code("bb144")
+    lx = oracle.logicals(hx, hz)
+    e64, c64, _, _ = oc.bpsf_batch(s_np, p, oparams(P), fp32=False, threads=THREADS)
+    f64 = oracle.logical_failures(hx, lx, e[idx], e64, c64).mean()
+    fg = oracle.logical_failures(hx, lx, e[idx], eg, conv.cpu().numpy()[idx]).mean()
+    sigma = np.sqrt(max(f64 * (1 - f64), 1e-12) / len(idx))
+    assert abs(fg - f64) <= sigma + 1e-12
