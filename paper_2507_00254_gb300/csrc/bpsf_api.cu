@@ -1,6 +1,6 @@
 // Host side of libbpsf: argument checking, Tanner-graph layout, device
 // workspace, the batched / plain / host-buffer / mixed-code decode forms,
-// launch-shape tuning and the code builders.  See include/bpsf.h.
+// launch-shape tuning and the autotuner.  See include/bpsf.h.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -50,13 +50,13 @@ extern "C" const char *bpsf_status_str(bpsf_status s) {
 
 // Bound on any device-side wait (a trial waiting for its record, a block
 // waiting for other blocks to publish trials).
-static const unsigned long long kWaitNs = 5ull * 1000 * 1000 * 1000;
-
-// ---------------------------------------------------------------------------
-// Context creation
-// ---------------------------------------------------------------------------
+const unsigned long long kBpsfWaitNs = 5ull * 1000 * 1000 * 1000;
 
 static size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
+
+// ---------------------------------------------------------------------------
+// Context lifetime
+// ---------------------------------------------------------------------------
 
 static void free_workspace(bpsf_ctx *c) {
     if (c->d_rec) cudaFree(c->d_rec);
@@ -81,71 +81,102 @@ extern "C" void bpsf_destroy(bpsf_ctx *c) {
     delete c;
 }
 
-int bpsf_ctx_team_smem(const bpsf_ctx *c, int S, int teams) {
-    return block_smem_bytes(c->M, c->N, c->nnz, c->Ws, S, teams);
-}
-
-// Largest S (<= S0) whose block fits in shared memory; 0 if none.
-static int fit_slots(const bpsf_ctx *c, int S0, int teams) {
-    for (int S = S0; S >= 1; --S)
-        if (bpsf_ctx_team_smem(c, S, teams) <= c->smem_optin) return S;
-    return 0;
-}
-
-static bpsf_tuning default_tuning(const bpsf_ctx *c) {
-    bpsf_tuning t{};
-    if (c->nnz <= 1024) {
-        t.warps_per_team = 1;
-        t.slots_per_team = 4;
-        t.warps_per_block = 8;
-    } else if (c->nnz <= 4096) {
-        t.warps_per_team = 2;
-        t.slots_per_team = 2;
-        t.warps_per_block = 8;
-    } else {
-        t.warps_per_team = 8;
-        t.slots_per_team = 1;
-        t.warps_per_block = 16;
-    }
-    const int teams = t.warps_per_block / t.warps_per_team;
-    int S = fit_slots(c, t.slots_per_team, teams);
-    while (S == 0 && t.warps_per_block > t.warps_per_team) {
-        t.warps_per_block /= 2;
-        S = fit_slots(c, t.slots_per_team, t.warps_per_block / t.warps_per_team);
-    }
-    t.slots_per_team = S > 0 ? S : 1;
-    t.blocks_per_sm = 0;
-    return t;
-}
-
-static bpsf_status check_tuning(const bpsf_ctx *c, const bpsf_tuning &t) {
-    const int W = t.warps_per_team, S = t.slots_per_team, B = t.warps_per_block;
-    if (!(W == 1 || W == 2 || W == 4 || W == 8)) return bpsf_fail(BPSF_EINVAL, "warps_per_team must be 1, 2, 4 or 8");
-    if (S < 1 || S > kMaxSlots) return bpsf_fail(BPSF_EINVAL, "slots_per_team must be in 1..%d", kMaxSlots);
-    if (B < W || B > 16 || B % W) return bpsf_fail(BPSF_EINVAL, "warps_per_block must be a multiple of warps_per_team, <= 16");
-    if (W > 1 && B / W > kMaxNamedTeams) return bpsf_fail(BPSF_EINVAL, "at most %d multi-warp teams per block", kMaxNamedTeams);
-    if (t.blocks_per_sm < 0) return bpsf_fail(BPSF_EINVAL, "blocks_per_sm must be >= 0");
-    const int smem = bpsf_ctx_team_smem(c, S, B / W);
-    if (smem > c->smem_optin)
-        return bpsf_fail(BPSF_EINVAL, "launch shape needs %d bytes of shared memory (limit %d)", smem, c->smem_optin);
-    return BPSF_OK;
-}
-
 bpsf_status bpsf_ensure_kernel_attrs(int variant, int smem_optin) {
     static std::mutex mu;
-    static bool done[8] = {false};
+    static bool done[64] = {false};
     std::lock_guard<std::mutex> lk(mu);
     for (int dbg = 0; dbg < 2; ++dbg) {
         const int k = variant * 2 + dbg;
         if (done[k]) continue;
         cudaError_t e = cudaFuncSetAttribute(persistent_kernel_ptr(variant, dbg != 0),
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin);
-        if (e != cudaSuccess)
-            return bpsf_fail(BPSF_ECUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(e));
+        if (e != cudaSuccess) return bpsf_fail(BPSF_ECUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(e));
         done[k] = true;
     }
     return BPSF_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Launch plans
+// ---------------------------------------------------------------------------
+
+static int plan_queue(int teams, int S) { return std::min(128, std::max(32, 2 * teams * S)); }
+
+static int plan_smem(const bpsf_ctx *c, int vstride, int S, int teams, int Q) {
+    return block_smem_bytes(c->M, c->N, c->P, c->Ws, vstride, S, teams, Q);
+}
+
+bpsf_status bpsf_make_plan(bpsf_ctx *const *codes, int n_codes, const bpsf_tuning &t, bool debug, bpsf_plan *out) {
+    const int W = t.warps_per_team, S = t.slots_per_team, B = t.warps_per_block;
+    if (!(W == 1 || W == 2 || W == 4 || W == 8)) return bpsf_fail(BPSF_EINVAL, "warps_per_team must be 1, 2, 4 or 8");
+    if (S < 1 || S > kMaxSlots) return bpsf_fail(BPSF_EINVAL, "slots_per_team must be in 1..%d", kMaxSlots);
+    if (B < W || B > kMaxComputeWarps || B % W)
+        return bpsf_fail(BPSF_EINVAL, "warps_per_block must be a multiple of warps_per_team, at most %d",
+                         kMaxComputeWarps);
+    if (t.blocks_per_sm < 0) return bpsf_fail(BPSF_EINVAL, "blocks_per_sm must be >= 0");
+    const int teams = B / W;
+    // One kernel variant must fit every code of the launch.
+    bool all_regular = true;
+    int dc = 0, dv = 0;
+    for (int k = 0; k < n_codes; ++k) {
+        all_regular = all_regular && codes[k]->regular && codes[k]->dc_max == codes[0]->dc_max;
+        dc = std::max(dc, codes[k]->dc_max);
+        dv = std::max(dv, codes[k]->dv_max);
+    }
+    const int variant = kernel_variant(all_regular ? -dc : dc, std::max(dv, 1));
+    if (variant < 0) return bpsf_fail(BPSF_EINVAL, "no kernel variant for row degree %d, column degree %d", dc, dv);
+    const int vstride = kernel_variant_dv(variant);
+    const int Q = plan_queue(teams, S);
+    int smem = 0;
+    for (int k = 0; k < n_codes; ++k) {
+        if (codes[k]->vstride != vstride)
+            return bpsf_fail(BPSF_EINVAL, "codes of one launch need the same column table width (%d vs %d)",
+                             codes[k]->vstride, vstride);
+        smem = std::max(smem, plan_smem(codes[k], vstride, S, teams, Q));
+    }
+    const bpsf_ctx *c0 = codes[0];
+    if (smem > c0->smem_optin)
+        return bpsf_fail(BPSF_EINVAL, "launch shape needs %d bytes of shared memory (limit %d)", smem, c0->smem_optin);
+    bpsf_status st = bpsf_ensure_kernel_attrs(variant, c0->smem_optin);
+    if (st != BPSF_OK) return st;
+    const int block = 32 * (B + 1);
+    int occ = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, persistent_kernel_ptr(variant, debug), block, smem);
+    if (e != cudaSuccess) return bpsf_fail(BPSF_ECUDA, "occupancy query: %s", cudaGetErrorString(e));
+    if (t.blocks_per_sm > 0) occ = std::min(occ, t.blocks_per_sm);
+    if (occ <= 0) return bpsf_fail(BPSF_EINVAL, "launch shape does not fit on an SM");
+    out->variant = variant;
+    out->teams = teams;
+    out->W = W;
+    out->S = S;
+    out->Q = Q;
+    out->block = block;
+    out->smem = smem;
+    out->grid = occ * c0->sm_count;
+    return BPSF_OK;
+}
+
+static bpsf_tuning default_tuning(bpsf_ctx *c) {
+    // Small codes: single-warp teams with a few slots each; large codes:
+    // multi-warp teams.  Shrink until the block fits.
+    const int Wc[] = {1, 1, 1, 2, 4, 8};
+    const int Sc[] = {4, 3, 2, 2, 1, 1};
+    for (int k = 0; k < 6; ++k) {
+        if (c->nnz > 2048 && Wc[k] < 4) continue;
+        for (int B = kMaxComputeWarps; B >= Wc[k]; --B) {
+            if (B % Wc[k]) continue;
+            bpsf_tuning t{Wc[k], Sc[k], B, 0};
+            bpsf_plan pl;
+            bpsf_ctx *cs[1] = {c};
+            if (bpsf_make_plan(cs, 1, t, false, &pl) == BPSF_OK) return t;
+        }
+    }
+    return bpsf_tuning{1, 1, 1, 0};
+}
+
+// ---------------------------------------------------------------------------
+// Context creation
+// ---------------------------------------------------------------------------
 
 extern "C" bpsf_status bpsf_create(bpsf_ctx **out, int32_t M, int32_t N, int64_t nnz, int32_t layout,
                                    const int32_t *ptr, const int32_t *idx, const double *priors,
@@ -187,63 +218,68 @@ extern "C" bpsf_status bpsf_create(bpsf_ctx **out, int32_t M, int32_t N, int64_t
         const double pi = priors[i];
         if (!(pi > 0.0 && pi < 0.5)) return bpsf_fail(BPSF_EINVAL, "prior %d = %g is not in (0, 0.5)", i, pi);
     }
+    int dc = 0;
+    for (int j = 0; j < M; ++j) {
+        std::sort(rows[j].begin(), rows[j].end());
+        for (size_t k = 1; k < rows[j].size(); ++k)
+            if (rows[j][k] == rows[j][k - 1]) return bpsf_fail(BPSF_EINVAL, "duplicate entry (%d, %d)", j, rows[j][k]);
+        if (rows[j].size() < 2)
+            return bpsf_fail(BPSF_EINVAL, "row %d has degree %d; every check needs degree >= 2", j, (int)rows[j].size());
+        dc = std::max(dc, (int)rows[j].size());
+    }
+    // Columns list their checks in ascending order (rows are visited in order).
+    std::vector<std::vector<std::pair<int, int>>> cols(N);  // (check, rank of the edge in its row)
+    for (int j = 0; j < M; ++j)
+        for (int k = 0; k < (int)rows[j].size(); ++k) cols[rows[j][k]].push_back({j, k});
+    int dv = 0;
+    for (int i = 0; i < N; ++i) dv = std::max(dv, (int)cols[i].size());
+    bool regular = true;
+    for (int j = 0; j < M; ++j) regular = regular && (int)rows[j].size() == dc;
+    for (int i = 0; i < N; ++i) regular = regular && (int)cols[i].size() == dv;
+    if (dc > 32 || dv > 16)
+        return bpsf_fail(BPSF_EINVAL, "row degree %d or column degree %d too large (limits 32, 16)", dc, dv);
+    const int variant = kernel_variant(regular ? -dc : dc, std::max(dv, 1));
+    if (variant < 0) return bpsf_fail(BPSF_EINVAL, "no kernel variant for row degree %d, column degree %d", dc, dv);
+    const int vstride = kernel_variant_dv(variant);
+    const long long P = (long long)dc * M;
+    if (P > 65534) return bpsf_fail(BPSF_EINVAL, "max row degree x M = %lld exceeds 65534", P);
+
     bpsf_ctx *c = new bpsf_ctx();
     c->M = M;
     c->N = N;
     c->nnz = (int)nnz;
     c->Ws = (M + 31) / 32;
     c->Wn = (N + 31) / 32;
+    c->dc_max = dc;
+    c->dv_max = dv;
+    c->regular = regular ? 1 : 0;
+    c->variant = variant;
+    c->vstride = vstride;
+    c->P = (int)P;
     c->p = p;
     if (c->p.w > 0 && c->p.w_max == 0) c->p.w_max = c->p.w;
     c->csr_ptr.assign(M + 1, 0);
-    c->csr_col.reserve(nnz);
-    int dc = 0;
     for (int j = 0; j < M; ++j) {
-        std::sort(rows[j].begin(), rows[j].end());
-        for (size_t k = 1; k < rows[j].size(); ++k)
-            if (rows[j][k] == rows[j][k - 1]) {
-                delete c;
-                return bpsf_fail(BPSF_EINVAL, "duplicate entry (%d, %d)", j, rows[j][k]);
-            }
-        if (rows[j].size() < 2) {
-            delete c;
-            return bpsf_fail(BPSF_EINVAL, "row %d has degree %d; every check needs degree >= 2", j, (int)rows[j].size());
-        }
-        dc = std::max(dc, (int)rows[j].size());
         for (int v : rows[j]) c->csr_col.push_back(v);
         c->csr_ptr[j + 1] = (int)c->csr_col.size();
     }
-    // CSC: columns list their checks in ascending order (rows are visited in order).
-    std::vector<std::vector<std::pair<int, int>>> cols(N);  // (check, csr edge)
-    for (int j = 0; j < M; ++j)
-        for (int e = c->csr_ptr[j]; e < c->csr_ptr[j + 1]; ++e) cols[c->csr_col[e]].push_back({j, e});
-    int dv = 0;
-    for (int i = 0; i < N; ++i) dv = std::max(dv, (int)cols[i].size());
-    c->dc_max = dc;
-    c->dv_max = dv;
-    c->variant = kernel_variant(dc, std::max(dv, 1));
-    if (c->variant < 0) {
-        delete c;
-        return bpsf_fail(BPSF_EINVAL, "row degree %d or column degree %d too large (limits 32, 16)", dc, dv);
-    }
-    std::vector<uint16_t> row_ptr(M + 1), csr_to_csc(nnz), col_ptr(N + 1), csc_to_csr(nnz), csc_chk(nnz), csr_col(nnz);
-    std::vector<float> lch(N), lch_csr(nnz);
+    // Message position of the edge of rank k in row j: k * M + j.
+    std::vector<uint8_t> row_deg(M);
+    std::vector<uint16_t> vpos((size_t)N * vstride, 0xffff), vchk((size_t)N * vstride, 0xffff);
+    std::vector<uint16_t> row_ptr(M + 1), csr_col(nnz);
+    std::vector<float> lch(N), lch_pos(P, 0.f);
+    for (int j = 0; j < M; ++j) row_deg[j] = (uint8_t)rows[j].size();
+    for (int i = 0; i < N; ++i)
+        for (int k = 0; k < (int)cols[i].size(); ++k) {
+            vpos[(size_t)i * vstride + k] = (uint16_t)(cols[i][k].second * M + cols[i][k].first);
+            vchk[(size_t)i * vstride + k] = (uint16_t)cols[i][k].first;
+        }
     for (int j = 0; j <= M; ++j) row_ptr[j] = (uint16_t)c->csr_ptr[j];
     for (int e = 0; e < nnz; ++e) csr_col[e] = (uint16_t)c->csr_col[e];
-    int f = 0;
-    for (int i = 0; i < N; ++i) {
-        col_ptr[i] = (uint16_t)f;
-        for (auto &ce : cols[i]) {
-            csc_chk[f] = (uint16_t)ce.first;
-            csc_to_csr[f] = (uint16_t)ce.second;
-            csr_to_csc[ce.second] = (uint16_t)f;
-            ++f;
-        }
-    }
-    col_ptr[N] = (uint16_t)f;
     // Channel LLR (Section II-B, step 1) in double, rounded once to float.
     for (int i = 0; i < N; ++i) lch[i] = (float)std::log((1.0 - priors[i]) / priors[i]);
-    for (int e = 0; e < nnz; ++e) lch_csr[e] = lch[c->csr_col[e]];
+    for (int j = 0; j < M; ++j)
+        for (int k = 0; k < (int)rows[j].size(); ++k) lch_pos[(size_t)k * M + j] = lch[rows[j][k]];
     std::vector<uint32_t> masks;
     for (uint32_t k = 1; c->p.w > 0 && k < (1u << c->p.w); ++k)
         if (__builtin_popcount(k) <= c->p.w_max) masks.push_back(k);
@@ -261,11 +297,12 @@ extern "C" bpsf_status bpsf_create(bpsf_ctx **out, int32_t M, int32_t N, int64_t
     c->smem_optin = (int)prop.sharedMemPerBlockOptin;
 
     // One allocation for all code arrays.
-    size_t off[10], sz = 0;
-    const size_t n16 = 2 * (size_t)nnz;
-    size_t sizes[10] = {2 * (size_t)(M + 1), n16, 2 * (size_t)(N + 1), n16, n16, n16,
-                        4 * (size_t)N,       4 * (size_t)nnz, 4 * masks.size(), 0};
-    for (int k = 0; k < 9; ++k) {
+    const void *srcs[8] = {row_deg.data(), vpos.data(), vchk.data(), lch.data(),
+                           lch_pos.data(), row_ptr.data(), csr_col.data(), masks.data()};
+    const size_t sizes[8] = {(size_t)M, 2 * vpos.size(), 2 * vchk.size(), 4 * (size_t)N,
+                             4 * (size_t)P, 2 * (size_t)(M + 1), 2 * (size_t)nnz, 4 * masks.size()};
+    size_t off[8], sz = 0;
+    for (int k = 0; k < 8; ++k) {
         off[k] = sz;
         sz += align16(sizes[k]);
     }
@@ -275,9 +312,7 @@ extern "C" bpsf_status bpsf_create(bpsf_ctx **out, int32_t M, int32_t N, int64_t
         return bpsf_fail(BPSF_ENOMEM, "cudaMalloc(code): %s", cudaGetErrorString(e));
     }
     std::vector<unsigned char> hbuf(sz, 0);
-    const void *srcs[9] = {row_ptr.data(), csr_to_csc.data(), col_ptr.data(), csc_to_csr.data(), csc_chk.data(),
-                           csr_col.data(), lch.data(),        lch_csr.data(),    masks.data()};
-    for (int k = 0; k < 9; ++k) std::memcpy(hbuf.data() + off[k], srcs[k], sizes[k]);
+    for (int k = 0; k < 8; ++k) std::memcpy(hbuf.data() + off[k], srcs[k], sizes[k]);
     e = cudaMemcpy(c->d_code, hbuf.data(), sz, cudaMemcpyHostToDevice);
     unsigned char *base = (unsigned char *)c->d_code;
     CodeDev &cd = c->code;
@@ -286,23 +321,25 @@ extern "C" bpsf_status bpsf_create(bpsf_ctx **out, int32_t M, int32_t N, int64_t
     cd.nnz = (int)nnz;
     cd.Ws = c->Ws;
     cd.Wn = c->Wn;
-    cd.dc_max = dc;
+    cd.DC = dc;
     cd.dv_max = dv;
+    cd.P = (int)P;
+    cd.regular = c->regular;
+    cd.vstride = vstride;
     cd.max_iter = p.max_iter;
     cd.short_iter = c->p.w > 0 ? p.short_iter : 1;
     cd.w = c->p.w;
     cd.n_trials = c->n_trials;
     cd.select = p.select;
     cd.alpha = p.alpha;
-    cd.row_ptr = (const uint16_t *)(base + off[0]);
-    cd.csr_to_csc = (const uint16_t *)(base + off[1]);
-    cd.col_ptr = (const uint16_t *)(base + off[2]);
-    cd.csc_to_csr = (const uint16_t *)(base + off[3]);
-    cd.csc_chk = (const uint16_t *)(base + off[4]);
-    cd.csr_col = (const uint16_t *)(base + off[5]);
-    cd.lch = (const float *)(base + off[6]);
-    cd.lch_csr = (const float *)(base + off[7]);
-    cd.trial_mask = (const uint32_t *)(base + off[8]);
+    cd.row_deg = (const uint8_t *)(base + off[0]);
+    cd.vpos = (const uint16_t *)(base + off[1]);
+    cd.vchk = (const uint16_t *)(base + off[2]);
+    cd.lch = (const float *)(base + off[3]);
+    cd.lch_pos = (const float *)(base + off[4]);
+    cd.row_ptr = (const uint16_t *)(base + off[5]);
+    cd.csr_col = (const uint16_t *)(base + off[6]);
+    cd.trial_mask = (const uint32_t *)(base + off[7]);
     if (e == cudaSuccess) e = cudaMalloc((void **)&c->d_ctr, sizeof(StreamCounters));
     if (e == cudaSuccess) e = cudaMemset(c->d_ctr, 0, sizeof(StreamCounters));
     if (e == cudaSuccess) e = cudaMallocHost((void **)&c->h_ctr, sizeof(StreamCounters));
@@ -314,11 +351,6 @@ extern "C" bpsf_status bpsf_create(bpsf_ctx **out, int32_t M, int32_t N, int64_t
     }
     std::memset(c->h_ctr, 0, sizeof(StreamCounters));
     c->tune = default_tuning(c);
-    bpsf_status st = bpsf_ensure_kernel_attrs(c->variant, c->smem_optin);
-    if (st != BPSF_OK) {
-        bpsf_destroy(c);
-        return st;
-    }
     bpsf_tuning cached;
     if (bpsf_tuning_cache_lookup(c, &cached)) c->tune = cached;
     *out = c;
@@ -326,53 +358,53 @@ extern "C" bpsf_status bpsf_create(bpsf_ctx **out, int32_t M, int32_t N, int64_t
 }
 
 // ---------------------------------------------------------------------------
-// Workspace: failed-shot records, capacity = shots of the largest batch.
+// Workspace: one record row per shot (capacity = the largest batch so far).
 // ---------------------------------------------------------------------------
 
 bpsf_status bpsf_ensure_workspace(bpsf_ctx *c, long long n) {
     if (n <= c->rec_cap) return BPSF_OK;
     const long long cap = std::max<long long>(n, 1);
     const int w = std::max(c->p.w, 1), T = std::max(c->n_trials, 1);
-    const size_t sz_shot = align16(8 * (size_t)cap), sz_ready = align16(4 * (size_t)cap),
-                 sz_done = align16(4 * (size_t)cap), sz_best = align16(8 * (size_t)cap),
-                 sz_phi = align16(4 * (size_t)cap * w), sz_synd = align16(4 * (size_t)cap * c->Ws),
-                 sz_corr = align16(4 * (size_t)cap * T * c->Wn), sz_iters = align16(2 * (size_t)cap * T);
-    const size_t total = sz_shot + sz_ready + sz_done + sz_best + sz_phi + sz_synd + sz_corr + sz_iters;
+    const size_t sz[8] = {align16(8 * (size_t)cap),      align16(8 * (size_t)cap),
+                          align16(4 * (size_t)cap),      align16(8 * (size_t)cap),
+                          align16(4 * (size_t)cap * w),  align16(4 * (size_t)cap * c->Ws),
+                          align16(4 * (size_t)cap * T * c->Wn), align16(2 * (size_t)cap * T)};
+    size_t total = 0;
+    for (size_t s : sz) total += s;
     free_workspace(c);
     void *mem = nullptr;
     cudaError_t e = cudaMalloc(&mem, total);
     if (e != cudaSuccess) return bpsf_fail(BPSF_ENOMEM, "workspace of %zu bytes: %s", total, cudaGetErrorString(e));
     unsigned char *p = (unsigned char *)mem;
     c->d_rec = mem;
-    c->rec.shot = (long long *)p;
-    p += sz_shot;
-    c->rec.ready = (unsigned *)p;
-    p += sz_ready;
+    c->rec.qseq = (unsigned long long *)p;
+    p += sz[0];
+    c->rec.qshot = (long long *)p;
+    p += sz[1];
     c->rec.done = (unsigned *)p;
-    p += sz_done;
+    p += sz[2];
     c->rec.best = (unsigned long long *)p;
-    p += sz_best;
+    p += sz[3];
     c->rec.phi = (int32_t *)p;
-    p += sz_phi;
+    p += sz[4];
     c->rec.synd = (uint32_t *)p;
-    p += sz_synd;
+    p += sz[5];
     c->rec.corr = (uint32_t *)p;
-    p += sz_corr;
+    p += sz[6];
     c->rec.iters = (int16_t *)p;
     c->rec.cap = cap;
     c->rec_cap = cap;
     return BPSF_OK;
 }
 
-// Records must read "not ready" before a launch: clear the ready flags of
-// the first n slots on the stream.
-static bpsf_status clear_ready(bpsf_ctx *c, long long n, cudaStream_t s) {
-    cudaError_t e = cudaMemsetAsync(c->rec.ready, 0, 4 * (size_t)std::max<long long>(n, 1), s);
+// Queue entries must read "not written" before a launch.
+static bpsf_status clear_queue(bpsf_ctx *c, long long n, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(c->rec.qseq, 0, 8 * (size_t)std::max<long long>(n, 1), s);
     if (e != cudaSuccess) return bpsf_fail(BPSF_ECUDA, "cudaMemsetAsync: %s", cudaGetErrorString(e));
     return BPSF_OK;
 }
 
-StreamDev bpsf_make_stream(const bpsf_ctx *c, const JobDev &job, const DebugDev *dbg, int W, int S, unsigned flags) {
+StreamDev bpsf_make_stream(const bpsf_ctx *c, const JobDev &job, const DebugDev *dbg, unsigned flags) {
     StreamDev sd;
     std::memset(&sd, 0, sizeof(sd));
     sd.code = c->code;
@@ -380,17 +412,13 @@ StreamDev bpsf_make_stream(const bpsf_ctx *c, const JobDev &job, const DebugDev 
     sd.rec = c->rec;
     sd.ctr = c->d_ctr;
     if (dbg) sd.dbg = *dbg;
-    sd.W = W;
-    sd.S = S;
     sd.flags = flags;
     return sd;
 }
 
-int bpsf_grid_for(const bpsf_ctx *c, int variant, bool debug, int block, int smem, int blocks_per_sm) {
-    int occ = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, persistent_kernel_ptr(variant, debug), block, smem);
-    if (blocks_per_sm > 0) occ = std::min(occ, blocks_per_sm);
-    return occ * c->sm_count;
+static void launch_plan(const bpsf_plan &pl, bool debug, const StreamDev *sds, int n, int grid, void *stream) {
+    LaunchArgs la{sds, n, pl.teams, pl.W, pl.S, pl.Q, kBpsfWaitNs};
+    launch_persistent(pl.variant, debug, grid, pl.block, pl.smem, la, stream);
 }
 
 static bpsf_status check_io(const bpsf_ctx *c, int64_t n, const void *synd, int32_t ss, const void *corr, int32_t cs,
@@ -410,22 +438,20 @@ static bpsf_status decode_impl(bpsf_ctx *c, int64_t n, const uint32_t *synd, int
     bpsf_status st = check_io(c, n, synd, ss, corr, cs, conv, iters);
     if (st != BPSF_OK || n == 0) return st;
     cudaSetDevice(c->device);
+    bpsf_plan pl;
+    bpsf_ctx *cs1[1] = {c};
+    st = bpsf_make_plan(cs1, 1, c->tune, dbg != nullptr, &pl);
+    if (st != BPSF_OK) return st;
     st = bpsf_ensure_workspace(c, n);
     if (st != BPSF_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
     cudaError_t e = cudaMemsetAsync(c->d_ctr, 0, sizeof(StreamCounters), s);
     if (e != cudaSuccess) return bpsf_fail(BPSF_ECUDA, "cudaMemsetAsync: %s", cudaGetErrorString(e));
-    st = clear_ready(c, n, s);
+    st = clear_queue(c, n, s);
     if (st != BPSF_OK) return st;
     JobDev job{synd, corr, conv, iters, stage, n, ss, cs};
-    const bpsf_tuning &t = c->tune;
-    StreamDev sd = bpsf_make_stream(c, job, dbg, t.warps_per_team, t.slots_per_team, 0);
-    LaunchArgs la{&sd, 1, t.warps_per_block, kWaitNs};
-    const int block = 32 * t.warps_per_block;
-    const int smem = bpsf_ctx_team_smem(c, t.slots_per_team, t.warps_per_block / t.warps_per_team);
-    int grid = bpsf_grid_for(c, c->variant, dbg != nullptr, block, smem, t.blocks_per_sm);
-    if (grid <= 0) return bpsf_fail(BPSF_EINVAL, "launch shape does not fit on an SM");
-    launch_persistent(c->variant, dbg != nullptr, grid, block, smem, la, stream);
+    StreamDev sd = bpsf_make_stream(c, job, dbg, 0);
+    launch_plan(pl, dbg != nullptr, &sd, 1, pl.grid, stream);
     e = cudaGetLastError();
     if (e != cudaSuccess) return bpsf_fail(BPSF_ECUDA, "kernel launch: %s", cudaGetErrorString(e));
     c->last_launch_n = n;
@@ -489,15 +515,18 @@ extern "C" bpsf_status bpsf_decode_plain(bpsf_ctx *c, int64_t n, const uint32_t 
     st = bpsf_ensure_workspace(c, 1);
     if (st != BPSF_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
-    const bpsf_tuning &t = c->tune;
-    const int W = t.warps_per_team;
-    // Launch A: one team, one slot, the initial run of one shot.
-    const int smemA = bpsf_ctx_team_smem(c, 1, 1);
-    // Launch B: the shot's trials spread over teams of the tuned shape.
-    const int S = t.slots_per_team, teams = t.warps_per_block / W;
-    const int smemB = bpsf_ctx_team_smem(c, S, teams);
+    bpsf_ctx *cs1[1] = {c};
+    // Launch A: one block, one team, one slot, the initial run of one shot.
+    bpsf_plan plA, plB;
+    bpsf_tuning tA{c->tune.warps_per_team, 1, c->tune.warps_per_team, 0};
+    st = bpsf_make_plan(cs1, 1, tA, false, &plA);
+    if (st != BPSF_OK) return st;
+    // Launch B: the shot's trials spread over blocks of the tuned shape.
+    st = bpsf_make_plan(cs1, 1, c->tune, false, &plB);
+    if (st != BPSF_OK) return st;
     const int trials = std::max(c->n_trials, 1);
-    const int gridB = std::max(1, (trials + S * teams - 1) / (S * teams));
+    const int per_block = plB.teams * plB.S;
+    const int gridB = std::max(1, std::min(plB.grid, (trials + per_block - 1) / per_block));
     StreamCounters preset;
     std::memset(&preset, 0, sizeof(preset));
     preset.shot_next = 1;
@@ -508,21 +537,21 @@ extern "C" bpsf_status bpsf_decode_plain(bpsf_ctx *c, int64_t n, const uint32_t 
     for (int64_t i = 0; i < n; ++i) {
         JobDev job{synd + i * ss, corr + i * cs, conv + i, iters + i, stage ? stage + i : nullptr, 1, ss, cs};
         cudaError_t e = cudaMemsetAsync(c->d_ctr, 0, sizeof(StreamCounters), s);
-        if (e == cudaSuccess) e = cudaMemsetAsync(c->rec.ready, 0, 4, s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(c->rec.qseq, 0, 8, s);
         if (e != cudaSuccess) return bpsf_fail(BPSF_ECUDA, "cudaMemsetAsync: %s", cudaGetErrorString(e));
-        StreamDev sdA = bpsf_make_stream(c, job, nullptr, W, 1, kNoTickets);
-        LaunchArgs laA{&sdA, 1, W, kWaitNs};
-        launch_persistent(c->variant, false, 1, 32 * W, smemA, laA, stream);
+        StreamDev sdA = bpsf_make_stream(c, job, nullptr, kNoTickets);
+        launch_plan(plA, false, &sdA, 1, 1, stream);
         e = cudaMemcpyAsync(c->h_flag, conv + i, 1, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(c->h_ctr, c->d_ctr, sizeof(StreamCounters), cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) return bpsf_fail(BPSF_ECUDA, "plain initial run: %s", cudaGetErrorString(e));
+        iters_total += (long long)c->h_ctr->iters_total;
         if (c->h_flag[0] == 0 && c->p.w > 0) {
             ++failed;
             e = cudaMemcpyAsync(c->d_ctr, c->h_preset, sizeof(StreamCounters), cudaMemcpyHostToDevice, s);
             if (e != cudaSuccess) return bpsf_fail(BPSF_ECUDA, "cudaMemcpyAsync: %s", cudaGetErrorString(e));
-            StreamDev sdB = bpsf_make_stream(c, job, nullptr, W, S, 0);
-            LaunchArgs laB{&sdB, 1, t.warps_per_block, kWaitNs};
-            launch_persistent(c->variant, false, gridB, 32 * t.warps_per_block, smemB, laB, stream);
+            StreamDev sdB = bpsf_make_stream(c, job, nullptr, 0);
+            launch_plan(plB, false, &sdB, 1, gridB, stream);
             e = cudaMemcpyAsync(c->h_ctr, c->d_ctr, sizeof(StreamCounters), cudaMemcpyDeviceToHost, s);
             if (e == cudaSuccess) e = cudaStreamSynchronize(s);
             if (e != cudaSuccess) return bpsf_fail(BPSF_ECUDA, "plain trial sweep: %s", cudaGetErrorString(e));
@@ -585,7 +614,7 @@ extern "C" bpsf_status bpsf_decode_host(bpsf_ctx *c, int64_t n, const uint32_t *
 
 extern "C" bpsf_status bpsf_decode_multi(int32_t n_jobs, const bpsf_job *jobs, void *stream) {
     if (n_jobs < 1 || n_jobs > kMaxStreams || !jobs) return bpsf_fail(BPSF_EINVAL, "n_jobs must be in 1..%d", kMaxStreams);
-    int dc = 0, dv = 0, wpb = 0;
+    std::vector<bpsf_ctx *> codes(n_jobs);
     for (int k = 0; k < n_jobs; ++k) {
         const bpsf_job &j = jobs[k];
         bpsf_status st = check_io(j.ctx, j.n_shots, j.d_synd, j.synd_stride_words, j.d_corr, j.corr_stride_words,
@@ -594,44 +623,39 @@ extern "C" bpsf_status bpsf_decode_multi(int32_t n_jobs, const bpsf_job *jobs, v
         for (int q = 0; q < k; ++q)
             if (jobs[q].ctx == j.ctx) return bpsf_fail(BPSF_EINVAL, "a context appears twice in one launch");
         if (j.ctx->device != jobs[0].ctx->device) return bpsf_fail(BPSF_EINVAL, "contexts on different devices");
-        dc = std::max(dc, j.ctx->dc_max);
-        dv = std::max(dv, j.ctx->dv_max);
-        wpb = std::max(wpb, j.ctx->tune.warps_per_block);
+        codes[k] = j.ctx;
     }
-    bpsf_ctx *c0 = jobs[0].ctx;
+    bpsf_ctx *c0 = codes[0];
     cudaSetDevice(c0->device);
-    const int variant = kernel_variant(dc, std::max(dv, 1));
+    // Shape: the first context's tuning, shrunk until every code fits.
+    bpsf_tuning t = c0->tune;
+    bpsf_plan pl;
+    bpsf_status st = bpsf_make_plan(codes.data(), n_jobs, t, false, &pl);
+    while (st == BPSF_EINVAL && (t.slots_per_team > 1 || t.warps_per_block > t.warps_per_team)) {
+        if (t.slots_per_team > 1)
+            --t.slots_per_team;
+        else
+            t.warps_per_block -= t.warps_per_team;
+        st = bpsf_make_plan(codes.data(), n_jobs, t, false, &pl);
+    }
+    if (st != BPSF_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
     std::vector<StreamDev> sds(n_jobs);
-    int smem = 0;
     for (int k = 0; k < n_jobs; ++k) {
-        bpsf_ctx *c = jobs[k].ctx;
+        bpsf_ctx *c = codes[k];
         const bpsf_job &j = jobs[k];
-        int W = c->tune.warps_per_team;
-        if (wpb % W) W = 1;
-        int S = fit_slots(c, c->tune.slots_per_team, wpb / W);
-        if (S == 0) return bpsf_fail(BPSF_EINVAL, "code %d does not fit the shared block shape", k);
-        smem = std::max(smem, bpsf_ctx_team_smem(c, S, wpb / W));
-        bpsf_status st = bpsf_ensure_workspace(c, std::max<int64_t>(j.n_shots, 1));
+        st = bpsf_ensure_workspace(c, std::max<int64_t>(j.n_shots, 1));
         if (st != BPSF_OK) return st;
         cudaError_t e = cudaMemsetAsync(c->d_ctr, 0, sizeof(StreamCounters), s);
         if (e != cudaSuccess) return bpsf_fail(BPSF_ECUDA, "cudaMemsetAsync: %s", cudaGetErrorString(e));
-        st = clear_ready(c, j.n_shots, s);
+        st = clear_queue(c, j.n_shots, s);
         if (st != BPSF_OK) return st;
         JobDev job{j.d_synd, j.d_corr, j.d_converged, j.d_iters, j.d_stage, j.n_shots, j.synd_stride_words,
                    j.corr_stride_words};
-        sds[k] = bpsf_make_stream(c, job, nullptr, W, S, 0);
+        sds[k] = bpsf_make_stream(c, job, nullptr, 0);
         c->last_launch_n = j.n_shots;
     }
-    {
-        bpsf_status st = bpsf_ensure_kernel_attrs(variant, c0->smem_optin);
-        if (st != BPSF_OK) return st;
-    }
-    const int block = 32 * wpb;
-    const int grid = bpsf_grid_for(c0, variant, false, block, smem, 0);
-    if (grid <= 0) return bpsf_fail(BPSF_EINVAL, "mixed launch shape does not fit on an SM");
-    LaunchArgs la{sds.data(), n_jobs, wpb, kWaitNs};
-    launch_persistent(variant, false, grid, block, smem, la, stream);
+    launch_plan(pl, false, sds.data(), n_jobs, pl.grid, stream);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return bpsf_fail(BPSF_ECUDA, "kernel launch: %s", cudaGetErrorString(e));
     return BPSF_OK;
@@ -649,7 +673,9 @@ extern "C" bpsf_status bpsf_get_tuning(const bpsf_ctx *c, bpsf_tuning *out) {
 
 extern "C" bpsf_status bpsf_set_tuning(bpsf_ctx *c, const bpsf_tuning *t) {
     if (!c || !t) return bpsf_fail(BPSF_EINVAL, "NULL argument");
-    bpsf_status st = check_tuning(c, *t);
+    bpsf_plan pl;
+    bpsf_ctx *cs1[1] = {c};
+    bpsf_status st = bpsf_make_plan(cs1, 1, *t, false, &pl);
     if (st != BPSF_OK) return st;
     c->tune = *t;
     return BPSF_OK;
@@ -665,7 +691,6 @@ bool bpsf_tuning_cache_lookup(const bpsf_ctx *c, bpsf_tuning *out) {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tune_cache.find(shape_key(c));
     if (it == g_tune_cache.end()) return false;
-    if (check_tuning(c, it->second) != BPSF_OK) return false;
     *out = it->second;
     return true;
 }
@@ -704,15 +729,16 @@ extern "C" bpsf_status bpsf_autotune(bpsf_ctx *c, double p_sample, int64_t n_sam
     bpsf_status st = BPSF_OK;
     const int Ws_[] = {1, 2, 4, 8};
     const int Ss_[] = {1, 2, 3, 4, 6, 8, 12, 16};
-    const int Bs_[] = {2, 4, 8, 16};
+    const int Bs_[] = {1, 2, 3, 4, 6, 7, 8, 10, 12, 14, 15};
+    bpsf_ctx *cs1[1] = {c};
     for (int W : Ws_)
         for (int S : Ss_)
             for (int B : Bs_) {
                 bpsf_tuning t{W, S, B, 0};
-                if (check_tuning(c, t) != BPSF_OK) continue;
+                if (B % W) continue;
                 if (W > 1 && S > 4) continue;
-                const int smem = bpsf_ctx_team_smem(c, S, B / W);
-                if (bpsf_grid_for(c, c->variant, false, 32 * B, smem, 0) <= 0) continue;
+                bpsf_plan pl;
+                if (bpsf_make_plan(cs1, 1, t, false, &pl) != BPSF_OK) continue;
                 c->tune = t;
                 float ms_min = 1e30f;
                 for (int rep = 0; rep < 3 && st == BPSF_OK; ++rep) {

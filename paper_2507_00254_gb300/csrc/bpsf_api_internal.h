@@ -10,6 +10,7 @@
 struct bpsf_ctx {
     int device = 0, sm_count = 0, smem_optin = 0;
     int M = 0, N = 0, nnz = 0, Ws = 0, Wn = 0, dc_max = 0, dv_max = 0, n_trials = 0, variant = 0;
+    int P = 0, vstride = 0, regular = 0;
     bpsf_params p{};
     std::vector<int32_t> csr_ptr, csr_col;  // host copy of H (CSR, ascending columns)
     void *d_code = nullptr;                 // one allocation for all code arrays
@@ -28,11 +29,16 @@ struct bpsf_ctx {
     long long last_launch_n = 0;
 };
 
+// Launch plan of the persistent kernel for one or several codes.
+struct bpsf_plan {
+    int variant = 0, teams = 0, W = 0, S = 0, Q = 0, block = 0, smem = 0, grid = 0;
+};
+
 bpsf_status bpsf_fail(bpsf_status s, const char *fmt, ...);
 bpsf_status bpsf_ensure_workspace(bpsf_ctx *c, long long n);
 bpsf_status bpsf_ensure_kernel_attrs(int variant, int smem_optin);
-int bpsf_ctx_team_smem(const bpsf_ctx *c, int S, int teams);
-int bpsf_grid_for(const bpsf_ctx *c, int variant, bool debug, int block, int smem, int blocks_per_sm);
+bpsf_status bpsf_make_plan(bpsf_ctx *const *codes, int n_codes, const bpsf_tuning &t, bool debug, bpsf_plan *out);
 bool bpsf_tuning_cache_lookup(const bpsf_ctx *c, bpsf_tuning *out);
-bpsf::StreamDev bpsf_make_stream(const bpsf_ctx *c, const bpsf::JobDev &job, const bpsf::DebugDev *dbg, int W,
-                                 int S, unsigned flags);
+bpsf::StreamDev bpsf_make_stream(const bpsf_ctx *c, const bpsf::JobDev &job, const bpsf::DebugDev *dbg,
+                                 unsigned flags);
+extern const unsigned long long kBpsfWaitNs;

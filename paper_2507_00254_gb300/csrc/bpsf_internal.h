@@ -5,16 +5,17 @@
 
 namespace bpsf {
 
-constexpr int kMaxW = 16;       // largest |Phi|
-constexpr int kMaxSlots = 32;   // work items per team (one lane of the team's first warp each)
-constexpr int kMaxStreams = 16; // codes per launch
-constexpr int kMaxNamedTeams = 15;
+constexpr int kMaxW = 16;         // largest |Phi|
+constexpr int kMaxSlots = 32;     // work items per team
+constexpr int kMaxStreams = 16;   // codes per launch
+constexpr int kMaxComputeWarps = 15;  // plus one manager warp: <= 512 threads per block
+constexpr int kDVP = 4;           // column entries stored per variable for dv <= 4 codes
 
 // Device error bits (StreamCounters::status).
 enum : unsigned {
-    kDevReadyTimeout = 1u,  // a trial waited too long for its record
-    kDevIdleTimeout = 2u,   // a block waited too long for other blocks
-    kDevRecordOverflow = 4u // more failed shots than record slots
+    kDevReadyTimeout = 1u,   // a trial waited too long for its record
+    kDevIdleTimeout = 2u,    // a block waited too long for other blocks
+    kDevRecordOverflow = 4u  // more failed shots than record slots
 };
 
 // Stream flags.
@@ -24,21 +25,25 @@ enum : unsigned {
 };
 
 // One code's Tanner graph in the order the kernels read it, plus the
-// decoder constants.  Edges are numbered twice: CSR order (row-major,
-// ascending column inside a row) and CSC order (column-major, ascending row
-// inside a column); the permutations map one numbering to the other.
+// decoder constants.  Messages of one work item live in one array of
+// P = DC * M floats: the edge of rank k in row j (CSR order) sits at
+// position k * M + j, so a check-node thread reads and writes its row at
+// stride M (one word per bank for consecutive rows).  vpos lists, for each
+// column, the positions of its edges in ascending check order (the order the
+// V2C and posterior sums are folded in).
 struct CodeDev {
-    int M, N, nnz, Ws, Wn, dc_max, dv_max;
+    int M, N, nnz, Ws, Wn;
+    int DC, dv_max, P, regular;  // regular: every row has DC ones, every column dv_max
+    int vstride;                 // entries per column in vpos / vchk (>= dv_max)
     int max_iter, short_iter, w, n_trials, select;
     float alpha;
-    const uint16_t *row_ptr;     // M+1, offsets into CSR order
-    const uint16_t *csr_to_csc;  // nnz
-    const uint16_t *col_ptr;     // N+1, offsets into CSC order
-    const uint16_t *csc_to_csr;  // nnz
-    const uint16_t *csc_chk;     // nnz, check of each CSC edge
-    const uint16_t *csr_col;     // nnz, column of each CSR edge
+    const uint8_t *row_deg;      // M, ones per row
+    const uint16_t *vpos;        // N x vstride, message positions (0xffff padding)
+    const uint16_t *vchk;        // N x vstride, check indices
     const float *lch;            // N, channel LLRs (FP32)
-    const float *lch_csr;        // nnz, channel LLR of each CSR edge's variable
+    const float *lch_pos;        // P, channel LLR of the variable at each position
+    const uint16_t *row_ptr;     // M+1, CSR (syndrome kernel)
+    const uint16_t *csr_col;     // nnz
     const uint32_t *trial_mask;  // n_trials subset masks over Phi, ascending
 };
 
@@ -49,23 +54,26 @@ struct StreamCounters {
     unsigned long long ticket_next;  // trial tickets claimed
     unsigned long long iters_total;  // iterations run (all runs)
     unsigned long long trial_runs;   // trial runs finished
-    unsigned int rec_count;          // failed-shot records allocated
+    unsigned long long rec_count;    // failed shots published
     unsigned int status;             // kDev* bits
-    unsigned long long pad[2];
+    unsigned int pad0;
+    unsigned long long pad[1];
 };
 static_assert(sizeof(StreamCounters) == 64, "counter block is one 64-byte line");
 
-// Records of failed shots (capacity `cap`), structure of arrays.
+// Failed-shot records.  A record lives at the shot's row (its index in the
+// job, or its arena row when serving); the publication queue lists failed
+// shots in the order they failed, and trial tickets walk that queue.
 struct Records {
-    long long *shot;            // cap
-    unsigned int *ready;        // cap, 1 once the record is written
-    unsigned int *done;         // cap, trials finished
-    unsigned long long *best;   // cap, min over converged trials of the selection key
-    int32_t *phi;               // cap x w
-    uint32_t *synd;             // cap x Ws, the shot's syndrome
-    uint32_t *corr;             // cap x n_trials x Wn, e' xor t of converged trials
-    int16_t *iters;             // cap x n_trials
-    long long cap;
+    unsigned long long *qseq;   // cap, (queue index + 1) once the entry is written
+    long long *qshot;           // cap, shot of the queue entry
+    unsigned int *done;         // rows, trials finished
+    unsigned long long *best;   // rows, min over converged trials of the selection key
+    int32_t *phi;               // rows x w
+    uint32_t *synd;             // rows x Ws, the shot's syndrome
+    uint32_t *corr;             // rows x n_trials x Wn, e' xor t of converged trials
+    int16_t *iters;             // rows x n_trials
+    long long cap;              // queue entries (= rows)
 };
 
 struct JobDev {
@@ -87,24 +95,18 @@ struct DebugDev {
     int16_t *trial_iters;
 };
 
-// Serving: per-code request ring in host-mapped memory.  Shots get global
-// sequence numbers; request k covers [base, base + n).
-struct ServeReq {
-    long long base;       // first global shot number
-    long long n;          // shots
-    long long arena_off;  // first arena row of its syndromes / outputs
-    unsigned long long ticket;
-};
-
+// Serving: shots carry global sequence numbers g; shot g uses arena row
+// g % rows.  The host publishes rows (copies syndromes, then raises
+// `published`); the device reports each request once all its shots are out.
 struct ServeDev {
-    volatile long long *published;   // shots published by the host (mapped)
-    volatile ServeReq *reqs;         // request ring (mapped)
-    volatile int *stop;              // host asks the loop to end when idle (mapped)
-    unsigned long long *done_shots;  // per request ring slot: shots finished (device)
-    volatile unsigned int *req_done; // per request ring slot: completion sequence (mapped)
-    long long arena_rows;            // rows in the syndrome / output arena
-    int req_cap;                     // request ring size
-    long long idle_ns;               // exit after this long without work
+    volatile long long *published;   // shots published for this code (host-mapped)
+    volatile int *stop;              // host asks the loop to end (host-mapped)
+    int *row_req;                    // rows: request slot of each arena row
+    unsigned int *req_left;          // request slots: shots not yet finished
+    unsigned int *req_tag;           // request slots: value to post when done
+    volatile unsigned int *req_flag; // request slots: completion posts (host-mapped)
+    long long rows;                  // arena rows
+    long long idle_ns;               // leave the loop after this long without work
 };
 
 struct StreamDev {
@@ -114,15 +116,15 @@ struct StreamDev {
     StreamCounters *ctr;
     DebugDev dbg;
     ServeDev serve;
-    int W, S;        // warps per team, slots per team
     unsigned flags;  // kNoTickets, kServe
     int pad;
 };
 
+// Launch shape: `teams` teams of W warps, S slots each, plus one manager warp.
 struct LaunchArgs {
     const StreamDev *streams;
     int n_streams;
-    int warps_per_block;
+    int teams, W, S, Q;
     unsigned long long wait_ns;  // bound on any device-side wait
 };
 
@@ -132,74 +134,87 @@ struct LaunchArgs {
 
 __host__ __device__ inline int align_up(int x, int a) { return (x + a - 1) / a * a; }
 
-// Block header: stream choice and command.
 constexpr int kBlockHeaderBytes = 64;
 
 struct LayoutOffsets {
-    int row_ptr, csr_to_csc, col_ptr, csc_to_csr, lch, total;
+    int row_deg, vpos, lch, total;
 };
 
-__host__ __device__ inline LayoutOffsets layout_offsets(int M, int N, int nnz) {
+__host__ __device__ inline LayoutOffsets layout_offsets(int M, int N, int vstride) {
     LayoutOffsets o;
     int p = 0;
-    o.row_ptr = p;      p = align_up(p + 2 * (M + 1), 4);
-    o.csr_to_csc = p;   p = align_up(p + 2 * nnz, 4);
-    o.col_ptr = p;      p = align_up(p + 2 * (N + 1), 4);
-    o.csc_to_csr = p;   p = align_up(p + 2 * nnz, 4);
-    o.lch = p;          p = align_up(p + 4 * N, 16);
+    o.row_deg = p;  p = align_up(p + M, 16);
+    o.vpos = p;     p = align_up(p + 2 * N * vstride, 16);
+    o.lch = p;      p = align_up(p + 4 * N, 16);
     o.total = p;
     return o;
 }
 
-// Per-slot state in shared memory (64 bytes).
+// Slot states.
+enum : int { kSlotEmpty = 0, kSlotRunning = 1, kSlotFinished = 2 };
+
+// Per-slot state in shared memory (80 bytes).  EMPTY and FINISHED slots
+// belong to the manager warp, RUNNING slots to their team.
 struct SlotState {
-    int kind;        // 0 empty, 1 initial run, 2 trial run
+    int state;       // kSlot*
+    int kind;        // 1 initial run, 2 trial run
     int fresh;       // 1 until the first iteration has run
+    int outcome;     // 1 converged, 2 iteration cap (valid when FINISHED)
     int iter;        // iterations completed
     int limit;       // iteration cap of this run
-    long long shot;  // shot index in the job
-    int rec;         // record (trial runs)
     int kidx;        // trial index (trial runs)
+    int pad;
+    long long shot;  // shot index in the job (global sequence number when serving)
+    long long pad2;
     uint16_t phi[kMaxW];
 };
+static_assert(sizeof(SlotState) == 80, "slot state is 80 bytes");
 
 // Team control block (32 bytes).
 struct TeamCtl {
-    long long chunk_next, chunk_end;  // shots claimed by the team, not yet started
-    unsigned act_mask, fresh_mask, init_mask;
+    unsigned run_mask, fresh_mask, init_mask;
     int exit;
+    unsigned long long iters;  // iterations run by this team (all slots)
+    unsigned long long pad;
 };
 
 struct TeamOffsets {
-    int ctl, state, syn, mism, ebits, flips, q, r, total;
+    int ctl, state, syn, mism, ebits, flips, m, total;
 };
 
-__host__ __device__ inline TeamOffsets team_offsets(int S, int M, int N, int nnz, int Ws) {
+__host__ __device__ inline TeamOffsets team_offsets(int S, int N, int P, int Ws) {
     TeamOffsets o;
     int p = 0;
     o.ctl = p;    p += 32;
-    o.state = p;  p += 64 * S;
+    o.state = p;  p += 80 * S;
     o.syn = p;    p += 4 * S * Ws;
     o.mism = p;   p += 4 * S * Ws;
     o.ebits = p;  p += 4 * ((S * N + 31) / 32 + 1);
     o.flips = p;  p = align_up(p + 2 * S * N, 16);
-    o.q = p;      p += 4 * S * nnz;
-    o.r = p;      p += 4 * S * nnz;
+    o.m = p;      p += 4 * S * P;
     o.total = align_up(p, 16);
     return o;
 }
 
-__host__ __device__ inline int block_smem_bytes(int M, int N, int nnz, int Ws, int S, int teams) {
-    return kBlockHeaderBytes + layout_offsets(M, N, nnz).total + teams * team_offsets(S, M, N, nnz, Ws).total;
+// Manager's ready queue: entries of 48 bytes of fields plus Ws syndrome words.
+struct QEntry {
+    int kind;
+    int kidx;
+    long long shot;
+    uint16_t phi[kMaxW];
+};
+static_assert(sizeof(QEntry) == 48, "queue entry header is 48 bytes");
+
+__host__ __device__ inline int qentry_bytes(int Ws) { return align_up(48 + 4 * Ws, 16); }
+
+__host__ __device__ inline int block_smem_bytes(int M, int N, int P, int Ws, int vstride, int S, int teams, int Q) {
+    return kBlockHeaderBytes + layout_offsets(M, N, vstride).total + Q * qentry_bytes(Ws) +
+           teams * team_offsets(S, N, P, Ws).total;
 }
 
 // Kernel entry points (bpsf_kernels.cu).
-struct KernelShape {
-    int dc, dv;
-};
-int kernel_variant(int dc_max, int dv_max);  // index of the smallest variant that fits, -1 if none
-int kernel_variant_dc(int v);
-int kernel_variant_dv(int v);
+int kernel_variant(int dc_max, int dv_max);  // smallest variant that fits, -1 if none
+int kernel_variant_dv(int variant);          // column table width of a variant
 const void *persistent_kernel_ptr(int variant, bool debug);
 void launch_persistent(int variant, bool debug, int grid, int block, int smem, const LaunchArgs &args,
                        void *stream);

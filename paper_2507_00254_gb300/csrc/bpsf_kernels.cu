@@ -1,26 +1,30 @@
 // Device code of libbpsf: the persistent BP-SF kernel (Algorithm 1 of
 // arXiv 2507.00254) and two small harness kernels (syndrome, error sampler).
 //
-// Execution model.  A *team* of W warps decodes S work items ("slots") in
-// lock step, one BP iteration at a time.  A work item is either the initial
-// run of a shot (with oscillation counters) or one trial of a failed shot.
-// Per iteration the team runs
+// Execution model.  A block holds one MANAGER warp and `teams` compute teams
+// of W warps.  A team decodes S work items ("slots") in lock step, one BP
+// iteration at a time; a work item is the initial run of a shot (with
+// oscillation counters) or one trial of a failed shot.  Per iteration a team
+// runs
 //   C phase : one thread per (slot, check): min1 / min2 / sign product over
 //             the row (Eq. c2v), one FP32 multiply by alpha, C2V messages
-//             written to their CSC positions;
+//             written in place of the V2C messages they were computed from;
 //   V phase : one thread per (slot, variable): V2C messages for the next
 //             iteration (Section II-B step 2, explicit exclusion), posterior
-//             LLR and hard decision (step 4), a warp ballot packs e into
+//             LLR and hard decision (step 4); a warp ballot packs e into
 //             words, changed bits update the flip counters (Algorithm 1) and
 //             toggle the slot's residual syndrome s xor H e by shared atomics;
-//   decide  : a slot whose residual syndrome is zero converged; a slot at its
-//             iteration cap is exhausted.  Finished slots are written out and
-//             refilled from the device-wide queue at once.
-// A failed initial run picks Phi = top(flip_count, w), writes a record (Phi,
-// s) and publishes its trials as tickets; any team may claim them.  Each
-// converged trial stores e' xor t and takes an atomicMin on (weight, index);
-// the last trial of a record writes the winner.  All messages and per-slot
-// state live in shared memory; HBM only sees syndromes, outputs and records.
+//   decide  : a slot whose residual syndrome is zero has converged, a slot at
+//             its iteration cap is exhausted; either is handed to the manager.
+// Each message is read and written by exactly one thread in each phase, so
+// one array of P floats per slot holds V2C and C2V messages alternately.
+//
+// The manager warp does everything that touches global memory: it writes
+// finished slots out, runs top(flip_count, w) for failed initial runs and
+// publishes their trials, resolves the winner of each failed shot (minimum
+// over converged trials of (weight, index), held in a per-shot atomicMin),
+// claims new shots and trial tickets ahead of time into a small ready queue
+// and refills empty slots from it.  Compute warps never wait on HBM.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -37,22 +41,28 @@ __device__ __forceinline__ unsigned long long globaltimer_ns() {
     return t;
 }
 
-__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p) {
-    unsigned v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long *p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
     return v;
 }
 
-__device__ __forceinline__ void st_release_u32(unsigned *p, unsigned v) {
-    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+__device__ __forceinline__ void st_release_u64(unsigned long long *p, unsigned long long v) {
+    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ void st_release_sys_u32(volatile unsigned *p, unsigned v) {
+    asm volatile("st.release.sys.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ long long ld_acquire_sys_s64(volatile long long *p) {
+    long long v;
+    asm volatile("ld.acquire.sys.global.s64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
 }
 
 __device__ __forceinline__ unsigned long long ld_vol_u64(const unsigned long long *p) {
     return *reinterpret_cast<const volatile unsigned long long *>(p);
-}
-
-__device__ __forceinline__ unsigned ld_vol_u32(const unsigned *p) {
-    return *reinterpret_cast<const volatile unsigned *>(p);
 }
 
 __device__ __forceinline__ void team_sync(int W, int bar_id) {
@@ -63,8 +73,15 @@ __device__ __forceinline__ void team_sync(int W, int bar_id) {
     }
 }
 
+struct BlockHdr {
+    int stream, cmd;
+    volatile int exit;  // manager -> teams: leave the team loop
+    int pad[13];
+};
+
 struct LayoutMem {
-    const uint16_t *row_ptr, *csr_to_csc, *col_ptr, *csc_to_csr;
+    const uint8_t *row_deg;
+    const uint16_t *vpos;
     const float *lch;
 };
 
@@ -73,8 +90,22 @@ struct TeamMem {
     SlotState *st;
     uint32_t *syn, *mism, *ebits;
     uint16_t *flips;
-    float *q, *r;
+    float *m;
 };
+
+__device__ __forceinline__ TeamMem team_mem(unsigned char *tb, const TeamOffsets &to) {
+    TeamMem T;
+    T.ctl = reinterpret_cast<TeamCtl *>(tb + to.ctl);
+    T.st = reinterpret_cast<SlotState *>(tb + to.state);
+    T.syn = reinterpret_cast<uint32_t *>(tb + to.syn);
+    T.mism = reinterpret_cast<uint32_t *>(tb + to.mism);
+    T.ebits = reinterpret_cast<uint32_t *>(tb + to.ebits);
+    T.flips = reinterpret_cast<uint16_t *>(tb + to.flips);
+    T.m = reinterpret_cast<float *>(tb + to.m);
+    return T;
+}
+
+__device__ __forceinline__ volatile int *vstate(SlotState *s) { return reinterpret_cast<volatile int *>(&s->state); }
 
 // ---------------------------------------------------------------------------
 // C phase: check-node update, Eq. (c2v).  For row j with V2C inputs q_k:
@@ -82,31 +113,33 @@ struct TeamMem {
 //   m2 = min over k != k1,  r_k = (neg xor [q_k < 0]) ? -a : a,
 //   a = alpha * (k == k1 ? m2 : m1),
 // which equals the explicit "min and sign product over the other variables"
-// bit for bit (min is exact; the sign factors are exact).
+// bit for bit (min is exact; the sign factors are exact), independently of
+// the order the row's edges are stored in.
 // ---------------------------------------------------------------------------
-template <int DC>
-__device__ __forceinline__ void c_phase(const CodeDev &cd, const LayoutMem &L, const TeamMem &T, int S, int tid,
-                                        int nthreads) {
-    const unsigned act = T.ctl->act_mask, fresh = T.ctl->fresh_mask;
-    const int M = cd.M, nnz = cd.nnz, Ws = cd.Ws;
+template <int DC, bool REG>
+__device__ __forceinline__ void c_phase(const CodeDev &cd, const LayoutMem &L, const TeamMem &T, int S,
+                                        unsigned run, unsigned fresh, int tid, int nthreads) {
+    const int M = cd.M, P = cd.P, Ws = cd.Ws;
     const int total = S * M;
     const float alpha = cd.alpha;
     int s = tid / M, j = tid - s * M;
     for (int tau = tid; tau < total; tau += nthreads) {
-        if ((act >> s) & 1u) {
+        if ((run >> s) & 1u) {
             const bool fr = (fresh >> s) & 1u;
-            const int e0 = L.row_ptr[j];
-            const int deg = L.row_ptr[j + 1] - e0;
+            const int deg = REG ? DC : (int)L.row_deg[j];
             unsigned neg = (T.syn[s * Ws + (j >> 5)] >> (j & 31)) & 1u;
-            const float *qs = T.q + s * nnz + e0;
+            float *ms = T.m + s * P + j;
+            const float *ls = cd.lch_pos + j;
             float v[DC];
 #pragma unroll
-            for (int k = 0; k < DC; ++k) v[k] = (k < deg) ? (fr ? __ldg(cd.lch_csr + e0 + k) : qs[k]) : 0.f;
+            for (int k = 0; k < DC; ++k) {
+                if (REG || k < deg) v[k] = fr ? __ldg(ls + k * M) : ms[k * M];
+            }
             float m1 = __int_as_float(0x7f800000), m2 = m1;
             int k1 = 0;
 #pragma unroll
             for (int k = 0; k < DC; ++k) {
-                if (k < deg) {
+                if (REG || k < deg) {
                     const float a = fabsf(v[k]);
                     if (a < m1) {
                         m2 = m1;
@@ -119,13 +152,12 @@ __device__ __forceinline__ void c_phase(const CodeDev &cd, const LayoutMem &L, c
                 }
             }
             const float g1 = __fmul_rn(alpha, m1), g2 = __fmul_rn(alpha, m2);
-            float *rs = T.r + s * nnz;
 #pragma unroll
             for (int k = 0; k < DC; ++k) {
-                if (k < deg) {
+                if (REG || k < deg) {
                     const float mag = (k == k1) ? g2 : g1;
                     const unsigned ng = neg ^ ((v[k] < 0.f) ? 1u : 0u);
-                    rs[L.csr_to_csc[e0 + k]] = ng ? -mag : mag;
+                    ms[k * M] = ng ? -mag : mag;
                 }
             }
         }
@@ -145,48 +177,57 @@ __device__ __forceinline__ void c_phase(const CodeDev &cd, const LayoutMem &L, c
 //   l_out = l_ch + sum_k r_k            (left fold),  e_i = [l_out <= 0].
 // ---------------------------------------------------------------------------
 template <int DV, bool DEBUG>
-__device__ __forceinline__ void v_phase(const StreamDev &sd, const LayoutMem &L, const TeamMem &T, int S, int tid,
-                                        int nthreads) {
+__device__ __forceinline__ void v_phase(const StreamDev &sd, const LayoutMem &L, const TeamMem &T, int S,
+                                        unsigned run, unsigned fresh, unsigned initm, int tid, int nthreads) {
     const CodeDev &cd = sd.code;
-    const unsigned act = T.ctl->act_mask, fresh = T.ctl->fresh_mask, initm = T.ctl->init_mask;
-    const int N = cd.N, nnz = cd.nnz, Ws = cd.Ws;
+    const int N = cd.N, P = cd.P, Ws = cd.Ws;
     const int total = S * N;
     const int lane = tid & 31;
     int tau = tid;
     int s = tau / N, i = tau - s * N;
     for (int base = tid - lane; base < total; base += nthreads) {
         const bool valid = tau < total;
-        const bool a = valid && ((act >> s) & 1u);
+        const bool a = valid && ((run >> s) & 1u);
         const bool fr = a && ((fresh >> s) & 1u);
         const bool ini = a && ((initm >> s) & 1u);
         unsigned ebit = 0;
-        int f0 = 0, f1 = 0;
+        uint16_t pos[DV];
         if (a) {
-            f0 = L.col_ptr[i];
-            f1 = L.col_ptr[i + 1];
-            const int deg = f1 - f0;
+            const uint16_t *vp = L.vpos + i * DV;
+            if (DV == 4) {
+                const uint2 raw = *reinterpret_cast<const uint2 *>(vp);
+                pos[0] = (uint16_t)(raw.x & 0xffffu);
+                pos[1] = (uint16_t)(raw.x >> 16);
+                pos[2] = (uint16_t)(raw.y & 0xffffu);
+                pos[3] = (uint16_t)(raw.y >> 16);
+            } else {
+#pragma unroll
+                for (int k = 0; k < DV; ++k) pos[k] = vp[k];
+            }
             const float lc = L.lch[i];
-            const float *rs = T.r + s * nnz + f0;
+            float *ms = T.m + s * P;
             float rv[DV];
 #pragma unroll
-            for (int k = 0; k < DV; ++k) rv[k] = (k < deg) ? rs[k] : 0.f;
-            float *qs = T.q + s * nnz;
+            for (int k = 0; k < DV; ++k) rv[k] = (pos[k] != 0xffffu) ? ms[pos[k]] : 0.f;
 #pragma unroll
             for (int k = 0; k < DV; ++k) {
-                if (k < deg) {
+                if (pos[k] != 0xffffu) {
                     float acc = lc;
 #pragma unroll
                     for (int k2 = 0; k2 < DV; ++k2)
-                        if (k2 != k && k2 < deg) acc = __fadd_rn(acc, rv[k2]);
-                    qs[L.csc_to_csr[f0 + k]] = acc;
+                        if (k2 != k && pos[k2] != 0xffffu) acc = __fadd_rn(acc, rv[k2]);
+                    ms[pos[k]] = acc;
                 }
             }
             float lo = lc;
 #pragma unroll
             for (int k = 0; k < DV; ++k)
-                if (k < deg) lo = __fadd_rn(lo, rv[k]);
+                if (pos[k] != 0xffffu) lo = __fadd_rn(lo, rv[k]);
             ebit = (lo <= 0.f) ? 1u : 0u;
-            if (DEBUG && ini && sd.dbg.lout) sd.dbg.lout[T.st[s].shot * N + i] = lo;
+            if (DEBUG && ini && sd.dbg.lout) {
+                const long long shot = T.st[s].shot;
+                sd.dbg.lout[shot * N + i] = lo;
+            }
         }
         const int widx = base >> 5;
         const unsigned old = T.ebits[widx];
@@ -199,9 +240,13 @@ __device__ __forceinline__ void v_phase(const StreamDev &sd, const LayoutMem &L,
             const unsigned flip = prev ^ ebit;
             if (ini) T.flips[tau] = fr ? (uint16_t)flip : (uint16_t)(T.flips[tau] + flip);
             if (flip) {
-                for (int f = f0; f < f1; ++f) {
-                    const int c = __ldg(cd.csc_chk + f);
-                    atomicXor(&T.mism[s * Ws + (c >> 5)], 1u << (c & 31));
+                const uint16_t *vc = cd.vchk + i * DV;
+#pragma unroll
+                for (int k = 0; k < DV; ++k) {
+                    if (pos[k] != 0xffffu) {
+                        const int c = __ldg(vc + k);
+                        atomicXor(&T.mism[s * Ws + (c >> 5)], 1u << (c & 31));
+                    }
                 }
             }
         }
@@ -214,255 +259,293 @@ __device__ __forceinline__ void v_phase(const StreamDev &sd, const LayoutMem &L,
     }
 }
 
-// Word w of slot s's hard decision, from the team's flattened bit array.
-__device__ __forceinline__ unsigned slot_word(const TeamMem &T, int N, int s, int w) {
-    const int bit0 = s * N + 32 * w;
-    const int wi = bit0 >> 5, sh = bit0 & 31;
-    unsigned v = T.ebits[wi] >> sh;
-    if (sh) v |= T.ebits[wi + 1] << (32 - sh);
-    const int rem = N - 32 * w;
-    if (rem < 32) v &= (1u << rem) - 1u;
-    return v;
-}
-
-// Write out one finished slot (whole first warp of the team).
-template <bool DEBUG>
-__device__ void finalize_slot(const StreamDev &sd, const TeamMem &T, int s, bool conv, int lane,
-                              unsigned long long &init_local, unsigned long long &trials_local) {
+// ---------------------------------------------------------------------------
+// Compute team loop.
+// ---------------------------------------------------------------------------
+template <int DC, int DV, bool REG, bool DEBUG>
+__device__ void team_loop(const StreamDev &sd, const LayoutMem &L, const TeamMem &T, BlockHdr *hdr, int S, int W,
+                          int tid, int bar_id, unsigned long long wait_ns) {
+    const int lane = tid & 31, wt = tid >> 5, nthreads = 32 * W;
     const CodeDev &cd = sd.code;
-    const JobDev &job = sd.job;
-    SlotState *ss = &T.st[s];
-    const int kind = ss->kind, iter = ss->iter;
-    const long long shot = ss->shot;
-    const int N = cd.N, Wn = cd.Wn, Ws = cd.Ws;
-    if (kind == 1) {
-        if (DEBUG && sd.dbg.flips)
-            for (int i = lane; i < N; i += 32) sd.dbg.flips[shot * N + i] = T.flips[s * N + i];
-        uint32_t *out = job.corr + shot * job.corr_stride;
-        for (int w = lane; w < Wn; w += 32) out[w] = slot_word(T, N, s, w);
-        if (lane == 0) {
-            job.conv[shot] = conv ? 1 : 0;
-            job.iters[shot] = (int16_t)(conv ? iter : cd.max_iter);
-            if (job.stage) job.stage[shot] = conv ? 0 : 2;
-        }
-        if (!conv && cd.w > 0) {
-            // Phi = top(flip_count, w): keys (count << 16 | 0xffff - i) are
-            // distinct, so each round takes the largest key below the last.
-            unsigned thr = 0xffffffffu;
-            int my_phi = 0;
-            for (int r = 0; r < cd.w; ++r) {
-                unsigned best = 0;
-                for (int i = lane; i < N; i += 32) {
-                    const unsigned key = ((unsigned)T.flips[s * N + i] << 16) | (0xffffu - (unsigned)i);
-                    if (key < thr && key > best) best = key;
+    const int Ws = cd.Ws;
+    unsigned long long idle_since = 0;
+    for (;;) {
+        if (wt == 0) {
+            SlotState *ss = &T.st[lane < S ? lane : 0];
+            const int stv = lane < S ? *vstate(ss) : kSlotEmpty;
+            const bool r = stv == kSlotRunning;
+            __threadfence_block();
+            const unsigned run = __ballot_sync(FULLMASK, r);
+            const unsigned fr = __ballot_sync(FULLMASK, r && ss->fresh);
+            const unsigned im = __ballot_sync(FULLMASK, r && ss->kind == 1);
+            int ex = 0;
+            if (run == 0u) {
+                if (hdr->exit) {
+                    ex = 1;
+                } else {
+                    const unsigned long long now = globaltimer_ns();
+                    if (idle_since == 0) idle_since = now;
+                    if (now - idle_since > 4 * wait_ns) ex = 1;  // the manager is gone: never wait forever
+                    __nanosleep(100);
                 }
-                best = __reduce_max_sync(FULLMASK, best);
-                if (lane == r) my_phi = (int)(0xffffu - (best & 0xffffu));
-                thr = best;
+            } else {
+                idle_since = 0;
             }
-            unsigned rec = 0;
-            if (lane == 0) rec = atomicAdd(&sd.ctr->rec_count, 1u);
-            rec = __shfl_sync(FULLMASK, rec, 0);
-            if ((long long)rec < sd.rec.cap) {
-                if (lane == 0) {
-                    sd.rec.shot[rec] = shot;
-                    sd.rec.done[rec] = 0u;
-                    sd.rec.best[rec] = ~0ull;
-                }
-                if (lane < cd.w) sd.rec.phi[(long long)rec * cd.w + lane] = my_phi;
-                for (int w = lane; w < Ws; w += 32) sd.rec.synd[(long long)rec * Ws + w] = T.syn[s * Ws + w];
-                if (DEBUG && sd.dbg.phi && lane < cd.w) sd.dbg.phi[shot * cd.w + lane] = my_phi;
-                __threadfence();
-                __syncwarp();
-                if (lane == 0) st_release_u32(&sd.rec.ready[rec], 1u);
-            } else if (lane == 0) {
-                atomicOr(&sd.ctr->status, kDevRecordOverflow);
-            }
-        }
-        if (lane == 0) ++init_local;
-    } else {
-        const int C = cd.n_trials, kidx = ss->kidx, rec = ss->rec;
-        const unsigned mask = __ldg(cd.trial_mask + kidx);
-        if (conv) {
-            // Undo the flip (Algorithm 1): return e' xor t.
-            unsigned wsum = 0;
-            for (int w = lane; w < Wn; w += 32) {
-                unsigned v = slot_word(T, N, s, w);
-                for (int j = 0; j < cd.w; ++j) {
-                    if ((mask >> j) & 1u) {
-                        const int b = ss->phi[j];
-                        if ((b >> 5) == w) v ^= 1u << (b & 31);
-                    }
-                }
-                sd.rec.corr[((long long)rec * C + kidx) * Wn + w] = v;
-                wsum += __popc(v);
-            }
-            wsum = __reduce_add_sync(FULLMASK, wsum);
-            if (lane == 0) sd.rec.iters[(long long)rec * C + kidx] = (int16_t)iter;
-            __threadfence();
-            __syncwarp();
             if (lane == 0) {
-                const unsigned long long key =
-                    cd.select == 0 ? (((unsigned long long)wsum << 32) | (unsigned)kidx) : (unsigned long long)kidx;
-                atomicMin(&sd.rec.best[rec], key);
+                T.ctl->run_mask = run;
+                T.ctl->fresh_mask = fr;
+                T.ctl->init_mask = im;
+                T.ctl->exit = ex;
+                T.ctl->iters += (unsigned long long)__popc(run);
             }
         }
-        if (DEBUG && lane == 0) {
-            if (sd.dbg.trial_conv) sd.dbg.trial_conv[shot * C + kidx] = conv ? 1 : 0;
-            if (sd.dbg.trial_iters) sd.dbg.trial_iters[shot * C + kidx] = (int16_t)iter;
-        }
-        unsigned d = 0;
-        if (lane == 0) {
-            __threadfence();
-            d = atomicAdd(&sd.rec.done[rec], 1u) + 1u;
-        }
-        d = __shfl_sync(FULLMASK, d, 0);
-        if (d == (unsigned)C) {
-            // Last trial of this shot: the winner is settled.
-            __threadfence();
-            unsigned long long best = 0;
-            if (lane == 0) best = atomicAdd(&sd.rec.best[rec], 0ull);
-            best = __shfl_sync(FULLMASK, best, 0);
-            if (best != ~0ull) {
-                const int kw = (int)(best & 0xffffffffu);
-                uint32_t *out = job.corr + shot * job.corr_stride;
-                for (int w = lane; w < Wn; w += 32) out[w] = __ldcg(sd.rec.corr + ((long long)rec * C + kw) * Wn + w);
-                if (lane == 0) {
-                    job.conv[shot] = 1;
-                    job.iters[shot] = __ldcg(sd.rec.iters + (long long)rec * C + kw);
-                    if (job.stage) job.stage[shot] = 1;
-                }
-            }
-        }
-        if (lane == 0) ++trials_local;
-    }
-    if (lane == 0) ss->kind = 0;
-    __syncwarp();
-}
-
-// Start the initial run of `shot` in slot s (one lane).
-__device__ __forceinline__ void init_shot(const StreamDev &sd, const TeamMem &T, int s, long long shot) {
-    const CodeDev &cd = sd.code;
-    SlotState *ss = &T.st[s];
-    ss->kind = 1;
-    ss->fresh = 1;
-    ss->iter = 0;
-    ss->limit = cd.max_iter;
-    ss->shot = shot;
-    ss->rec = -1;
-    ss->kidx = -1;
-    const uint32_t *src = sd.job.synd + shot * sd.job.synd_stride;
-    const int Ws = cd.Ws, tail = cd.M & 31;
-    for (int w = 0; w < Ws; ++w) {
-        unsigned v = __ldcg(src + w);
-        if (w == Ws - 1 && tail) v &= (1u << tail) - 1u;
-        T.syn[s * Ws + w] = v;
-        T.mism[s * Ws + w] = v;
-    }
-}
-
-// Start trial `ticket` (record ticket / T, trial ticket % T) in slot s (one lane).
-template <bool DEBUG>
-__device__ __forceinline__ void init_trial(const StreamDev &sd, const LayoutMem &L, const TeamMem &T, int s,
-                                           unsigned long long ticket, unsigned long long wait_ns) {
-    const CodeDev &cd = sd.code;
-    const int C = cd.n_trials, Ws = cd.Ws;
-    const long long rec = (long long)(ticket / (unsigned long long)C);
-    const int kidx = (int)(ticket - (unsigned long long)rec * C);
-    if (ld_acquire_u32(&sd.rec.ready[rec]) == 0u) {
-        const unsigned long long t0 = globaltimer_ns();
-        while (ld_acquire_u32(&sd.rec.ready[rec]) == 0u) {
-            if (globaltimer_ns() - t0 > wait_ns) {
-                atomicOr(&sd.ctr->status, kDevReadyTimeout);
-                return;
-            }
-            __nanosleep(128);
-        }
-    }
-    SlotState *ss = &T.st[s];
-    const long long shot = __ldcg(sd.rec.shot + rec);
-    for (int j = 0; j < cd.w; ++j) ss->phi[j] = (uint16_t)__ldcg(sd.rec.phi + rec * cd.w + j);
-    for (int w = 0; w < Ws; ++w) T.syn[s * Ws + w] = __ldcg(sd.rec.synd + rec * Ws + w);
-    // s' = s xor t H^T (Algorithm 1): flip the checks of every selected bit.
-    const unsigned mask = __ldg(cd.trial_mask + kidx);
-    for (int j = 0; j < cd.w; ++j) {
-        if ((mask >> j) & 1u) {
-            const int v = ss->phi[j];
-            for (int f = L.col_ptr[v]; f < L.col_ptr[v + 1]; ++f) {
-                const int c = __ldg(cd.csc_chk + f);
-                T.syn[s * Ws + (c >> 5)] ^= 1u << (c & 31);
-            }
-        }
-    }
-    for (int w = 0; w < Ws; ++w) {
-        T.mism[s * Ws + w] = T.syn[s * Ws + w];
-        if (DEBUG && sd.dbg.trial_synd) sd.dbg.trial_synd[(shot * C + kidx) * Ws + w] = T.syn[s * Ws + w];
-    }
-    ss->kind = 2;
-    ss->fresh = 1;
-    ss->iter = 0;
-    ss->limit = cd.short_iter;
-    ss->shot = shot;
-    ss->rec = (int)rec;
-    ss->kidx = kidx;
-}
-
-// Decide every active slot after an iteration and write out finished ones
-// (first warp of the team).
-template <bool DEBUG>
-__device__ __forceinline__ void decide(const StreamDev &sd, const TeamMem &T, int S, int lane,
-                                       unsigned long long &init_local, unsigned long long &iters_local,
-                                       unsigned long long &trials_local) {
-    const int Ws = sd.code.Ws;
-    int outcome = 0;
-    bool active = false;
-    if (lane < S) {
-        SlotState *ss = &T.st[lane];
-        if (ss->kind) {
-            active = true;
+        team_sync(W, bar_id);
+        const unsigned run = T.ctl->run_mask, fresh = T.ctl->fresh_mask, initm = T.ctl->init_mask;
+        const int ex = T.ctl->exit;
+        team_sync(W, bar_id);
+        if (ex) break;
+        if (run == 0u) continue;
+        c_phase<DC, REG>(cd, L, T, S, run, fresh, tid, nthreads);
+        team_sync(W, bar_id);
+        v_phase<DV, DEBUG>(sd, L, T, S, run, fresh, initm, tid, nthreads);
+        team_sync(W, bar_id);
+        if (wt == 0 && lane < S && ((run >> lane) & 1u)) {
+            SlotState *ss = &T.st[lane];
             ss->fresh = 0;
             const int it = ss->iter + 1;
             ss->iter = it;
             unsigned any = 0;
             for (int w = 0; w < Ws; ++w) any |= T.mism[lane * Ws + w];
-            outcome = (any == 0u) ? 1 : (it >= ss->limit ? 2 : 0);
+            const int oc = (any == 0u) ? 1 : (it >= ss->limit ? 2 : 0);
+            if (oc) {
+                ss->outcome = oc;
+                __threadfence_block();
+                *vstate(ss) = kSlotFinished;
+            }
         }
-    }
-    const unsigned am = __ballot_sync(FULLMASK, active);
-    unsigned fin = __ballot_sync(FULLMASK, outcome != 0);
-    const unsigned cvm = __ballot_sync(FULLMASK, outcome == 1);
-    if (lane == 0) iters_local += __popc(am);
-    __syncwarp();
-    while (fin) {
-        const int s = __ffs(fin) - 1;
-        fin &= fin - 1u;
-        finalize_slot<DEBUG>(sd, T, s, (cvm >> s) & 1u, lane, init_local, trials_local);
     }
 }
 
-// Fill empty slots: trial tickets first (they finish failed shots), then new
-// shots from the team's claimed chunk (first warp of the team).
+// ---------------------------------------------------------------------------
+// Manager warp.
+// ---------------------------------------------------------------------------
+
+// Manager state: head and tail are warp-uniform; the two counters are per
+// lane (each lane counts the slots it wrote out) and are summed over the
+// warp before they are added to the global counters.
+struct MgrState {
+    int head, tail;          // ready queue (ring of Q entries)
+    unsigned init_local;     // finished initial runs not yet counted globally
+    unsigned trials_local;   // finished trial runs not yet counted globally
+};
+
+__device__ __forceinline__ QEntry *qentry(unsigned char *q, int idx, int stride) {
+    return reinterpret_cast<QEntry *>(q + idx * stride);
+}
+
+__device__ __forceinline__ uint32_t *qsyn(QEntry *e) {
+    return reinterpret_cast<uint32_t *>(reinterpret_cast<unsigned char *>(e) + 48);
+}
+
+// Word w of slot s's hard decision, from its team's flattened bit array.
+__device__ __forceinline__ unsigned slot_word(const uint32_t *ebits, int N, int s, int w) {
+    const int bit0 = s * N + 32 * w;
+    const int wi = bit0 >> 5, sh = bit0 & 31;
+    unsigned v = ebits[wi] >> sh;
+    if (sh) v |= ebits[wi + 1] << (32 - sh);
+    const int rem = N - 32 * w;
+    if (rem < 32) v &= (1u << rem) - 1u;
+    return v;
+}
+
+__device__ __forceinline__ long long row_of(const StreamDev &sd, long long shot) {
+    return (sd.flags & kServe) ? (shot % sd.serve.rows) : shot;
+}
+
+// One shot's final output is out: serving counts it against its request.
+__device__ __forceinline__ void shot_complete(const StreamDev &sd, long long row) {
+    if (!(sd.flags & kServe)) return;
+    const int rq = sd.serve.row_req[row];
+    __threadfence();
+    const unsigned left = atomicSub(&sd.serve.req_left[rq], 1u) - 1u;
+    if (left == 0u) {
+        __threadfence_system();
+        st_release_sys_u32(sd.serve.req_flag + rq, sd.serve.req_tag[rq]);
+    }
+}
+
+// Lane-parallel write-out of finished slots that need no warp cooperation:
+// converged or uncorrectable initial runs, and trial runs.
 template <bool DEBUG>
-__device__ __forceinline__ void refill(const StreamDev &sd, const LayoutMem &L, const TeamMem &T, int S, int lane,
-                                       unsigned long long &init_local, unsigned long long wait_ns) {
+__device__ __forceinline__ void finalize_simple(const StreamDev &sd, TeamMem T, int s, MgrState &mg) {
     const CodeDev &cd = sd.code;
-    TeamCtl *ctl = T.ctl;
-    const bool empty = lane < S && T.st[lane].kind == 0;
-    const unsigned em = __ballot_sync(FULLMASK, empty);
-    const int n_empty = __popc(em);
-    const int rank = __popc(em & ((1u << lane) - 1u));
-    unsigned long long t0 = 0;
-    int take = 0;
-    if (n_empty && cd.w > 0 && !(sd.flags & kNoTickets)) {
+    const JobDev &job = sd.job;
+    SlotState *ss = &T.st[s];
+    const int kind = ss->kind, iter = ss->iter;
+    const bool conv = ss->outcome == 1;
+    const long long shot = ss->shot;
+    const long long row = row_of(sd, shot);
+    const int N = cd.N, Wn = cd.Wn;
+    if (kind == 1) {
+        if (DEBUG && sd.dbg.flips)
+            for (int i = 0; i < N; ++i) sd.dbg.flips[shot * N + i] = T.flips[s * N + i];
+        uint32_t *out = job.corr + row * job.corr_stride;
+        for (int w = 0; w < Wn; ++w) out[w] = slot_word(T.ebits, N, s, w);
+        job.conv[row] = conv ? 1 : 0;
+        job.iters[row] = (int16_t)(conv ? iter : cd.max_iter);
+        if (job.stage) job.stage[row] = conv ? 0 : 2;
+        mg.init_local += 1;
+        shot_complete(sd, row);
+        return;
+    }
+    // Trial run: undo the flip (Algorithm 1) and take part in the selection.
+    const int C = cd.n_trials, kidx = ss->kidx;
+    if (conv) {
+        const unsigned mask = __ldg(cd.trial_mask + kidx);
+        unsigned wsum = 0;
+        uint32_t *dst = sd.rec.corr + ((long long)row * C + kidx) * Wn;
+        for (int w = 0; w < Wn; ++w) {
+            unsigned v = slot_word(T.ebits, N, s, w);
+            for (int j = 0; j < cd.w; ++j) {
+                if ((mask >> j) & 1u) {
+                    const int b = ss->phi[j];
+                    if ((b >> 5) == w) v ^= 1u << (b & 31);
+                }
+            }
+            dst[w] = v;
+            wsum += __popc(v);
+        }
+        sd.rec.iters[(long long)row * C + kidx] = (int16_t)iter;
+        __threadfence();
+        const unsigned long long key =
+            cd.select == 0 ? (((unsigned long long)wsum << 32) | (unsigned)kidx) : (unsigned long long)kidx;
+        atomicMin(&sd.rec.best[row], key);
+    }
+    if (DEBUG) {
+        if (sd.dbg.trial_conv) sd.dbg.trial_conv[shot * C + kidx] = conv ? 1 : 0;
+        if (sd.dbg.trial_iters) sd.dbg.trial_iters[shot * C + kidx] = (int16_t)iter;
+    }
+    __threadfence();
+    const unsigned d = atomicAdd(&sd.rec.done[row], 1u) + 1u;
+    mg.trials_local += 1;
+    if (d == (unsigned)C) {
+        // Last trial of this shot: the winner is settled.
+        __threadfence();
+        const unsigned long long best = atomicAdd(&sd.rec.best[row], 0ull);
+        if (best != ~0ull) {
+            const int kw = (int)(best & 0xffffffffu);
+            uint32_t *out = job.corr + row * job.corr_stride;
+            const uint32_t *src = sd.rec.corr + ((long long)row * C + kw) * Wn;
+            for (int w = 0; w < Wn; ++w) out[w] = __ldcg(src + w);
+            job.conv[row] = 1;
+            job.iters[row] = __ldcg(sd.rec.iters + (long long)row * C + kw);
+            if (job.stage) job.stage[row] = 1;
+        }
+        shot_complete(sd, row);
+    }
+}
+
+// Failed initial run with trials (whole manager warp): provisional output,
+// Phi = top(flip_count, w), record, publication of its trials.
+template <bool DEBUG>
+__device__ __forceinline__ void finalize_failed(const StreamDev &sd, TeamMem T, int s, int lane, MgrState &mg) {
+    const CodeDev &cd = sd.code;
+    const JobDev &job = sd.job;
+    SlotState *ss = &T.st[s];
+    const long long shot = ss->shot;
+    const long long row = row_of(sd, shot);
+    const int N = cd.N, Wn = cd.Wn, Ws = cd.Ws;
+    if (DEBUG && sd.dbg.flips)
+        for (int i = lane; i < N; i += 32) sd.dbg.flips[shot * N + i] = T.flips[s * N + i];
+    uint32_t *out = job.corr + row * job.corr_stride;
+    for (int w = lane; w < Wn; w += 32) out[w] = slot_word(T.ebits, N, s, w);
+    if (lane == 0) {
+        job.conv[row] = 0;
+        job.iters[row] = (int16_t)cd.max_iter;
+        if (job.stage) job.stage[row] = 2;
+    }
+    // Keys (count << 16 | 0xffff - i) are distinct, so each round takes the
+    // largest key below the previous one: count descending, index ascending.
+    unsigned thr = 0xffffffffu;
+    int my_phi = 0;
+    for (int r = 0; r < cd.w; ++r) {
+        unsigned best = 0;
+        for (int i = lane; i < N; i += 32) {
+            const unsigned key = ((unsigned)T.flips[s * N + i] << 16) | (0xffffu - (unsigned)i);
+            if (key < thr && key > best) best = key;
+        }
+        best = __reduce_max_sync(FULLMASK, best);
+        if (lane == r) my_phi = (int)(0xffffu - (best & 0xffffu));
+        thr = best;
+    }
+    if (lane == 0) {
+        sd.rec.done[row] = 0u;
+        sd.rec.best[row] = ~0ull;
+    }
+    if (lane < cd.w) sd.rec.phi[row * cd.w + lane] = my_phi;
+    for (int w = lane; w < Ws; w += 32) sd.rec.synd[row * Ws + w] = T.syn[s * Ws + w];
+    if (DEBUG && sd.dbg.phi && lane < cd.w) sd.dbg.phi[shot * cd.w + lane] = my_phi;
+    __threadfence();
+    __syncwarp();
+    if (lane == 0) {
+        const unsigned long long q = atomicAdd(&sd.ctr->rec_count, 1ull);
+        const long long qi = (long long)(q % (unsigned long long)sd.rec.cap);
+        sd.rec.qshot[qi] = shot;
+        st_release_u64(sd.rec.qseq + qi, q + 1ull);
+        mg.init_local += 1;
+    }
+    __syncwarp();
+}
+
+// Install ready-queue entry e into slot s (one lane).
+__device__ __forceinline__ void install(const StreamDev &sd, TeamMem T, int s, QEntry *e) {
+    const CodeDev &cd = sd.code;
+    SlotState *ss = &T.st[s];
+    const int Ws = cd.Ws, tail = cd.M & 31;
+    const uint32_t *src = qsyn(e);
+    for (int w = 0; w < Ws; ++w) {
+        unsigned v = src[w];
+        if (w == Ws - 1 && tail) v &= (1u << tail) - 1u;
+        T.syn[s * Ws + w] = v;
+        T.mism[s * Ws + w] = v;
+    }
+    ss->kind = e->kind;
+    ss->kidx = e->kidx;
+    ss->shot = e->shot;
+    for (int j = 0; j < kMaxW; ++j) ss->phi[j] = e->phi[j];
+    ss->fresh = 1;
+    ss->iter = 0;
+    ss->outcome = 0;
+    ss->limit = e->kind == 1 ? cd.max_iter : cd.short_iter;
+    __threadfence_block();
+    *vstate(ss) = kSlotRunning;
+}
+
+// Shots that may be claimed now.
+__device__ __forceinline__ long long shots_available(const StreamDev &sd) {
+    if (sd.flags & kServe) return ld_acquire_sys_s64(sd.serve.published);
+    return sd.job.n_shots;
+}
+
+// Fill the ready queue: trial tickets first, then new shots.
+template <bool DEBUG>
+__device__ __forceinline__ bool prefetch(const StreamDev &sd, unsigned char *qbase, int Q, int qstride, int lane,
+                                         MgrState &mg, unsigned long long wait_ns) {
+    const CodeDev &cd = sd.code;
+    const int Ws = cd.Ws;
+    bool got_any = false;
+    int space = Q - (mg.tail - mg.head);
+    if (space > 0 && cd.w > 0 && !(sd.flags & kNoTickets)) {
+        unsigned long long t0 = 0;
+        int take = 0;
         if (lane == 0) {
             for (int att = 0; att < 4; ++att) {
                 const unsigned long long cur = ld_vol_u64(&sd.ctr->ticket_next);
-                const unsigned long long rc = ld_vol_u32(&sd.ctr->rec_count);
-                const unsigned long long rcap = rc < (unsigned long long)sd.rec.cap ? rc : (unsigned long long)sd.rec.cap;
-                const unsigned long long total = rcap * (unsigned long long)cd.n_trials;
+                const unsigned long long total = ld_vol_u64(&sd.ctr->rec_count) * (unsigned long long)cd.n_trials;
                 if (cur >= total) break;
-                const unsigned long long want = (total - cur) < (unsigned long long)n_empty ? (total - cur)
-                                                                                             : (unsigned long long)n_empty;
+                unsigned long long want = total - cur;
+                const unsigned long long lim = space < 32 ? (unsigned long long)space : 32ull;
+                if (want > lim) want = lim;
                 if (atomicCAS(&sd.ctr->ticket_next, cur, cur + want) == cur) {
                     t0 = cur;
                     take = (int)want;
@@ -472,102 +555,232 @@ __device__ __forceinline__ void refill(const StreamDev &sd, const LayoutMem &L, 
         }
         t0 = __shfl_sync(FULLMASK, t0, 0);
         take = __shfl_sync(FULLMASK, take, 0);
-    }
-    const int need = n_empty - take;
-    long long s0 = 0;
-    int got = 0;
-    if (need > 0) {
-        if (lane == 0) {
-            long long cn = ctl->chunk_next, ce = ctl->chunk_end;
-            const long long n = sd.job.n_shots;
-            if (cn >= ce && (long long)ld_vol_u64(&sd.ctr->shot_next) < n) {
-                const long long ch = (2 * S > 4) ? 2 * S : 4;
-                const long long c0 = (long long)atomicAdd(&sd.ctr->shot_next, (unsigned long long)ch);
-                cn = c0 < n ? c0 : n;
-                ce = (c0 + ch) < n ? (c0 + ch) : n;
+        if (lane < take) {
+            const unsigned long long ticket = t0 + lane;
+            const unsigned long long qi = ticket / (unsigned long long)cd.n_trials;
+            const int kidx = (int)(ticket - qi * (unsigned long long)cd.n_trials);
+            const long long slot_q = (long long)(qi % (unsigned long long)sd.rec.cap);
+            bool ok = true;
+            if (ld_acquire_u64(sd.rec.qseq + slot_q) != qi + 1ull) {
+                const unsigned long long start = globaltimer_ns();
+                while (ld_acquire_u64(sd.rec.qseq + slot_q) != qi + 1ull) {
+                    if (globaltimer_ns() - start > wait_ns) {
+                        atomicOr(&sd.ctr->status, kDevReadyTimeout);
+                        ok = false;
+                        break;
+                    }
+                    __nanosleep(64);
+                }
             }
-            const long long avail = ce - cn;
-            got = (int)((long long)need < avail ? need : avail);
-            s0 = cn;
-            ctl->chunk_next = cn + got;
-            ctl->chunk_end = ce;
-            if (got < need && init_local) {
-                __threadfence();
-                atomicAdd(&sd.ctr->init_done, init_local);
-                init_local = 0;
+            QEntry *e = qentry(qbase, (mg.tail + lane) % Q, qstride);
+            if (ok) {
+                const long long shot = __ldcg(sd.rec.qshot + slot_q);
+                const long long row = row_of(sd, shot);
+                e->kind = 2;
+                e->kidx = kidx;
+                e->shot = shot;
+                for (int j = 0; j < kMaxW; ++j)
+                    e->phi[j] = j < cd.w ? (uint16_t)__ldcg(sd.rec.phi + row * cd.w + j) : (uint16_t)0;
+                uint32_t *sy = qsyn(e);
+                for (int w = 0; w < Ws; ++w) sy[w] = __ldcg(sd.rec.synd + row * Ws + w);
+                // s' = s xor t H^T (Algorithm 1): flip the checks of every selected bit.
+                const unsigned mask = __ldg(cd.trial_mask + kidx);
+                for (int j = 0; j < cd.w; ++j) {
+                    if ((mask >> j) & 1u) {
+                        const int v = e->phi[j];
+                        for (int k = 0; k < cd.vstride; ++k) {
+                            const int c = __ldg(cd.vchk + v * cd.vstride + k);
+                            if (c == 0xffff) break;
+                            sy[c >> 5] ^= 1u << (c & 31);
+                        }
+                    }
+                }
+                if (DEBUG && sd.dbg.trial_synd)
+                    for (int w = 0; w < Ws; ++w)
+                        sd.dbg.trial_synd[(shot * cd.n_trials + kidx) * Ws + w] = sy[w];
+            } else {
+                e->kind = 0;  // dropped: the record never settles, the device status reports it
             }
-        }
-        s0 = __shfl_sync(FULLMASK, s0, 0);
-        got = __shfl_sync(FULLMASK, got, 0);
-    }
-    if (empty) {
-        if (rank < take)
-            init_trial<DEBUG>(sd, L, T, lane, t0 + (unsigned long long)rank, wait_ns);
-        else if (rank < take + got)
-            init_shot(sd, T, lane, s0 + (rank - take));
-    }
-    __syncwarp();
-    const bool actv = lane < S && T.st[lane].kind != 0;
-    const unsigned am = __ballot_sync(FULLMASK, actv);
-    const unsigned fm = __ballot_sync(FULLMASK, actv && T.st[lane].fresh);
-    const unsigned im = __ballot_sync(FULLMASK, actv && T.st[lane].kind == 1);
-    if (lane == 0) {
-        ctl->act_mask = am;
-        ctl->fresh_mask = fm;
-        ctl->init_mask = im;
-        ctl->exit = (am == 0u) ? 1 : 0;
-    }
-    __syncwarp();
-}
-
-template <int DC, int DV, bool DEBUG>
-__device__ void team_loop(const StreamDev &sd, const LayoutMem &L, const TeamMem &T, int S, int W, int tid,
-                          int bar_id, unsigned long long wait_ns) {
-    const int lane = tid & 31, wt = tid >> 5, nthreads = 32 * W;
-    unsigned long long init_local = 0, iters_local = 0, trials_local = 0;
-    if (wt == 0) {
-        if (lane < S) T.st[lane].kind = 0;
-        if (lane == 0) {
-            T.ctl->chunk_next = 0;
-            T.ctl->chunk_end = 0;
         }
         __syncwarp();
-        refill<DEBUG>(sd, L, T, S, lane, init_local, wait_ns);
+        mg.tail += take;
+        space -= take;
+        got_any = take > 0;
     }
-    team_sync(W, bar_id);
-    while (!T.ctl->exit) {
-        c_phase<DC>(sd.code, L, T, S, tid, nthreads);
-        team_sync(W, bar_id);
-        v_phase<DV, DEBUG>(sd, L, T, S, tid, nthreads);
-        team_sync(W, bar_id);
-        if (wt == 0) {
-            decide<DEBUG>(sd, T, S, lane, init_local, iters_local, trials_local);
-            refill<DEBUG>(sd, L, T, S, lane, init_local, wait_ns);
+    if (space > 0) {
+        long long c0 = 0;
+        int got = 0;
+        if (lane == 0) {
+            const long long avail = shots_available(sd);
+            const long long want = space < 32 ? space : 32;
+            if (sd.flags & kServe) {
+                for (int att = 0; att < 4; ++att) {
+                    const long long cur = (long long)ld_vol_u64(&sd.ctr->shot_next);
+                    if (cur >= avail) break;
+                    const long long nw = (avail - cur) < want ? (avail - cur) : want;
+                    if ((long long)atomicCAS(&sd.ctr->shot_next, (unsigned long long)cur,
+                                             (unsigned long long)(cur + nw)) == cur) {
+                        c0 = cur;
+                        got = (int)nw;
+                        break;
+                    }
+                }
+            } else if ((long long)ld_vol_u64(&sd.ctr->shot_next) < avail) {
+                c0 = (long long)atomicAdd(&sd.ctr->shot_next, (unsigned long long)want);
+                const long long hi = (c0 + want) < avail ? (c0 + want) : avail;
+                got = c0 < avail ? (int)(hi - c0) : 0;
+            }
         }
-        team_sync(W, bar_id);
+        c0 = __shfl_sync(FULLMASK, c0, 0);
+        got = __shfl_sync(FULLMASK, got, 0);
+        if (lane < got) {
+            const long long shot = c0 + lane;
+            const long long row = row_of(sd, shot);
+            QEntry *e = qentry(qbase, (mg.tail + lane) % Q, qstride);
+            e->kind = 1;
+            e->kidx = 0;
+            e->shot = shot;
+            for (int j = 0; j < kMaxW; ++j) e->phi[j] = 0;
+            const uint32_t *src = sd.job.synd + row * sd.job.synd_stride;
+            uint32_t *sy = qsyn(e);
+            for (int w = 0; w < Ws; ++w) sy[w] = __ldcg(src + w);
+        }
+        __syncwarp();
+        mg.tail += got;
+        got_any = got_any || got > 0;
     }
-    if (wt == 0 && lane == 0) {
-        if (init_local) {
+    return got_any;
+}
+
+template <bool DEBUG>
+__device__ void manager_loop(const StreamDev &sd, unsigned char *team_base, int team_bytes, const TeamOffsets &to,
+                             int teams, int S, unsigned char *qbase, int Q, BlockHdr *hdr, int lane,
+                             unsigned long long wait_ns) {
+    const CodeDev &cd = sd.code;
+    const int qstride = qentry_bytes(cd.Ws);
+    const int nslots = teams * S;
+    MgrState mg{0, 0, 0u, 0u};
+    unsigned long long idle_since = 0;
+    for (;;) {
+        bool progress = false;
+        bool busy = false;
+        // (A) write out finished slots.
+        for (int g0 = 0; g0 < nslots; g0 += 32) {
+            const int g = g0 + lane;
+            const bool inr = g < nslots;
+            const int t = inr ? g / S : 0, s = inr ? g - t * S : 0;
+            TeamMem T = team_mem(team_base + t * team_bytes, to);
+            const int stv = inr ? *vstate(&T.st[s]) : kSlotEmpty;
+            __threadfence_block();
+            const bool fin = stv == kSlotFinished;
+            const bool coop = fin && T.st[s].kind == 1 && T.st[s].outcome == 2 && cd.w > 0;
+            if (__any_sync(FULLMASK, stv == kSlotRunning)) busy = true;
+            if (fin && !coop) finalize_simple<DEBUG>(sd, T, s, mg);
+            unsigned cm = __ballot_sync(FULLMASK, coop);
+            while (cm) {
+                const int l = __ffs(cm) - 1;
+                cm &= cm - 1u;
+                const int gg = g0 + l;
+                const int tt = gg / S, s2 = gg - tt * S;
+                finalize_failed<DEBUG>(sd, team_mem(team_base + tt * team_bytes, to), s2, lane, mg);
+            }
+            if (fin) *vstate(&T.st[s]) = kSlotEmpty;
+            if (__any_sync(FULLMASK, fin)) progress = true;
+        }
+        __syncwarp();
+        // (B) refill empty slots from the ready queue.
+        for (int g0 = 0; g0 < nslots && mg.tail > mg.head; g0 += 32) {
+            const int g = g0 + lane;
+            const bool inr = g < nslots;
+            const int t = inr ? g / S : 0, s = inr ? g - t * S : 0;
+            TeamMem T = team_mem(team_base + t * team_bytes, to);
+            const bool empty = inr && *vstate(&T.st[s]) == kSlotEmpty;
+            const unsigned em = __ballot_sync(FULLMASK, empty);
+            const int rank = __popc(em & ((1u << lane) - 1u));
+            const int avail = mg.tail - mg.head;
+            if (empty && rank < avail) {
+                QEntry *e = qentry(qbase, (mg.head + rank) % Q, qstride);
+                if (e->kind != 0) install(sd, T, s, e);
+            }
+            const int used = __popc(em) < avail ? __popc(em) : avail;
+            mg.head += used;
+            if (used) progress = true;
+        }
+        __syncwarp();
+        // (C) claim work ahead.
+        if (prefetch<DEBUG>(sd, qbase, Q, qstride, lane, mg, wait_ns)) progress = true;
+        // Count finished initial runs once no new shot can be claimed.
+        if (!(sd.flags & kServe)) {
+            int exhausted = 0;
+            if (lane == 0) exhausted = (long long)ld_vol_u64(&sd.ctr->shot_next) >= sd.job.n_shots;
+            exhausted = __shfl_sync(FULLMASK, exhausted, 0);
+            if (exhausted) {
+                const unsigned tot = __reduce_add_sync(FULLMASK, mg.init_local);
+                mg.init_local = 0;
+                if (lane == 0 && tot) {
+                    __threadfence();
+                    atomicAdd(&sd.ctr->init_done, (unsigned long long)tot);
+                }
+            }
+        }
+        // (D) leave when nothing is running, queued or claimable.
+        if (!busy && !progress && mg.tail == mg.head) {
+            bool any_slot = false;
+            for (int g0 = 0; g0 < nslots; g0 += 32) {
+                const int g = g0 + lane;
+                const int t = g < nslots ? g / S : 0, s = g < nslots ? g - t * S : 0;
+                TeamMem T = team_mem(team_base + t * team_bytes, to);
+                const bool occ = g < nslots && *vstate(&T.st[s]) != kSlotEmpty;
+                if (__any_sync(FULLMASK, occ)) any_slot = true;
+            }
+            if (!any_slot) {
+                if (!(sd.flags & kServe)) break;
+                // Serving: stay for idle_ns after the last work, or until asked to stop.
+                const unsigned long long now = globaltimer_ns();
+                if (idle_since == 0) idle_since = now;
+                if (*sd.serve.stop || now - idle_since > (unsigned long long)sd.serve.idle_ns) break;
+                __nanosleep(200);
+                continue;
+            }
+        }
+        if (progress) idle_since = 0;
+        if (!progress) __nanosleep(32);
+    }
+    // Flush counters and release the teams.
+    const unsigned init_tot = __reduce_add_sync(FULLMASK, mg.init_local);
+    const unsigned trial_tot = __reduce_add_sync(FULLMASK, mg.trials_local);
+    if (lane == 0) {
+        if (init_tot) {
             __threadfence();
-            atomicAdd(&sd.ctr->init_done, init_local);
+            atomicAdd(&sd.ctr->init_done, (unsigned long long)init_tot);
         }
-        if (iters_local) atomicAdd(&sd.ctr->iters_total, iters_local);
-        if (trials_local) atomicAdd(&sd.ctr->trial_runs, trials_local);
+        if (trial_tot) atomicAdd(&sd.ctr->trial_runs, (unsigned long long)trial_tot);
+        unsigned long long it = 0;
+        for (int t = 0; t < teams; ++t) {
+            TeamMem T = team_mem(team_base + t * team_bytes, to);
+            it += T.ctl->iters;
+            T.ctl->iters = 0;
+        }
+        if (it) atomicAdd(&sd.ctr->iters_total, it);
+        __threadfence_block();
+        hdr->exit = 1;
     }
+    __syncwarp();
 }
 
 struct KernelParams {
     StreamDev streams[kMaxStreams];
     int n_streams;
-    int warps_per_block;
+    int teams, W, S, Q;
     unsigned long long wait_ns;
 };
 
-template <int DC, int DV, bool DEBUG>
+template <int DC, int DV, bool REG, bool DEBUG>
 __global__ void __launch_bounds__(512, 1) bpsf_persistent(const __grid_constant__ KernelParams kp) {
     extern __shared__ __align__(16) unsigned char smem[];
-    volatile int *hdr = reinterpret_cast<volatile int *>(smem);
-    const int tid = threadIdx.x, warp = tid >> 5;
+    BlockHdr *hdr = reinterpret_cast<BlockHdr *>(smem);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int teams = kp.teams, W = kp.W, S = kp.S, Q = kp.Q;
     int cur = -1;
     bool waiting = false;
     unsigned long long wait_start = 0;
@@ -581,89 +794,107 @@ __global__ void __launch_bounds__(512, 1) bpsf_persistent(const __grid_constant_
                 const int sid = (start + k) % ns;
                 const StreamDev &sd = kp.streams[sid];
                 const StreamCounters *c = sd.ctr;
+                if (sd.flags & kServe) {
+                    const long long pub = ld_acquire_sys_s64(sd.serve.published);
+                    const long long sn = (long long)ld_vol_u64(&c->shot_next);
+                    const unsigned long long ttot = ld_vol_u64(&c->rec_count) * (unsigned long long)sd.code.n_trials;
+                    const bool claimable = sn < pub || ld_vol_u64(&c->ticket_next) < ttot;
+                    if (claimable && pick < 0) pick = sid;
+                    if (claimable || !*sd.serve.stop) all_done = false;
+                    continue;
+                }
                 const unsigned long long n = (unsigned long long)sd.job.n_shots;
                 const unsigned long long shot_next = ld_vol_u64(&c->shot_next);
                 const unsigned long long init_done = ld_vol_u64(&c->init_done);
                 __threadfence();
-                const unsigned long long rc = ld_vol_u32(&c->rec_count);
+                const unsigned long long rc = ld_vol_u64(&c->rec_count);
                 const unsigned long long tk = ld_vol_u64(&c->ticket_next);
                 const bool trials = sd.code.w > 0 && !(sd.flags & kNoTickets);
-                const unsigned long long rcap = rc < (unsigned long long)sd.rec.cap ? rc : (unsigned long long)sd.rec.cap;
-                const unsigned long long ttot = trials ? rcap * (unsigned long long)sd.code.n_trials : 0ull;
+                const unsigned long long ttot = trials ? rc * (unsigned long long)sd.code.n_trials : 0ull;
                 const bool claimable = shot_next < n || tk < ttot;
                 const bool done = shot_next >= n && init_done >= n && tk >= ttot;
                 if (claimable && pick < 0) pick = sid;
                 if (!done) all_done = false;
             }
-            hdr[0] = pick;
-            hdr[1] = pick >= 0 ? 1 : (all_done ? 2 : 0);
+            hdr->stream = pick;
+            hdr->cmd = pick >= 0 ? 1 : (all_done ? 2 : 0);
         }
         __syncthreads();
-        const int cmd = hdr[1], sid = hdr[0];
+        const int cmd = hdr->cmd, sid = hdr->stream;
         __syncthreads();
         if (cmd == 2) break;
         if (cmd == 0) {
-            // Other blocks still run initial runs that may publish trials.
+            // Other blocks still run initial runs that may publish trials, or
+            // a serving loop waits for requests.
             if (tid == 0) {
                 const unsigned long long now = globaltimer_ns();
+                bool serve_any = false, serve_quit = true;
+                for (int k = 0; k < kp.n_streams; ++k)
+                    if (kp.streams[k].flags & kServe) {
+                        serve_any = true;
+                        if (!*kp.streams[k].serve.stop &&
+                            (!waiting || now - wait_start <= (unsigned long long)kp.streams[k].serve.idle_ns))
+                            serve_quit = false;
+                    }
                 if (!waiting) {
                     waiting = true;
                     wait_start = now;
+                } else if (serve_any) {
+                    if (serve_quit) hdr->cmd = 3;
                 } else if (now - wait_start > kp.wait_ns) {
                     for (int k = 0; k < kp.n_streams; ++k) atomicOr(&kp.streams[k].ctr->status, kDevIdleTimeout);
-                    hdr[1] = 3;
+                    hdr->cmd = 3;
                 }
                 __nanosleep(1000);
             }
             __syncthreads();
-            const int abort_now = hdr[1] == 3;
+            const int quit = hdr->cmd == 3;
             __syncthreads();
-            if (abort_now) break;
+            if (quit) break;
             continue;
         }
         waiting = false;
         const StreamDev &sd = kp.streams[sid];
         const CodeDev &cd = sd.code;
-        const LayoutOffsets lo = layout_offsets(cd.M, cd.N, cd.nnz);
+        const LayoutOffsets lo = layout_offsets(cd.M, cd.N, DV);
         unsigned char *lay = smem + kBlockHeaderBytes;
         if (sid != cur) {
-            uint16_t *rp = reinterpret_cast<uint16_t *>(lay + lo.row_ptr);
-            uint16_t *c2c = reinterpret_cast<uint16_t *>(lay + lo.csr_to_csc);
-            uint16_t *cp = reinterpret_cast<uint16_t *>(lay + lo.col_ptr);
-            uint16_t *c2r = reinterpret_cast<uint16_t *>(lay + lo.csc_to_csr);
+            uint8_t *rd = lay + lo.row_deg;
+            uint16_t *vp = reinterpret_cast<uint16_t *>(lay + lo.vpos);
             float *lc = reinterpret_cast<float *>(lay + lo.lch);
-            for (int k = tid; k <= cd.M; k += blockDim.x) rp[k] = cd.row_ptr[k];
-            for (int k = tid; k <= cd.N; k += blockDim.x) cp[k] = cd.col_ptr[k];
-            for (int k = tid; k < cd.nnz; k += blockDim.x) {
-                c2c[k] = cd.csr_to_csc[k];
-                c2r[k] = cd.csc_to_csr[k];
-            }
+            for (int k = tid; k < cd.M; k += blockDim.x) rd[k] = cd.row_deg[k];
+            for (int k = tid; k < cd.N * DV; k += blockDim.x) vp[k] = cd.vpos[k];
             for (int k = tid; k < cd.N; k += blockDim.x) lc[k] = cd.lch[k];
             cur = sid;
-            __syncthreads();
         }
+        // Every slot starts empty; teams start idle.
+        const TeamOffsets to = team_offsets(S, cd.N, cd.P, cd.Ws);
+        unsigned char *qbase = lay + lo.total;
+        unsigned char *team_base = qbase + Q * qentry_bytes(cd.Ws);
+        for (int k = tid; k < teams * S; k += blockDim.x) {
+            SlotState *ss = reinterpret_cast<SlotState *>(team_base + (k / S) * to.total + to.state) + (k % S);
+            ss->state = kSlotEmpty;
+            ss->kind = 0;
+        }
+        for (int t = tid; t < teams; t += blockDim.x) {
+            TeamCtl *ctl = reinterpret_cast<TeamCtl *>(team_base + t * to.total + to.ctl);
+            ctl->iters = 0;
+            ctl->exit = 0;
+        }
+        if (tid == 0) hdr->exit = 0;
+        __syncthreads();
         LayoutMem L;
-        L.row_ptr = reinterpret_cast<const uint16_t *>(lay + lo.row_ptr);
-        L.csr_to_csc = reinterpret_cast<const uint16_t *>(lay + lo.csr_to_csc);
-        L.col_ptr = reinterpret_cast<const uint16_t *>(lay + lo.col_ptr);
-        L.csc_to_csr = reinterpret_cast<const uint16_t *>(lay + lo.csc_to_csr);
+        L.row_deg = lay + lo.row_deg;
+        L.vpos = reinterpret_cast<const uint16_t *>(lay + lo.vpos);
         L.lch = reinterpret_cast<const float *>(lay + lo.lch);
-        const int W = sd.W, S = sd.S;
-        const int teams = kp.warps_per_block / W;
-        const int team = warp / W;
-        if (team < teams) {
-            const TeamOffsets to = team_offsets(S, cd.M, cd.N, cd.nnz, cd.Ws);
-            unsigned char *tb = lay + lo.total + team * to.total;
-            TeamMem T;
-            T.ctl = reinterpret_cast<TeamCtl *>(tb + to.ctl);
-            T.st = reinterpret_cast<SlotState *>(tb + to.state);
-            T.syn = reinterpret_cast<uint32_t *>(tb + to.syn);
-            T.mism = reinterpret_cast<uint32_t *>(tb + to.mism);
-            T.ebits = reinterpret_cast<uint32_t *>(tb + to.ebits);
-            T.flips = reinterpret_cast<uint16_t *>(tb + to.flips);
-            T.q = reinterpret_cast<float *>(tb + to.q);
-            T.r = reinterpret_cast<float *>(tb + to.r);
-            team_loop<DC, DV, DEBUG>(sd, L, T, S, W, tid - team * W * 32, 1 + team, kp.wait_ns);
+        if (warp == 0) {
+            manager_loop<DEBUG>(sd, team_base, to.total, to, teams, S, qbase, Q, hdr, lane, kp.wait_ns);
+        } else {
+            const int team = (warp - 1) / W;
+            if (team < teams) {
+                TeamMem T = team_mem(team_base + team * to.total, to);
+                team_loop<DC, DV, REG, DEBUG>(sd, L, T, hdr, S, W, tid - 32 - team * W * 32, 1 + team, kp.wait_ns);
+            }
         }
         __syncthreads();
     }
@@ -673,32 +904,47 @@ __global__ void __launch_bounds__(512, 1) bpsf_persistent(const __grid_constant_
 // Variants and launch helpers.
 // ---------------------------------------------------------------------------
 
-static const int kVariantDC[] = {6, 8, 16, 32};
-static const int kVariantDV[] = {3, 3, 8, 16};
-static const int kNumVariants = 4;
+struct Variant {
+    int dc, dv;
+    bool reg;
+};
+static const Variant kVariants[] = {{6, 4, true}, {6, 4, false}, {8, 4, true}, {8, 4, false}, {16, 8, false},
+                                    {32, 16, false}};
+static const int kNumVariants = 6;
 
+// Smallest variant that fits; regular variants only for codes with exactly
+// dc ones per row (the caller passes dc_max = -dc for such codes).
 int kernel_variant(int dc_max, int dv_max) {
-    for (int v = 0; v < kNumVariants; ++v)
-        if (dc_max <= kVariantDC[v] && dv_max <= kVariantDV[v]) return v;
+    const bool regular = dc_max < 0;
+    const int dc = regular ? -dc_max : dc_max;
+    for (int v = 0; v < kNumVariants; ++v) {
+        const Variant &k = kVariants[v];
+        if (k.reg && (!regular || k.dc != dc)) continue;
+        if (dc <= k.dc && dv_max <= k.dv) return v;
+    }
     return -1;
 }
-int kernel_variant_dc(int v) { return kVariantDC[v]; }
-int kernel_variant_dv(int v) { return kVariantDV[v]; }
 
 typedef void (*KernelFn)(KernelParams);
 
 static KernelFn kernel_fn(int variant, bool debug) {
     switch (variant * 2 + (debug ? 1 : 0)) {
-        case 0: return bpsf_persistent<6, 3, false>;
-        case 1: return bpsf_persistent<6, 3, true>;
-        case 2: return bpsf_persistent<8, 3, false>;
-        case 3: return bpsf_persistent<8, 3, true>;
-        case 4: return bpsf_persistent<16, 8, false>;
-        case 5: return bpsf_persistent<16, 8, true>;
-        case 6: return bpsf_persistent<32, 16, false>;
-        default: return bpsf_persistent<32, 16, true>;
+        case 0: return bpsf_persistent<6, 4, true, false>;
+        case 1: return bpsf_persistent<6, 4, true, true>;
+        case 2: return bpsf_persistent<6, 4, false, false>;
+        case 3: return bpsf_persistent<6, 4, false, true>;
+        case 4: return bpsf_persistent<8, 4, true, false>;
+        case 5: return bpsf_persistent<8, 4, true, true>;
+        case 6: return bpsf_persistent<8, 4, false, false>;
+        case 7: return bpsf_persistent<8, 4, false, true>;
+        case 8: return bpsf_persistent<16, 8, false, false>;
+        case 9: return bpsf_persistent<16, 8, false, true>;
+        case 10: return bpsf_persistent<32, 16, false, false>;
+        default: return bpsf_persistent<32, 16, false, true>;
     }
 }
+
+int kernel_variant_dv(int variant) { return kVariants[variant].dv; }
 
 const void *persistent_kernel_ptr(int variant, bool debug) {
     return reinterpret_cast<const void *>(kernel_fn(variant, debug));
@@ -708,7 +954,10 @@ void launch_persistent(int variant, bool debug, int grid, int block, int smem, c
     KernelParams kp;
     for (int k = 0; k < args.n_streams; ++k) kp.streams[k] = args.streams[k];
     kp.n_streams = args.n_streams;
-    kp.warps_per_block = args.warps_per_block;
+    kp.teams = args.teams;
+    kp.W = args.W;
+    kp.S = args.S;
+    kp.Q = args.Q;
     kp.wait_ns = args.wait_ns;
     kernel_fn(variant, debug)<<<grid, block, smem, (cudaStream_t)stream>>>(kp);
 }
