@@ -119,7 +119,8 @@ bpsf_status bpsf_make_plan(bpsf_ctx *const *codes, int n_codes, const bpsf_tunin
     bool all_regular = true;
     int dc = 0, dv = 0;
     for (int k = 0; k < n_codes; ++k) {
-        all_regular = all_regular && codes[k]->regular && codes[k]->dc_max == codes[0]->dc_max;
+        all_regular = all_regular && codes[k]->regular && codes[k]->dc_max == codes[0]->dc_max &&
+                      codes[k]->dv_max == codes[0]->dv_max;
         dc = std::max(dc, codes[k]->dc_max);
         dv = std::max(dv, codes[k]->dv_max);
     }

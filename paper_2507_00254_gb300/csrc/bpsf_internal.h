@@ -137,15 +137,16 @@ __host__ __device__ inline int align_up(int x, int a) { return (x + a - 1) / a *
 constexpr int kBlockHeaderBytes = 64;
 
 struct LayoutOffsets {
-    int row_deg, vpos, lch, total;
+    int row_deg, vpos, lch, lch_pos, total;
 };
 
-__host__ __device__ inline LayoutOffsets layout_offsets(int M, int N, int vstride) {
+__host__ __device__ inline LayoutOffsets layout_offsets(int M, int N, int vstride, int P) {
     LayoutOffsets o;
     int p = 0;
     o.row_deg = p;  p = align_up(p + M, 16);
     o.vpos = p;     p = align_up(p + 2 * N * vstride, 16);
     o.lch = p;      p = align_up(p + 4 * N, 16);
+    o.lch_pos = p;  p = align_up(p + 4 * P, 16);
     o.total = p;
     return o;
 }
@@ -208,7 +209,7 @@ static_assert(sizeof(QEntry) == 48, "queue entry header is 48 bytes");
 __host__ __device__ inline int qentry_bytes(int Ws) { return align_up(48 + 4 * Ws, 16); }
 
 __host__ __device__ inline int block_smem_bytes(int M, int N, int P, int Ws, int vstride, int S, int teams, int Q) {
-    return kBlockHeaderBytes + layout_offsets(M, N, vstride).total + Q * qentry_bytes(Ws) +
+    return kBlockHeaderBytes + layout_offsets(M, N, vstride, P).total + Q * qentry_bytes(Ws) +
            teams * team_offsets(S, N, P, Ws).total;
 }
 

@@ -83,6 +83,7 @@ struct LayoutMem {
     const uint8_t *row_deg;
     const uint16_t *vpos;
     const float *lch;
+    const float *lch_pos;
 };
 
 struct TeamMem {
@@ -114,54 +115,84 @@ __device__ __forceinline__ volatile int *vstate(SlotState *s) { return reinterpr
 //   a = alpha * (k == k1 ? m2 : m1),
 // which equals the explicit "min and sign product over the other variables"
 // bit for bit (min is exact; the sign factors are exact), independently of
-// the order the row's edges are stored in.
+// the order the row's edges are stored in.  V2C messages are never -0 (each
+// is a fold that starts at a channel LLR > 0, and an exact cancellation
+// rounds to +0), so the sign bit of q_k is [q_k < 0] and the sign product is
+// an XOR of sign bits.  m2 = min(m2, max(m1, a)) keeps the second smallest
+// value branch-free, equal to m1 on ties.
 // ---------------------------------------------------------------------------
+template <int DC, bool REG>
+struct CTask {
+    float v[DC];
+    float *dst;
+    unsigned sall;  // bit 31: s_j xor the sign bits of all inputs
+    int deg;
+    bool on;
+};
+
+template <int DC, bool REG>
+__device__ __forceinline__ void c_load(CTask<DC, REG> &t, const CodeDev &cd, const LayoutMem &L, const TeamMem &T,
+                                       int s, int j, bool valid, unsigned run, unsigned fresh) {
+    t.on = valid && ((run >> s) & 1u);
+    if (!t.on) return;
+    const int M = cd.M;
+    t.deg = REG ? DC : (int)L.row_deg[j];
+    t.dst = T.m + s * cd.P + j;
+    const float *src = ((fresh >> s) & 1u) ? (L.lch_pos + j) : t.dst;
+    t.sall = ((T.syn[s * cd.Ws + (j >> 5)] >> (j & 31)) & 1u) << 31;
+#pragma unroll
+    for (int k = 0; k < DC; ++k)
+        if (REG || k < t.deg) t.v[k] = src[k * M];
+}
+
+template <int DC, bool REG>
+__device__ __forceinline__ void c_compute_store(CTask<DC, REG> &t, int M, float alpha) {
+    if (!t.on) return;
+    float m1 = __int_as_float(0x7f800000), m2 = m1;
+    int k1 = 0;
+    unsigned sx = t.sall;
+#pragma unroll
+    for (int k = 0; k < DC; ++k) {
+        if (REG || k < t.deg) {
+            const float a = fabsf(t.v[k]);
+            k1 = (a < m1) ? k : k1;
+            m2 = fminf(m2, fmaxf(m1, a));
+            m1 = fminf(m1, a);
+            sx ^= __float_as_uint(t.v[k]);
+        }
+    }
+    const float g1 = __fmul_rn(alpha, m1), g2 = __fmul_rn(alpha, m2);
+#pragma unroll
+    for (int k = 0; k < DC; ++k) {
+        if (REG || k < t.deg) {
+            const float mag = (k == k1) ? g2 : g1;
+            const unsigned bits = __float_as_uint(mag) | ((sx ^ __float_as_uint(t.v[k])) & 0x80000000u);
+            t.dst[k * M] = __uint_as_float(bits);
+        }
+    }
+}
+
 template <int DC, bool REG>
 __device__ __forceinline__ void c_phase(const CodeDev &cd, const LayoutMem &L, const TeamMem &T, int S,
                                         unsigned run, unsigned fresh, int tid, int nthreads) {
-    const int M = cd.M, P = cd.P, Ws = cd.Ws;
+    const int M = cd.M;
     const int total = S * M;
     const float alpha = cd.alpha;
     int s = tid / M, j = tid - s * M;
-    for (int tau = tid; tau < total; tau += nthreads) {
-        if ((run >> s) & 1u) {
-            const bool fr = (fresh >> s) & 1u;
-            const int deg = REG ? DC : (int)L.row_deg[j];
-            unsigned neg = (T.syn[s * Ws + (j >> 5)] >> (j & 31)) & 1u;
-            float *ms = T.m + s * P + j;
-            const float *ls = cd.lch_pos + j;
-            float v[DC];
-#pragma unroll
-            for (int k = 0; k < DC; ++k) {
-                if (REG || k < deg) v[k] = fr ? __ldg(ls + k * M) : ms[k * M];
-            }
-            float m1 = __int_as_float(0x7f800000), m2 = m1;
-            int k1 = 0;
-#pragma unroll
-            for (int k = 0; k < DC; ++k) {
-                if (REG || k < deg) {
-                    const float a = fabsf(v[k]);
-                    if (a < m1) {
-                        m2 = m1;
-                        m1 = a;
-                        k1 = k;
-                    } else if (a < m2) {
-                        m2 = a;
-                    }
-                    neg ^= (v[k] < 0.f) ? 1u : 0u;
-                }
-            }
-            const float g1 = __fmul_rn(alpha, m1), g2 = __fmul_rn(alpha, m2);
-#pragma unroll
-            for (int k = 0; k < DC; ++k) {
-                if (REG || k < deg) {
-                    const float mag = (k == k1) ? g2 : g1;
-                    const unsigned ng = neg ^ ((v[k] < 0.f) ? 1u : 0u);
-                    ms[k * M] = ng ? -mag : mag;
-                }
-            }
+    // Two rows per step: both rows' loads are issued before either row's stores.
+    for (int tau = tid; tau < total; tau += 2 * nthreads) {
+        int sB = s, jB = j + nthreads;
+        while (jB >= M) {
+            jB -= M;
+            ++sB;
         }
-        j += nthreads;
+        CTask<DC, REG> A, B;
+        c_load<DC, REG>(A, cd, L, T, s, j, true, run, fresh);
+        c_load<DC, REG>(B, cd, L, T, sB, jB, tau + nthreads < total, run, fresh);
+        c_compute_store<DC, REG>(A, M, alpha);
+        c_compute_store<DC, REG>(B, M, alpha);
+        s = sB;
+        j = jB + nthreads;
         while (j >= M) {
             j -= M;
             ++s;
@@ -176,7 +207,7 @@ __device__ __forceinline__ void c_phase(const CodeDev &cd, const LayoutMem &L, c
 //   q_k   = l_ch + sum_{k' != k} r_k'   (left fold, ascending k'),
 //   l_out = l_ch + sum_k r_k            (left fold),  e_i = [l_out <= 0].
 // ---------------------------------------------------------------------------
-template <int DV, bool DEBUG>
+template <int DVS, int DVX, bool DEBUG>
 __device__ __forceinline__ void v_phase(const StreamDev &sd, const LayoutMem &L, const TeamMem &T, int S,
                                         unsigned run, unsigned fresh, unsigned initm, int tid, int nthreads) {
     const CodeDev &cd = sd.code;
@@ -191,10 +222,10 @@ __device__ __forceinline__ void v_phase(const StreamDev &sd, const LayoutMem &L,
         const bool fr = a && ((fresh >> s) & 1u);
         const bool ini = a && ((initm >> s) & 1u);
         unsigned ebit = 0;
-        uint16_t pos[DV];
+        uint16_t pos[DVS];
         if (a) {
-            const uint16_t *vp = L.vpos + i * DV;
-            if (DV == 4) {
+            const uint16_t *vp = L.vpos + i * DVS;
+            if (DVS == 4) {
                 const uint2 raw = *reinterpret_cast<const uint2 *>(vp);
                 pos[0] = (uint16_t)(raw.x & 0xffffu);
                 pos[1] = (uint16_t)(raw.x >> 16);
@@ -202,27 +233,41 @@ __device__ __forceinline__ void v_phase(const StreamDev &sd, const LayoutMem &L,
                 pos[3] = (uint16_t)(raw.y >> 16);
             } else {
 #pragma unroll
-                for (int k = 0; k < DV; ++k) pos[k] = vp[k];
+                for (int k = 0; k < DVS; ++k) pos[k] = vp[k];
             }
             const float lc = L.lch[i];
             float *ms = T.m + s * P;
-            float rv[DV];
+            float lo;
+            if (DVX == 3) {
+                // Three checks: shared prefix l_ch + r0.
+                const float r0 = ms[pos[0]], r1 = ms[pos[1]], r2 = ms[pos[2]];
+                const float t0 = __fadd_rn(lc, r0);
+                const float q2 = __fadd_rn(t0, r1);
+                lo = __fadd_rn(q2, r2);
+                const float q1 = __fadd_rn(t0, r2);
+                const float q0 = __fadd_rn(__fadd_rn(lc, r1), r2);
+                ms[pos[0]] = q0;
+                ms[pos[1]] = q1;
+                ms[pos[2]] = q2;
+            } else {
+                float rv[DVS];
 #pragma unroll
-            for (int k = 0; k < DV; ++k) rv[k] = (pos[k] != 0xffffu) ? ms[pos[k]] : 0.f;
+                for (int k = 0; k < DVS; ++k) rv[k] = (pos[k] != 0xffffu) ? ms[pos[k]] : 0.f;
 #pragma unroll
-            for (int k = 0; k < DV; ++k) {
-                if (pos[k] != 0xffffu) {
-                    float acc = lc;
+                for (int k = 0; k < DVS; ++k) {
+                    if (pos[k] != 0xffffu) {
+                        float acc = lc;
 #pragma unroll
-                    for (int k2 = 0; k2 < DV; ++k2)
-                        if (k2 != k && pos[k2] != 0xffffu) acc = __fadd_rn(acc, rv[k2]);
-                    ms[pos[k]] = acc;
+                        for (int k2 = 0; k2 < DVS; ++k2)
+                            if (k2 != k && pos[k2] != 0xffffu) acc = __fadd_rn(acc, rv[k2]);
+                        ms[pos[k]] = acc;
+                    }
                 }
-            }
-            float lo = lc;
+                lo = lc;
 #pragma unroll
-            for (int k = 0; k < DV; ++k)
-                if (pos[k] != 0xffffu) lo = __fadd_rn(lo, rv[k]);
+                for (int k = 0; k < DVS; ++k)
+                    if (pos[k] != 0xffffu) lo = __fadd_rn(lo, rv[k]);
+            }
             ebit = (lo <= 0.f) ? 1u : 0u;
             if (DEBUG && ini && sd.dbg.lout) {
                 const long long shot = T.st[s].shot;
@@ -240,10 +285,10 @@ __device__ __forceinline__ void v_phase(const StreamDev &sd, const LayoutMem &L,
             const unsigned flip = prev ^ ebit;
             if (ini) T.flips[tau] = fr ? (uint16_t)flip : (uint16_t)(T.flips[tau] + flip);
             if (flip) {
-                const uint16_t *vc = cd.vchk + i * DV;
+                const uint16_t *vc = cd.vchk + i * DVS;
 #pragma unroll
-                for (int k = 0; k < DV; ++k) {
-                    if (pos[k] != 0xffffu) {
+                for (int k = 0; k < DVS; ++k) {
+                    if (DVX > 0 ? (k < DVX) : (pos[k] != 0xffffu)) {
                         const int c = __ldg(vc + k);
                         atomicXor(&T.mism[s * Ws + (c >> 5)], 1u << (c & 31));
                     }
@@ -262,7 +307,7 @@ __device__ __forceinline__ void v_phase(const StreamDev &sd, const LayoutMem &L,
 // ---------------------------------------------------------------------------
 // Compute team loop.
 // ---------------------------------------------------------------------------
-template <int DC, int DV, bool REG, bool DEBUG>
+template <int DC, int DVS, int DVX, bool DEBUG>
 __device__ void team_loop(const StreamDev &sd, const LayoutMem &L, const TeamMem &T, BlockHdr *hdr, int S, int W,
                           int tid, int bar_id, unsigned long long wait_ns) {
     const int lane = tid & 31, wt = tid >> 5, nthreads = 32 * W;
@@ -305,9 +350,9 @@ __device__ void team_loop(const StreamDev &sd, const LayoutMem &L, const TeamMem
         team_sync(W, bar_id);
         if (ex) break;
         if (run == 0u) continue;
-        c_phase<DC, REG>(cd, L, T, S, run, fresh, tid, nthreads);
+        c_phase<DC, (DVX > 0)>(cd, L, T, S, run, fresh, tid, nthreads);
         team_sync(W, bar_id);
-        v_phase<DV, DEBUG>(sd, L, T, S, run, fresh, initm, tid, nthreads);
+        v_phase<DVS, DVX, DEBUG>(sd, L, T, S, run, fresh, initm, tid, nthreads);
         team_sync(W, bar_id);
         if (wt == 0 && lane < S && ((run >> lane) & 1u)) {
             SlotState *ss = &T.st[lane];
@@ -775,7 +820,7 @@ struct KernelParams {
     unsigned long long wait_ns;
 };
 
-template <int DC, int DV, bool REG, bool DEBUG>
+template <int DC, int DVS, int DVX, bool DEBUG>
 __global__ void __launch_bounds__(512, 1) bpsf_persistent(const __grid_constant__ KernelParams kp) {
     extern __shared__ __align__(16) unsigned char smem[];
     BlockHdr *hdr = reinterpret_cast<BlockHdr *>(smem);
@@ -856,15 +901,17 @@ __global__ void __launch_bounds__(512, 1) bpsf_persistent(const __grid_constant_
         waiting = false;
         const StreamDev &sd = kp.streams[sid];
         const CodeDev &cd = sd.code;
-        const LayoutOffsets lo = layout_offsets(cd.M, cd.N, DV);
+        const LayoutOffsets lo = layout_offsets(cd.M, cd.N, DVS, cd.P);
         unsigned char *lay = smem + kBlockHeaderBytes;
         if (sid != cur) {
             uint8_t *rd = lay + lo.row_deg;
             uint16_t *vp = reinterpret_cast<uint16_t *>(lay + lo.vpos);
             float *lc = reinterpret_cast<float *>(lay + lo.lch);
+            float *lp = reinterpret_cast<float *>(lay + lo.lch_pos);
             for (int k = tid; k < cd.M; k += blockDim.x) rd[k] = cd.row_deg[k];
-            for (int k = tid; k < cd.N * DV; k += blockDim.x) vp[k] = cd.vpos[k];
+            for (int k = tid; k < cd.N * DVS; k += blockDim.x) vp[k] = cd.vpos[k];
             for (int k = tid; k < cd.N; k += blockDim.x) lc[k] = cd.lch[k];
+            for (int k = tid; k < cd.P; k += blockDim.x) lp[k] = cd.lch_pos[k];
             cur = sid;
         }
         // Every slot starts empty; teams start idle.
@@ -887,13 +934,14 @@ __global__ void __launch_bounds__(512, 1) bpsf_persistent(const __grid_constant_
         L.row_deg = lay + lo.row_deg;
         L.vpos = reinterpret_cast<const uint16_t *>(lay + lo.vpos);
         L.lch = reinterpret_cast<const float *>(lay + lo.lch);
+        L.lch_pos = reinterpret_cast<const float *>(lay + lo.lch_pos);
         if (warp == 0) {
             manager_loop<DEBUG>(sd, team_base, to.total, to, teams, S, qbase, Q, hdr, lane, kp.wait_ns);
         } else {
             const int team = (warp - 1) / W;
             if (team < teams) {
                 TeamMem T = team_mem(team_base + team * to.total, to);
-                team_loop<DC, DV, REG, DEBUG>(sd, L, T, hdr, S, W, tid - 32 - team * W * 32, 1 + team, kp.wait_ns);
+                team_loop<DC, DVS, DVX, DEBUG>(sd, L, T, hdr, S, W, tid - 32 - team * W * 32, 1 + team, kp.wait_ns);
             }
         }
         __syncthreads();
@@ -905,22 +953,24 @@ __global__ void __launch_bounds__(512, 1) bpsf_persistent(const __grid_constant_
 // ---------------------------------------------------------------------------
 
 struct Variant {
-    int dc, dv;
-    bool reg;
+    int dc, dvs, dvx;  // row-degree bound, column table width, exact column degree (0 = any)
 };
-static const Variant kVariants[] = {{6, 4, true}, {6, 4, false}, {8, 4, true}, {8, 4, false}, {16, 8, false},
-                                    {32, 16, false}};
-static const int kNumVariants = 6;
+static const Variant kVariants[] = {{6, 4, 3}, {6, 4, 0}, {8, 4, 0}, {16, 8, 0}, {32, 16, 0}};
+static const int kNumVariants = 5;
 
-// Smallest variant that fits; regular variants only for codes with exactly
-// dc ones per row (the caller passes dc_max = -dc for such codes).
+// Smallest variant that fits.  The exact-degree variant serves codes with
+// exactly dc ones in every row and dvx in every column; the caller marks
+// such codes by passing dc_max = -dc.
 int kernel_variant(int dc_max, int dv_max) {
     const bool regular = dc_max < 0;
     const int dc = regular ? -dc_max : dc_max;
     for (int v = 0; v < kNumVariants; ++v) {
         const Variant &k = kVariants[v];
-        if (k.reg && (!regular || k.dc != dc)) continue;
-        if (dc <= k.dc && dv_max <= k.dv) return v;
+        if (k.dvx > 0) {
+            if (regular && dc == k.dc && dv_max == k.dvx) return v;
+            continue;
+        }
+        if (dc <= k.dc && dv_max <= k.dvs) return v;
     }
     return -1;
 }
@@ -929,22 +979,20 @@ typedef void (*KernelFn)(KernelParams);
 
 static KernelFn kernel_fn(int variant, bool debug) {
     switch (variant * 2 + (debug ? 1 : 0)) {
-        case 0: return bpsf_persistent<6, 4, true, false>;
-        case 1: return bpsf_persistent<6, 4, true, true>;
-        case 2: return bpsf_persistent<6, 4, false, false>;
-        case 3: return bpsf_persistent<6, 4, false, true>;
-        case 4: return bpsf_persistent<8, 4, true, false>;
-        case 5: return bpsf_persistent<8, 4, true, true>;
-        case 6: return bpsf_persistent<8, 4, false, false>;
-        case 7: return bpsf_persistent<8, 4, false, true>;
-        case 8: return bpsf_persistent<16, 8, false, false>;
-        case 9: return bpsf_persistent<16, 8, false, true>;
-        case 10: return bpsf_persistent<32, 16, false, false>;
-        default: return bpsf_persistent<32, 16, false, true>;
+        case 0: return bpsf_persistent<6, 4, 3, false>;
+        case 1: return bpsf_persistent<6, 4, 3, true>;
+        case 2: return bpsf_persistent<6, 4, 0, false>;
+        case 3: return bpsf_persistent<6, 4, 0, true>;
+        case 4: return bpsf_persistent<8, 4, 0, false>;
+        case 5: return bpsf_persistent<8, 4, 0, true>;
+        case 6: return bpsf_persistent<16, 8, 0, false>;
+        case 7: return bpsf_persistent<16, 8, 0, true>;
+        case 8: return bpsf_persistent<32, 16, 0, false>;
+        default: return bpsf_persistent<32, 16, 0, true>;
     }
 }
 
-int kernel_variant_dv(int variant) { return kVariants[variant].dv; }
+int kernel_variant_dv(int variant) { return kVariants[variant].dvs; }
 
 const void *persistent_kernel_ptr(int variant, bool debug) {
     return reinterpret_cast<const void *>(kernel_fn(variant, debug));
