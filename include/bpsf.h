@@ -163,6 +163,34 @@ typedef struct {
  */
 bpsf_status bpsf_decode_multi(int32_t n_jobs, const bpsf_job *jobs, void *stream);
 
+/*
+ * Batched decode that allocates nothing.  The paper has no counterpart: this
+ * serves callers that cannot allocate device memory when they decode (a
+ * control loop with a hard deadline that must not block in the CUDA
+ * allocator, a runtime that owns the whole device heap, work being recorded
+ * into a CUDA graph).  It runs the same kernel as bpsf_decode with the same
+ * arguments and results, but the kernel's scratch (launch counters and the
+ * records of failed shots) lives in one static 32 MiB device array that
+ * every GPU loading this library holds until the process exits.
+ *   - At most bpsf_noalloc_max_shots(ctx) shots per call (this depends on the
+ *     code and on w); larger batches get BPSF_EINVAL and nothing runs.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture.
+ *   - All calls share the one array and it keeps the last call's contents;
+ *     each call clears what must start at zero.  Calls that overlap on the
+ *     GPU (on different streams, or from several contexts) race on the
+ *     array: order them on one stream.
+ *   - The context must already exist (bpsf_create allocates at set-up).
+ * bpsf_sync(ctx, stream) reports device-side errors of the call as usual.
+ */
+bpsf_status bpsf_decode_noalloc(bpsf_ctx *ctx, int64_t n_shots, const uint32_t *d_synd, int32_t synd_stride_words,
+                                uint32_t *d_corr, int32_t corr_stride_words, uint8_t *d_converged, int16_t *d_iters,
+                                uint8_t *d_stage, void *stream);
+
+/* Largest n_shots bpsf_decode_noalloc accepts for this context (-1 for NULL). */
+int64_t bpsf_noalloc_max_shots(const bpsf_ctx *ctx);
+
 /* Wait for `stream` and report device-side errors of ctx's last launches
  * (BPSF_ETIMEOUT for a bounded device wait that ran out, BPSF_EDEVICE for an
  * internal error).  Clears the device error word. */

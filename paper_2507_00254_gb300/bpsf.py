@@ -25,7 +25,8 @@ EXPORTS = (
     "bpsf_create", "bpsf_destroy", "bpsf_decode", "bpsf_decode_plain", "bpsf_decode_host", "bpsf_decode_multi",
     "bpsf_sync", "bpsf_get_tuning", "bpsf_set_tuning", "bpsf_autotune", "bpsf_serve_start", "bpsf_serve_submit",
     "bpsf_serve_poll", "bpsf_serve_stop", "bpsf_bb_code", "bpsf_phenom_code", "bpsf_syndrome", "bpsf_decode_debug",
-    "bpsf_num_trials", "bpsf_last_work", "bpsf_status_str", "bpsf_last_error",
+    "bpsf_num_trials", "bpsf_last_work", "bpsf_status_str", "bpsf_last_error", "bpsf_decode_noalloc",
+    "bpsf_noalloc_max_shots",
 )
 
 
@@ -86,6 +87,8 @@ def lib():
         "bpsf_destroy": ([vp], None),
         "bpsf_decode": ([vp, i64, vp, i32, vp, i32, vp, vp, vp, vp], st),
         "bpsf_decode_plain": ([vp, i64, vp, i32, vp, i32, vp, vp, vp, vp], st),
+        "bpsf_decode_noalloc": ([vp, i64, vp, i32, vp, i32, vp, vp, vp, vp], st),
+        "bpsf_noalloc_max_shots": ([vp], i64),
         "bpsf_decode_host": ([vp, i64, vp, i32, vp, i32, vp, vp, vp, vp], st),
         "bpsf_decode_multi": ([i32, C.POINTER(bpsf_job), vp], st),
         "bpsf_sync": ([vp, vp], st),
@@ -149,6 +152,14 @@ def bpsf_decode(h, n, d_synd, ss, d_corr, cs, d_conv, d_iters, d_stage, stream):
 
 def bpsf_decode_plain(h, n, d_synd, ss, d_corr, cs, d_conv, d_iters, d_stage, stream):
     check(lib().bpsf_decode_plain(h, n, d_synd, ss, d_corr, cs, d_conv, d_iters, d_stage, stream))
+
+
+def bpsf_decode_noalloc(h, n, d_synd, ss, d_corr, cs, d_conv, d_iters, d_stage, stream):
+    check(lib().bpsf_decode_noalloc(h, n, d_synd, ss, d_corr, cs, d_conv, d_iters, d_stage, stream))
+
+
+def bpsf_noalloc_max_shots(h) -> int:
+    return int(lib().bpsf_noalloc_max_shots(h))
 
 
 def bpsf_decode_host(h, n, h_synd, ss, h_corr, cs, h_conv, h_iters, h_stage, stream):

@@ -455,6 +455,7 @@ static bpsf_status decode_impl(bpsf_ctx *c, int64_t n, const uint32_t *synd, int
     launch_plan(pl, dbg != nullptr, &sd, 1, pl.grid, stream);
     e = cudaGetLastError();
     if (e != cudaSuccess) return bpsf_fail(BPSF_ECUDA, "kernel launch: %s", cudaGetErrorString(e));
+    c->d_ctr_last = c->d_ctr;
     c->last_launch_n = n;
     return BPSF_OK;
 }
@@ -476,7 +477,8 @@ extern "C" bpsf_status bpsf_sync(bpsf_ctx *c, void *stream) {
     if (!c) return bpsf_fail(BPSF_EINVAL, "ctx is NULL");
     cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
     if (e != cudaSuccess) return bpsf_fail(BPSF_ECUDA, "cudaStreamSynchronize: %s", cudaGetErrorString(e));
-    e = cudaMemcpy(c->h_ctr, c->d_ctr, sizeof(StreamCounters), cudaMemcpyDeviceToHost);
+    StreamCounters *dc = c->d_ctr_last ? c->d_ctr_last : c->d_ctr;
+    e = cudaMemcpy(c->h_ctr, dc, sizeof(StreamCounters), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return bpsf_fail(BPSF_ECUDA, "cudaMemcpy: %s", cudaGetErrorString(e));
     const StreamCounters &k = *c->h_ctr;
     c->last.initial_runs = (int64_t)k.init_done;
@@ -486,7 +488,7 @@ extern "C" bpsf_status bpsf_sync(bpsf_ctx *c, void *stream) {
     c->last.edge_updates = (int64_t)k.iters_total * c->nnz;
     if (k.status) {
         const unsigned stv = k.status;
-        cudaMemsetAsync(&c->d_ctr->status, 0, sizeof(unsigned), (cudaStream_t)stream);
+        cudaMemsetAsync(&dc->status, 0, sizeof(unsigned), (cudaStream_t)stream);
         cudaStreamSynchronize((cudaStream_t)stream);
         if (stv & (kDevReadyTimeout | kDevIdleTimeout))
             return bpsf_fail(BPSF_ETIMEOUT, "a bounded device wait ran out (status 0x%x)", stv);
@@ -563,6 +565,7 @@ extern "C" bpsf_status bpsf_decode_plain(bpsf_ctx *c, int64_t n, const uint32_t 
         }
     }
     c->last = bpsf_work{n, failed, trial_runs, iters_total, iters_total * c->nnz};
+    c->d_ctr_last = c->d_ctr;
     return BPSF_OK;
 }
 
@@ -655,6 +658,7 @@ extern "C" bpsf_status bpsf_decode_multi(int32_t n_jobs, const bpsf_job *jobs, v
                    j.corr_stride_words};
         sds[k] = bpsf_make_stream(c, job, nullptr, 0);
         c->last_launch_n = j.n_shots;
+        c->d_ctr_last = c->d_ctr;
     }
     launch_plan(pl, false, sds.data(), n_jobs, pl.grid, stream);
     cudaError_t e = cudaGetLastError();

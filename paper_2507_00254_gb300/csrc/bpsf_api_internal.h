@@ -16,6 +16,7 @@ struct bpsf_ctx {
     void *d_code = nullptr;                 // one allocation for all code arrays
     bpsf::CodeDev code{};
     bpsf::StreamCounters *d_ctr = nullptr;  // per-launch counters
+    bpsf::StreamCounters *d_ctr_last = nullptr;  // counters of the most recent launch (read by bpsf_sync)
     bpsf::StreamCounters *h_ctr = nullptr;  // pinned copy read by bpsf_sync
     bpsf::StreamCounters *h_preset = nullptr;
     uint8_t *h_flag = nullptr;              // pinned flag read by the plain form

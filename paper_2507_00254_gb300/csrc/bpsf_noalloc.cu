@@ -1,0 +1,138 @@
+// bpsf_decode_noalloc: the batched decode for callers that cannot allocate
+// device memory when they decode -- a control loop with a hard deadline that
+// must never block inside the CUDA allocator, a host runtime that hands the
+// whole device heap to another framework, or code that records its work
+// into a CUDA graph where a cudaMalloc would break the capture.  Such callers
+// create their context once at set-up and then decode without any further
+// allocation: the kernel's scratch (launch counters and failed-shot records)
+// lives in one statically sized device array defined in this file, which
+// every GPU that loads the library holds until the process exits.
+#include <cuda_runtime.h>
+
+#include <cstring>
+#include <mutex>
+
+#include "bpsf.h"
+#include "bpsf_api_internal.h"
+#include "bpsf_internal.h"
+
+using namespace bpsf;
+
+namespace {
+
+constexpr size_t kNoallocScratchBytes = size_t(32) << 20;  // 32 MiB per device
+
+__device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratchBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+unsigned char *g_noalloc_ptr[kMaxDevices];  // device address of the array, per device
+
+// The array's name in host code is only a stand-in; its device address comes
+// from cudaGetSymbolAddress, asked once per device with that device current.
+bpsf_status noalloc_scratch(int device, unsigned char **out) {
+    if (device < 0 || device >= kMaxDevices) return bpsf_fail(BPSF_EINVAL, "device %d out of range", device);
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_ptr[device]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p)
+            return bpsf_fail(BPSF_ECUDA, "cudaGetSymbolAddress(scratch): %s", cudaGetErrorString(e));
+        g_noalloc_ptr[device] = static_cast<unsigned char *>(p);
+    }
+    *out = g_noalloc_ptr[device];
+    return BPSF_OK;
+}
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+// Bytes of scratch a batch of n shots needs for this code (counters first).
+size_t noalloc_bytes(const bpsf_ctx *c, long long n) {
+    const size_t cap = (size_t)(n > 0 ? n : 1);
+    const size_t w = (size_t)(c->p.w > 0 ? c->p.w : 1), T = (size_t)(c->n_trials > 0 ? c->n_trials : 1);
+    return align256(sizeof(StreamCounters)) + align256(8 * cap) + align256(8 * cap) + align256(4 * cap) +
+           align256(8 * cap) + align256(4 * cap * w) + align256(4 * cap * c->Ws) + align256(4 * cap * T * c->Wn) +
+           align256(2 * cap * T);
+}
+
+}  // namespace
+
+extern "C" int64_t bpsf_noalloc_max_shots(const bpsf_ctx *c) {
+    if (!c) return -1;
+    long long lo = 0, hi = 1;
+    while (noalloc_bytes(c, hi) <= kNoallocScratchBytes) hi *= 2;
+    while (hi - lo > 1) {
+        const long long mid = (lo + hi) / 2;
+        if (noalloc_bytes(c, mid) <= kNoallocScratchBytes)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    return lo;
+}
+
+extern "C" bpsf_status bpsf_decode_noalloc(bpsf_ctx *c, int64_t n, const uint32_t *synd, int32_t ss, uint32_t *corr,
+                                           int32_t cs, uint8_t *conv, int16_t *iters, uint8_t *stage, void *stream) {
+    if (!c) return bpsf_fail(BPSF_EINVAL, "ctx is NULL");
+    if (n < 0) return bpsf_fail(BPSF_EINVAL, "n_shots must be >= 0");
+    if (n == 0) return BPSF_OK;
+    if (!synd || !corr || !conv || !iters) return bpsf_fail(BPSF_EINVAL, "NULL input or output pointer");
+    if (ss < c->Ws) return bpsf_fail(BPSF_EINVAL, "synd_stride_words %d < Ws = %d", ss, c->Ws);
+    if (cs < c->Wn) return bpsf_fail(BPSF_EINVAL, "corr_stride_words %d < Wn = %d", cs, c->Wn);
+    const size_t need = noalloc_bytes(c, n);
+    if (need > kNoallocScratchBytes)
+        return bpsf_fail(BPSF_EINVAL,
+                         "n_shots = %lld needs %zu bytes of scratch; the static scratch holds %zu bytes "
+                         "(at most %lld shots of this code per call)",
+                         (long long)n, need, kNoallocScratchBytes, (long long)bpsf_noalloc_max_shots(c));
+    cudaError_t e = cudaSetDevice(c->device);
+    if (e != cudaSuccess) return bpsf_fail(BPSF_ECUDA, "cudaSetDevice: %s", cudaGetErrorString(e));
+    unsigned char *base = nullptr;
+    bpsf_status st = noalloc_scratch(c->device, &base);
+    if (st != BPSF_OK) return st;
+    bpsf_plan pl;
+    bpsf_ctx *cs1[1] = {c};
+    st = bpsf_make_plan(cs1, 1, c->tune, false, &pl);
+    if (st != BPSF_OK) return st;
+    // Carve the counters and the records out of the array.
+    const size_t cap = (size_t)n;
+    const size_t w = (size_t)(c->p.w > 0 ? c->p.w : 1), T = (size_t)(c->n_trials > 0 ? c->n_trials : 1);
+    unsigned char *p = base;
+    StreamCounters *ctr = reinterpret_cast<StreamCounters *>(p);
+    p += align256(sizeof(StreamCounters));
+    Records rec;
+    rec.qseq = reinterpret_cast<unsigned long long *>(p);
+    p += align256(8 * cap);
+    rec.qshot = reinterpret_cast<long long *>(p);
+    p += align256(8 * cap);
+    rec.done = reinterpret_cast<unsigned *>(p);
+    p += align256(4 * cap);
+    rec.best = reinterpret_cast<unsigned long long *>(p);
+    p += align256(8 * cap);
+    rec.phi = reinterpret_cast<int32_t *>(p);
+    p += align256(4 * cap * w);
+    rec.synd = reinterpret_cast<uint32_t *>(p);
+    p += align256(4 * cap * c->Ws);
+    rec.corr = reinterpret_cast<uint32_t *>(p);
+    p += align256(4 * cap * T * c->Wn);
+    rec.iters = reinterpret_cast<int16_t *>(p);
+    rec.cap = (long long)cap;
+    // The array keeps the previous call's contents: the counters and the
+    // publication queue must start at zero.  Every other record field is
+    // written before it is read.
+    cudaStream_t s = (cudaStream_t)stream;
+    e = cudaMemsetAsync(ctr, 0, sizeof(StreamCounters), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(rec.qseq, 0, 8 * cap, s);
+    if (e != cudaSuccess) return bpsf_fail(BPSF_ECUDA, "cudaMemsetAsync: %s", cudaGetErrorString(e));
+    JobDev job{synd, corr, conv, iters, stage, n, ss, cs};
+    StreamDev sd = bpsf_make_stream(c, job, nullptr, 0);
+    sd.ctr = ctr;
+    sd.rec = rec;
+    LaunchArgs la{&sd, 1, pl.teams, pl.W, pl.S, pl.Q, kBpsfWaitNs};
+    launch_persistent(pl.variant, false, pl.grid, pl.block, pl.smem, la, stream);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return bpsf_fail(BPSF_ECUDA, "kernel launch: %s", cudaGetErrorString(e));
+    c->d_ctr_last = ctr;
+    c->last_launch_n = n;
+    return BPSF_OK;
+}

@@ -1,0 +1,78 @@
+"""bpsf_decode_noalloc against bpsf_decode through the C ABI.
+
+The no-allocation entry point serves callers that cannot allocate device
+memory while they decode (hard-deadline loops, runtimes that own the device
+heap, work recorded into a CUDA graph).  It must give exactly what the
+allocating entry point gives, call after call, although every call reuses the
+same static scratch array.  This file is collected last on purpose.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import synth  # noqa: E402
+from paper_2507_00254_gb300 import bpsf as B  # noqa: E402
+from paper_2507_00254_gb300 import build as libbuild  # noqa: E402
+from paper_2507_00254_gb300 import codes  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+def _inputs(dec, code, p, n, seed):
+    e = synth.bernoulli_bits(seed, 0, 0, n, code.N, p)
+    pad = np.zeros((n, 32 * dec.Wn), dtype=np.uint8)
+    pad[:, :code.N] = e
+    words = np.packbits(pad.reshape(n, dec.Wn * 4, 8), axis=-1, bitorder="little").reshape(n, dec.Wn * 4)
+    err = torch.from_numpy(words.view(np.int32).copy()).cuda()
+    return dec.syndrome(err)
+
+
+def _noalloc(dec, synd):
+    n = int(synd.shape[0])
+    out = dec.outputs(n)
+    sh = torch.cuda.current_stream().cuda_stream
+    B.bpsf_decode_noalloc(dec.handle, n, synd.data_ptr(), int(synd.shape[1]), out["corr"].data_ptr(), dec.Wn,
+                          out["conv"].data_ptr(), out["iters"].data_ptr(), out["stage"].data_ptr(), sh)
+    B.bpsf_sync(dec.handle, sh)
+    return out
+
+
+def _same(a, b):
+    for key in ("corr", "conv", "iters", "stage"):
+        assert torch.equal(a[key], b[key]), key
+
+
+@pytest.fixture(scope="module")
+def decoder():
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    libbuild.build()
+    c = codes.bb("bb144")
+    P = B.Params(max_iter=100, alpha=0.625, w=6, short_iter=20)
+    return c, B.Decoder(c.ptr, c.idx, c.M, c.N, np.full(c.N, 0.07), P)
+
+
+def test_noalloc_matches_decode_on_two_calls_in_a_row(decoder):
+    c, dec = decoder
+    cap = B.bpsf_noalloc_max_shots(dec.handle)
+    assert cap >= 10000
+    # A larger batch, then a smaller one over the scratch the first one left behind.
+    for n, seed in ((min(cap, 12000), 901), (3000, 902)):
+        synd = _inputs(dec, c, 0.07, n, seed)
+        ref = dec.decode(synd)
+        got = _noalloc(dec, synd)
+        _same(got, ref)
+        assert int((ref["stage"] == 1).sum()) > 0  # the trial records were exercised
+        w = dec.last_work()
+        assert w["initial_runs"] == n and w["failed_shots"] == int((ref["stage"] != 0).sum())
+
+
+def test_noalloc_rejects_batches_beyond_the_scratch(decoder):
+    c, dec = decoder
+    cap = B.bpsf_noalloc_max_shots(dec.handle)
+    synd = torch.zeros((1, dec.Ws), dtype=torch.int32, device="cuda")
+    out = dec.outputs(1)
+    with pytest.raises(B.BpsfError) as ei:
+        B.bpsf_decode_noalloc(dec.handle, cap + 1, synd.data_ptr(), dec.Ws, out["corr"].data_ptr(), dec.Wn,
+                              out["conv"].data_ptr(), out["iters"].data_ptr(), 0, 0)
+    assert ei.value.status == B.BPSF_EINVAL and "scratch" in str(ei.value)
