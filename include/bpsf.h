@@ -25,6 +25,9 @@
  *     reports errors the device found (timeouts, record overflow).
  *   - Every function returns a bpsf_status and never aborts or throws; on
  *     failure bpsf_last_error() gives a message for the calling thread.
+ *   - A context holds per-launch counters and workspace: decode calls on one
+ *     context must not overlap (one thread, one stream at a time).  Servers
+ *     keep their own device state and may run beside such calls.
  *   - Messages are FP32.  Each add and multiply is rounded on its own, in
  *     one fixed order (V2C and posterior sums fold from the channel LLR over
  *     the checks of a column in ascending check index), so results do not
@@ -225,17 +228,23 @@ bpsf_status bpsf_autotune(bpsf_ctx *ctx, double p_sample, int64_t n_sample, void
 /* Serving: continuous batching of a request stream (mixed codes).        */
 /* ---------------------------------------------------------------------- */
 
-typedef struct bpsf_server bpsf_server;
-
 /*
- * Serving configuration.
- *   max_inflight_shots  device slots for admitted shots, per code (admission
- *                       limit; a request that does not fit waits or gets
- *                       BPSF_EBUSY).
- *   blocks              persistent blocks of the serving kernel (0 = all SMs).
- *   idle_exit_us        the device loop exits after this long without work
- *                       (bounded wait; the next submit relaunches it).
- *   max_requests        request slots in flight (tickets not yet polled).
+ * A server keeps one persistent decode loop on the device over several codes
+ * (the paper's streaming setting: syndromes arrive one request at a time,
+ * Section VI).  Each code has an arena of max_inflight_shots device rows; a
+ * request takes consecutive rows and is admitted only when they are free
+ * (admission by device memory).  Shots of requests that arrive while others
+ * run join the same device work pool as slots free up; results are written
+ * to host-mapped rows and each request's completion is posted by the device.
+ * The device loop leaves after idle_exit_us without work and a host thread
+ * relaunches it when admitted work is pending, so no device wait is unbounded.
+ * While the loop runs it holds the SMs: other kernels on the same device wait.
+ *
+ *   max_inflight_shots  rows per code (default 65536).
+ *   blocks              persistent blocks of the loop (0 = as many as fit).
+ *   idle_exit_us        device idle time before the loop leaves (default 20000).
+ *   max_requests        requests admitted and not yet polled (default 4096).
+ *   flags               reserved, must be 0.
  */
 typedef struct {
     int64_t max_inflight_shots;
@@ -245,28 +254,34 @@ typedef struct {
     uint32_t flags;
 } bpsf_serve_cfg;
 
-/* Start a server over n_codes contexts (not owned; they must outlive it). */
+typedef struct bpsf_server bpsf_server;
+
+/* Start a server over n_codes contexts (1..16; not owned, they must outlive
+ * the server; all on the current device).  cfg is nullable (defaults). */
 bpsf_status bpsf_serve_start(bpsf_server **out, bpsf_ctx *const *codes, int32_t n_codes, const bpsf_serve_cfg *cfg);
 
 /*
- * Submit n shots of code index `code` (h_synd: n rows of that code's Ws
- * words, host memory, copied before return).  Blocks while the code's
- * device slots are full, up to timeout_us (0 = do not wait: BPSF_EBUSY).
- * On success *ticket identifies the request.  Thread-safe.
+ * Submit n shots of code index `code` (h_synd: n rows of that code's Ws words,
+ * host memory, copied to the device before return).  Waits while the code's
+ * rows or the request slots are full, up to timeout_us (<= 0: do not wait);
+ * then BPSF_EBUSY.  n larger than the arena is BPSF_EINVAL.  On success
+ * *ticket identifies the request.  Thread-safe.
  */
 bpsf_status bpsf_serve_submit(bpsf_server *s, int32_t code, int64_t n, const uint32_t *h_synd, int64_t timeout_us,
                               uint64_t *ticket);
 
 /*
- * Wait up to timeout_us for a request (BPSF_ETIMEOUT if not done), then copy
- * its results (Wn words per shot, converged bytes, int16 iterations; h_stage
- * nullable) and release the ticket.  Thread-safe.
+ * Wait up to timeout_us for a request (BPSF_ETIMEOUT if not done; the ticket
+ * stays valid), then copy its results (Wn words per shot, converged bytes,
+ * int16 iterations, stage bytes; each output pointer nullable), release the
+ * request's rows and the ticket.  Unknown tickets: BPSF_EINVAL.  Thread-safe.
  */
 bpsf_status bpsf_serve_poll(bpsf_server *s, uint64_t ticket, int64_t timeout_us, uint32_t *h_corr,
                             uint8_t *h_converged, int16_t *h_iters, uint8_t *h_stage);
 
-/* Stop accepting requests, let admitted ones finish, stop the device loop
- * and free the server.  Tickets not yet polled are lost. */
+/* Stop: new submits get BPSF_ECLOSED, admitted requests finish on the device
+ * (bounded wait), the device loop ends and the server is freed.  Results not
+ * yet polled are dropped.  Returns BPSF_ETIMEOUT if a device wait ran out. */
 bpsf_status bpsf_serve_stop(bpsf_server *s);
 
 /* ---------------------------------------------------------------------- */
@@ -316,6 +331,16 @@ bpsf_status bpsf_decode_debug(bpsf_ctx *ctx, int64_t n_shots, const uint32_t *d_
                               uint32_t *d_corr, int32_t corr_stride_words, uint8_t *d_converged, int16_t *d_iters,
                               uint8_t *d_stage, float *d_lout, uint16_t *d_flips, int32_t *d_phi,
                               uint32_t *d_trial_synd, uint8_t *d_trial_conv, int16_t *d_trial_iters, void *stream);
+
+/*
+ * Failure-detection self test (no paper counterpart).  Runs the trial sweep
+ * of one failed shot whose record is never published, so every device wait
+ * for it must give up after wait_us (1..10^7) instead of spinning forever;
+ * the kernel then records the timeout in its status word and ends normally.
+ * Synchronises `stream` and returns BPSF_ETIMEOUT when the bounded waits
+ * worked (BPSF_OK would mean a wait did not run).  Nothing faults or hangs.
+ */
+bpsf_status bpsf_selftest_wait(bpsf_ctx *ctx, int64_t wait_us, void *stream);
 
 /* Number of trials per failed shot (masks with popcount <= w_max). */
 int32_t bpsf_num_trials(const bpsf_ctx *ctx);

@@ -26,7 +26,7 @@ EXPORTS = (
     "bpsf_sync", "bpsf_get_tuning", "bpsf_set_tuning", "bpsf_autotune", "bpsf_serve_start", "bpsf_serve_submit",
     "bpsf_serve_poll", "bpsf_serve_stop", "bpsf_bb_code", "bpsf_phenom_code", "bpsf_syndrome", "bpsf_decode_debug",
     "bpsf_num_trials", "bpsf_last_work", "bpsf_status_str", "bpsf_last_error", "bpsf_decode_noalloc",
-    "bpsf_noalloc_max_shots",
+    "bpsf_noalloc_max_shots", "bpsf_selftest_wait",
 )
 
 
@@ -104,6 +104,7 @@ def lib():
         "bpsf_syndrome": ([vp, i64, vp, i32, vp, i32, vp], st),
         "bpsf_decode_debug": ([vp, i64, vp, i32, vp, i32, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp], st),
         "bpsf_num_trials": ([vp], i32),
+        "bpsf_selftest_wait": ([vp, i64, vp], st),
         "bpsf_last_work": ([vp, C.POINTER(bpsf_work)], st),
         "bpsf_status_str": ([st], C.c_char_p),
         "bpsf_last_error": ([], C.c_char_p),
@@ -209,6 +210,36 @@ def bpsf_last_work(h) -> bpsf_work:
     w = bpsf_work()
     check(lib().bpsf_last_work(h, C.byref(w)))
     return w
+
+
+def bpsf_selftest_wait(h, wait_us: int, stream) -> int:
+    """Run the bounded-wait self test; returns the raw status (BPSF_ETIMEOUT expected)."""
+    return int(lib().bpsf_selftest_wait(h, wait_us, stream))
+
+
+def bpsf_serve_start(handles, cfg: "bpsf_serve_cfg") -> int:
+    arr = (C.c_void_p * len(handles))(*handles)
+    s = C.c_void_p()
+    check(lib().bpsf_serve_start(C.byref(s), arr, len(handles), C.byref(cfg)))
+    return s.value
+
+
+def bpsf_serve_submit(s, code: int, n: int, h_synd, timeout_us: int) -> int:
+    t = C.c_uint64(0)
+    check(lib().bpsf_serve_submit(s, code, n, h_synd, timeout_us, C.byref(t)))
+    return t.value
+
+
+def bpsf_serve_poll(s, ticket: int, timeout_us: int, h_corr, h_conv, h_iters, h_stage) -> int:
+    """Returns the raw status so callers can tell BPSF_ETIMEOUT from errors."""
+    st = int(lib().bpsf_serve_poll(s, ticket, timeout_us, h_corr, h_conv, h_iters, h_stage))
+    if st not in (BPSF_OK, BPSF_ETIMEOUT):
+        check(st)
+    return st
+
+
+def bpsf_serve_stop(s) -> None:
+    check(lib().bpsf_serve_stop(s))
 
 
 def bpsf_bb_code(l: int, m: int, a_terms, b_terms, which: int = 0):
@@ -366,6 +397,46 @@ class Decoder:
         w = bpsf_last_work(self.handle)
         return dict(initial_runs=w.initial_runs, failed_shots=w.failed_shots, trial_runs=w.trial_runs,
                     iterations=w.iterations, edge_updates=w.edge_updates)
+
+
+class Server:
+    """Continuous-batching server over several decoders (one code each)."""
+
+    def __init__(self, decoders, max_inflight_shots=1 << 16, blocks=0, idle_exit_us=20000, max_requests=4096):
+        self.decoders = list(decoders)
+        cfg = bpsf_serve_cfg(max_inflight_shots, blocks, idle_exit_us, max_requests, 0)
+        self.handle = bpsf_serve_start([d.handle for d in self.decoders], cfg)
+
+    def submit(self, code: int, synd: np.ndarray, timeout_us: int = 10_000_000) -> int:
+        synd = np.ascontiguousarray(synd).view(np.uint32)
+        d = self.decoders[code]
+        if synd.ndim != 2 or synd.shape[1] != d.Ws:
+            raise ValueError("expected (n, %d) packed syndromes" % d.Ws)
+        return bpsf_serve_submit(self.handle, code, int(synd.shape[0]), _np_ptr(synd), timeout_us)
+
+    def poll(self, ticket: int, n: int, code: int, timeout_us: int = 10_000_000):
+        """Results of a request, or None if it is not done within timeout_us."""
+        d = self.decoders[code]
+        corr = np.zeros((n, d.Wn), dtype=np.uint32)
+        conv = np.zeros(n, dtype=np.uint8)
+        iters = np.zeros(n, dtype=np.int16)
+        stage = np.zeros(n, dtype=np.uint8)
+        st = bpsf_serve_poll(self.handle, ticket, timeout_us, _np_ptr(corr), _np_ptr(conv), _np_ptr(iters),
+                             _np_ptr(stage))
+        if st == BPSF_ETIMEOUT:
+            return None
+        return dict(corr=corr, conv=conv, iters=iters, stage=stage)
+
+    def stop(self):
+        h, self.handle = self.handle, None
+        if h:
+            bpsf_serve_stop(h)
+
+    def __del__(self):
+        try:
+            self.stop()
+        except Exception:
+            pass
 
 
 def decode_multi(decoders, synds, outs=None, stream=None, sync=True):

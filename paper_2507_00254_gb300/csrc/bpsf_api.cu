@@ -106,7 +106,8 @@ static int plan_smem(const bpsf_ctx *c, int vstride, int S, int teams, int Q) {
     return block_smem_bytes(c->M, c->N, c->P, c->Ws, vstride, S, teams, Q);
 }
 
-bpsf_status bpsf_make_plan(bpsf_ctx *const *codes, int n_codes, const bpsf_tuning &t, bool debug, bpsf_plan *out) {
+bpsf_status bpsf_make_plan(bpsf_ctx *const *codes, int n_codes, const bpsf_tuning &t, bool debug, bpsf_plan *out,
+                           bool shrink_slots) {
     const int W = t.warps_per_team, S = t.slots_per_team, B = t.warps_per_block;
     if (!(W == 1 || W == 2 || W == 4 || W == 8)) return bpsf_fail(BPSF_EINVAL, "warps_per_team must be 1, 2, 4 or 8");
     if (S < 1 || S > kMaxSlots) return bpsf_fail(BPSF_EINVAL, "slots_per_team must be in 1..%d", kMaxSlots);
@@ -128,16 +129,23 @@ bpsf_status bpsf_make_plan(bpsf_ctx *const *codes, int n_codes, const bpsf_tunin
     if (variant < 0) return bpsf_fail(BPSF_EINVAL, "no kernel variant for row degree %d, column degree %d", dc, dv);
     const int vstride = kernel_variant_dv(variant);
     const int Q = plan_queue(teams, S);
+    const bpsf_ctx *c0 = codes[0];
+    // Slots per team for each code: the tuned S, or (for mixed launches) the
+    // largest S' <= S that fits this code's block in shared memory.
     int smem = 0;
     for (int k = 0; k < n_codes; ++k) {
         if (codes[k]->vstride != vstride)
             return bpsf_fail(BPSF_EINVAL, "codes of one launch need the same column table width (%d vs %d)",
                              codes[k]->vstride, vstride);
-        smem = std::max(smem, plan_smem(codes[k], vstride, S, teams, Q));
+        int Sk = S;
+        while (shrink_slots && Sk > 1 && plan_smem(codes[k], vstride, Sk, teams, Q) > c0->smem_optin) --Sk;
+        const int need = plan_smem(codes[k], vstride, Sk, teams, Q);
+        if (need > c0->smem_optin)
+            return bpsf_fail(BPSF_EINVAL, "launch shape needs %d bytes of shared memory (limit %d)", need,
+                             c0->smem_optin);
+        out->S_code[k] = Sk;
+        smem = std::max(smem, need);
     }
-    const bpsf_ctx *c0 = codes[0];
-    if (smem > c0->smem_optin)
-        return bpsf_fail(BPSF_EINVAL, "launch shape needs %d bytes of shared memory (limit %d)", smem, c0->smem_optin);
     bpsf_status st = bpsf_ensure_kernel_attrs(variant, c0->smem_optin);
     if (st != BPSF_OK) return st;
     const int block = 32 * (B + 1);
@@ -417,8 +425,9 @@ StreamDev bpsf_make_stream(const bpsf_ctx *c, const JobDev &job, const DebugDev 
     return sd;
 }
 
-static void launch_plan(const bpsf_plan &pl, bool debug, const StreamDev *sds, int n, int grid, void *stream) {
-    LaunchArgs la{sds, n, pl.teams, pl.W, pl.S, pl.Q, kBpsfWaitNs};
+void bpsf_launch_plan(const bpsf_plan &pl, bool debug, StreamDev *sds, int n, int grid, void *stream) {
+    for (int k = 0; k < n; ++k) sds[k].S = pl.S_code[k];
+    LaunchArgs la{sds, n, pl.teams, pl.W, pl.Q, kBpsfWaitNs};
     launch_persistent(pl.variant, debug, grid, pl.block, pl.smem, la, stream);
 }
 
@@ -452,7 +461,7 @@ static bpsf_status decode_impl(bpsf_ctx *c, int64_t n, const uint32_t *synd, int
     if (st != BPSF_OK) return st;
     JobDev job{synd, corr, conv, iters, stage, n, ss, cs};
     StreamDev sd = bpsf_make_stream(c, job, dbg, 0);
-    launch_plan(pl, dbg != nullptr, &sd, 1, pl.grid, stream);
+    bpsf_launch_plan(pl, dbg != nullptr, &sd, 1, pl.grid, stream);
     e = cudaGetLastError();
     if (e != cudaSuccess) return bpsf_fail(BPSF_ECUDA, "kernel launch: %s", cudaGetErrorString(e));
     c->d_ctr_last = c->d_ctr;
@@ -528,7 +537,7 @@ extern "C" bpsf_status bpsf_decode_plain(bpsf_ctx *c, int64_t n, const uint32_t 
     st = bpsf_make_plan(cs1, 1, c->tune, false, &plB);
     if (st != BPSF_OK) return st;
     const int trials = std::max(c->n_trials, 1);
-    const int per_block = plB.teams * plB.S;
+    const int per_block = plB.teams * plB.S_code[0];
     const int gridB = std::max(1, std::min(plB.grid, (trials + per_block - 1) / per_block));
     StreamCounters preset;
     std::memset(&preset, 0, sizeof(preset));
@@ -543,7 +552,7 @@ extern "C" bpsf_status bpsf_decode_plain(bpsf_ctx *c, int64_t n, const uint32_t 
         if (e == cudaSuccess) e = cudaMemsetAsync(c->rec.qseq, 0, 8, s);
         if (e != cudaSuccess) return bpsf_fail(BPSF_ECUDA, "cudaMemsetAsync: %s", cudaGetErrorString(e));
         StreamDev sdA = bpsf_make_stream(c, job, nullptr, kNoTickets);
-        launch_plan(plA, false, &sdA, 1, 1, stream);
+        bpsf_launch_plan(plA, false, &sdA, 1, 1, stream);
         e = cudaMemcpyAsync(c->h_flag, conv + i, 1, cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaMemcpyAsync(c->h_ctr, c->d_ctr, sizeof(StreamCounters), cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -554,7 +563,7 @@ extern "C" bpsf_status bpsf_decode_plain(bpsf_ctx *c, int64_t n, const uint32_t 
             e = cudaMemcpyAsync(c->d_ctr, c->h_preset, sizeof(StreamCounters), cudaMemcpyHostToDevice, s);
             if (e != cudaSuccess) return bpsf_fail(BPSF_ECUDA, "cudaMemcpyAsync: %s", cudaGetErrorString(e));
             StreamDev sdB = bpsf_make_stream(c, job, nullptr, 0);
-            launch_plan(plB, false, &sdB, 1, gridB, stream);
+            bpsf_launch_plan(plB, false, &sdB, 1, gridB, stream);
             e = cudaMemcpyAsync(c->h_ctr, c->d_ctr, sizeof(StreamCounters), cudaMemcpyDeviceToHost, s);
             if (e == cudaSuccess) e = cudaStreamSynchronize(s);
             if (e != cudaSuccess) return bpsf_fail(BPSF_ECUDA, "plain trial sweep: %s", cudaGetErrorString(e));
@@ -634,13 +643,10 @@ extern "C" bpsf_status bpsf_decode_multi(int32_t n_jobs, const bpsf_job *jobs, v
     // Shape: the first context's tuning, shrunk until every code fits.
     bpsf_tuning t = c0->tune;
     bpsf_plan pl;
-    bpsf_status st = bpsf_make_plan(codes.data(), n_jobs, t, false, &pl);
-    while (st == BPSF_EINVAL && (t.slots_per_team > 1 || t.warps_per_block > t.warps_per_team)) {
-        if (t.slots_per_team > 1)
-            --t.slots_per_team;
-        else
-            t.warps_per_block -= t.warps_per_team;
-        st = bpsf_make_plan(codes.data(), n_jobs, t, false, &pl);
+    bpsf_status st = bpsf_make_plan(codes.data(), n_jobs, t, false, &pl, true);
+    while (st == BPSF_EINVAL && t.warps_per_block > t.warps_per_team) {
+        t.warps_per_block -= t.warps_per_team;
+        st = bpsf_make_plan(codes.data(), n_jobs, t, false, &pl, true);
     }
     if (st != BPSF_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
@@ -660,7 +666,7 @@ extern "C" bpsf_status bpsf_decode_multi(int32_t n_jobs, const bpsf_job *jobs, v
         c->last_launch_n = j.n_shots;
         c->d_ctr_last = c->d_ctr;
     }
-    launch_plan(pl, false, sds.data(), n_jobs, pl.grid, stream);
+    bpsf_launch_plan(pl, false, sds.data(), n_jobs, pl.grid, stream);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return bpsf_fail(BPSF_ECUDA, "kernel launch: %s", cudaGetErrorString(e));
     return BPSF_OK;
@@ -772,6 +778,46 @@ extern "C" bpsf_status bpsf_autotune(bpsf_ctx *c, double p_sample, int64_t n_sam
     }
     if (chosen) *chosen = best;
     return BPSF_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Bounded-wait self test: trial tickets of a record that is never published.
+// ---------------------------------------------------------------------------
+
+extern "C" bpsf_status bpsf_selftest_wait(bpsf_ctx *c, int64_t wait_us, void *stream) {
+    if (!c) return bpsf_fail(BPSF_EINVAL, "ctx is NULL");
+    if (wait_us < 1 || wait_us > 10000000) return bpsf_fail(BPSF_EINVAL, "wait_us must be in 1..10^7");
+    if (c->p.w <= 0) return bpsf_fail(BPSF_EINVAL, "the context has no trials (w = 0)");
+    cudaSetDevice(c->device);
+    bpsf_status st = bpsf_ensure_workspace(c, 1);
+    if (st != BPSF_OK) return st;
+    bpsf_plan pl;
+    bpsf_ctx *cs1[1] = {c};
+    st = bpsf_make_plan(cs1, 1, c->tune, false, &pl);
+    if (st != BPSF_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    // One failed shot is announced (rec_count = 1) but its queue entry is
+    // never written, so claimed tickets wait for it in vain.
+    StreamCounters preset;
+    std::memset(&preset, 0, sizeof(preset));
+    preset.shot_next = 1;
+    preset.init_done = 1;
+    preset.rec_count = 1;
+    *c->h_preset = preset;
+    cudaError_t e = cudaMemcpyAsync(c->d_ctr, c->h_preset, sizeof(StreamCounters), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->rec.qseq, 0, 8, s);
+    if (e != cudaSuccess) return bpsf_fail(BPSF_ECUDA, "self test set-up: %s", cudaGetErrorString(e));
+    // Outputs of the (never settled) shot go to the workspace's own rows.
+    JobDev job{c->rec.synd, c->rec.corr, reinterpret_cast<uint8_t *>(c->rec.done),
+               reinterpret_cast<int16_t *>(c->rec.done), nullptr, 1, c->Ws, c->Wn};
+    StreamDev sd = bpsf_make_stream(c, job, nullptr, 0);
+    for (int k = 0; k < 1; ++k) sd.S = pl.S_code[0];
+    LaunchArgs la{&sd, 1, pl.teams, pl.W, pl.Q, (unsigned long long)wait_us * 1000ull};
+    launch_persistent(pl.variant, false, 1, pl.block, pl.smem, la, stream);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return bpsf_fail(BPSF_ECUDA, "kernel launch: %s", cudaGetErrorString(e));
+    c->d_ctr_last = c->d_ctr;
+    return bpsf_sync(c, stream);
 }
 
 // ---------------------------------------------------------------------------

@@ -33,12 +33,15 @@ struct bpsf_ctx {
 // Launch plan of the persistent kernel for one or several codes.
 struct bpsf_plan {
     int variant = 0, teams = 0, W = 0, S = 0, Q = 0, block = 0, smem = 0, grid = 0;
+    int S_code[bpsf::kMaxStreams] = {0};  // slots per team for each code of the launch
 };
 
 bpsf_status bpsf_fail(bpsf_status s, const char *fmt, ...);
 bpsf_status bpsf_ensure_workspace(bpsf_ctx *c, long long n);
 bpsf_status bpsf_ensure_kernel_attrs(int variant, int smem_optin);
-bpsf_status bpsf_make_plan(bpsf_ctx *const *codes, int n_codes, const bpsf_tuning &t, bool debug, bpsf_plan *out);
+bpsf_status bpsf_make_plan(bpsf_ctx *const *codes, int n_codes, const bpsf_tuning &t, bool debug, bpsf_plan *out,
+                           bool shrink_slots = false);
+void bpsf_launch_plan(const bpsf_plan &pl, bool debug, bpsf::StreamDev *sds, int n, int grid, void *stream);
 bool bpsf_tuning_cache_lookup(const bpsf_ctx *c, bpsf_tuning *out);
 bpsf::StreamDev bpsf_make_stream(const bpsf_ctx *c, const bpsf::JobDev &job, const bpsf::DebugDev *dbg,
                                  unsigned flags);

@@ -117,14 +117,15 @@ struct StreamDev {
     DebugDev dbg;
     ServeDev serve;
     unsigned flags;  // kNoTickets, kServe
-    int pad;
+    int S;           // slots per team for this code
 };
 
-// Launch shape: `teams` teams of W warps, S slots each, plus one manager warp.
+// Launch shape: `teams` teams of W warps (slots per team set per stream),
+// plus one manager warp; Q ready-queue entries.
 struct LaunchArgs {
     const StreamDev *streams;
     int n_streams;
-    int teams, W, S, Q;
+    int teams, W, Q;
     unsigned long long wait_ns;  // bound on any device-side wait
 };
 

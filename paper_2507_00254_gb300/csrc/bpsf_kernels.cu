@@ -75,8 +75,9 @@ __device__ __forceinline__ void team_sync(int W, int bar_id) {
 
 struct BlockHdr {
     int stream, cmd;
-    volatile int exit;  // manager -> teams: leave the team loop
-    int pad[13];
+    volatile int exit;            // manager -> teams: leave the team loop
+    volatile unsigned heartbeat;  // manager passes; idle teams give up only if it stalls
+    int pad[12];
 };
 
 struct LayoutMem {
@@ -314,6 +315,7 @@ __device__ void team_loop(const StreamDev &sd, const LayoutMem &L, const TeamMem
     const CodeDev &cd = sd.code;
     const int Ws = cd.Ws;
     unsigned long long idle_since = 0;
+    unsigned last_beat = 0;
     for (;;) {
         if (wt == 0) {
             SlotState *ss = &T.st[lane < S ? lane : 0];
@@ -328,9 +330,15 @@ __device__ void team_loop(const StreamDev &sd, const LayoutMem &L, const TeamMem
                 if (hdr->exit) {
                     ex = 1;
                 } else {
+                    // Never wait forever: give up only if the manager has made
+                    // no pass for twice the bound on any of its own waits.
                     const unsigned long long now = globaltimer_ns();
-                    if (idle_since == 0) idle_since = now;
-                    if (now - idle_since > 4 * wait_ns) ex = 1;  // the manager is gone: never wait forever
+                    const unsigned beat = hdr->heartbeat;
+                    if (idle_since == 0 || beat != last_beat) {
+                        idle_since = now;
+                        last_beat = beat;
+                    }
+                    if (now - idle_since > 2 * wait_ns) ex = 1;
                     __nanosleep(100);
                 }
             } else {
@@ -408,14 +416,15 @@ __device__ __forceinline__ long long row_of(const StreamDev &sd, long long shot)
 }
 
 // One shot's final output is out: serving counts it against its request.
+// Serving outputs live in host-mapped memory, hence system-scope fences.
 __device__ __forceinline__ void shot_complete(const StreamDev &sd, long long row) {
     if (!(sd.flags & kServe)) return;
-    const int rq = sd.serve.row_req[row];
-    __threadfence();
+    const int rq = *reinterpret_cast<volatile int *>(sd.serve.row_req + row);
+    __threadfence_system();
     const unsigned left = atomicSub(&sd.serve.req_left[rq], 1u) - 1u;
     if (left == 0u) {
         __threadfence_system();
-        st_release_sys_u32(sd.serve.req_flag + rq, sd.serve.req_tag[rq]);
+        st_release_sys_u32(sd.serve.req_flag + rq, *reinterpret_cast<volatile unsigned *>(sd.serve.req_tag + rq));
     }
 }
 
@@ -709,6 +718,7 @@ __device__ void manager_loop(const StreamDev &sd, unsigned char *team_base, int 
     for (;;) {
         bool progress = false;
         bool busy = false;
+        if (lane == 0) hdr->heartbeat = hdr->heartbeat + 1u;
         // (A) write out finished slots.
         for (int g0 = 0; g0 < nslots; g0 += 32) {
             const int g = g0 + lane;
@@ -816,7 +826,7 @@ __device__ void manager_loop(const StreamDev &sd, unsigned char *team_base, int 
 struct KernelParams {
     StreamDev streams[kMaxStreams];
     int n_streams;
-    int teams, W, S, Q;
+    int teams, W, Q;
     unsigned long long wait_ns;
 };
 
@@ -825,7 +835,7 @@ __global__ void __launch_bounds__(512, 1) bpsf_persistent(const __grid_constant_
     extern __shared__ __align__(16) unsigned char smem[];
     BlockHdr *hdr = reinterpret_cast<BlockHdr *>(smem);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int teams = kp.teams, W = kp.W, S = kp.S, Q = kp.Q;
+    const int teams = kp.teams, W = kp.W, Q = kp.Q;
     int cur = -1;
     bool waiting = false;
     unsigned long long wait_start = 0;
@@ -901,6 +911,7 @@ __global__ void __launch_bounds__(512, 1) bpsf_persistent(const __grid_constant_
         waiting = false;
         const StreamDev &sd = kp.streams[sid];
         const CodeDev &cd = sd.code;
+        const int S = sd.S;
         const LayoutOffsets lo = layout_offsets(cd.M, cd.N, DVS, cd.P);
         unsigned char *lay = smem + kBlockHeaderBytes;
         if (sid != cur) {
@@ -928,7 +939,10 @@ __global__ void __launch_bounds__(512, 1) bpsf_persistent(const __grid_constant_
             ctl->iters = 0;
             ctl->exit = 0;
         }
-        if (tid == 0) hdr->exit = 0;
+        if (tid == 0) {
+            hdr->exit = 0;
+            hdr->heartbeat = 0u;
+        }
         __syncthreads();
         LayoutMem L;
         L.row_deg = lay + lo.row_deg;
@@ -1004,7 +1018,6 @@ void launch_persistent(int variant, bool debug, int grid, int block, int smem, c
     kp.n_streams = args.n_streams;
     kp.teams = args.teams;
     kp.W = args.W;
-    kp.S = args.S;
     kp.Q = args.Q;
     kp.wait_ns = args.wait_ns;
     kernel_fn(variant, debug)<<<grid, block, smem, (cudaStream_t)stream>>>(kp);

@@ -128,8 +128,7 @@ extern "C" bpsf_status bpsf_decode_noalloc(bpsf_ctx *c, int64_t n, const uint32_
     StreamDev sd = bpsf_make_stream(c, job, nullptr, 0);
     sd.ctr = ctr;
     sd.rec = rec;
-    LaunchArgs la{&sd, 1, pl.teams, pl.W, pl.S, pl.Q, kBpsfWaitNs};
-    launch_persistent(pl.variant, false, pl.grid, pl.block, pl.smem, la, stream);
+    bpsf_launch_plan(pl, false, &sd, 1, pl.grid, stream);
     e = cudaGetLastError();
     if (e != cudaSuccess) return bpsf_fail(BPSF_ECUDA, "kernel launch: %s", cudaGetErrorString(e));
     c->d_ctr_last = ctr;
