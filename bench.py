@@ -177,7 +177,7 @@ def run_gpu(args, rank, world, pool):
     from paper_2507_00254_gb300 import build as libbuild
     libbuild.build()
     from paper_2507_00254_gb300 import bpsf as B
-    from paper_2507_00254_gb300 import codes, harness
+    from paper_2507_00254_gb300 import codes, harness, replicas
 
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     dist = None
@@ -185,7 +185,7 @@ def run_gpu(args, rank, world, pool):
         import torch.distributed as dist
         dist.init_process_group("nccl")
     n = args.shots_per_p
-    shot0 = rank * n  # weak scaling: each rank decodes its own 10^6 shots per p
+    shot0 = replicas.shot_offset(rank, n)  # weak scaling: each replica decodes its own 10^6 shots per p
     c = codes.bb(CODE)
     Pm = B.Params(**PARAMS)
     decs = [B.Decoder(c.ptr, c.idx, c.M, c.N, np.full(c.N, p), Pm) for p in P_LIST]
@@ -237,13 +237,9 @@ def run_gpu(args, rank, world, pool):
         B.bpsf_sync(d.handle, stream.cuda_stream)
         work.append(d.last_work())
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    ms = float(np.mean(step_ms))
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = replicas.max_over_ranks(float(np.mean(step_ms)), dist, device="cuda")
     shots_step = n * len(P_LIST)
-    value = shots_step * world / (ms / 1e3)
+    value = replicas.job_rate(shots_step, world, ms / 1e3)
 
     # Roofline of the persistent kernel (the one launch per step).
     edge_updates = sum(w["edge_updates"] for w in work)
@@ -319,6 +315,12 @@ def run_gpu(args, rank, world, pool):
     h2d = len(P_LIST) * n * 3 * 4
     d2h = len(P_LIST) * n * (5 * 4 + 1 + 2 + 1)
 
+    extras = {}
+    if rank == 0 and not args.no_extras:
+        extras["phenomenological"] = run_phenom(B, codes, torch)
+        extras["mixed_one_launch"] = run_mixed(B, codes, torch)
+        extras["served"] = run_served(B, codes, torch, (1e4, 1e5, 1e6, 3.16e6, 1e7), seconds=args.serve_seconds)
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu = pool.apply(oracle_sample, (args.cpu_shots,)) if pool else oracle_sample(args.cpu_shots)
@@ -353,10 +355,166 @@ def run_gpu(args, rank, world, pool):
                      "trial_runs_per_step": sum(w["trial_runs"] for w in work)},
             "input_gen_s": t_gen, "wall_timed_s": t_wall,
         }
+        line.update(extras)
         print(json.dumps(line), flush=True)
     if dist:
         dist.barrier()
         dist.destroy_process_group()
+
+
+
+# --------------------------------------------------------------------------
+# Secondary measurements (reported beside the headline line)
+# --------------------------------------------------------------------------
+
+SERVE_BB = ("bb72", "bb90", "bb108", "bb144", "bb288")
+PHENOM_PARAMS = dict(max_iter=200, alpha=0.625, w=5, w_max=0, short_iter=30, select=0)
+
+
+def _packed_errors_dev(torch, bits, wn):
+    n, nb = bits.shape
+    pad = np.zeros((n, 32 * wn), dtype=np.uint8)
+    pad[:, :nb] = bits
+    w = np.packbits(pad.reshape(n, wn * 4, 8), axis=-1, bitorder="little").reshape(n, wn * 4)
+    return torch.from_numpy(w.view(np.int32).copy()).cuda()
+
+
+def run_phenom(B, codes, torch, n=100_000):
+    """12-round phenomenological [[144,12,12]] (864 x 2592), p = q in {0.002, 0.004}, batched."""
+    import synth
+    c = codes.phenom("bb144")
+    out = {}
+    for k, p in enumerate((0.002, 0.004)):
+        d = B.Decoder(c.ptr, c.idx, c.M, c.N, np.full(c.N, p), B.Params(**PHENOM_PARAMS))
+        e = synth.phenom_error_bits(synth.SEEDS["bb144_phenom"][k], 0, 0, n, 144, 72, 12, p, p)
+        synd = d.syndrome(_packed_errors_dev(torch, e, d.Wn))
+        o = d.outputs(n)
+        d.decode(synd, out=o)  # warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        d.decode(synd, out=o)
+        dt = time.perf_counter() - t0
+        w = d.last_work()
+        st = np.bincount(o["stage"].cpu().numpy(), minlength=3).tolist()
+        out[str(p)] = {"shots": n, "shots_per_s": n / dt, "ms": dt * 1e3, "edge_updates_per_s": w["edge_updates"] / dt,
+                       "stage_counts": st, "tuning": list(d.tuning)}
+        d.close()
+    return out
+
+
+def run_mixed(B, codes, torch):
+    """[[72]], [[90]], [[108]], [[144]], [[288]] at p = 0.05, counts U{10^3..10^5}, in ONE launch."""
+    import synth
+    counts = synth.uniform_ints(synth.SEEDS["mixed_counts"], 0, len(SERVE_BB), 1000, 100000)
+    decs, synds = [], []
+    for k, name in enumerate(SERVE_BB):
+        c = codes.bb(name)
+        d = B.Decoder(c.ptr, c.idx, c.M, c.N, np.full(c.N, 0.05), B.Params(**PARAMS))
+        e = synth.bernoulli_bits(synth.SEEDS["mixed"][k], 0, 0, int(counts[k]), c.N, 0.05)
+        synds.append(d.syndrome(_packed_errors_dev(torch, e, d.Wn)))
+        decs.append(d)
+    outs = B.decode_multi(decs, synds)  # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    B.decode_multi(decs, synds, outs=outs)
+    dt = time.perf_counter() - t0
+    total = int(counts.sum())
+    res = {"codes": list(SERVE_BB), "shots": [int(x) for x in counts], "shots_per_s": total / dt, "ms": dt * 1e3}
+    for d in decs:
+        d.close()
+    return res
+
+
+def run_served(B, codes, torch, loads, seconds=2.0, pool_shots=8192):
+    """Poisson request stream over the five BB codes (p = 0.05) and the 12-round
+    phenomenological [[144]] model (p = q = 0.003), through bpsf_serve_*.
+    Requests carry b = max(1, load / 20000) shots so the host submits at most
+    ~2*10^4 requests/s; latency is request arrival -> results in host memory."""
+    import queue
+    import threading
+    import synth
+    decs, pools = [], []
+    for k, name in enumerate(SERVE_BB):
+        c = codes.bb(name)
+        d = B.Decoder(c.ptr, c.idx, c.M, c.N, np.full(c.N, 0.05), B.Params(**PARAMS))
+        e = synth.bernoulli_bits(synth.SEEDS["serve"], 1 + k, 0, pool_shots, c.N, 0.05)
+        pools.append(d.syndrome(_packed_errors_dev(torch, e, d.Wn)).cpu().numpy().view(np.uint32))
+        decs.append(d)
+    c = codes.phenom("bb144")
+    d = B.Decoder(c.ptr, c.idx, c.M, c.N, np.full(c.N, 0.003), B.Params(**PHENOM_PARAMS))
+    e = synth.phenom_error_bits(synth.SEEDS["serve"], 9, 0, pool_shots // 4, 144, 72, 12, 0.003, 0.003)
+    pools.append(d.syndrome(_packed_errors_dev(torch, e, d.Wn)).cpu().numpy().view(np.uint32))
+    decs.append(d)
+    # Plain per-shot latency on the same mix (launch -> flag readback per shot).
+    lat_plain = []
+    for k, dk in enumerate(decs):
+        for i in range(40):
+            s = torch.from_numpy(pools[k][i:i + 1].view(np.int32).copy()).cuda()
+            o = dk.outputs(1)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            dk.decode(s, out=o, plain=True)
+            lat_plain.append(time.perf_counter() - t0)
+    lat_plain = np.array(lat_plain) * 1e3
+    srv = B.Server(decs, max_inflight_shots=1 << 16, idle_exit_us=50000)
+    results = []
+    try:
+        for li, load in enumerate(loads):
+            b = max(1, int(load // 20000))
+            rate = load / b
+            n_req = max(50, int(rate * seconds))
+            arrivals = synth.poisson_arrivals(synth.SEEDS["serve"], 100 + li, n_req, rate)
+            which = synth.uniform_choice(synth.SEEDS["serve"], 200 + li, n_req, len(decs))
+            q = queue.Queue()
+            done = np.zeros(n_req)
+            errs = []
+
+            def poller():
+                try:
+                    for _ in range(n_req):
+                        i, t, k, nn = q.get()
+                        r = srv.poll(t, nn, k, timeout_us=60_000_000)
+                        done[i] = time.perf_counter()
+                        if r is None:
+                            errs.append("timeout")
+                except Exception as exc:
+                    errs.append(repr(exc))
+
+            th = threading.Thread(target=poller, daemon=True)
+            th.start()
+            cursor = [0] * len(decs)
+            t0 = time.perf_counter()
+            shots = 0
+            for i in range(n_req):
+                k = int(which[i])
+                nn = b if k < len(SERVE_BB) else max(1, b // 4)
+                pool = pools[k]
+                a = cursor[k] % (pool.shape[0] - nn)
+                cursor[k] += nn
+                target = t0 + arrivals[i]
+                while True:
+                    now = time.perf_counter()
+                    if now >= target:
+                        break
+                    if target - now > 2e-4:
+                        time.sleep(target - now - 1e-4)
+                t = srv.submit(k, pool[a:a + nn])
+                q.put((i, t, k, nn))
+                shots += nn
+            th.join(timeout=120)
+            lat = (done - (t0 + arrivals)) * 1e3
+            span = done.max() - t0
+            results.append({"offered_shots_per_s": load, "shots_per_request": b, "requests": n_req,
+                            "achieved_shots_per_s": shots / span, "p50_ms": float(np.percentile(lat, 50)),
+                            "p99_ms": float(np.percentile(lat, 99)), "p999_ms": float(np.percentile(lat, 99.9)),
+                            "errors": errs[:3]})
+    finally:
+        srv.stop()
+    for dk in decs:
+        dk.close()
+    return {"mix": list(SERVE_BB) + ["bb144_phenom12"], "loads": results,
+            "plain_per_shot_ms": {"p50": float(np.percentile(lat_plain, 50)), "p99": float(np.percentile(lat_plain, 99)),
+                                  "p999": float(np.percentile(lat_plain, 99.9))}}
 
 
 def main():
@@ -372,6 +530,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--autotune", type=int, default=1)
     ap.add_argument("--traffic-bytes", type=float, default=0.0)
+    ap.add_argument("--no-extras", action="store_true", help="skip the served / phenomenological / mixed lines")
+    ap.add_argument("--serve-seconds", type=float, default=2.0)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
