@@ -428,10 +428,9 @@ def run_mixed(B, codes, torch):
 def run_served(B, codes, torch, loads, seconds=2.0, pool_shots=8192):
     """Poisson request stream over the five BB codes (p = 0.05) and the 12-round
     phenomenological [[144]] model (p = q = 0.003), through bpsf_serve_*.
-    Requests carry b = max(1, load / 20000) shots so the host submits at most
-    ~2*10^4 requests/s; latency is request arrival -> results in host memory."""
-    import queue
-    import threading
+    Requests carry b = max(1, load / 10000) shots (at most ~10^4 requests/s);
+    the trace is replayed open loop by the library (bpsf_serve_replay), and
+    latency is scheduled arrival -> results ready in host memory."""
     import synth
     decs, pools = [], []
     for k, name in enumerate(SERVE_BB):
@@ -458,61 +457,51 @@ def run_served(B, codes, torch, loads, seconds=2.0, pool_shots=8192):
     lat_plain = np.array(lat_plain) * 1e3
     srv = B.Server(decs, max_inflight_shots=1 << 16, idle_exit_us=50000)
     results = []
+    # Closed loop: one single-shot request at a time (submit -> results in host memory).
+    closed = {}
+    for k in range(len(decs)):
+        ts = []
+        for i in range(200):
+            t1 = time.perf_counter()
+            srv.poll(srv.submit(k, pools[k][i:i + 1]), 1, k)
+            ts.append(time.perf_counter() - t1)
+        ts = np.array(ts[20:]) * 1e3
+        closed[(list(SERVE_BB) + ["bb144_phenom12"])[k]] = [float(np.percentile(ts, 50)), float(np.percentile(ts, 99))]
     try:
         for li, load in enumerate(loads):
-            b = max(1, int(load // 20000))
+            b = max(1, int(load // 10000))
             rate = load / b
             n_req = max(50, int(rate * seconds))
             arrivals = synth.poisson_arrivals(synth.SEEDS["serve"], 100 + li, n_req, rate)
             which = synth.uniform_choice(synth.SEEDS["serve"], 200 + li, n_req, len(decs))
-            q = queue.Queue()
-            done = np.zeros(n_req)
-            errs = []
-
-            def poller():
-                try:
-                    for _ in range(n_req):
-                        i, t, k, nn = q.get()
-                        r = srv.poll(t, nn, k, timeout_us=60_000_000)
-                        done[i] = time.perf_counter()
-                        if r is None:
-                            errs.append("timeout")
-                except Exception as exc:
-                    errs.append(repr(exc))
-
-            th = threading.Thread(target=poller, daemon=True)
-            th.start()
+            reqs = []
             cursor = [0] * len(decs)
-            t0 = time.perf_counter()
-            shots = 0
             for i in range(n_req):
                 k = int(which[i])
                 nn = b if k < len(SERVE_BB) else max(1, b // 4)
                 pool = pools[k]
                 a = cursor[k] % (pool.shape[0] - nn)
                 cursor[k] += nn
-                target = t0 + arrivals[i]
-                while True:
-                    now = time.perf_counter()
-                    if now >= target:
-                        break
-                    if target - now > 2e-4:
-                        time.sleep(target - now - 1e-4)
-                t = srv.submit(k, pool[a:a + nn])
-                q.put((i, t, k, nn))
-                shots += nn
-            th.join(timeout=120)
-            lat = (done - (t0 + arrivals)) * 1e3
-            span = done.max() - t0
+                reqs.append(pool[a:a + nn])
+            lat_s, span = srv.replay(arrivals, which, reqs)
+            lat = lat_s * 1e3
+            shots = sum(x.shape[0] for x in reqs)
+            errs = []
+            per_code = {}
+            for k in range(len(decs)):
+                sel = lat[which == k]
+                if sel.size:
+                    per_code[(list(SERVE_BB) + ["bb144_phenom12"])[k]] = [float(np.percentile(sel, 50)),
+                                                                        float(np.percentile(sel, 99))]
             results.append({"offered_shots_per_s": load, "shots_per_request": b, "requests": n_req,
                             "achieved_shots_per_s": shots / span, "p50_ms": float(np.percentile(lat, 50)),
                             "p99_ms": float(np.percentile(lat, 99)), "p999_ms": float(np.percentile(lat, 99.9)),
-                            "errors": errs[:3]})
+                            "per_code_p50_p99_ms": per_code, "errors": errs[:3]})
     finally:
         srv.stop()
     for dk in decs:
         dk.close()
-    return {"mix": list(SERVE_BB) + ["bb144_phenom12"], "loads": results,
+    return {"mix": list(SERVE_BB) + ["bb144_phenom12"], "loads": results, "closed_loop_p50_p99_ms": closed,
             "plain_per_shot_ms": {"p50": float(np.percentile(lat_plain, 50)), "p99": float(np.percentile(lat_plain, 99)),
                                   "p999": float(np.percentile(lat_plain, 99.9))}}
 
@@ -532,6 +521,7 @@ def main():
     ap.add_argument("--traffic-bytes", type=float, default=0.0)
     ap.add_argument("--no-extras", action="store_true", help="skip the served / phenomenological / mixed lines")
     ap.add_argument("--serve-seconds", type=float, default=2.0)
+    ap.add_argument("--only-served", action="store_true", help="run only the served measurement (diagnostics)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -539,6 +529,14 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.only_served:
+        import torch
+        from paper_2507_00254_gb300 import build as libbuild
+        libbuild.build()
+        from paper_2507_00254_gb300 import bpsf as B
+        from paper_2507_00254_gb300 import codes
+        print(json.dumps(run_served(B, codes, torch, (1e4, 1e5, 1e6, 3.16e6, 1e7), seconds=args.serve_seconds)))
         return
     # Input generation and the oracle baseline use a spawn pool created before CUDA starts.
     ctx = mp.get_context("spawn")

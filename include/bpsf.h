@@ -279,6 +279,18 @@ bpsf_status bpsf_serve_submit(bpsf_server *s, int32_t code, int64_t n, const uin
 bpsf_status bpsf_serve_poll(bpsf_server *s, uint64_t ticket, int64_t timeout_us, uint32_t *h_corr,
                             uint8_t *h_converged, int16_t *h_iters, uint8_t *h_stage);
 
+/*
+ * Open-loop replay of a request trace (latency measurement, thread-safe
+ * against other clients).  Request i (code[i], n_shots[i] rows at synd[i])
+ * is submitted at arrival_s[i] seconds (non-decreasing) after the call
+ * starts, by one host thread, while another polls every outstanding request;
+ * results are dropped.  On return latency_s[i] = completion time - scheduled
+ * arrival of request i, and *span_s (nullable) = time from the start to the
+ * last completion.
+ */
+bpsf_status bpsf_serve_replay(bpsf_server *s, int64_t n_req, const double *arrival_s, const int32_t *code,
+                              const int64_t *n_shots, const uint32_t *const *synd, double *latency_s, double *span_s);
+
 /* Stop: new submits get BPSF_ECLOSED, admitted requests finish on the device
  * (bounded wait), the device loop ends and the server is freed.  Results not
  * yet polled are dropped.  Returns BPSF_ETIMEOUT if a device wait ran out. */

@@ -26,7 +26,7 @@ EXPORTS = (
     "bpsf_sync", "bpsf_get_tuning", "bpsf_set_tuning", "bpsf_autotune", "bpsf_serve_start", "bpsf_serve_submit",
     "bpsf_serve_poll", "bpsf_serve_stop", "bpsf_bb_code", "bpsf_phenom_code", "bpsf_syndrome", "bpsf_decode_debug",
     "bpsf_num_trials", "bpsf_last_work", "bpsf_status_str", "bpsf_last_error", "bpsf_decode_noalloc",
-    "bpsf_noalloc_max_shots", "bpsf_selftest_wait",
+    "bpsf_noalloc_max_shots", "bpsf_selftest_wait", "bpsf_serve_replay",
 )
 
 
@@ -99,6 +99,7 @@ def lib():
         "bpsf_serve_submit": ([vp, i32, i64, vp, i64, C.POINTER(C.c_uint64)], st),
         "bpsf_serve_poll": ([vp, C.c_uint64, i64, vp, vp, vp, vp], st),
         "bpsf_serve_stop": ([vp], st),
+        "bpsf_serve_replay": ([vp, i64, vp, vp, vp, vp, vp, C.POINTER(C.c_double)], st),
         "bpsf_bb_code": ([i32, i32, i32, vp, vp, i32, vp, vp, i32, vp, vp, i64, C.POINTER(i64)], st),
         "bpsf_phenom_code": ([i32, i32, vp, vp, i32, vp, vp, i64, C.POINTER(i64)], st),
         "bpsf_syndrome": ([vp, i64, vp, i32, vp, i32, vp], st),
@@ -426,6 +427,20 @@ class Server:
         if st == BPSF_ETIMEOUT:
             return None
         return dict(corr=corr, conv=conv, iters=iters, stage=stage)
+
+    def replay(self, arrival_s, codes, synds):
+        """Open-loop replay; returns (per-request latency in s, span in s)."""
+        n = len(arrival_s)
+        arr = np.ascontiguousarray(arrival_s, dtype=np.float64)
+        cd = np.ascontiguousarray(codes, dtype=np.int32)
+        synds = [np.ascontiguousarray(x).view(np.uint32) for x in synds]
+        ns = np.array([x.shape[0] for x in synds], dtype=np.int64)
+        ptrs = (C.c_void_p * n)(*[x.ctypes.data for x in synds])
+        lat = np.zeros(n, dtype=np.float64)
+        span = C.c_double(0.0)
+        check(lib().bpsf_serve_replay(self.handle, n, _np_ptr(arr), _np_ptr(cd), _np_ptr(ns), ptrs, _np_ptr(lat),
+                                      C.byref(span)))
+        return lat, span.value
 
     def stop(self):
         h, self.handle = self.handle, None

@@ -106,8 +106,7 @@ static int plan_smem(const bpsf_ctx *c, int vstride, int S, int teams, int Q) {
     return block_smem_bytes(c->M, c->N, c->P, c->Ws, vstride, S, teams, Q);
 }
 
-bpsf_status bpsf_make_plan(bpsf_ctx *const *codes, int n_codes, const bpsf_tuning &t, bool debug, bpsf_plan *out,
-                           bool shrink_slots) {
+static bpsf_status check_shape(const bpsf_tuning &t) {
     const int W = t.warps_per_team, S = t.slots_per_team, B = t.warps_per_block;
     if (!(W == 1 || W == 2 || W == 4 || W == 8)) return bpsf_fail(BPSF_EINVAL, "warps_per_team must be 1, 2, 4 or 8");
     if (S < 1 || S > kMaxSlots) return bpsf_fail(BPSF_EINVAL, "slots_per_team must be in 1..%d", kMaxSlots);
@@ -115,35 +114,56 @@ bpsf_status bpsf_make_plan(bpsf_ctx *const *codes, int n_codes, const bpsf_tunin
         return bpsf_fail(BPSF_EINVAL, "warps_per_block must be a multiple of warps_per_team, at most %d",
                          kMaxComputeWarps);
     if (t.blocks_per_sm < 0) return bpsf_fail(BPSF_EINVAL, "blocks_per_sm must be >= 0");
-    const int teams = B / W;
+    return BPSF_OK;
+}
+
+bpsf_status bpsf_make_plan(bpsf_ctx *const *codes, int n_codes, const bpsf_tuning *tunes, bool debug,
+                           bpsf_plan *out, bool shrink) {
     // One kernel variant must fit every code of the launch.
     bool all_regular = true;
-    int dc = 0, dv = 0;
+    int dc = 0, dv = 0, B = 0, bps = 0;
     for (int k = 0; k < n_codes; ++k) {
+        bpsf_status st = check_shape(tunes[k]);
+        if (st != BPSF_OK) return st;
         all_regular = all_regular && codes[k]->regular && codes[k]->dc_max == codes[0]->dc_max &&
                       codes[k]->dv_max == codes[0]->dv_max;
         dc = std::max(dc, codes[k]->dc_max);
         dv = std::max(dv, codes[k]->dv_max);
+        B = std::max(B, tunes[k].warps_per_block);
+        if (tunes[k].blocks_per_sm > 0) bps = bps > 0 ? std::min(bps, tunes[k].blocks_per_sm) : tunes[k].blocks_per_sm;
     }
     const int variant = kernel_variant(all_regular ? -dc : dc, std::max(dv, 1));
     if (variant < 0) return bpsf_fail(BPSF_EINVAL, "no kernel variant for row degree %d, column degree %d", dc, dv);
     const int vstride = kernel_variant_dv(variant);
-    const int Q = plan_queue(teams, S);
     const bpsf_ctx *c0 = codes[0];
-    // Slots per team for each code: the tuned S, or (for mixed launches) the
-    // largest S' <= S that fits this code's block in shared memory.
+    int Q = 32;
+    for (int k = 0; k < n_codes; ++k)
+        Q = std::max(Q, plan_queue(tunes[k].warps_per_block / tunes[k].warps_per_team, tunes[k].slots_per_team));
+    // Team shape per code: its own tuning; when shrinking, fewer slots per
+    // team first, then fewer teams, until the code's block fits.
     int smem = 0;
     for (int k = 0; k < n_codes; ++k) {
         if (codes[k]->vstride != vstride)
             return bpsf_fail(BPSF_EINVAL, "codes of one launch need the same column table width (%d vs %d)",
                              codes[k]->vstride, vstride);
-        int Sk = S;
-        while (shrink_slots && Sk > 1 && plan_smem(codes[k], vstride, Sk, teams, Q) > c0->smem_optin) --Sk;
-        const int need = plan_smem(codes[k], vstride, Sk, teams, Q);
+        const int W = tunes[k].warps_per_team;
+        int S = tunes[k].slots_per_team, teams = tunes[k].warps_per_block / W;
+        while (shrink && plan_smem(codes[k], vstride, S, teams, Q) > c0->smem_optin) {
+            if (S > 1)
+                --S;
+            else if (teams > 1)
+                --teams;
+            else
+                break;
+        }
+        const int need = plan_smem(codes[k], vstride, S, teams, Q);
         if (need > c0->smem_optin)
             return bpsf_fail(BPSF_EINVAL, "launch shape needs %d bytes of shared memory (limit %d)", need,
                              c0->smem_optin);
-        out->S_code[k] = Sk;
+        if (W > 1 && teams > kMaxNamedTeams) return bpsf_fail(BPSF_EINVAL, "too many multi-warp teams");
+        out->S_code[k] = S;
+        out->W_code[k] = W;
+        out->teams_code[k] = teams;
         smem = std::max(smem, need);
     }
     bpsf_status st = bpsf_ensure_kernel_attrs(variant, c0->smem_optin);
@@ -152,12 +172,9 @@ bpsf_status bpsf_make_plan(bpsf_ctx *const *codes, int n_codes, const bpsf_tunin
     int occ = 0;
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, persistent_kernel_ptr(variant, debug), block, smem);
     if (e != cudaSuccess) return bpsf_fail(BPSF_ECUDA, "occupancy query: %s", cudaGetErrorString(e));
-    if (t.blocks_per_sm > 0) occ = std::min(occ, t.blocks_per_sm);
+    if (bps > 0) occ = std::min(occ, bps);
     if (occ <= 0) return bpsf_fail(BPSF_EINVAL, "launch shape does not fit on an SM");
     out->variant = variant;
-    out->teams = teams;
-    out->W = W;
-    out->S = S;
     out->Q = Q;
     out->block = block;
     out->smem = smem;
@@ -177,7 +194,7 @@ static bpsf_tuning default_tuning(bpsf_ctx *c) {
             bpsf_tuning t{Wc[k], Sc[k], B, 0};
             bpsf_plan pl;
             bpsf_ctx *cs[1] = {c};
-            if (bpsf_make_plan(cs, 1, t, false, &pl) == BPSF_OK) return t;
+            if (bpsf_make_plan(cs, 1, &t, false, &pl) == BPSF_OK) return t;
         }
     }
     return bpsf_tuning{1, 1, 1, 0};
@@ -426,8 +443,12 @@ StreamDev bpsf_make_stream(const bpsf_ctx *c, const JobDev &job, const DebugDev 
 }
 
 void bpsf_launch_plan(const bpsf_plan &pl, bool debug, StreamDev *sds, int n, int grid, void *stream) {
-    for (int k = 0; k < n; ++k) sds[k].S = pl.S_code[k];
-    LaunchArgs la{sds, n, pl.teams, pl.W, pl.Q, kBpsfWaitNs};
+    for (int k = 0; k < n; ++k) {
+        sds[k].S = pl.S_code[k];
+        sds[k].W = pl.W_code[k];
+        sds[k].teams = pl.teams_code[k];
+    }
+    LaunchArgs la{sds, n, pl.Q, kBpsfWaitNs};
     launch_persistent(pl.variant, debug, grid, pl.block, pl.smem, la, stream);
 }
 
@@ -450,7 +471,7 @@ static bpsf_status decode_impl(bpsf_ctx *c, int64_t n, const uint32_t *synd, int
     cudaSetDevice(c->device);
     bpsf_plan pl;
     bpsf_ctx *cs1[1] = {c};
-    st = bpsf_make_plan(cs1, 1, c->tune, dbg != nullptr, &pl);
+    st = bpsf_make_plan(cs1, 1, &c->tune, dbg != nullptr, &pl);
     if (st != BPSF_OK) return st;
     st = bpsf_ensure_workspace(c, n);
     if (st != BPSF_OK) return st;
@@ -531,13 +552,13 @@ extern "C" bpsf_status bpsf_decode_plain(bpsf_ctx *c, int64_t n, const uint32_t 
     // Launch A: one block, one team, one slot, the initial run of one shot.
     bpsf_plan plA, plB;
     bpsf_tuning tA{c->tune.warps_per_team, 1, c->tune.warps_per_team, 0};
-    st = bpsf_make_plan(cs1, 1, tA, false, &plA);
+    st = bpsf_make_plan(cs1, 1, &tA, false, &plA);
     if (st != BPSF_OK) return st;
     // Launch B: the shot's trials spread over blocks of the tuned shape.
-    st = bpsf_make_plan(cs1, 1, c->tune, false, &plB);
+    st = bpsf_make_plan(cs1, 1, &c->tune, false, &plB);
     if (st != BPSF_OK) return st;
     const int trials = std::max(c->n_trials, 1);
-    const int per_block = plB.teams * plB.S_code[0];
+    const int per_block = plB.teams_code[0] * plB.S_code[0];
     const int gridB = std::max(1, std::min(plB.grid, (trials + per_block - 1) / per_block));
     StreamCounters preset;
     std::memset(&preset, 0, sizeof(preset));
@@ -640,14 +661,11 @@ extern "C" bpsf_status bpsf_decode_multi(int32_t n_jobs, const bpsf_job *jobs, v
     }
     bpsf_ctx *c0 = codes[0];
     cudaSetDevice(c0->device);
-    // Shape: the first context's tuning, shrunk until every code fits.
-    bpsf_tuning t = c0->tune;
+    // Each code keeps its own team shape (shrunk if its block does not fit).
+    std::vector<bpsf_tuning> tunes(n_jobs);
+    for (int k = 0; k < n_jobs; ++k) tunes[k] = codes[k]->tune;
     bpsf_plan pl;
-    bpsf_status st = bpsf_make_plan(codes.data(), n_jobs, t, false, &pl, true);
-    while (st == BPSF_EINVAL && t.warps_per_block > t.warps_per_team) {
-        t.warps_per_block -= t.warps_per_team;
-        st = bpsf_make_plan(codes.data(), n_jobs, t, false, &pl, true);
-    }
+    bpsf_status st = bpsf_make_plan(codes.data(), n_jobs, tunes.data(), false, &pl, true);
     if (st != BPSF_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
     std::vector<StreamDev> sds(n_jobs);
@@ -686,7 +704,7 @@ extern "C" bpsf_status bpsf_set_tuning(bpsf_ctx *c, const bpsf_tuning *t) {
     if (!c || !t) return bpsf_fail(BPSF_EINVAL, "NULL argument");
     bpsf_plan pl;
     bpsf_ctx *cs1[1] = {c};
-    bpsf_status st = bpsf_make_plan(cs1, 1, *t, false, &pl);
+    bpsf_status st = bpsf_make_plan(cs1, 1, t, false, &pl);
     if (st != BPSF_OK) return st;
     c->tune = *t;
     return BPSF_OK;
@@ -749,7 +767,7 @@ extern "C" bpsf_status bpsf_autotune(bpsf_ctx *c, double p_sample, int64_t n_sam
                 if (B % W) continue;
                 if (W > 1 && S > 4) continue;
                 bpsf_plan pl;
-                if (bpsf_make_plan(cs1, 1, t, false, &pl) != BPSF_OK) continue;
+                if (bpsf_make_plan(cs1, 1, &t, false, &pl) != BPSF_OK) continue;
                 c->tune = t;
                 float ms_min = 1e30f;
                 for (int rep = 0; rep < 3 && st == BPSF_OK; ++rep) {
@@ -793,7 +811,7 @@ extern "C" bpsf_status bpsf_selftest_wait(bpsf_ctx *c, int64_t wait_us, void *st
     if (st != BPSF_OK) return st;
     bpsf_plan pl;
     bpsf_ctx *cs1[1] = {c};
-    st = bpsf_make_plan(cs1, 1, c->tune, false, &pl);
+    st = bpsf_make_plan(cs1, 1, &c->tune, false, &pl);
     if (st != BPSF_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
     // One failed shot is announced (rec_count = 1) but its queue entry is
@@ -811,8 +829,10 @@ extern "C" bpsf_status bpsf_selftest_wait(bpsf_ctx *c, int64_t wait_us, void *st
     JobDev job{c->rec.synd, c->rec.corr, reinterpret_cast<uint8_t *>(c->rec.done),
                reinterpret_cast<int16_t *>(c->rec.done), nullptr, 1, c->Ws, c->Wn};
     StreamDev sd = bpsf_make_stream(c, job, nullptr, 0);
-    for (int k = 0; k < 1; ++k) sd.S = pl.S_code[0];
-    LaunchArgs la{&sd, 1, pl.teams, pl.W, pl.Q, (unsigned long long)wait_us * 1000ull};
+    sd.S = pl.S_code[0];
+    sd.W = pl.W_code[0];
+    sd.teams = pl.teams_code[0];
+    LaunchArgs la{&sd, 1, pl.Q, (unsigned long long)wait_us * 1000ull};
     launch_persistent(pl.variant, false, 1, pl.block, pl.smem, la, stream);
     e = cudaGetLastError();
     if (e != cudaSuccess) return bpsf_fail(BPSF_ECUDA, "kernel launch: %s", cudaGetErrorString(e));

@@ -32,15 +32,20 @@ struct bpsf_ctx {
 
 // Launch plan of the persistent kernel for one or several codes.
 struct bpsf_plan {
-    int variant = 0, teams = 0, W = 0, S = 0, Q = 0, block = 0, smem = 0, grid = 0;
-    int S_code[bpsf::kMaxStreams] = {0};  // slots per team for each code of the launch
+    int variant = 0, Q = 0, block = 0, smem = 0, grid = 0;
+    int S_code[bpsf::kMaxStreams] = {0};      // slots per team, per code of the launch
+    int W_code[bpsf::kMaxStreams] = {0};      // warps per team, per code
+    int teams_code[bpsf::kMaxStreams] = {0};  // teams per block, per code
 };
 
 bpsf_status bpsf_fail(bpsf_status s, const char *fmt, ...);
 bpsf_status bpsf_ensure_workspace(bpsf_ctx *c, long long n);
 bpsf_status bpsf_ensure_kernel_attrs(int variant, int smem_optin);
-bpsf_status bpsf_make_plan(bpsf_ctx *const *codes, int n_codes, const bpsf_tuning &t, bool debug, bpsf_plan *out,
-                           bool shrink_slots = false);
+// Plan one launch over n_codes codes; tunes[k] is code k's team shape (a
+// single tuning for a one-code launch).  With shrink, a code whose block does
+// not fit gets fewer slots per team, then fewer teams.
+bpsf_status bpsf_make_plan(bpsf_ctx *const *codes, int n_codes, const bpsf_tuning *tunes, bool debug,
+                           bpsf_plan *out, bool shrink = false);
 void bpsf_launch_plan(const bpsf_plan &pl, bool debug, bpsf::StreamDev *sds, int n, int grid, void *stream);
 bool bpsf_tuning_cache_lookup(const bpsf_ctx *c, bpsf_tuning *out);
 bpsf::StreamDev bpsf_make_stream(const bpsf_ctx *c, const bpsf::JobDev &job, const bpsf::DebugDev *dbg,

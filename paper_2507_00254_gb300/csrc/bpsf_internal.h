@@ -9,6 +9,7 @@ constexpr int kMaxW = 16;         // largest |Phi|
 constexpr int kMaxSlots = 32;     // work items per team
 constexpr int kMaxStreams = 16;   // codes per launch
 constexpr int kMaxComputeWarps = 15;  // plus one manager warp: <= 512 threads per block
+constexpr int kMaxNamedTeams = 15;    // named barriers 1..15 for multi-warp teams
 constexpr int kDVP = 4;           // column entries stored per variable for dv <= 4 codes
 
 // Device error bits (StreamCounters::status).
@@ -96,15 +97,14 @@ struct DebugDev {
 };
 
 // Serving: shots carry global sequence numbers g; shot g uses arena row
-// g % rows.  The host publishes rows (copies syndromes, then raises
-// `published`); the device reports each request once all its shots are out.
+// g % rows.  The host copies a request's syndromes into its rows and then,
+// on the same copy stream, the new published count (so the count never runs
+// ahead of the rows); the device posts g + 1 to the row's completion word
+// once the shot's results are in the host-mapped output rows.
 struct ServeDev {
-    volatile long long *published;   // shots published for this code (host-mapped)
+    volatile long long *published;   // shots published for this code (device memory)
     volatile int *stop;              // host asks the loop to end (host-mapped)
-    int *row_req;                    // rows: request slot of each arena row
-    unsigned int *req_left;          // request slots: shots not yet finished
-    unsigned int *req_tag;           // request slots: value to post when done
-    volatile unsigned int *req_flag; // request slots: completion posts (host-mapped)
+    volatile unsigned *row_done;     // rows: (g + 1) once the shot's results are out (host-mapped)
     long long rows;                  // arena rows
     long long idle_ns;               // leave the loop after this long without work
 };
@@ -117,15 +117,16 @@ struct StreamDev {
     DebugDev dbg;
     ServeDev serve;
     unsigned flags;  // kNoTickets, kServe
-    int S;           // slots per team for this code
+    int S, W, teams; // team shape for this code: teams of W warps with S slots each
+    int pad;
 };
 
-// Launch shape: `teams` teams of W warps (slots per team set per stream),
-// plus one manager warp; Q ready-queue entries.
+// Launch: the team shape is set per stream (StreamDev::S, W, teams); each
+// block has one manager warp besides; Q ready-queue entries.
 struct LaunchArgs {
     const StreamDev *streams;
     int n_streams;
-    int teams, W, Q;
+    int Q;
     unsigned long long wait_ns;  // bound on any device-side wait
 };
 

@@ -55,7 +55,7 @@ __device__ __forceinline__ void st_release_sys_u32(volatile unsigned *p, unsigne
     asm volatile("st.release.sys.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-__device__ __forceinline__ long long ld_acquire_sys_s64(volatile long long *p) {
+__device__ __forceinline__ long long ld_acquire_sys_s64(const volatile long long *p) {
     long long v;
     asm volatile("ld.acquire.sys.global.s64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
     return v;
@@ -415,17 +415,13 @@ __device__ __forceinline__ long long row_of(const StreamDev &sd, long long shot)
     return (sd.flags & kServe) ? (shot % sd.serve.rows) : shot;
 }
 
-// One shot's final output is out: serving counts it against its request.
-// Serving outputs live in host-mapped memory, hence system-scope fences.
-__device__ __forceinline__ void shot_complete(const StreamDev &sd, long long row) {
+// One shot's final output is out: when serving, post it to the row's
+// completion word (the outputs live in host-mapped memory, hence the
+// system-scope fence before the release).
+__device__ __forceinline__ void shot_complete(const StreamDev &sd, long long row, long long shot) {
     if (!(sd.flags & kServe)) return;
-    const int rq = *reinterpret_cast<volatile int *>(sd.serve.row_req + row);
     __threadfence_system();
-    const unsigned left = atomicSub(&sd.serve.req_left[rq], 1u) - 1u;
-    if (left == 0u) {
-        __threadfence_system();
-        st_release_sys_u32(sd.serve.req_flag + rq, *reinterpret_cast<volatile unsigned *>(sd.serve.req_tag + rq));
-    }
+    st_release_sys_u32(sd.serve.row_done + row, (unsigned)(shot + 1));
 }
 
 // Lane-parallel write-out of finished slots that need no warp cooperation:
@@ -449,7 +445,7 @@ __device__ __forceinline__ void finalize_simple(const StreamDev &sd, TeamMem T, 
         job.iters[row] = (int16_t)(conv ? iter : cd.max_iter);
         if (job.stage) job.stage[row] = conv ? 0 : 2;
         mg.init_local += 1;
-        shot_complete(sd, row);
+        shot_complete(sd, row, shot);
         return;
     }
     // Trial run: undo the flip (Algorithm 1) and take part in the selection.
@@ -495,7 +491,7 @@ __device__ __forceinline__ void finalize_simple(const StreamDev &sd, TeamMem T, 
             job.iters[row] = __ldcg(sd.rec.iters + (long long)row * C + kw);
             if (job.stage) job.stage[row] = 1;
         }
-        shot_complete(sd, row);
+        shot_complete(sd, row, shot);
     }
 }
 
@@ -714,7 +710,6 @@ __device__ void manager_loop(const StreamDev &sd, unsigned char *team_base, int 
     const int qstride = qentry_bytes(cd.Ws);
     const int nslots = teams * S;
     MgrState mg{0, 0, 0u, 0u};
-    unsigned long long idle_since = 0;
     for (;;) {
         bool progress = false;
         bool busy = false;
@@ -788,17 +783,10 @@ __device__ void manager_loop(const StreamDev &sd, unsigned char *team_base, int 
                 const bool occ = g < nslots && *vstate(&T.st[s]) != kSlotEmpty;
                 if (__any_sync(FULLMASK, occ)) any_slot = true;
             }
-            if (!any_slot) {
-                if (!(sd.flags & kServe)) break;
-                // Serving: stay for idle_ns after the last work, or until asked to stop.
-                const unsigned long long now = globaltimer_ns();
-                if (idle_since == 0) idle_since = now;
-                if (*sd.serve.stop || now - idle_since > (unsigned long long)sd.serve.idle_ns) break;
-                __nanosleep(200);
-                continue;
-            }
+            // Nothing left for this code: hand the block back, which then
+            // waits across all codes (serving) or for other blocks' trials.
+            if (!any_slot) break;
         }
-        if (progress) idle_since = 0;
         if (!progress) __nanosleep(32);
     }
     // Flush counters and release the teams.
@@ -826,7 +814,7 @@ __device__ void manager_loop(const StreamDev &sd, unsigned char *team_base, int 
 struct KernelParams {
     StreamDev streams[kMaxStreams];
     int n_streams;
-    int teams, W, Q;
+    int Q;
     unsigned long long wait_ns;
 };
 
@@ -835,7 +823,7 @@ __global__ void __launch_bounds__(512, 1) bpsf_persistent(const __grid_constant_
     extern __shared__ __align__(16) unsigned char smem[];
     BlockHdr *hdr = reinterpret_cast<BlockHdr *>(smem);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int teams = kp.teams, W = kp.W, Q = kp.Q;
+    const int Q = kp.Q;
     int cur = -1;
     bool waiting = false;
     unsigned long long wait_start = 0;
@@ -911,7 +899,7 @@ __global__ void __launch_bounds__(512, 1) bpsf_persistent(const __grid_constant_
         waiting = false;
         const StreamDev &sd = kp.streams[sid];
         const CodeDev &cd = sd.code;
-        const int S = sd.S;
+        const int S = sd.S, W = sd.W, teams = sd.teams;
         const LayoutOffsets lo = layout_offsets(cd.M, cd.N, DVS, cd.P);
         unsigned char *lay = smem + kBlockHeaderBytes;
         if (sid != cur) {
@@ -1016,8 +1004,6 @@ void launch_persistent(int variant, bool debug, int grid, int block, int smem, c
     KernelParams kp;
     for (int k = 0; k < args.n_streams; ++k) kp.streams[k] = args.streams[k];
     kp.n_streams = args.n_streams;
-    kp.teams = args.teams;
-    kp.W = args.W;
     kp.Q = args.Q;
     kp.wait_ns = args.wait_ns;
     kernel_fn(variant, debug)<<<grid, block, smem, (cudaStream_t)stream>>>(kp);

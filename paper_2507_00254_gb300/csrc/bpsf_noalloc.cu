@@ -92,7 +92,7 @@ extern "C" bpsf_status bpsf_decode_noalloc(bpsf_ctx *c, int64_t n, const uint32_
     if (st != BPSF_OK) return st;
     bpsf_plan pl;
     bpsf_ctx *cs1[1] = {c};
-    st = bpsf_make_plan(cs1, 1, c->tune, false, &pl);
+    st = bpsf_make_plan(cs1, 1, &c->tune, false, &pl);
     if (st != BPSF_OK) return st;
     // Carve the counters and the records out of the array.
     const size_t cap = (size_t)n;

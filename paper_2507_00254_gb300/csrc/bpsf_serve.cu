@@ -3,17 +3,18 @@
 //
 // Each code owns an arena of `rows` shot rows.  A request of n shots takes n
 // consecutive rows of its code's ring (admission by device memory: a request
-// waits until rows are free).  Submitting copies the syndromes into the
-// device arena, notes each row's request, and raises the code's published
-// shot count in host-mapped memory.  The persistent kernel (the batched
-// kernel with kServe streams) claims published shots as slots free up, so
-// requests that arrive while others run join the same device work pool; trial
-// tickets of failed shots keep priority over new shots.  The kernel writes
-// results into host-mapped output rows and, when the last shot of a request
-// is out, posts the request's tag to its completion flag.  Polling waits for
-// that flag, copies the rows out and releases them (rows are released in
-// order).  The kernel leaves after idle_exit_us without work; a host pump
-// thread relaunches it whenever admitted work is unfinished.
+// waits until rows are free).  Submitting stages the syndromes in pinned
+// memory and enqueues, on one copy stream, the copy of those rows into the
+// device arena followed by the copy of the code's new published shot count,
+// so the count never runs ahead of the rows (no host synchronisation).  The
+// persistent kernel (the batched kernel with kServe streams) claims published
+// shots as slots free up, so requests that arrive while others run join the
+// same device work pool; trial tickets of failed shots keep priority over new
+// shots.  The kernel writes results into host-mapped output rows and then
+// posts g + 1 to the row's completion word.  Polling waits for those words,
+// copies the rows out and releases them (rows are released in order).  The
+// kernel leaves after idle_exit_us without work; a host pump thread
+// relaunches it whenever admitted work is unfinished.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -39,27 +40,29 @@ size_t a16(size_t x) { return (x + 15) & ~size_t(15); }
 struct SrvCode {
     bpsf_ctx *ctx = nullptr;
     long long rows = 0;
-    uint32_t *d_synd = nullptr;                  // rows x Ws, device
-    void *h_out = nullptr;                       // mapped output rows
+    uint32_t *d_synd = nullptr;                      // rows x Ws, device arena
+    uint32_t *h_stage = nullptr;                     // rows x Ws, pinned staging
+    long long *d_pub = nullptr;                      // published shot count (device)
+    long long *h_pub_stage = nullptr;                // per request slot: the count to copy (pinned)
+    void *h_out = nullptr;                           // mapped output rows
     uint32_t *h_corr = nullptr, *m_corr = nullptr;
     uint8_t *h_conv = nullptr, *m_conv = nullptr;
     int16_t *h_iters = nullptr, *m_iters = nullptr;
-    uint8_t *h_stage = nullptr, *m_stage = nullptr;
-    int *h_row_req = nullptr, *m_row_req = nullptr;  // mapped: request slot of each row
-    long long *h_pub = nullptr, *m_pub = nullptr;    // mapped: published shot count
+    uint8_t *h_stage8 = nullptr, *m_stage8 = nullptr;
+    unsigned *h_done = nullptr, *m_done = nullptr;   // mapped: completion word per row
     StreamCounters *d_ctr = nullptr;
     void *d_rec = nullptr;
     Records rec{};
-    long long next_g = 0;                        // next global shot number
-    long long released = 0;                      // shots below this have free rows
-    std::map<long long, long long> polled;       // polled requests not yet released: g0 -> n
+    long long next_g = 0;                            // next global shot number
+    long long released = 0;                          // shots below this have free rows
+    std::map<long long, long long> polled;           // polled requests not yet released: g0 -> n
 };
 
 struct SrvReq {
     int code = -1;
     long long g0 = 0, n = 0;
+    long long checked = 0;  // rows known to be done (from the start of the request)
     uint64_t ticket = 0;
-    unsigned tag = 0;
     bool live = false;
 };
 
@@ -68,16 +71,11 @@ struct SrvReq {
 struct bpsf_server {
     int device = 0, n_codes = 0, max_req = 0, grid = 0;
     SrvCode codes[kMaxStreams];
-    unsigned *d_req_left = nullptr;                       // device: shots left per request slot
-    unsigned *h_left = nullptr;                           // pinned staging for d_req_left
-    unsigned *h_req_tag = nullptr, *m_req_tag = nullptr;  // mapped
-    unsigned *h_req_flag = nullptr, *m_req_flag = nullptr;  // mapped, written by the device
-    int *h_stop = nullptr, *m_stop = nullptr;             // mapped
+    int *h_stop = nullptr, *m_stop = nullptr;  // mapped
     std::vector<SrvReq> reqs;
     std::vector<int> free_slots;
     std::map<uint64_t, int> by_ticket;
     uint64_t next_ticket = 1;
-    unsigned next_tag = 1;
     cudaStream_t kstream = nullptr, cstream = nullptr;
     cudaEvent_t kdone = nullptr;
     bool launched = false;
@@ -88,10 +86,9 @@ struct bpsf_server {
     std::condition_variable cv;
     std::thread pump;
     std::atomic<bool> quit{false}, closing{false};
-    std::atomic<int> unfinished{0};  // admitted requests whose flag has not been seen
 };
 
-// Relaunch the persistent kernel if it has left and admitted work is pending.
+// Relaunch the persistent kernel if it has left (the caller holds mu).
 static bpsf_status ensure_running(bpsf_server *s) {
     if (s->launched) {
         const cudaError_t q = cudaEventQuery(s->kdone);
@@ -107,8 +104,18 @@ static bpsf_status ensure_running(bpsf_server *s) {
     return BPSF_OK;
 }
 
-static bool request_done(const bpsf_server *s, int q) {
-    return *reinterpret_cast<volatile unsigned *>(s->h_req_flag + q) == s->reqs[q].tag;
+// True once every shot of request q has posted its completion word; advances
+// the request's cursor over rows already seen done.
+static bool request_done(bpsf_server *s, int q) {
+    SrvReq &r = s->reqs[q];
+    SrvCode &sc = s->codes[r.code];
+    const volatile unsigned *done = sc.h_done;
+    while (r.checked < r.n) {
+        const long long g = r.g0 + r.checked;
+        if (done[g % sc.rows] != (unsigned)(g + 1)) return false;
+        ++r.checked;
+    }
+    return true;
 }
 
 static void pump_loop(bpsf_server *s) {
@@ -117,13 +124,8 @@ static void pump_loop(bpsf_server *s) {
         std::this_thread::sleep_for(std::chrono::microseconds(50));
         std::lock_guard<std::mutex> lk(s->mu);
         bool pending = false;
-        int unf = 0;
-        for (int q = 0; q < s->max_req; ++q)
-            if (s->reqs[q].live && !request_done(s, q)) {
-                pending = true;
-                ++unf;
-            }
-        s->unfinished.store(unf);
+        for (int q = 0; q < s->max_req && !pending; ++q)
+            if (s->reqs[q].live && !request_done(s, q)) pending = true;
         if (pending) ensure_running(s);
     }
 }
@@ -132,14 +134,13 @@ static void free_server(bpsf_server *s) {
     for (int k = 0; k < s->n_codes; ++k) {
         SrvCode &c = s->codes[k];
         if (c.d_synd) cudaFree(c.d_synd);
+        if (c.h_stage) cudaFreeHost(c.h_stage);
+        if (c.d_pub) cudaFree(c.d_pub);
+        if (c.h_pub_stage) cudaFreeHost(c.h_pub_stage);
         if (c.h_out) cudaFreeHost(c.h_out);
         if (c.d_ctr) cudaFree(c.d_ctr);
         if (c.d_rec) cudaFree(c.d_rec);
     }
-    if (s->d_req_left) cudaFree(s->d_req_left);
-    if (s->h_left) cudaFreeHost(s->h_left);
-    if (s->h_req_tag) cudaFreeHost(s->h_req_tag);
-    if (s->h_req_flag) cudaFreeHost(s->h_req_flag);
     if (s->h_stop) cudaFreeHost(s->h_stop);
     if (s->kdone) cudaEventDestroy(s->kdone);
     if (s->kstream) cudaStreamDestroy(s->kstream);
@@ -186,15 +187,11 @@ extern "C" bpsf_status bpsf_serve_start(bpsf_server **out, bpsf_ctx *const *code
     s->max_req = c.max_requests;
     s->idle_ns = (long long)c.idle_exit_us * 1000;
     cudaSetDevice(s->device);
-    // One launch shape for all codes: the first code's tuning, slots per team
-    // shrunk per code to fit, fewer warps if still needed.
+    // Each code keeps its own team shape (shrunk if its block does not fit).
     std::vector<bpsf_ctx *> cs(codes, codes + n_codes);
-    bpsf_tuning t = codes[0]->tune;
-    bpsf_status st = bpsf_make_plan(cs.data(), n_codes, t, false, &s->plan, true);
-    while (st == BPSF_EINVAL && t.warps_per_block > t.warps_per_team) {
-        t.warps_per_block -= t.warps_per_team;
-        st = bpsf_make_plan(cs.data(), n_codes, t, false, &s->plan, true);
-    }
+    std::vector<bpsf_tuning> tunes(n_codes);
+    for (int k = 0; k < n_codes; ++k) tunes[k] = codes[k]->tune;
+    bpsf_status st = bpsf_make_plan(cs.data(), n_codes, tunes.data(), false, &s->plan, true);
     if (st != BPSF_OK) {
         delete s;
         return st;
@@ -204,10 +201,6 @@ extern "C" bpsf_status bpsf_serve_start(bpsf_server **out, bpsf_ctx *const *code
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->kstream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->cstream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->kdone, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaMalloc((void **)&s->d_req_left, 4 * (size_t)s->max_req);
-    if (e == cudaSuccess) e = cudaMallocHost((void **)&s->h_left, 4 * (size_t)s->max_req);
-    if (e == cudaSuccess) e = host_mapped(&s->h_req_tag, &s->m_req_tag, 4 * (size_t)s->max_req);
-    if (e == cudaSuccess) e = host_mapped(&s->h_req_flag, &s->m_req_flag, 4 * (size_t)s->max_req);
     if (e == cudaSuccess) e = host_mapped(&s->h_stop, &s->m_stop, 64);
     for (int k = 0; k < n_codes && e == cudaSuccess; ++k) {
         SrvCode &sc = s->codes[k];
@@ -216,10 +209,14 @@ extern "C" bpsf_status bpsf_serve_start(bpsf_server **out, bpsf_ctx *const *code
         sc.rows = c.max_inflight_shots;
         const size_t R = (size_t)sc.rows;
         e = cudaMalloc((void **)&sc.d_synd, 4 * R * x->Ws);
+        if (e == cudaSuccess) e = cudaMallocHost((void **)&sc.h_stage, 4 * R * x->Ws);
+        if (e == cudaSuccess) e = cudaMalloc((void **)&sc.d_pub, 64);
+        if (e == cudaSuccess) e = cudaMemset(sc.d_pub, 0, 64);
+        if (e == cudaSuccess) e = cudaMallocHost((void **)&sc.h_pub_stage, 8 * (size_t)s->max_req);
         if (e != cudaSuccess) break;
-        // Mapped outputs and bookkeeping: corr | conv | iters | stage | row_req | published.
+        // Mapped outputs: corr | conv | iters | stage | completion words.
         const size_t o_corr = 0, o_conv = a16(o_corr + 4 * R * x->Wn), o_it = a16(o_conv + R), o_st = a16(o_it + 2 * R),
-                     o_rq = a16(o_st + R), o_pub = a16(o_rq + 4 * R), total = a16(o_pub + 64);
+                     o_dn = a16(o_st + R), total = a16(o_dn + 4 * R);
         unsigned char *h = nullptr, *m = nullptr;
         e = host_mapped(&h, &m, total);
         if (e != cudaSuccess) break;
@@ -230,12 +227,10 @@ extern "C" bpsf_status bpsf_serve_start(bpsf_server **out, bpsf_ctx *const *code
         sc.m_conv = m + o_conv;
         sc.h_iters = (int16_t *)(h + o_it);
         sc.m_iters = (int16_t *)(m + o_it);
-        sc.h_stage = h + o_st;
-        sc.m_stage = m + o_st;
-        sc.h_row_req = (int *)(h + o_rq);
-        sc.m_row_req = (int *)(m + o_rq);
-        sc.h_pub = (long long *)(h + o_pub);
-        sc.m_pub = (long long *)(m + o_pub);
+        sc.h_stage8 = h + o_st;
+        sc.m_stage8 = m + o_st;
+        sc.h_done = (unsigned *)(h + o_dn);
+        sc.m_done = (unsigned *)(m + o_dn);
         e = cudaMalloc((void **)&sc.d_ctr, sizeof(StreamCounters));
         if (e == cudaSuccess) e = cudaMemset(sc.d_ctr, 0, sizeof(StreamCounters));
         if (e != cudaSuccess) break;
@@ -267,16 +262,13 @@ extern "C" bpsf_status bpsf_serve_start(bpsf_server **out, bpsf_ctx *const *code
         sc.rec.cap = (long long)R;
         e = cudaMemset(sc.rec.qseq, 0, 8 * R);
         // The serving stream of this code.
-        JobDev job{sc.d_synd, sc.m_corr, sc.m_conv, sc.m_iters, sc.m_stage, 0, x->Ws, x->Wn};
+        JobDev job{sc.d_synd, sc.m_corr, sc.m_conv, sc.m_iters, sc.m_stage8, 0, x->Ws, x->Wn};
         StreamDev sd = bpsf_make_stream(x, job, nullptr, kServe);
         sd.rec = sc.rec;
         sd.ctr = sc.d_ctr;
-        sd.serve.published = sc.m_pub;
+        sd.serve.published = sc.d_pub;
         sd.serve.stop = s->m_stop;
-        sd.serve.row_req = sc.m_row_req;
-        sd.serve.req_left = s->d_req_left;
-        sd.serve.req_tag = s->m_req_tag;
-        sd.serve.req_flag = s->m_req_flag;
+        sd.serve.row_done = sc.m_done;
         sd.serve.rows = sc.rows;
         sd.serve.idle_ns = s->idle_ns;
         s->sds[k] = sd;
@@ -315,20 +307,17 @@ extern "C" bpsf_status bpsf_serve_submit(bpsf_server *s, int32_t code, int64_t n
     s->free_slots.pop_back();
     const long long g0 = sc.next_g;
     const int Ws = sc.ctx->Ws;
+    // Stage (the caller's buffer is free on return), then copy rows, then the count.
     const long long r0 = g0 % sc.rows, first = std::min<long long>(n, sc.rows - r0);
-    cudaError_t e = cudaMemcpyAsync(sc.d_synd + r0 * Ws, h_synd, 4 * (size_t)first * Ws, cudaMemcpyHostToDevice,
-                                    s->cstream);
+    std::memcpy(sc.h_stage + r0 * Ws, h_synd, 4 * (size_t)first * Ws);
+    if (first < n) std::memcpy(sc.h_stage, h_synd + first * Ws, 4 * (size_t)(n - first) * Ws);
+    cudaError_t e = cudaMemcpyAsync(sc.d_synd + r0 * Ws, sc.h_stage + r0 * Ws, 4 * (size_t)first * Ws,
+                                    cudaMemcpyHostToDevice, s->cstream);
     if (e == cudaSuccess && first < n)
-        e = cudaMemcpyAsync(sc.d_synd, h_synd + first * Ws, 4 * (size_t)(n - first) * Ws, cudaMemcpyHostToDevice,
-                            s->cstream);
-    s->h_left[q] = (unsigned)n;
-    if (e == cudaSuccess) e = cudaMemcpyAsync(s->d_req_left + q, s->h_left + q, 4, cudaMemcpyHostToDevice, s->cstream);
-    for (long long i = 0; i < n; ++i) sc.h_row_req[(g0 + i) % sc.rows] = q;
-    const unsigned tag = s->next_tag++;
-    if (s->next_tag == 0) s->next_tag = 1;
-    reinterpret_cast<volatile unsigned *>(s->h_req_flag)[q] = 0u;
-    reinterpret_cast<volatile unsigned *>(s->h_req_tag)[q] = tag;
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s->cstream);
+        e = cudaMemcpyAsync(sc.d_synd, sc.h_stage, 4 * (size_t)(n - first) * Ws, cudaMemcpyHostToDevice, s->cstream);
+    sc.h_pub_stage[q] = g0 + n;
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(sc.d_pub, sc.h_pub_stage + q, 8, cudaMemcpyHostToDevice, s->cstream);
     if (e != cudaSuccess) {
         s->free_slots.push_back(q);
         return bpsf_fail(BPSF_ECUDA, "request copy: %s", cudaGetErrorString(e));
@@ -337,16 +326,11 @@ extern "C" bpsf_status bpsf_serve_submit(bpsf_server *s, int32_t code, int64_t n
     r.code = code;
     r.g0 = g0;
     r.n = n;
+    r.checked = 0;
     r.ticket = s->next_ticket++;
-    r.tag = tag;
     r.live = true;
     s->by_ticket[r.ticket] = q;
     sc.next_g = g0 + n;
-    // Publish: every write above is visible before the new count.
-    std::atomic_thread_fence(std::memory_order_seq_cst);
-    *reinterpret_cast<volatile long long *>(sc.h_pub) = g0 + n;
-    std::atomic_thread_fence(std::memory_order_seq_cst);
-    s->unfinished.fetch_add(1);
     bpsf_status st = ensure_running(s);
     if (st != BPSF_OK) return st;
     *ticket = r.ticket;
@@ -367,24 +351,30 @@ extern "C" bpsf_status bpsf_serve_poll(bpsf_server *s, uint64_t ticket, int64_t 
         q = it->second;
         r = s->reqs[q];
     }
+    SrvCode &sc = s->codes[r.code];
+    const volatile unsigned *done = sc.h_done;
     const auto start = std::chrono::steady_clock::now();
-    long long spins = 0;
-    while (*reinterpret_cast<volatile unsigned *>(s->h_req_flag + q) != r.tag) {
+    long long spins = 0, i = r.checked;
+    while (i < r.n) {
+        const long long g = r.g0 + i;
+        if (done[g % sc.rows] == (unsigned)(g + 1)) {
+            ++i;
+            continue;
+        }
         const auto el = std::chrono::duration_cast<std::chrono::microseconds>(std::chrono::steady_clock::now() - start);
         if (el.count() >= timeout_us) return bpsf_fail(BPSF_ETIMEOUT, "request not finished");
-        if (++spins > 2000) std::this_thread::sleep_for(std::chrono::microseconds(5));
+        if (++spins > 4000) std::this_thread::sleep_for(std::chrono::microseconds(2));
     }
     std::atomic_thread_fence(std::memory_order_acquire);
-    SrvCode &sc = s->codes[r.code];
     const int Wn = sc.ctx->Wn;
-    for (long long i = 0; i < r.n;) {
-        const long long row = (r.g0 + i) % sc.rows;
-        const long long len = std::min<long long>(r.n - i, sc.rows - row);
-        if (h_corr) std::memcpy(h_corr + i * Wn, sc.h_corr + row * Wn, 4 * (size_t)len * Wn);
-        if (h_conv) std::memcpy(h_conv + i, sc.h_conv + row, (size_t)len);
-        if (h_iters) std::memcpy(h_iters + i, sc.h_iters + row, 2 * (size_t)len);
-        if (h_stage) std::memcpy(h_stage + i, sc.h_stage + row, (size_t)len);
-        i += len;
+    for (long long k = 0; k < r.n;) {
+        const long long row = (r.g0 + k) % sc.rows;
+        const long long len = std::min<long long>(r.n - k, sc.rows - row);
+        if (h_corr) std::memcpy(h_corr + k * Wn, sc.h_corr + row * Wn, 4 * (size_t)len * Wn);
+        if (h_conv) std::memcpy(h_conv + k, sc.h_conv + row, (size_t)len);
+        if (h_iters) std::memcpy(h_iters + k, sc.h_iters + row, 2 * (size_t)len);
+        if (h_stage) std::memcpy(h_stage + k, sc.h_stage8 + row, (size_t)len);
+        k += len;
     }
     {
         std::lock_guard<std::mutex> lk(s->mu);
@@ -413,8 +403,9 @@ extern "C" bpsf_status bpsf_serve_stop(bpsf_server *s) {
         bool pending = false;
         {
             std::lock_guard<std::mutex> lk(s->mu);
-            for (int q = 0; q < s->max_req; ++q)
+            for (int q = 0; q < s->max_req && !pending; ++q)
                 if (s->reqs[q].live && !request_done(s, q)) pending = true;
+            if (pending) ensure_running(s);
         }
         if (!pending) break;
         if (std::chrono::steady_clock::now() - start > std::chrono::seconds(30)) {
@@ -429,6 +420,7 @@ extern "C" bpsf_status bpsf_serve_stop(bpsf_server *s) {
     std::atomic_thread_fence(std::memory_order_seq_cst);
     cudaSetDevice(s->device);
     cudaError_t e = cudaStreamSynchronize(s->kstream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->cstream);
     if (e != cudaSuccess && st == BPSF_OK) st = bpsf_fail(BPSF_ECUDA, "serving kernel: %s", cudaGetErrorString(e));
     for (int k = 0; k < s->n_codes && st == BPSF_OK; ++k) {
         StreamCounters h;
@@ -437,4 +429,78 @@ extern "C" bpsf_status bpsf_serve_stop(bpsf_server *s) {
     }
     free_server(s);
     return st;
+}
+
+// Open-loop trace replay for latency measurement: one thread submits request
+// i at its scheduled arrival time, another polls every outstanding request
+// and stamps its completion, so neither side waits on the other.
+extern "C" bpsf_status bpsf_serve_replay(bpsf_server *s, int64_t n_req, const double *arrival_s, const int32_t *code,
+                                         const int64_t *n_shots, const uint32_t *const *synd, double *latency_s,
+                                         double *span_s) {
+    if (!s || n_req < 1 || !arrival_s || !code || !n_shots || !synd || !latency_s)
+        return bpsf_fail(BPSF_EINVAL, "bad replay arguments");
+    for (int64_t i = 0; i < n_req; ++i) {
+        if (code[i] < 0 || code[i] >= s->n_codes || n_shots[i] < 1 || !synd[i])
+            return bpsf_fail(BPSF_EINVAL, "bad request %lld", (long long)i);
+        if (i > 0 && arrival_s[i] < arrival_s[i - 1]) return bpsf_fail(BPSF_EINVAL, "arrivals must not decrease");
+    }
+    using clk = std::chrono::steady_clock;
+    std::vector<uint64_t> tickets((size_t)n_req, 0);
+    std::vector<std::atomic<int>> submitted((size_t)n_req);
+    for (auto &a : submitted) a.store(0);
+    std::atomic<int64_t> n_sub{0};
+    std::atomic<bool> failed{false};
+    bpsf_status sub_st = BPSF_OK;
+    const clk::time_point t0 = clk::now();
+    std::thread submitter([&] {
+        for (int64_t i = 0; i < n_req && !failed.load(); ++i) {
+            const clk::time_point at = t0 + std::chrono::nanoseconds((long long)(arrival_s[i] * 1e9));
+            while (clk::now() < at) {
+            }
+            uint64_t t = 0;
+            bpsf_status st = bpsf_serve_submit(s, code[i], n_shots[i], synd[i], 60000000, &t);
+            if (st != BPSF_OK) {
+                sub_st = st;
+                failed.store(true);
+                break;
+            }
+            tickets[(size_t)i] = t;
+            submitted[(size_t)i].store(1, std::memory_order_release);
+            n_sub.fetch_add(1);
+        }
+    });
+    bpsf_status st = BPSF_OK;
+    std::vector<int64_t> open;
+    int64_t next = 0, done = 0;
+    clk::time_point last = t0;
+    const clk::time_point deadline = t0 + std::chrono::seconds(600);
+    while (done < n_req && !failed.load()) {
+        while (next < n_req && submitted[(size_t)next].load(std::memory_order_acquire)) open.push_back(next++);
+        for (size_t k = 0; k < open.size();) {
+            const int64_t i = open[k];
+            const bpsf_status ps = bpsf_serve_poll(s, tickets[(size_t)i], 0, nullptr, nullptr, nullptr, nullptr);
+            if (ps == BPSF_OK) {
+                last = clk::now();
+                latency_s[i] = std::chrono::duration<double>(last - t0).count() - arrival_s[i];
+                ++done;
+                open[k] = open.back();
+                open.pop_back();
+            } else if (ps == BPSF_ETIMEOUT) {
+                ++k;
+            } else {
+                st = ps;
+                failed.store(true);
+                break;
+            }
+        }
+        if (clk::now() > deadline) {
+            st = bpsf_fail(BPSF_ETIMEOUT, "replay did not finish");
+            failed.store(true);
+        }
+    }
+    submitter.join();
+    if (sub_st != BPSF_OK) return sub_st;
+    if (st != BPSF_OK) return st;
+    if (span_s) *span_s = std::chrono::duration<double>(last - t0).count();
+    return BPSF_OK;
 }
