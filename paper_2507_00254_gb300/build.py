@@ -41,8 +41,12 @@ def up_to_date() -> bool:
     return all(os.path.getmtime(p) <= t for p in _deps())
 
 
-def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) -> str:
-    if not force and up_to_date():
+def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False, out: str = None) -> str:
+    """Compile every .cu file of csrc/ and link libbpsf.so.  Extra nvcc flags
+    may be given in BPSF_NVCC_FLAGS (e.g. -DBPSF_MIN_BLOCKS=2); `out` builds a
+    separate copy of the library instead of the in-tree one."""
+    lib_path = out or LIB
+    if not force and out is None and up_to_date():
         return LIB
     os.makedirs(BUILD, exist_ok=True)
     cc = nvcc()
@@ -50,9 +54,13 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
                     "--expt-relaxed-constexpr"]
     if ptxas_info:
         flags += ["-Xptxas", "-v"]
+    flags += os.environ.get("BPSF_NVCC_FLAGS", "").split()
+
+    obj_dir = os.path.join(os.path.dirname(lib_path), "_obj") if out else BUILD
+    os.makedirs(obj_dir, exist_ok=True)
 
     def compile_one(src):
-        obj = os.path.join(BUILD, os.path.basename(src) + ".o")
+        obj = os.path.join(obj_dir, os.path.basename(src) + ".o")
         cmd = [cc] + flags + ["-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
@@ -63,14 +71,14 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
 
     with cf.ThreadPoolExecutor(max_workers=max(1, min(8, os.cpu_count() or 1))) as ex:
         objs = list(ex.map(compile_one, _sources()))
-    tmp = LIB + ".tmp"
+    tmp = lib_path + ".tmp"
     cmd = [cc] + ARCH + ["-shared", "-cudart", "shared", "-o", tmp] + objs + \
         ["-Xlinker", "-rpath=/usr/local/cuda/lib64"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n%s\n%s" % (r.stdout, r.stderr))
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib_path)
+    return lib_path
 
 
 if __name__ == "__main__":

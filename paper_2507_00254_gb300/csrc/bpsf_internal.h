@@ -192,7 +192,7 @@ __host__ __device__ inline TeamOffsets team_offsets(int S, int N, int P, int Ws)
     o.state = p;  p += 80 * S;
     o.syn = p;    p += 4 * S * Ws;
     o.mism = p;   p += 4 * S * Ws;
-    o.ebits = p;  p += 4 * ((S * N + 31) / 32 + 1);
+    o.ebits = p;  p += 4 * S * ((N + 31) / 32);
     o.flips = p;  p = align_up(p + 2 * S * N, 16);
     o.m = p;      p += 4 * S * P;
     o.total = align_up(p, 16);

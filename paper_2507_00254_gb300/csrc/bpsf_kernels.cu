@@ -11,11 +11,13 @@
 //             written in place of the V2C messages they were computed from;
 //   V phase : one thread per (slot, variable): V2C messages for the next
 //             iteration (Section II-B step 2, explicit exclusion), posterior
-//             LLR and hard decision (step 4); a warp ballot packs e into
-//             words, changed bits update the flip counters (Algorithm 1) and
-//             toggle the slot's residual syndrome s xor H e by shared atomics;
+//             LLR and hard decision (step 4), kept with the variable's flip
+//             counter (Algorithm 1) in one 16-bit word; a changed decision
+//             bumps the counter and toggles the slot's residual syndrome
+//             s xor H e at the column's checks by shared atomics;
 //   decide  : a slot whose residual syndrome is zero has converged, a slot at
-//             its iteration cap is exhausted; either is handed to the manager.
+//             its iteration cap is exhausted; either has its decision packed
+//             into words and is handed to the manager.
 // Each message is read and written by exactly one thread in each phase, so
 // one array of P floats per slot holds V2C and C2V messages alternately.
 //
@@ -149,27 +151,47 @@ __device__ __forceinline__ void c_load(CTask<DC, REG> &t, const CodeDev &cd, con
 template <int DC, bool REG>
 __device__ __forceinline__ void c_compute_store(CTask<DC, REG> &t, int M, float alpha) {
     if (!t.on) return;
+    // m1 <= m2 are the two smallest |q_k| (equal on ties).  The message to
+    // edge k excludes k itself: alpha * m2 if |q_k| == m1, else alpha * m1
+    // (on a tie m2 == m1, so either choice gives the same value).
     float m1 = __int_as_float(0x7f800000), m2 = m1;
-    int k1 = 0;
     unsigned sx = t.sall;
 #pragma unroll
     for (int k = 0; k < DC; ++k) {
         if (REG || k < t.deg) {
             const float a = fabsf(t.v[k]);
-            k1 = (a < m1) ? k : k1;
             m2 = fminf(m2, fmaxf(m1, a));
             m1 = fminf(m1, a);
             sx ^= __float_as_uint(t.v[k]);
         }
     }
     const float g1 = __fmul_rn(alpha, m1), g2 = __fmul_rn(alpha, m2);
+    sx &= 0x80000000u;
 #pragma unroll
     for (int k = 0; k < DC; ++k) {
         if (REG || k < t.deg) {
-            const float mag = (k == k1) ? g2 : g1;
+            const float mag = (fabsf(t.v[k]) == m1) ? g2 : g1;
             const unsigned bits = __float_as_uint(mag) | ((sx ^ __float_as_uint(t.v[k])) & 0x80000000u);
             t.dst[k * M] = __uint_as_float(bits);
         }
+    }
+}
+
+// Rows (C phase) and columns (V phase) a thread handles per step: their
+// loads are all issued before any of their stores, for instruction-level
+// parallelism (the tasks of one step touch disjoint messages).
+#ifndef BPSF_CU
+#define BPSF_CU 2
+#endif
+#ifndef BPSF_VU
+#define BPSF_VU 2
+#endif
+
+__device__ __forceinline__ void advance(int &s, int &j, int step, int M) {
+    j += step;
+    while (j >= M) {
+        j -= M;
+        ++s;
     }
 }
 
@@ -180,24 +202,15 @@ __device__ __forceinline__ void c_phase(const CodeDev &cd, const LayoutMem &L, c
     const int total = S * M;
     const float alpha = cd.alpha;
     int s = tid / M, j = tid - s * M;
-    // Two rows per step: both rows' loads are issued before either row's stores.
-    for (int tau = tid; tau < total; tau += 2 * nthreads) {
-        int sB = s, jB = j + nthreads;
-        while (jB >= M) {
-            jB -= M;
-            ++sB;
+    for (int tau = tid; tau < total; tau += BPSF_CU * nthreads) {
+        CTask<DC, REG> t[BPSF_CU];
+#pragma unroll
+        for (int u = 0; u < BPSF_CU; ++u) {
+            c_load<DC, REG>(t[u], cd, L, T, s, j, tau + u * nthreads < total, run, fresh);
+            advance(s, j, nthreads, M);
         }
-        CTask<DC, REG> A, B;
-        c_load<DC, REG>(A, cd, L, T, s, j, true, run, fresh);
-        c_load<DC, REG>(B, cd, L, T, sB, jB, tau + nthreads < total, run, fresh);
-        c_compute_store<DC, REG>(A, M, alpha);
-        c_compute_store<DC, REG>(B, M, alpha);
-        s = sB;
-        j = jB + nthreads;
-        while (j >= M) {
-            j -= M;
-            ++s;
-        }
+#pragma unroll
+        for (int u = 0; u < BPSF_CU; ++u) c_compute_store<DC, REG>(t[u], M, alpha);
     }
 }
 
@@ -208,100 +221,113 @@ __device__ __forceinline__ void c_phase(const CodeDev &cd, const LayoutMem &L, c
 //   q_k   = l_ch + sum_{k' != k} r_k'   (left fold, ascending k'),
 //   l_out = l_ch + sum_k r_k            (left fold),  e_i = [l_out <= 0].
 // ---------------------------------------------------------------------------
+template <int DVS>
+struct VTask {
+    uint16_t pos[DVS];
+    float r[DVS];
+    float lc;
+    unsigned f;  // decision (bit 15) and flip count of (slot, variable)
+    int s, i, tau;
+    bool on, fr;
+};
+
+template <int DVS, int DVX>
+__device__ __forceinline__ void v_load(VTask<DVS> &t, const LayoutMem &L, const TeamMem &T, int P, int s, int i,
+                                       int tau, bool valid, unsigned run, unsigned fresh) {
+    t.on = valid && ((run >> s) & 1u);
+    if (!t.on) return;
+    t.s = s;
+    t.i = i;
+    t.tau = tau;
+    const uint16_t *vp = L.vpos + i * DVS;
+    if (DVS == 4) {
+        const uint2 raw = *reinterpret_cast<const uint2 *>(vp);
+        t.pos[0] = (uint16_t)(raw.x & 0xffffu);
+        t.pos[1] = (uint16_t)(raw.x >> 16);
+        t.pos[2] = (uint16_t)(raw.y & 0xffffu);
+        t.pos[3] = (uint16_t)(raw.y >> 16);
+    } else {
+#pragma unroll
+        for (int k = 0; k < DVS; ++k) t.pos[k] = vp[k];
+    }
+    t.lc = L.lch[i];
+    const float *ms = T.m + s * P;
+#pragma unroll
+    for (int k = 0; k < DVS; ++k)
+        if (DVX > 0 ? (k < DVX) : true) t.r[k] = (DVX > 0 || t.pos[k] != 0xffffu) ? ms[t.pos[k]] : 0.f;
+    t.fr = (fresh >> s) & 1u;
+    t.f = t.fr ? 0u : (unsigned)T.flips[tau];
+}
+
+template <int DVS, int DVX, bool DEBUG>
+__device__ __forceinline__ void v_compute_store(const VTask<DVS> &t, const StreamDev &sd, const TeamMem &T, int P,
+                                                int N, int Ws, unsigned initm) {
+    if (!t.on) return;
+    float *ms = T.m + t.s * P;
+    float lo;
+    if (DVX == 3) {
+        // Three checks: shared prefix l_ch + r0.
+        const float t0 = __fadd_rn(t.lc, t.r[0]);
+        const float q2 = __fadd_rn(t0, t.r[1]);
+        lo = __fadd_rn(q2, t.r[2]);
+        const float q1 = __fadd_rn(t0, t.r[2]);
+        const float q0 = __fadd_rn(__fadd_rn(t.lc, t.r[1]), t.r[2]);
+        ms[t.pos[0]] = q0;
+        ms[t.pos[1]] = q1;
+        ms[t.pos[2]] = q2;
+    } else {
+#pragma unroll
+        for (int k = 0; k < DVS; ++k) {
+            if (t.pos[k] != 0xffffu) {
+                float acc = t.lc;
+#pragma unroll
+                for (int k2 = 0; k2 < DVS; ++k2)
+                    if (k2 != k && t.pos[k2] != 0xffffu) acc = __fadd_rn(acc, t.r[k2]);
+                ms[t.pos[k]] = acc;
+            }
+        }
+        lo = t.lc;
+#pragma unroll
+        for (int k = 0; k < DVS; ++k)
+            if (t.pos[k] != 0xffffu) lo = __fadd_rn(lo, t.r[k]);
+    }
+    const unsigned ebit = (lo <= 0.f) ? 1u : 0u;
+    if (DEBUG && ((initm >> t.s) & 1u) && sd.dbg.lout) sd.dbg.lout[T.st[t.s].shot * N + t.i] = lo;
+    // One 16-bit word per (slot, variable): bit 15 is the current hard
+    // decision, bits 0..14 count its flips (Algorithm 1; at most
+    // max_iter <= 32767).  A fresh slot starts from e = 0, count 0.
+    if ((t.f >> 15) != ebit) {
+        T.flips[t.tau] = (uint16_t)((t.f ^ 0x8000u) + 1u);
+        // The residual syndrome s xor H e toggles at this column's checks.
+        const uint16_t *vc = sd.code.vchk + t.i * DVS;
+#pragma unroll
+        for (int k = 0; k < DVS; ++k) {
+            if (DVX > 0 ? (k < DVX) : (t.pos[k] != 0xffffu)) {
+                const int c = __ldg(vc + k);
+                atomicXor(&T.mism[t.s * Ws + (c >> 5)], 1u << (c & 31));
+            }
+        }
+    } else if (t.fr) {
+        T.flips[t.tau] = 0;
+    }
+}
+
 template <int DVS, int DVX, bool DEBUG>
 __device__ __forceinline__ void v_phase(const StreamDev &sd, const LayoutMem &L, const TeamMem &T, int S,
                                         unsigned run, unsigned fresh, unsigned initm, int tid, int nthreads) {
     const CodeDev &cd = sd.code;
     const int N = cd.N, P = cd.P, Ws = cd.Ws;
     const int total = S * N;
-    const int lane = tid & 31;
-    int tau = tid;
-    int s = tau / N, i = tau - s * N;
-    for (int base = tid - lane; base < total; base += nthreads) {
-        const bool valid = tau < total;
-        const bool a = valid && ((run >> s) & 1u);
-        const bool fr = a && ((fresh >> s) & 1u);
-        const bool ini = a && ((initm >> s) & 1u);
-        unsigned ebit = 0;
-        uint16_t pos[DVS];
-        if (a) {
-            const uint16_t *vp = L.vpos + i * DVS;
-            if (DVS == 4) {
-                const uint2 raw = *reinterpret_cast<const uint2 *>(vp);
-                pos[0] = (uint16_t)(raw.x & 0xffffu);
-                pos[1] = (uint16_t)(raw.x >> 16);
-                pos[2] = (uint16_t)(raw.y & 0xffffu);
-                pos[3] = (uint16_t)(raw.y >> 16);
-            } else {
+    int s = tid / N, i = tid - s * N;
+    for (int tau = tid; tau < total; tau += BPSF_VU * nthreads) {
+        VTask<DVS> t[BPSF_VU];
 #pragma unroll
-                for (int k = 0; k < DVS; ++k) pos[k] = vp[k];
-            }
-            const float lc = L.lch[i];
-            float *ms = T.m + s * P;
-            float lo;
-            if (DVX == 3) {
-                // Three checks: shared prefix l_ch + r0.
-                const float r0 = ms[pos[0]], r1 = ms[pos[1]], r2 = ms[pos[2]];
-                const float t0 = __fadd_rn(lc, r0);
-                const float q2 = __fadd_rn(t0, r1);
-                lo = __fadd_rn(q2, r2);
-                const float q1 = __fadd_rn(t0, r2);
-                const float q0 = __fadd_rn(__fadd_rn(lc, r1), r2);
-                ms[pos[0]] = q0;
-                ms[pos[1]] = q1;
-                ms[pos[2]] = q2;
-            } else {
-                float rv[DVS];
-#pragma unroll
-                for (int k = 0; k < DVS; ++k) rv[k] = (pos[k] != 0xffffu) ? ms[pos[k]] : 0.f;
-#pragma unroll
-                for (int k = 0; k < DVS; ++k) {
-                    if (pos[k] != 0xffffu) {
-                        float acc = lc;
-#pragma unroll
-                        for (int k2 = 0; k2 < DVS; ++k2)
-                            if (k2 != k && pos[k2] != 0xffffu) acc = __fadd_rn(acc, rv[k2]);
-                        ms[pos[k]] = acc;
-                    }
-                }
-                lo = lc;
-#pragma unroll
-                for (int k = 0; k < DVS; ++k)
-                    if (pos[k] != 0xffffu) lo = __fadd_rn(lo, rv[k]);
-            }
-            ebit = (lo <= 0.f) ? 1u : 0u;
-            if (DEBUG && ini && sd.dbg.lout) {
-                const long long shot = T.st[s].shot;
-                sd.dbg.lout[shot * N + i] = lo;
-            }
+        for (int u = 0; u < BPSF_VU; ++u) {
+            v_load<DVS, DVX>(t[u], L, T, P, s, i, tau + u * nthreads, tau + u * nthreads < total, run, fresh);
+            advance(s, i, nthreads, N);
         }
-        const int widx = base >> 5;
-        const unsigned old = T.ebits[widx];
-        const unsigned am = __ballot_sync(FULLMASK, a);
-        const unsigned nb = __ballot_sync(FULLMASK, ebit != 0);
-        __syncwarp();
-        if (lane == 0) T.ebits[widx] = (nb & am) | (old & ~am);
-        if (a) {
-            const unsigned prev = fr ? 0u : ((old >> lane) & 1u);
-            const unsigned flip = prev ^ ebit;
-            if (ini) T.flips[tau] = fr ? (uint16_t)flip : (uint16_t)(T.flips[tau] + flip);
-            if (flip) {
-                const uint16_t *vc = cd.vchk + i * DVS;
 #pragma unroll
-                for (int k = 0; k < DVS; ++k) {
-                    if (DVX > 0 ? (k < DVX) : (pos[k] != 0xffffu)) {
-                        const int c = __ldg(vc + k);
-                        atomicXor(&T.mism[s * Ws + (c >> 5)], 1u << (c & 31));
-                    }
-                }
-            }
-        }
-        tau += nthreads;
-        i += nthreads;
-        while (i >= N) {
-            i -= N;
-            ++s;
-        }
+        for (int u = 0; u < BPSF_VU; ++u) v_compute_store<DVS, DVX, DEBUG>(t[u], sd, T, P, N, Ws, initm);
     }
 }
 
@@ -313,7 +339,7 @@ __device__ void team_loop(const StreamDev &sd, const LayoutMem &L, const TeamMem
                           int tid, int bar_id, unsigned long long wait_ns) {
     const int lane = tid & 31, wt = tid >> 5, nthreads = 32 * W;
     const CodeDev &cd = sd.code;
-    const int Ws = cd.Ws;
+    const int Ws = cd.Ws, Wn = cd.Wn, N = cd.N;
     unsigned long long idle_since = 0;
     unsigned last_beat = 0;
     for (;;) {
@@ -362,18 +388,37 @@ __device__ void team_loop(const StreamDev &sd, const LayoutMem &L, const TeamMem
         team_sync(W, bar_id);
         v_phase<DVS, DVX, DEBUG>(sd, L, T, S, run, fresh, initm, tid, nthreads);
         team_sync(W, bar_id);
-        if (wt == 0 && lane < S && ((run >> lane) & 1u)) {
-            SlotState *ss = &T.st[lane];
-            ss->fresh = 0;
-            const int it = ss->iter + 1;
-            ss->iter = it;
-            unsigned any = 0;
-            for (int w = 0; w < Ws; ++w) any |= T.mism[lane * Ws + w];
-            const int oc = (any == 0u) ? 1 : (it >= ss->limit ? 2 : 0);
-            if (oc) {
-                ss->outcome = oc;
+        if (wt == 0) {
+            bool done = false;
+            if (lane < S && ((run >> lane) & 1u)) {
+                SlotState *ss = &T.st[lane];
+                ss->fresh = 0;
+                const int it = ss->iter + 1;
+                ss->iter = it;
+                unsigned any = 0;
+                for (int w = 0; w < Ws; ++w) any |= T.mism[lane * Ws + w];
+                const int oc = (any == 0u) ? 1 : (it >= ss->limit ? 2 : 0);
+                if (oc) {
+                    ss->outcome = oc;
+                    done = true;
+                }
+            }
+            // Pack the hard decision of each finished slot into words for the manager.
+            unsigned fm = __ballot_sync(FULLMASK, done);
+            while (fm) {
+                const int s = __ffs(fm) - 1;
+                fm &= fm - 1u;
+                for (int w = 0; w < Wn; ++w) {
+                    const int i = 32 * w + lane;
+                    const unsigned b = i < N ? ((unsigned)T.flips[s * N + i] >> 15) : 0u;
+                    const unsigned word = __ballot_sync(FULLMASK, b != 0u);
+                    if (lane == 0) T.ebits[s * Wn + w] = word;
+                }
+            }
+            __syncwarp();
+            if (done) {
                 __threadfence_block();
-                *vstate(ss) = kSlotFinished;
+                *vstate(&T.st[lane]) = kSlotFinished;
             }
         }
     }
@@ -400,16 +445,11 @@ __device__ __forceinline__ uint32_t *qsyn(QEntry *e) {
     return reinterpret_cast<uint32_t *>(reinterpret_cast<unsigned char *>(e) + 48);
 }
 
-// Word w of slot s's hard decision, from its team's flattened bit array.
-__device__ __forceinline__ unsigned slot_word(const uint32_t *ebits, int N, int s, int w) {
-    const int bit0 = s * N + 32 * w;
-    const int wi = bit0 >> 5, sh = bit0 & 31;
-    unsigned v = ebits[wi] >> sh;
-    if (sh) v |= ebits[wi + 1] << (32 - sh);
-    const int rem = N - 32 * w;
-    if (rem < 32) v &= (1u << rem) - 1u;
-    return v;
-}
+// Word w of finished slot s's hard decision (packed by its team).
+__device__ __forceinline__ unsigned slot_word(const uint32_t *ebits, int Wn, int s, int w) { return ebits[s * Wn + w]; }
+
+// Flip count of (slot, variable) word f: bits 0..14 (bit 15 is the decision).
+__device__ __forceinline__ unsigned flip_count(uint16_t f) { return (unsigned)f & 0x7fffu; }
 
 __device__ __forceinline__ long long row_of(const StreamDev &sd, long long shot) {
     return (sd.flags & kServe) ? (shot % sd.serve.rows) : shot;
@@ -438,9 +478,9 @@ __device__ __forceinline__ void finalize_simple(const StreamDev &sd, TeamMem T, 
     const int N = cd.N, Wn = cd.Wn;
     if (kind == 1) {
         if (DEBUG && sd.dbg.flips)
-            for (int i = 0; i < N; ++i) sd.dbg.flips[shot * N + i] = T.flips[s * N + i];
+            for (int i = 0; i < N; ++i) sd.dbg.flips[shot * N + i] = (uint16_t)flip_count(T.flips[s * N + i]);
         uint32_t *out = job.corr + row * job.corr_stride;
-        for (int w = 0; w < Wn; ++w) out[w] = slot_word(T.ebits, N, s, w);
+        for (int w = 0; w < Wn; ++w) out[w] = slot_word(T.ebits, Wn, s, w);
         job.conv[row] = conv ? 1 : 0;
         job.iters[row] = (int16_t)(conv ? iter : cd.max_iter);
         if (job.stage) job.stage[row] = conv ? 0 : 2;
@@ -455,7 +495,7 @@ __device__ __forceinline__ void finalize_simple(const StreamDev &sd, TeamMem T, 
         unsigned wsum = 0;
         uint32_t *dst = sd.rec.corr + ((long long)row * C + kidx) * Wn;
         for (int w = 0; w < Wn; ++w) {
-            unsigned v = slot_word(T.ebits, N, s, w);
+            unsigned v = slot_word(T.ebits, Wn, s, w);
             for (int j = 0; j < cd.w; ++j) {
                 if ((mask >> j) & 1u) {
                     const int b = ss->phi[j];
@@ -506,9 +546,9 @@ __device__ __forceinline__ void finalize_failed(const StreamDev &sd, TeamMem T, 
     const long long row = row_of(sd, shot);
     const int N = cd.N, Wn = cd.Wn, Ws = cd.Ws;
     if (DEBUG && sd.dbg.flips)
-        for (int i = lane; i < N; i += 32) sd.dbg.flips[shot * N + i] = T.flips[s * N + i];
+        for (int i = lane; i < N; i += 32) sd.dbg.flips[shot * N + i] = (uint16_t)flip_count(T.flips[s * N + i]);
     uint32_t *out = job.corr + row * job.corr_stride;
-    for (int w = lane; w < Wn; w += 32) out[w] = slot_word(T.ebits, N, s, w);
+    for (int w = lane; w < Wn; w += 32) out[w] = slot_word(T.ebits, Wn, s, w);
     if (lane == 0) {
         job.conv[row] = 0;
         job.iters[row] = (int16_t)cd.max_iter;
@@ -521,7 +561,7 @@ __device__ __forceinline__ void finalize_failed(const StreamDev &sd, TeamMem T, 
     for (int r = 0; r < cd.w; ++r) {
         unsigned best = 0;
         for (int i = lane; i < N; i += 32) {
-            const unsigned key = ((unsigned)T.flips[s * N + i] << 16) | (0xffffu - (unsigned)i);
+            const unsigned key = (flip_count(T.flips[s * N + i]) << 16) | (0xffffu - (unsigned)i);
             if (key < thr && key > best) best = key;
         }
         best = __reduce_max_sync(FULLMASK, best);
@@ -818,8 +858,14 @@ struct KernelParams {
     unsigned long long wait_ns;
 };
 
+// Minimum resident blocks per SM the register allocation must allow
+// (2 caps registers at 64 per thread so two 512-thread blocks fit).
+#ifndef BPSF_MIN_BLOCKS
+#define BPSF_MIN_BLOCKS 1
+#endif
+
 template <int DC, int DVS, int DVX, bool DEBUG>
-__global__ void __launch_bounds__(512, 1) bpsf_persistent(const __grid_constant__ KernelParams kp) {
+__global__ void __launch_bounds__(512, BPSF_MIN_BLOCKS) bpsf_persistent(const __grid_constant__ KernelParams kp) {
     extern __shared__ __align__(16) unsigned char smem[];
     BlockHdr *hdr = reinterpret_cast<BlockHdr *>(smem);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
