@@ -202,13 +202,14 @@ bpsf_status bpsf_sync(bpsf_ctx *ctx, void *stream);
 /*
  * Launch shape of the batched kernel for one context (the autotuner's
  * search space).  A team of warps_per_team warps decodes slots_per_team work
- * items in lock step; warps_per_block / warps_per_team teams share a block
+ * items in lock step (interleaved in shared memory, so each lane serves one
+ * fixed slot); warps_per_block / warps_per_team teams share a block
  * together with one manager warp that writes results and refills slots;
  * blocks_per_sm blocks per SM (0 = as many as fit).
  */
 typedef struct {
     int32_t warps_per_team;  /* 1, 2, 4 or 8 */
-    int32_t slots_per_team;  /* 1..32 */
+    int32_t slots_per_team;  /* 1, 2, 4, 8, 16 or 32 */
     int32_t warps_per_block; /* compute warps: a multiple of warps_per_team, <= 15 */
     int32_t blocks_per_sm;   /* 0 = occupancy limit */
 } bpsf_tuning;

@@ -109,7 +109,8 @@ static int plan_smem(const bpsf_ctx *c, int vstride, int S, int teams, int Q) {
 static bpsf_status check_shape(const bpsf_tuning &t) {
     const int W = t.warps_per_team, S = t.slots_per_team, B = t.warps_per_block;
     if (!(W == 1 || W == 2 || W == 4 || W == 8)) return bpsf_fail(BPSF_EINVAL, "warps_per_team must be 1, 2, 4 or 8");
-    if (S < 1 || S > kMaxSlots) return bpsf_fail(BPSF_EINVAL, "slots_per_team must be in 1..%d", kMaxSlots);
+    if (S < 1 || S > kMaxSlots || (S & (S - 1)))
+        return bpsf_fail(BPSF_EINVAL, "slots_per_team must be a power of two in 1..%d", kMaxSlots);
     if (B < W || B > kMaxComputeWarps || B % W)
         return bpsf_fail(BPSF_EINVAL, "warps_per_block must be a multiple of warps_per_team, at most %d",
                          kMaxComputeWarps);
@@ -150,7 +151,7 @@ bpsf_status bpsf_make_plan(bpsf_ctx *const *codes, int n_codes, const bpsf_tunin
         int S = tunes[k].slots_per_team, teams = tunes[k].warps_per_block / W;
         while (shrink && plan_smem(codes[k], vstride, S, teams, Q) > c0->smem_optin) {
             if (S > 1)
-                --S;
+                S >>= 1;
             else if (teams > 1)
                 --teams;
             else
@@ -186,7 +187,7 @@ static bpsf_tuning default_tuning(bpsf_ctx *c) {
     // Small codes: single-warp teams with a few slots each; large codes:
     // multi-warp teams.  Shrink until the block fits.
     const int Wc[] = {1, 1, 1, 2, 4, 8};
-    const int Sc[] = {4, 3, 2, 2, 1, 1};
+    const int Sc[] = {4, 2, 1, 2, 1, 1};
     for (int k = 0; k < 6; ++k) {
         if (c->nnz > 2048 && Wc[k] < 4) continue;
         for (int B = kMaxComputeWarps; B >= Wc[k]; --B) {
@@ -757,7 +758,7 @@ extern "C" bpsf_status bpsf_autotune(bpsf_ctx *c, double p_sample, int64_t n_sam
     float best_ms = 1e30f;
     bpsf_status st = BPSF_OK;
     const int Ws_[] = {1, 2, 4, 8};
-    const int Ss_[] = {1, 2, 3, 4, 6, 8, 12, 16};
+    const int Ss_[] = {1, 2, 4, 8, 16, 32};
     const int Bs_[] = {1, 2, 3, 4, 6, 7, 8, 10, 12, 14, 15};
     bpsf_ctx *cs1[1] = {c};
     for (int W : Ws_)

@@ -161,7 +161,7 @@ enum : int { kSlotEmpty = 0, kSlotRunning = 1, kSlotFinished = 2 };
 struct SlotState {
     int state;       // kSlot*
     int kind;        // 1 initial run, 2 trial run
-    int fresh;       // 1 until the first iteration has run
+    int spare;
     int outcome;     // 1 converged, 2 iteration cap (valid when FINISHED)
     int iter;        // iterations completed
     int limit;       // iteration cap of this run
@@ -175,23 +175,34 @@ static_assert(sizeof(SlotState) == 80, "slot state is 80 bytes");
 
 // Team control block (32 bytes).
 struct TeamCtl {
-    unsigned run_mask, fresh_mask, init_mask;
+    unsigned run_mask, spare, init_mask;
     int exit;
     unsigned long long iters;  // iterations run by this team (all slots)
     unsigned long long pad;
 };
 
+// Per-team shared memory.  The S slots of a team (S a power of two <= 32)
+// are interleaved: item x of slot s sits at x*S + s, so lane l always serves
+// slot l mod S and the 32 lanes of a warp touch 32 consecutive items.
+//   syn, mism : bit j*S + s = s_j, resp. the residual syndrome (s xor H e)_j,
+//               of slot s, in (S*M + 31)/32 words each
+//   ebits     : S x Wn words, the hard decision of a finished slot, packed
+//   flips     : 16-bit word i*S + s = decision (bit 15) and flip count of
+//               variable i in slot s
+//   m         : float k*S + s = the message of edge position k = r*M + j
+//               (r-th edge of row j) in slot s: V2C and C2V alternately
 struct TeamOffsets {
     int ctl, state, syn, mism, ebits, flips, m, total;
 };
 
-__host__ __device__ inline TeamOffsets team_offsets(int S, int N, int P, int Ws) {
+__host__ __device__ inline TeamOffsets team_offsets(int S, int M, int N, int P) {
     TeamOffsets o;
+    const int sw = (S * M + 31) / 32;
     int p = 0;
     o.ctl = p;    p += 32;
     o.state = p;  p += 80 * S;
-    o.syn = p;    p += 4 * S * Ws;
-    o.mism = p;   p += 4 * S * Ws;
+    o.syn = p;    p += 4 * sw;
+    o.mism = p;   p += 4 * sw;
     o.ebits = p;  p += 4 * S * ((N + 31) / 32);
     o.flips = p;  p = align_up(p + 2 * S * N, 16);
     o.m = p;      p += 4 * S * P;
@@ -212,7 +223,7 @@ __host__ __device__ inline int qentry_bytes(int Ws) { return align_up(48 + 4 * W
 
 __host__ __device__ inline int block_smem_bytes(int M, int N, int P, int Ws, int vstride, int S, int teams, int Q) {
     return kBlockHeaderBytes + layout_offsets(M, N, vstride, P).total + Q * qentry_bytes(Ws) +
-           teams * team_offsets(S, N, P, Ws).total;
+           teams * team_offsets(S, M, N, P).total;
 }
 
 // Kernel entry points (bpsf_kernels.cu).

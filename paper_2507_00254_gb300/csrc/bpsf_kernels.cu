@@ -20,6 +20,11 @@
 //             into words and is handed to the manager.
 // Each message is read and written by exactly one thread in each phase, so
 // one array of P floats per slot holds V2C and C2V messages alternately.
+// The S slots of a team are interleaved item by item (S is a power of two):
+// lane l serves slot l mod S in both phases, task tau = j*S + s (row j) or
+// i*S + s (column i) addresses its data directly, and a warp's 32 lanes
+// touch consecutive words.  Installing a slot sets its messages to the
+// channel LLRs, so the phases have no first-iteration special case.
 //
 // The manager warp does everything that touches global memory: it writes
 // finished slots out, runs top(flip_count, w) for failed initial runs and
@@ -127,29 +132,28 @@ __device__ __forceinline__ volatile int *vstate(SlotState *s) { return reinterpr
 template <int DC, bool REG>
 struct CTask {
     float v[DC];
-    float *dst;
+    float *p;       // message of edge rank 0 of this (row, slot); rank k sits k*M*S further
     unsigned sall;  // bit 31: s_j xor the sign bits of all inputs
     int deg;
     bool on;
 };
 
+// Task tau = j*S + s of the interleaved team layout: row j of slot s.
 template <int DC, bool REG>
-__device__ __forceinline__ void c_load(CTask<DC, REG> &t, const CodeDev &cd, const LayoutMem &L, const TeamMem &T,
-                                       int s, int j, bool valid, unsigned run, unsigned fresh) {
-    t.on = valid && ((run >> s) & 1u);
-    if (!t.on) return;
-    const int M = cd.M;
-    t.deg = REG ? DC : (int)L.row_deg[j];
-    t.dst = T.m + s * cd.P + j;
-    const float *src = ((fresh >> s) & 1u) ? (L.lch_pos + j) : t.dst;
-    t.sall = ((T.syn[s * cd.Ws + (j >> 5)] >> (j & 31)) & 1u) << 31;
+__device__ __forceinline__ void c_load(CTask<DC, REG> &t, const LayoutMem &L, const TeamMem &T, int MS, int lgS,
+                                       int tau, bool on) {
+    t.on = on;
+    if (!on) return;
+    t.deg = REG ? DC : (int)L.row_deg[tau >> lgS];
+    t.p = T.m + tau;
+    t.sall = (T.syn[tau >> 5] >> (tau & 31)) << 31;
 #pragma unroll
     for (int k = 0; k < DC; ++k)
-        if (REG || k < t.deg) t.v[k] = src[k * M];
+        if (REG || k < t.deg) t.v[k] = t.p[k * MS];
 }
 
 template <int DC, bool REG>
-__device__ __forceinline__ void c_compute_store(CTask<DC, REG> &t, int M, float alpha) {
+__device__ __forceinline__ void c_compute_store(CTask<DC, REG> &t, int MS, float alpha) {
     if (!t.on) return;
     // m1 <= m2 are the two smallest |q_k| (equal on ties).  The message to
     // edge k excludes k itself: alpha * m2 if |q_k| == m1, else alpha * m1
@@ -172,7 +176,7 @@ __device__ __forceinline__ void c_compute_store(CTask<DC, REG> &t, int M, float 
         if (REG || k < t.deg) {
             const float mag = (fabsf(t.v[k]) == m1) ? g2 : g1;
             const unsigned bits = __float_as_uint(mag) | ((sx ^ __float_as_uint(t.v[k])) & 0x80000000u);
-            t.dst[k * M] = __uint_as_float(bits);
+            t.p[k * MS] = __uint_as_float(bits);
         }
     }
 }
@@ -181,36 +185,23 @@ __device__ __forceinline__ void c_compute_store(CTask<DC, REG> &t, int M, float 
 // loads are all issued before any of their stores, for instruction-level
 // parallelism (the tasks of one step touch disjoint messages).
 #ifndef BPSF_CU
-#define BPSF_CU 2
+#define BPSF_CU 1
 #endif
 #ifndef BPSF_VU
-#define BPSF_VU 2
+#define BPSF_VU 1
 #endif
 
-__device__ __forceinline__ void advance(int &s, int &j, int step, int M) {
-    j += step;
-    while (j >= M) {
-        j -= M;
-        ++s;
-    }
-}
-
 template <int DC, bool REG>
-__device__ __forceinline__ void c_phase(const CodeDev &cd, const LayoutMem &L, const TeamMem &T, int S,
-                                        unsigned run, unsigned fresh, int tid, int nthreads) {
-    const int M = cd.M;
-    const int total = S * M;
+__device__ __forceinline__ void c_phase(const CodeDev &cd, const LayoutMem &L, const TeamMem &T, int lgS,
+                                        int tid, int nthreads) {
+    const int MS = cd.M << lgS;
     const float alpha = cd.alpha;
-    int s = tid / M, j = tid - s * M;
-    for (int tau = tid; tau < total; tau += BPSF_CU * nthreads) {
+    for (int tau = tid; tau < MS; tau += BPSF_CU * nthreads) {
         CTask<DC, REG> t[BPSF_CU];
 #pragma unroll
-        for (int u = 0; u < BPSF_CU; ++u) {
-            c_load<DC, REG>(t[u], cd, L, T, s, j, tau + u * nthreads < total, run, fresh);
-            advance(s, j, nthreads, M);
-        }
+        for (int u = 0; u < BPSF_CU; ++u) c_load<DC, REG>(t[u], L, T, MS, lgS, tau + u * nthreads, tau + u * nthreads < MS);
 #pragma unroll
-        for (int u = 0; u < BPSF_CU; ++u) c_compute_store<DC, REG>(t[u], M, alpha);
+        for (int u = 0; u < BPSF_CU; ++u) c_compute_store<DC, REG>(t[u], MS, alpha);
     }
 }
 
@@ -223,22 +214,23 @@ __device__ __forceinline__ void c_phase(const CodeDev &cd, const LayoutMem &L, c
 // ---------------------------------------------------------------------------
 template <int DVS>
 struct VTask {
-    uint16_t pos[DVS];
+    uint16_t pos[DVS];  // edge positions k*M + j of the column's checks
     float r[DVS];
     float lc;
-    unsigned f;  // decision (bit 15) and flip count of (slot, variable)
-    int s, i, tau;
-    bool on, fr;
+    unsigned f;  // decision (bit 15) and flip count of (variable, slot)
+    int tau;
+    bool on;
 };
 
+// Task tau = i*S + s of the interleaved team layout: column i of slot s
+// (s is the lane's fixed slot).
 template <int DVS, int DVX>
-__device__ __forceinline__ void v_load(VTask<DVS> &t, const LayoutMem &L, const TeamMem &T, int P, int s, int i,
-                                       int tau, bool valid, unsigned run, unsigned fresh) {
-    t.on = valid && ((run >> s) & 1u);
-    if (!t.on) return;
-    t.s = s;
-    t.i = i;
+__device__ __forceinline__ void v_load(VTask<DVS> &t, const LayoutMem &L, const TeamMem &T, int lgS, int s, int tau,
+                                       bool on) {
+    t.on = on;
+    if (!on) return;
     t.tau = tau;
+    const int i = tau >> lgS;
     const uint16_t *vp = L.vpos + i * DVS;
     if (DVS == 4) {
         const uint2 raw = *reinterpret_cast<const uint2 *>(vp);
@@ -251,19 +243,19 @@ __device__ __forceinline__ void v_load(VTask<DVS> &t, const LayoutMem &L, const 
         for (int k = 0; k < DVS; ++k) t.pos[k] = vp[k];
     }
     t.lc = L.lch[i];
-    const float *ms = T.m + s * P;
+    const float *ms = T.m + s;
 #pragma unroll
     for (int k = 0; k < DVS; ++k)
-        if (DVX > 0 ? (k < DVX) : true) t.r[k] = (DVX > 0 || t.pos[k] != 0xffffu) ? ms[t.pos[k]] : 0.f;
-    t.fr = (fresh >> s) & 1u;
-    t.f = t.fr ? 0u : (unsigned)T.flips[tau];
+        if (DVX > 0 ? (k < DVX) : true)
+            t.r[k] = (DVX > 0 || t.pos[k] != 0xffffu) ? ms[(int)t.pos[k] << lgS] : 0.f;
+    t.f = (unsigned)T.flips[tau];
 }
 
 template <int DVS, int DVX, bool DEBUG>
-__device__ __forceinline__ void v_compute_store(const VTask<DVS> &t, const StreamDev &sd, const TeamMem &T, int P,
-                                                int N, int Ws, unsigned initm) {
+__device__ __forceinline__ void v_compute_store(const VTask<DVS> &t, const StreamDev &sd, const TeamMem &T, int lgS,
+                                                int s, unsigned initm) {
     if (!t.on) return;
-    float *ms = T.m + t.s * P;
+    float *ms = T.m + s;
     float lo;
     if (DVX == 3) {
         // Three checks: shared prefix l_ch + r0.
@@ -272,9 +264,9 @@ __device__ __forceinline__ void v_compute_store(const VTask<DVS> &t, const Strea
         lo = __fadd_rn(q2, t.r[2]);
         const float q1 = __fadd_rn(t0, t.r[2]);
         const float q0 = __fadd_rn(__fadd_rn(t.lc, t.r[1]), t.r[2]);
-        ms[t.pos[0]] = q0;
-        ms[t.pos[1]] = q1;
-        ms[t.pos[2]] = q2;
+        ms[(int)t.pos[0] << lgS] = q0;
+        ms[(int)t.pos[1] << lgS] = q1;
+        ms[(int)t.pos[2] << lgS] = q2;
     } else {
 #pragma unroll
         for (int k = 0; k < DVS; ++k) {
@@ -283,7 +275,7 @@ __device__ __forceinline__ void v_compute_store(const VTask<DVS> &t, const Strea
 #pragma unroll
                 for (int k2 = 0; k2 < DVS; ++k2)
                     if (k2 != k && t.pos[k2] != 0xffffu) acc = __fadd_rn(acc, t.r[k2]);
-                ms[t.pos[k]] = acc;
+                ms[(int)t.pos[k] << lgS] = acc;
             }
         }
         lo = t.lc;
@@ -292,43 +284,47 @@ __device__ __forceinline__ void v_compute_store(const VTask<DVS> &t, const Strea
             if (t.pos[k] != 0xffffu) lo = __fadd_rn(lo, t.r[k]);
     }
     const unsigned ebit = (lo <= 0.f) ? 1u : 0u;
-    if (DEBUG && ((initm >> t.s) & 1u) && sd.dbg.lout) sd.dbg.lout[T.st[t.s].shot * N + t.i] = lo;
-    // One 16-bit word per (slot, variable): bit 15 is the current hard
+    const int i = t.tau >> lgS;
+    if (DEBUG && ((initm >> s) & 1u) && sd.dbg.lout) sd.dbg.lout[T.st[s].shot * sd.code.N + i] = lo;
+    // One 16-bit word per (variable, slot): bit 15 is the current hard
     // decision, bits 0..14 count its flips (Algorithm 1; at most
-    // max_iter <= 32767).  A fresh slot starts from e = 0, count 0.
+    // max_iter <= 32767).  Installing a slot zeroes them (e = 0, count 0).
     if ((t.f >> 15) != ebit) {
         T.flips[t.tau] = (uint16_t)((t.f ^ 0x8000u) + 1u);
-        // The residual syndrome s xor H e toggles at this column's checks.
-        const uint16_t *vc = sd.code.vchk + t.i * DVS;
+        // The residual syndrome s xor H e toggles at this column's checks
+        // (bit c*S + s of the team's residual-syndrome words).
+        const uint16_t *vc = sd.code.vchk + i * DVS;
 #pragma unroll
         for (int k = 0; k < DVS; ++k) {
             if (DVX > 0 ? (k < DVX) : (t.pos[k] != 0xffffu)) {
-                const int c = __ldg(vc + k);
-                atomicXor(&T.mism[t.s * Ws + (c >> 5)], 1u << (c & 31));
+                const int b = ((int)__ldg(vc + k) << lgS) + s;
+                atomicXor(&T.mism[b >> 5], 1u << (b & 31));
             }
         }
-    } else if (t.fr) {
-        T.flips[t.tau] = 0;
     }
 }
 
 template <int DVS, int DVX, bool DEBUG>
-__device__ __forceinline__ void v_phase(const StreamDev &sd, const LayoutMem &L, const TeamMem &T, int S,
-                                        unsigned run, unsigned fresh, unsigned initm, int tid, int nthreads) {
-    const CodeDev &cd = sd.code;
-    const int N = cd.N, P = cd.P, Ws = cd.Ws;
-    const int total = S * N;
-    int s = tid / N, i = tid - s * N;
+__device__ __forceinline__ void v_phase(const StreamDev &sd, const LayoutMem &L, const TeamMem &T, int lgS,
+                                        unsigned initm, int tid, int nthreads) {
+    const int total = sd.code.N << lgS;
+    const int s = tid & ((1 << lgS) - 1);
     for (int tau = tid; tau < total; tau += BPSF_VU * nthreads) {
         VTask<DVS> t[BPSF_VU];
 #pragma unroll
-        for (int u = 0; u < BPSF_VU; ++u) {
-            v_load<DVS, DVX>(t[u], L, T, P, s, i, tau + u * nthreads, tau + u * nthreads < total, run, fresh);
-            advance(s, i, nthreads, N);
-        }
+        for (int u = 0; u < BPSF_VU; ++u)
+            v_load<DVS, DVX>(t[u], L, T, lgS, s, tau + u * nthreads, tau + u * nthreads < total);
 #pragma unroll
-        for (int u = 0; u < BPSF_VU; ++u) v_compute_store<DVS, DVX, DEBUG>(t[u], sd, T, P, N, Ws, initm);
+        for (int u = 0; u < BPSF_VU; ++u) v_compute_store<DVS, DVX, DEBUG>(t[u], sd, T, lgS, s, initm);
     }
+}
+
+// Bits b of a 32-bit word with b = s (mod S): the residual-syndrome bits
+// of slot s when shifted left by s (S is a power of two dividing 32).
+__device__ __forceinline__ unsigned slot_pattern(int S) {
+    unsigned p = 1u;
+    for (int w = S; w < 32; w <<= 1) p |= p << w;
+    return p;
 }
 
 // ---------------------------------------------------------------------------
@@ -339,7 +335,11 @@ __device__ void team_loop(const StreamDev &sd, const LayoutMem &L, const TeamMem
                           int tid, int bar_id, unsigned long long wait_ns) {
     const int lane = tid & 31, wt = tid >> 5, nthreads = 32 * W;
     const CodeDev &cd = sd.code;
-    const int Ws = cd.Ws, Wn = cd.Wn, N = cd.N;
+    const int Wn = cd.Wn, N = cd.N;
+    const int lgS = __ffs(S) - 1;
+    const int my_slot = lane & (S - 1);             // the slot this lane serves in every phase
+    const int n_rwords = ((cd.M << lgS) + 31) >> 5;  // residual-syndrome words of the team
+    const unsigned pat = slot_pattern(S) << (lane < S ? lane : 0);
     unsigned long long idle_since = 0;
     unsigned last_beat = 0;
     for (;;) {
@@ -349,7 +349,6 @@ __device__ void team_loop(const StreamDev &sd, const LayoutMem &L, const TeamMem
             const bool r = stv == kSlotRunning;
             __threadfence_block();
             const unsigned run = __ballot_sync(FULLMASK, r);
-            const unsigned fr = __ballot_sync(FULLMASK, r && ss->fresh);
             const unsigned im = __ballot_sync(FULLMASK, r && ss->kind == 1);
             int ex = 0;
             if (run == 0u) {
@@ -372,32 +371,33 @@ __device__ void team_loop(const StreamDev &sd, const LayoutMem &L, const TeamMem
             }
             if (lane == 0) {
                 T.ctl->run_mask = run;
-                T.ctl->fresh_mask = fr;
                 T.ctl->init_mask = im;
                 T.ctl->exit = ex;
                 T.ctl->iters += (unsigned long long)__popc(run);
             }
         }
         team_sync(W, bar_id);
-        const unsigned run = T.ctl->run_mask, fresh = T.ctl->fresh_mask, initm = T.ctl->init_mask;
+        const unsigned run = T.ctl->run_mask, initm = T.ctl->init_mask;
         const int ex = T.ctl->exit;
         team_sync(W, bar_id);
         if (ex) break;
         if (run == 0u) continue;
-        c_phase<DC, (DVX > 0)>(cd, L, T, S, run, fresh, tid, nthreads);
+        const bool lane_on = (run >> my_slot) & 1u;
+        if (lane_on) c_phase<DC, (DVX > 0)>(cd, L, T, lgS, tid, nthreads);
         team_sync(W, bar_id);
-        v_phase<DVS, DVX, DEBUG>(sd, L, T, S, run, fresh, initm, tid, nthreads);
+        if (lane_on) v_phase<DVS, DVX, DEBUG>(sd, L, T, lgS, initm, tid, nthreads);
         team_sync(W, bar_id);
         if (wt == 0) {
+            // Slot s owns bits s, s + S, s + 2S, ... of every residual-syndrome word.
+            unsigned acc = 0;
+            for (int w = lane; w < n_rwords; w += 32) acc |= T.mism[w];
+            acc = __reduce_or_sync(FULLMASK, acc);
             bool done = false;
             if (lane < S && ((run >> lane) & 1u)) {
                 SlotState *ss = &T.st[lane];
-                ss->fresh = 0;
                 const int it = ss->iter + 1;
                 ss->iter = it;
-                unsigned any = 0;
-                for (int w = 0; w < Ws; ++w) any |= T.mism[lane * Ws + w];
-                const int oc = (any == 0u) ? 1 : (it >= ss->limit ? 2 : 0);
+                const int oc = ((acc & pat) == 0u) ? 1 : (it >= ss->limit ? 2 : 0);
                 if (oc) {
                     ss->outcome = oc;
                     done = true;
@@ -410,7 +410,7 @@ __device__ void team_loop(const StreamDev &sd, const LayoutMem &L, const TeamMem
                 fm &= fm - 1u;
                 for (int w = 0; w < Wn; ++w) {
                     const int i = 32 * w + lane;
-                    const unsigned b = i < N ? ((unsigned)T.flips[s * N + i] >> 15) : 0u;
+                    const unsigned b = i < N ? ((unsigned)T.flips[(i << lgS) + s] >> 15) : 0u;
                     const unsigned word = __ballot_sync(FULLMASK, b != 0u);
                     if (lane == 0) T.ebits[s * Wn + w] = word;
                 }
@@ -478,7 +478,7 @@ __device__ __forceinline__ void finalize_simple(const StreamDev &sd, TeamMem T, 
     const int N = cd.N, Wn = cd.Wn;
     if (kind == 1) {
         if (DEBUG && sd.dbg.flips)
-            for (int i = 0; i < N; ++i) sd.dbg.flips[shot * N + i] = (uint16_t)flip_count(T.flips[s * N + i]);
+            for (int i = 0; i < N; ++i) sd.dbg.flips[shot * N + i] = (uint16_t)flip_count(T.flips[i * sd.S + s]);
         uint32_t *out = job.corr + row * job.corr_stride;
         for (int w = 0; w < Wn; ++w) out[w] = slot_word(T.ebits, Wn, s, w);
         job.conv[row] = conv ? 1 : 0;
@@ -544,9 +544,9 @@ __device__ __forceinline__ void finalize_failed(const StreamDev &sd, TeamMem T, 
     SlotState *ss = &T.st[s];
     const long long shot = ss->shot;
     const long long row = row_of(sd, shot);
-    const int N = cd.N, Wn = cd.Wn, Ws = cd.Ws;
+    const int N = cd.N, Wn = cd.Wn, Ws = cd.Ws, S = sd.S;
     if (DEBUG && sd.dbg.flips)
-        for (int i = lane; i < N; i += 32) sd.dbg.flips[shot * N + i] = (uint16_t)flip_count(T.flips[s * N + i]);
+        for (int i = lane; i < N; i += 32) sd.dbg.flips[shot * N + i] = (uint16_t)flip_count(T.flips[i * S + s]);
     uint32_t *out = job.corr + row * job.corr_stride;
     for (int w = lane; w < Wn; w += 32) out[w] = slot_word(T.ebits, Wn, s, w);
     if (lane == 0) {
@@ -561,7 +561,7 @@ __device__ __forceinline__ void finalize_failed(const StreamDev &sd, TeamMem T, 
     for (int r = 0; r < cd.w; ++r) {
         unsigned best = 0;
         for (int i = lane; i < N; i += 32) {
-            const unsigned key = (flip_count(T.flips[s * N + i]) << 16) | (0xffffu - (unsigned)i);
+            const unsigned key = (flip_count(T.flips[i * S + s]) << 16) | (0xffffu - (unsigned)i);
             if (key < thr && key > best) best = key;
         }
         best = __reduce_max_sync(FULLMASK, best);
@@ -573,7 +573,14 @@ __device__ __forceinline__ void finalize_failed(const StreamDev &sd, TeamMem T, 
         sd.rec.best[row] = ~0ull;
     }
     if (lane < cd.w) sd.rec.phi[row * cd.w + lane] = my_phi;
-    for (int w = lane; w < Ws; w += 32) sd.rec.synd[row * Ws + w] = T.syn[s * Ws + w];
+    // The shot's syndrome, gathered from bits j*S + s of the team's words.
+    for (int w = 0; w < Ws; ++w) {
+        const int j = 32 * w + lane;
+        const int b = j * S + s;
+        const unsigned bit = j < cd.M ? (T.syn[b >> 5] >> (b & 31)) & 1u : 0u;
+        const unsigned word = __ballot_sync(FULLMASK, bit != 0u);
+        if (lane == 0) sd.rec.synd[row * Ws + w] = word;
+    }
     if (DEBUG && sd.dbg.phi && lane < cd.w) sd.dbg.phi[shot * cd.w + lane] = my_phi;
     __threadfence();
     __syncwarp();
@@ -587,28 +594,43 @@ __device__ __forceinline__ void finalize_failed(const StreamDev &sd, TeamMem T, 
     __syncwarp();
 }
 
-// Install ready-queue entry e into slot s (one lane).
-__device__ __forceinline__ void install(const StreamDev &sd, TeamMem T, int s, QEntry *e) {
+// Install ready-queue entry e into slot s (whole manager warp): the slot's
+// bits of the syndrome and residual-syndrome words, its V2C messages set to
+// the channel LLRs (the first C phase reads l_ch on every edge), its
+// decision and flip-count words zeroed.  Bits of other slots in the same
+// words may change meanwhile (the team's atomics on running slots), never
+// this slot's: only bits that differ are toggled, atomically.
+__device__ __forceinline__ void install(const StreamDev &sd, const LayoutMem &L, TeamMem T, int s, const QEntry *e,
+                                        int lane) {
     const CodeDev &cd = sd.code;
+    const int S = sd.S;
     SlotState *ss = &T.st[s];
-    const int Ws = cd.Ws, tail = cd.M & 31;
-    const uint32_t *src = qsyn(e);
-    for (int w = 0; w < Ws; ++w) {
-        unsigned v = src[w];
-        if (w == Ws - 1 && tail) v &= (1u << tail) - 1u;
-        T.syn[s * Ws + w] = v;
-        T.mism[s * Ws + w] = v;
+    const uint32_t *src = qsyn(const_cast<QEntry *>(e));
+    volatile uint32_t *vsyn = T.syn, *vmism = T.mism;
+    for (int j = lane; j < cd.M; j += 32) {
+        const unsigned want = (src[j >> 5] >> (j & 31)) & 1u;
+        const int b = j * S + s;
+        const unsigned m = 1u << (b & 31);
+        if (((vsyn[b >> 5] & m) != 0u) != (want != 0u)) atomicXor(&T.syn[b >> 5], m);
+        if (((vmism[b >> 5] & m) != 0u) != (want != 0u)) atomicXor(&T.mism[b >> 5], m);
     }
-    ss->kind = e->kind;
-    ss->kidx = e->kidx;
-    ss->shot = e->shot;
-    for (int j = 0; j < kMaxW; ++j) ss->phi[j] = e->phi[j];
-    ss->fresh = 1;
-    ss->iter = 0;
-    ss->outcome = 0;
-    ss->limit = e->kind == 1 ? cd.max_iter : cd.short_iter;
-    __threadfence_block();
-    *vstate(ss) = kSlotRunning;
+    for (int k = lane; k < cd.P; k += 32) T.m[k * S + s] = L.lch_pos[k];
+    for (int i = lane; i < cd.N; i += 32) T.flips[i * S + s] = 0;
+    if (lane == 0) {
+        ss->kind = e->kind;
+        ss->kidx = e->kidx;
+        ss->shot = e->shot;
+        for (int j = 0; j < kMaxW; ++j) ss->phi[j] = e->phi[j];
+        ss->iter = 0;
+        ss->outcome = 0;
+        ss->limit = e->kind == 1 ? cd.max_iter : cd.short_iter;
+    }
+    __syncwarp();
+    if (lane == 0) {
+        __threadfence_block();
+        *vstate(ss) = kSlotRunning;
+    }
+    __syncwarp();
 }
 
 // Shots that may be claimed now.
@@ -743,9 +765,9 @@ __device__ __forceinline__ bool prefetch(const StreamDev &sd, unsigned char *qba
 }
 
 template <bool DEBUG>
-__device__ void manager_loop(const StreamDev &sd, unsigned char *team_base, int team_bytes, const TeamOffsets &to,
-                             int teams, int S, unsigned char *qbase, int Q, BlockHdr *hdr, int lane,
-                             unsigned long long wait_ns) {
+__device__ void manager_loop(const StreamDev &sd, const LayoutMem &L, unsigned char *team_base, int team_bytes,
+                             const TeamOffsets &to, int teams, int S, unsigned char *qbase, int Q, BlockHdr *hdr,
+                             int lane, unsigned long long wait_ns) {
     const CodeDev &cd = sd.code;
     const int qstride = qentry_bytes(cd.Ws);
     const int nslots = teams * S;
@@ -785,14 +807,18 @@ __device__ void manager_loop(const StreamDev &sd, unsigned char *team_base, int 
             const int t = inr ? g / S : 0, s = inr ? g - t * S : 0;
             TeamMem T = team_mem(team_base + t * team_bytes, to);
             const bool empty = inr && *vstate(&T.st[s]) == kSlotEmpty;
-            const unsigned em = __ballot_sync(FULLMASK, empty);
-            const int rank = __popc(em & ((1u << lane) - 1u));
+            unsigned em = __ballot_sync(FULLMASK, empty);
             const int avail = mg.tail - mg.head;
-            if (empty && rank < avail) {
-                QEntry *e = qentry(qbase, (mg.head + rank) % Q, qstride);
-                if (e->kind != 0) install(sd, T, s, e);
-            }
             const int used = __popc(em) < avail ? __popc(em) : avail;
+            // The first `used` empty slots take the next queue entries, in order.
+            for (int r = 0; r < used; ++r) {
+                const int l = __ffs(em) - 1;
+                em &= em - 1u;
+                const int gg = g0 + l;
+                const int tt = gg / S, s2 = gg - tt * S;
+                const QEntry *e = qentry(qbase, (mg.head + r) % Q, qstride);
+                if (e->kind != 0) install(sd, L, team_mem(team_base + tt * team_bytes, to), s2, e, lane);
+            }
             mg.head += used;
             if (used) progress = true;
         }
@@ -960,7 +986,7 @@ __global__ void __launch_bounds__(512, BPSF_MIN_BLOCKS) bpsf_persistent(const __
             cur = sid;
         }
         // Every slot starts empty; teams start idle.
-        const TeamOffsets to = team_offsets(S, cd.N, cd.P, cd.Ws);
+        const TeamOffsets to = team_offsets(S, cd.M, cd.N, cd.P);
         unsigned char *qbase = lay + lo.total;
         unsigned char *team_base = qbase + Q * qentry_bytes(cd.Ws);
         for (int k = tid; k < teams * S; k += blockDim.x) {
@@ -973,6 +999,16 @@ __global__ void __launch_bounds__(512, BPSF_MIN_BLOCKS) bpsf_persistent(const __
             ctl->iters = 0;
             ctl->exit = 0;
         }
+        // Syndrome and residual-syndrome words start at zero: installs toggle
+        // only their own slot's bits, and the padding bits past S*M are read
+        // by the convergence test.
+        {
+            const int sw = (to.mism - to.syn) / 4;
+            for (int k = tid; k < teams * 2 * sw; k += blockDim.x) {
+                const int t = k / (2 * sw), w = k - t * 2 * sw;
+                reinterpret_cast<uint32_t *>(team_base + t * to.total + to.syn)[w] = 0u;
+            }
+        }
         if (tid == 0) {
             hdr->exit = 0;
             hdr->heartbeat = 0u;
@@ -984,7 +1020,7 @@ __global__ void __launch_bounds__(512, BPSF_MIN_BLOCKS) bpsf_persistent(const __
         L.lch = reinterpret_cast<const float *>(lay + lo.lch);
         L.lch_pos = reinterpret_cast<const float *>(lay + lo.lch_pos);
         if (warp == 0) {
-            manager_loop<DEBUG>(sd, team_base, to.total, to, teams, S, qbase, Q, hdr, lane, kp.wait_ns);
+            manager_loop<DEBUG>(sd, L, team_base, to.total, to, teams, S, qbase, Q, hdr, lane, kp.wait_ns);
         } else {
             const int team = (warp - 1) / W;
             if (team < teams) {
