@@ -766,7 +766,6 @@ extern "C" bpsf_status bpsf_autotune(bpsf_ctx *c, double p_sample, int64_t n_sam
             for (int B : Bs_) {
                 bpsf_tuning t{W, S, B, 0};
                 if (B % W) continue;
-                if (W > 1 && S > 4) continue;
                 bpsf_plan pl;
                 if (bpsf_make_plan(cs1, 1, &t, false, &pl) != BPSF_OK) continue;
                 c->tune = t;

@@ -169,14 +169,16 @@ __device__ __forceinline__ void c_compute_store(CTask<DC, REG> &t, int MS, float
             sx ^= __float_as_uint(t.v[k]);
         }
     }
-    const float g1 = __fmul_rn(alpha, m1), g2 = __fmul_rn(alpha, m2);
+    // The row's sign product goes into both magnitudes (they are >= 0); each
+    // output then flips it by its own input's sign bit.
     sx &= 0x80000000u;
+    const unsigned g1 = __float_as_uint(__fmul_rn(alpha, m1)) | sx;
+    const unsigned g2 = __float_as_uint(__fmul_rn(alpha, m2)) | sx;
 #pragma unroll
     for (int k = 0; k < DC; ++k) {
         if (REG || k < t.deg) {
-            const float mag = (fabsf(t.v[k]) == m1) ? g2 : g1;
-            const unsigned bits = __float_as_uint(mag) | ((sx ^ __float_as_uint(t.v[k])) & 0x80000000u);
-            t.p[k * MS] = __uint_as_float(bits);
+            const unsigned mag = (fabsf(t.v[k]) == m1) ? g2 : g1;
+            t.p[k * MS] = __uint_as_float(mag ^ (__float_as_uint(t.v[k]) & 0x80000000u));
         }
     }
 }
@@ -884,14 +886,17 @@ struct KernelParams {
     unsigned long long wait_ns;
 };
 
-// Minimum resident blocks per SM the register allocation must allow
-// (2 caps registers at 64 per thread so two 512-thread blocks fit).
+// Minimum resident blocks per SM the register allocation must allow: two
+// caps registers at 64 per thread, so two 512-thread blocks (or three
+// smaller ones) fit on an SM.  Only the exact-degree variant takes it; the
+// others (wider rows, irregular codes whose shared-memory needs allow few
+// slots per SM anyway) keep the full register budget.
 #ifndef BPSF_MIN_BLOCKS
-#define BPSF_MIN_BLOCKS 1
+#define BPSF_MIN_BLOCKS 2
 #endif
 
 template <int DC, int DVS, int DVX, bool DEBUG>
-__global__ void __launch_bounds__(512, BPSF_MIN_BLOCKS) bpsf_persistent(const __grid_constant__ KernelParams kp) {
+__global__ void __launch_bounds__(512, (DVX > 0 ? BPSF_MIN_BLOCKS : 1)) bpsf_persistent(const __grid_constant__ KernelParams kp) {
     extern __shared__ __align__(16) unsigned char smem[];
     BlockHdr *hdr = reinterpret_cast<BlockHdr *>(smem);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;

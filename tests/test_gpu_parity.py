@@ -194,7 +194,8 @@ def test_launch_shape_does_not_change_results():
     oc, e, s = make_inputs("bb144", 0.07, 4000, 5)
     dec = decoder("bb144", 0.07, P)
     ref = gpu_decode(dec, s)
-    for t in [(1, 1, 4, 0), (1, 16, 4, 0), (2, 2, 8, 0), (4, 1, 8, 1), (1, 8, 4, 0), (1, 2, 15, 0), (8, 1, 8, 0), (1, 32, 2, 0)]:
+    for t in [(1, 1, 4, 0), (1, 16, 4, 0), (2, 2, 8, 0), (4, 1, 8, 1), (1, 8, 4, 0), (1, 2, 15, 0), (8, 1, 8, 0),
+              (1, 32, 2, 0), (8, 32, 8, 0), (4, 16, 12, 0)]:
         dec.tuning = t
         got = gpu_decode(dec, s)
         for key in ("corr", "conv", "iters", "stage"):
