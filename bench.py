@@ -319,7 +319,8 @@ def run_gpu(args, rank, world, pool):
     if rank == 0 and not args.no_extras:
         extras["phenomenological"] = run_phenom(B, codes, torch)
         extras["mixed_one_launch"] = run_mixed(B, codes, torch)
-        extras["served"] = run_served(B, codes, torch, (1e4, 1e5, 1e6, 3.16e6, 1e7), seconds=args.serve_seconds)
+        extras["served"] = run_served(B, codes, torch, (1e4, 1e5, 1e6, 3.16e6, 1e7), seconds=args.serve_seconds,
+                                      tuning=args.serve_tuning)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -368,6 +369,8 @@ def run_gpu(args, rank, world, pool):
 # --------------------------------------------------------------------------
 
 SERVE_BB = ("bb72", "bb90", "bb108", "bb144", "bb288")
+# Served BB codes run latency-oriented teams (a lone slot's iteration is short).
+SERVE_TUNING = (1, 1, 15, 0)
 PHENOM_PARAMS = dict(max_iter=200, alpha=0.625, w=5, w_max=0, short_iter=30, select=0)
 
 
@@ -425,7 +428,7 @@ def run_mixed(B, codes, torch):
     return res
 
 
-def run_served(B, codes, torch, loads, seconds=2.0, pool_shots=8192):
+def run_served(B, codes, torch, loads, seconds=2.0, pool_shots=8192, tuning=None):
     """Poisson request stream over the five BB codes (p = 0.05) and the 12-round
     phenomenological [[144]] model (p = q = 0.003), through bpsf_serve_*.
     Requests carry b = max(1, load / 10000) shots (at most ~10^4 requests/s);
@@ -436,6 +439,8 @@ def run_served(B, codes, torch, loads, seconds=2.0, pool_shots=8192):
     for k, name in enumerate(SERVE_BB):
         c = codes.bb(name)
         d = B.Decoder(c.ptr, c.idx, c.M, c.N, np.full(c.N, 0.05), B.Params(**PARAMS))
+        if tuning:
+            d.tuning = tuning  # team shape of the served BB codes (latency vs throughput)
         e = synth.bernoulli_bits(synth.SEEDS["serve"], 1 + k, 0, pool_shots, c.N, 0.05)
         pools.append(d.syndrome(_packed_errors_dev(torch, e, d.Wn)).cpu().numpy().view(np.uint32))
         decs.append(d)
@@ -501,7 +506,8 @@ def run_served(B, codes, torch, loads, seconds=2.0, pool_shots=8192):
         srv.stop()
     for dk in decs:
         dk.close()
-    return {"mix": list(SERVE_BB) + ["bb144_phenom12"], "loads": results, "closed_loop_p50_p99_ms": closed,
+    return {"mix": list(SERVE_BB) + ["bb144_phenom12"], "tuning_bb": list(tuning) if tuning else "default",
+            "loads": results, "closed_loop_p50_p99_ms": closed,
             "plain_per_shot_ms": {"p50": float(np.percentile(lat_plain, 50)), "p99": float(np.percentile(lat_plain, 99)),
                                   "p999": float(np.percentile(lat_plain, 99.9))}}
 
@@ -522,6 +528,8 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="skip the served / phenomenological / mixed lines")
     ap.add_argument("--serve-seconds", type=float, default=2.0)
     ap.add_argument("--only-served", action="store_true", help="run only the served measurement (diagnostics)")
+    ap.add_argument("--serve-tuning", type=lambda x: tuple(int(v) for v in x.split(",")), default=SERVE_TUNING,
+                    help="team shape W,S,B,blocks_per_sm of the served BB codes")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -536,7 +544,8 @@ def main():
         libbuild.build()
         from paper_2507_00254_gb300 import bpsf as B
         from paper_2507_00254_gb300 import codes
-        print(json.dumps(run_served(B, codes, torch, (1e4, 1e5, 1e6, 3.16e6, 1e7), seconds=args.serve_seconds)))
+        print(json.dumps(run_served(B, codes, torch, (1e4, 1e5, 1e6, 3.16e6, 1e7), seconds=args.serve_seconds,
+                                    tuning=args.serve_tuning)))
         return
     # Input generation and the oracle baseline use a spawn pool created before CUDA starts.
     ctx = mp.get_context("spawn")

@@ -644,7 +644,7 @@ __device__ __forceinline__ long long shots_available(const StreamDev &sd) {
 // Fill the ready queue: trial tickets first, then new shots.
 template <bool DEBUG>
 __device__ __forceinline__ bool prefetch(const StreamDev &sd, unsigned char *qbase, int Q, int qstride, int lane,
-                                         MgrState &mg, unsigned long long wait_ns) {
+                                         MgrState &mg, int n_empty, unsigned long long wait_ns) {
     const CodeDev &cd = sd.code;
     const int Ws = cd.Ws;
     bool got_any = false;
@@ -658,7 +658,11 @@ __device__ __forceinline__ bool prefetch(const StreamDev &sd, unsigned char *qba
                 const unsigned long long total = ld_vol_u64(&sd.ctr->rec_count) * (unsigned long long)cd.n_trials;
                 if (cur >= total) break;
                 unsigned long long want = total - cur;
-                const unsigned long long lim = space < 32 ? (unsigned long long)space : 32ull;
+                unsigned long long lim = space < 32 ? (unsigned long long)space : 32ull;
+                // Few tickets left (the tail of a failed shot's trials): take
+                // no more than the slots free now, so they spread over blocks.
+                if (want < 128ull && lim > (unsigned long long)n_empty) lim = (unsigned long long)n_empty;
+                if (lim == 0ull) break;
                 if (want > lim) want = lim;
                 if (atomicCAS(&sd.ctr->ticket_next, cur, cur + want) == cur) {
                     t0 = cur;
@@ -777,6 +781,7 @@ __device__ void manager_loop(const StreamDev &sd, const LayoutMem &L, unsigned c
     for (;;) {
         bool progress = false;
         bool busy = false;
+        int n_empty = 0;  // empty slots of the block (warp-uniform)
         if (lane == 0) hdr->heartbeat = hdr->heartbeat + 1u;
         // (A) write out finished slots.
         for (int g0 = 0; g0 < nslots; g0 += 32) {
@@ -800,6 +805,7 @@ __device__ void manager_loop(const StreamDev &sd, const LayoutMem &L, unsigned c
             }
             if (fin) *vstate(&T.st[s]) = kSlotEmpty;
             if (__any_sync(FULLMASK, fin)) progress = true;
+            n_empty += __popc(__ballot_sync(FULLMASK, inr && (fin || stv == kSlotEmpty)));
         }
         __syncwarp();
         // (B) refill empty slots from the ready queue.
@@ -822,11 +828,12 @@ __device__ void manager_loop(const StreamDev &sd, const LayoutMem &L, unsigned c
                 if (e->kind != 0) install(sd, L, team_mem(team_base + tt * team_bytes, to), s2, e, lane);
             }
             mg.head += used;
+            n_empty -= used;
             if (used) progress = true;
         }
         __syncwarp();
         // (C) claim work ahead.
-        if (prefetch<DEBUG>(sd, qbase, Q, qstride, lane, mg, wait_ns)) progress = true;
+        if (prefetch<DEBUG>(sd, qbase, Q, qstride, lane, mg, n_empty, wait_ns)) progress = true;
         // Count finished initial runs once no new shot can be claimed.
         if (!(sd.flags & kServe)) {
             int exhausted = 0;
