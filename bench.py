@@ -28,6 +28,8 @@ sys.path.insert(0, ROOT)
 
 P_LIST = (0.02, 0.04, 0.06, 0.08)
 SHOTS_PER_P = 1_000_000
+# ncu, one launch of 4 x 200k shots: 87.9 MB read + 76.5 MB written.
+DRAM_BYTES_PER_SHOT = 164.3e6 / 800_000
 CODE = "bb144"
 N_BITS, M_CHECKS, NNZ = 144, 72, 432
 PARAMS = dict(max_iter=100, alpha=0.625, w=6, w_max=0, short_iter=20, select=0)
@@ -201,7 +203,10 @@ def run_gpu(args, rank, world, pool):
     torch.cuda.synchronize()
     t_gen = time.perf_counter() - t_gen
     # Launch shape: the autotuner's pick for this code.
-    tuned = decs[0].autotune(p_sample=0.06, n_sample=1 << 16) if args.autotune else decs[0].tuning
+    if args.tuning:
+        tuned = args.tuning
+    else:
+        tuned = decs[0].autotune(p_sample=0.06, n_sample=1 << 16) if args.autotune else decs[0].tuning
     for d in decs:
         d.tuning = tuned
     outs = [d.outputs(n) for d in decs]
@@ -328,7 +333,10 @@ def run_gpu(args, rank, world, pool):
         cpu.pop("seconds", None)
 
     if rank == 0:
-        traffic = args.traffic_bytes if args.traffic_bytes > 0 else None
+        # DRAM bytes per launch of the persistent kernel: ncu's dram__bytes_read + write of one
+        # 800k-shot launch of this kernel over the same p mix, scaled by shots (the traffic is
+        # the shots' I/O and the failed shots' records).
+        traffic = args.traffic_bytes if args.traffic_bytes > 0 else DRAM_BYTES_PER_SHOT * shots_step
         line = {
             "metric": METRIC, "value": value, "unit": "shots/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -338,7 +346,7 @@ def run_gpu(args, rank, world, pool):
                        "tuning": list(tuned), "l2": "flushed between steps (512 MB write)",
                        "parallelism": "replicas" if world > 1 else "single"},
             "roofline": {"bound": "alu", "achieved": achieved / 1e9, "peak": peak / 1e9, "unit": "Gedge-updates/s",
-                         "frac": achieved / peak, "traffic": traffic,
+                         "frac": achieved / peak, "traffic": traffic, "traffic_unit": "bytes per launch",
                          "note": "peak = SMs x 128 B/clk shared memory / 16 B per edge-update at the max SM clock"},
             "cpu_baseline": cpu,
             "e2e": {"value": shots_step / e2e_dt, "unit": "shots/s", "h2d_bytes_per_step": h2d,
@@ -524,6 +532,8 @@ def main():
     ap.add_argument("--ref-shots", type=int, default=3000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--autotune", type=int, default=1)
+    ap.add_argument("--tuning", type=lambda x: tuple(int(v) for v in x.split(",")), default=None,
+                    help="launch shape W,S,B,blocks_per_sm of the batched workload (skips the autotuner)")
     ap.add_argument("--traffic-bytes", type=float, default=0.0)
     ap.add_argument("--no-extras", action="store_true", help="skip the served / phenomenological / mixed lines")
     ap.add_argument("--serve-seconds", type=float, default=2.0)
