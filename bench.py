@@ -361,7 +361,8 @@ def run_gpu(args, rank, world, pool):
                       "plain": plain},
             "ler": ler,
             "work": {"edge_updates_per_step": edge_updates, "failed_shots_per_step": sum(w["failed_shots"] for w in work),
-                     "trial_runs_per_step": sum(w["trial_runs"] for w in work)},
+                     "trial_runs_per_step": sum(w["trial_runs"] for w in work),
+                     "slot_occupancy": sum(w["iterations"] for w in work) / max(1, sum(w["slot_capacity"] for w in work))},
             "input_gen_s": t_gen, "wall_timed_s": t_wall,
         }
         line.update(extras)

@@ -359,13 +359,17 @@ bpsf_status bpsf_selftest_wait(bpsf_ctx *ctx, int64_t wait_us, void *stream);
 int32_t bpsf_num_trials(const bpsf_ctx *ctx);
 
 /* Work counters of the last decode on ctx (after bpsf_sync): runs started,
- * failed shots (records) and edge-updates (iterations x nnz summed over runs). */
+ * failed shots (records), iterations and edge-updates (iterations x nnz
+ * summed over runs), and the slot-iterations the teams offered while they
+ * had work (team iterations with a running slot x slots per team);
+ * iterations / slot_capacity is the slot occupancy of the launch. */
 typedef struct {
     int64_t initial_runs;
     int64_t failed_shots;
     int64_t trial_runs;
     int64_t iterations;
     int64_t edge_updates;
+    int64_t slot_capacity;
 } bpsf_work;
 bpsf_status bpsf_last_work(bpsf_ctx *ctx, bpsf_work *out);
 

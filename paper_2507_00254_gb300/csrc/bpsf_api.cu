@@ -100,7 +100,9 @@ bpsf_status bpsf_ensure_kernel_attrs(int variant, int smem_optin) {
 // Launch plans
 // ---------------------------------------------------------------------------
 
-static int plan_queue(int teams, int S) { return std::min(128, std::max(32, 2 * teams * S)); }
+// The slots' inboxes hold one item each besides the ready queue, so the
+// queue only covers claim batches.
+static int plan_queue(int teams, int S) { return std::min(32, std::max(16, teams * S / 2)); }
 
 static int plan_smem(const bpsf_ctx *c, int vstride, int S, int teams, int Q) {
     return block_smem_bytes(c->M, c->N, c->P, c->Ws, vstride, S, teams, Q);
@@ -517,6 +519,7 @@ extern "C" bpsf_status bpsf_sync(bpsf_ctx *c, void *stream) {
     c->last.trial_runs = (int64_t)k.trial_runs;
     c->last.iterations = (int64_t)k.iters_total;
     c->last.edge_updates = (int64_t)k.iters_total * c->nnz;
+    c->last.slot_capacity = (int64_t)k.slot_capacity;
     if (k.status) {
         const unsigned stv = k.status;
         cudaMemsetAsync(&dc->status, 0, sizeof(unsigned), (cudaStream_t)stream);
@@ -567,7 +570,7 @@ extern "C" bpsf_status bpsf_decode_plain(bpsf_ctx *c, int64_t n, const uint32_t 
     preset.init_done = 1;
     preset.rec_count = 1;
     *c->h_preset = preset;
-    long long iters_total = 0, trial_runs = 0, failed = 0;
+    long long iters_total = 0, trial_runs = 0, failed = 0, cap = 0;
     for (int64_t i = 0; i < n; ++i) {
         JobDev job{synd + i * ss, corr + i * cs, conv + i, iters + i, stage ? stage + i : nullptr, 1, ss, cs};
         cudaError_t e = cudaMemsetAsync(c->d_ctr, 0, sizeof(StreamCounters), s);
@@ -580,6 +583,7 @@ extern "C" bpsf_status bpsf_decode_plain(bpsf_ctx *c, int64_t n, const uint32_t 
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) return bpsf_fail(BPSF_ECUDA, "plain initial run: %s", cudaGetErrorString(e));
         iters_total += (long long)c->h_ctr->iters_total;
+        cap += (long long)c->h_ctr->slot_capacity;
         if (c->h_flag[0] == 0 && c->p.w > 0) {
             ++failed;
             e = cudaMemcpyAsync(c->d_ctr, c->h_preset, sizeof(StreamCounters), cudaMemcpyHostToDevice, s);
@@ -593,9 +597,10 @@ extern "C" bpsf_status bpsf_decode_plain(bpsf_ctx *c, int64_t n, const uint32_t 
                 return bpsf_fail(BPSF_ETIMEOUT, "device status 0x%x in the trial sweep", c->h_ctr->status);
             trial_runs += (long long)c->h_ctr->trial_runs;
             iters_total += (long long)c->h_ctr->iters_total;
+            cap += (long long)c->h_ctr->slot_capacity;
         }
     }
-    c->last = bpsf_work{n, failed, trial_runs, iters_total, iters_total * c->nnz};
+    c->last = bpsf_work{n, failed, trial_runs, iters_total, iters_total * c->nnz, cap};
     c->d_ctr_last = c->d_ctr;
     return BPSF_OK;
 }

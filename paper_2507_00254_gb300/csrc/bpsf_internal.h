@@ -58,7 +58,7 @@ struct StreamCounters {
     unsigned long long rec_count;    // failed shots published
     unsigned int status;             // kDev* bits
     unsigned int pad0;
-    unsigned long long pad[1];
+    unsigned long long slot_capacity;  // slot-iterations offered: team iterations with work x S
 };
 static_assert(sizeof(StreamCounters) == 64, "counter block is one 64-byte line");
 
@@ -153,16 +153,17 @@ __host__ __device__ inline LayoutOffsets layout_offsets(int M, int N, int vstrid
     return o;
 }
 
-// Slot states.
-enum : int { kSlotEmpty = 0, kSlotRunning = 1, kSlotFinished = 2 };
+// Slot states.  Only the slot's team writes them: RUNNING while a run is in
+// progress, PENDING once it has finished and until its facts are in the
+// slot's outbox, EMPTY when the slot may take the item in its inbox.
+enum : int { kSlotEmpty = 0, kSlotRunning = 1, kSlotPending = 2 };
 
-// Per-slot state in shared memory (80 bytes).  EMPTY and FINISHED slots
-// belong to the manager warp, RUNNING slots to their team.
+// Per-slot state in shared memory (80 bytes), owned by the slot's team.
 struct SlotState {
     int state;       // kSlot*
     int kind;        // 1 initial run, 2 trial run
     int spare;
-    int outcome;     // 1 converged, 2 iteration cap (valid when FINISHED)
+    int outcome;     // 1 converged, 2 iteration cap (valid when PENDING)
     int iter;        // iterations completed
     int limit;       // iteration cap of this run
     int kidx;        // trial index (trial runs)
@@ -173,44 +174,34 @@ struct SlotState {
 };
 static_assert(sizeof(SlotState) == 80, "slot state is 80 bytes");
 
+// A finished run's facts, handed from the team to the manager (64 bytes;
+// the packed hard decision goes with it in the team's ebits words).  The
+// team fills an outbox whose flag is 0 and then sets it; the manager writes
+// the results out and clears it.  phi: Phi = top(flip_count, w) for a failed
+// initial run, the trial's own Phi for a trial run.
+struct OutBox {
+    int full;
+    int kind;
+    int kidx;
+    int outcome;
+    int iter;
+    int pad;
+    long long shot;
+    uint16_t phi[kMaxW];
+};
+static_assert(sizeof(OutBox) == 64, "outbox is 64 bytes");
+
 // Team control block (32 bytes).
 struct TeamCtl {
     unsigned run_mask, spare, init_mask;
     int exit;
     unsigned long long iters;  // iterations run by this team (all slots)
-    unsigned long long pad;
+    unsigned long long cap;    // team iterations with a running slot, times S
 };
 
-// Per-team shared memory.  The S slots of a team (S a power of two <= 32)
-// are interleaved: item x of slot s sits at x*S + s, so lane l always serves
-// slot l mod S and the 32 lanes of a warp touch 32 consecutive items.
-//   syn, mism : bit j*S + s = s_j, resp. the residual syndrome (s xor H e)_j,
-//               of slot s, in (S*M + 31)/32 words each
-//   ebits     : S x Wn words, the hard decision of a finished slot, packed
-//   flips     : 16-bit word i*S + s = decision (bit 15) and flip count of
-//               variable i in slot s
-//   m         : float k*S + s = the message of edge position k = r*M + j
-//               (r-th edge of row j) in slot s: V2C and C2V alternately
-struct TeamOffsets {
-    int ctl, state, syn, mism, ebits, flips, m, total;
-};
-
-__host__ __device__ inline TeamOffsets team_offsets(int S, int M, int N, int P) {
-    TeamOffsets o;
-    const int sw = (S * M + 31) / 32;
-    int p = 0;
-    o.ctl = p;    p += 32;
-    o.state = p;  p += 80 * S;
-    o.syn = p;    p += 4 * sw;
-    o.mism = p;   p += 4 * sw;
-    o.ebits = p;  p += 4 * S * ((N + 31) / 32);
-    o.flips = p;  p = align_up(p + 2 * S * N, 16);
-    o.m = p;      p += 4 * S * P;
-    o.total = align_up(p, 16);
-    return o;
-}
-
-// Manager's ready queue: entries of 48 bytes of fields plus Ws syndrome words.
+// Work items of the manager's ready queue and of the slots' inboxes: 48
+// bytes of fields plus Ws syndrome words.  kind 1 = initial run of a shot,
+// 2 = trial run, 0 = nothing to run (an item dropped after a timed-out wait).
 struct QEntry {
     int kind;
     int kidx;
@@ -221,9 +212,48 @@ static_assert(sizeof(QEntry) == 48, "queue entry header is 48 bytes");
 
 __host__ __device__ inline int qentry_bytes(int Ws) { return align_up(48 + 4 * Ws, 16); }
 
+// Per-team shared memory.  The S slots of a team (S a power of two <= 32)
+// are interleaved: item x of slot s sits at x*S + s, so lane l always serves
+// slot l mod S and the 32 lanes of a warp touch 32 consecutive items.
+//   syn, mism : bit j*S + s = s_j, resp. the residual syndrome (s xor H e)_j,
+//               of slot s, in (S*M + 31)/32 words each
+//   ebits     : S x Wn words, the hard decision of a finished run, packed
+//               (part of the slot's outbox)
+//   flips     : 16-bit word i*S + s = decision (bit 15) and flip count of
+//               variable i in slot s
+//   m         : float k*S + s = the message of edge position k = r*M + j
+//               (r-th edge of row j) in slot s: V2C and C2V alternately
+//   outbox    : S OutBox entries
+//   inflag    : S flags, 1 while the slot's inbox holds an item
+//   inbox     : S work items (qentry_bytes(Ws) each), filled by the manager
+//               ahead of time and installed by the team as soon as the slot
+//               is free, so a slot does not wait for the manager between runs
+struct TeamOffsets {
+    int ctl, state, syn, mism, ebits, flips, m, outbox, inflag, inbox, ibstride, total;
+};
+
+__host__ __device__ inline TeamOffsets team_offsets(int S, int M, int N, int P, int Ws) {
+    TeamOffsets o;
+    const int sw = (S * M + 31) / 32;
+    int p = 0;
+    o.ctl = p;     p += 32;
+    o.state = p;   p += 80 * S;
+    o.outbox = p;  p += 64 * S;
+    o.syn = p;     p += 4 * sw;
+    o.mism = p;    p += 4 * sw;
+    o.ebits = p;   p += 4 * S * ((N + 31) / 32);
+    o.inflag = p;  p = align_up(p + 4 * S, 16);
+    o.ibstride = qentry_bytes(Ws);
+    o.inbox = p;   p += o.ibstride * S;
+    o.flips = p;   p = align_up(p + 2 * S * N, 16);
+    o.m = p;       p += 4 * S * P;
+    o.total = align_up(p, 16);
+    return o;
+}
+
 __host__ __device__ inline int block_smem_bytes(int M, int N, int P, int Ws, int vstride, int S, int teams, int Q) {
     return kBlockHeaderBytes + layout_offsets(M, N, vstride, P).total + Q * qentry_bytes(Ws) +
-           teams * team_offsets(S, M, N, P).total;
+           teams * team_offsets(S, M, N, P, Ws).total;
 }
 
 // Kernel entry points (bpsf_kernels.cu).

@@ -100,6 +100,10 @@ struct TeamMem {
     uint32_t *syn, *mism, *ebits;
     uint16_t *flips;
     float *m;
+    OutBox *ob;         // per slot: a finished run's facts for the manager
+    int *ibf;           // per slot: 1 while the inbox holds an item
+    unsigned char *ib;  // per slot: the next work item
+    int ibstride;
 };
 
 __device__ __forceinline__ TeamMem team_mem(unsigned char *tb, const TeamOffsets &to) {
@@ -111,10 +115,18 @@ __device__ __forceinline__ TeamMem team_mem(unsigned char *tb, const TeamOffsets
     T.ebits = reinterpret_cast<uint32_t *>(tb + to.ebits);
     T.flips = reinterpret_cast<uint16_t *>(tb + to.flips);
     T.m = reinterpret_cast<float *>(tb + to.m);
+    T.ob = reinterpret_cast<OutBox *>(tb + to.outbox);
+    T.ibf = reinterpret_cast<int *>(tb + to.inflag);
+    T.ib = tb + to.inbox;
+    T.ibstride = to.ibstride;
     return T;
 }
 
 __device__ __forceinline__ volatile int *vstate(SlotState *s) { return reinterpret_cast<volatile int *>(&s->state); }
+__device__ __forceinline__ volatile int *vflag(int *f) { return reinterpret_cast<volatile int *>(f); }
+
+// Flip count of a (variable, slot) word: bits 0..14 (bit 15 is the decision).
+__device__ __forceinline__ unsigned flip_count(uint16_t f) { return (unsigned)f & 0x7fffu; }
 
 // ---------------------------------------------------------------------------
 // C phase: check-node update, Eq. (c2v).  For row j with V2C inputs q_k:
@@ -330,6 +342,136 @@ __device__ __forceinline__ unsigned slot_pattern(int S) {
 }
 
 // ---------------------------------------------------------------------------
+// Team-side slot service (warp 0 of the team, all lanes).  A finished slot
+// (PENDING) hands its facts to its outbox as soon as the manager has drained
+// the previous ones; a free slot (EMPTY) installs the item the manager put
+// in its inbox.  The slot therefore runs again at the team's next iteration,
+// without a round trip through the manager.
+// ---------------------------------------------------------------------------
+
+// Pack finished slot s into its outbox: the hard decision into words, the
+// run's facts, and for a failed initial run Phi = top(flip_count, w) (keys
+// (count << 16 | 0xffff - i) are distinct, so each round takes the largest
+// key below the previous one: count descending, index ascending).
+template <bool DEBUG>
+__device__ __forceinline__ void team_pack(const StreamDev &sd, const TeamMem &T, int lgS, int s, int lane) {
+    const CodeDev &cd = sd.code;
+    const int N = cd.N, Wn = cd.Wn;
+    const SlotState *ss = &T.st[s];
+    OutBox *ob = &T.ob[s];
+    for (int w = 0; w < Wn; ++w) {
+        const int i = 32 * w + lane;
+        const unsigned b = i < N ? ((unsigned)T.flips[(i << lgS) + s] >> 15) : 0u;
+        const unsigned word = __ballot_sync(FULLMASK, b != 0u);
+        if (lane == 0) T.ebits[s * Wn + w] = word;
+    }
+    const int kind = ss->kind, outcome = ss->outcome;
+    if (kind == 1 && outcome == 2 && cd.w > 0) {
+        unsigned thr = 0xffffffffu;
+        for (int r = 0; r < cd.w; ++r) {
+            unsigned best = 0;
+            for (int i = lane; i < N; i += 32) {
+                const unsigned key = (flip_count(T.flips[(i << lgS) + s]) << 16) | (0xffffu - (unsigned)i);
+                if (key < thr && key > best) best = key;
+            }
+            best = __reduce_max_sync(FULLMASK, best);
+            if (lane == 0) ob->phi[r] = (uint16_t)(0xffffu - (best & 0xffffu));
+            thr = best;
+        }
+    } else if (lane < kMaxW) {
+        ob->phi[lane] = ss->phi[lane];
+    }
+    if (DEBUG && kind == 1 && sd.dbg.flips)
+        for (int i = lane; i < N; i += 32)
+            sd.dbg.flips[ss->shot * N + i] = (uint16_t)flip_count(T.flips[(i << lgS) + s]);
+    if (lane == 0) {
+        ob->kind = kind;
+        ob->kidx = ss->kidx;
+        ob->outcome = outcome;
+        ob->iter = ss->iter;
+        ob->shot = ss->shot;
+    }
+    __syncwarp();
+    if (lane == 0) {
+        __threadfence_block();
+        *vflag(&ob->full) = 1;
+    }
+    __syncwarp();
+}
+
+// Install slot s's inbox item: the slot's bits of the syndrome and
+// residual-syndrome words (atomic toggles of the bits that differ: lanes
+// share words), its V2C messages set to the channel LLRs (the first C phase
+// reads l_ch on every edge), its decision and flip-count words zeroed.
+__device__ __forceinline__ void team_install(const StreamDev &sd, const LayoutMem &L, const TeamMem &T, int S, int s,
+                                             int lane) {
+    const CodeDev &cd = sd.code;
+    const QEntry *e = reinterpret_cast<const QEntry *>(T.ib + s * T.ibstride);
+    const uint32_t *src = reinterpret_cast<const uint32_t *>(T.ib + s * T.ibstride + 48);
+    SlotState *ss = &T.st[s];
+    volatile uint32_t *vsyn = T.syn, *vmism = T.mism;
+    for (int j = lane; j < cd.M; j += 32) {
+        const unsigned want = (src[j >> 5] >> (j & 31)) & 1u;
+        const int b = j * S + s;
+        const unsigned m = 1u << (b & 31);
+        if (((vsyn[b >> 5] & m) != 0u) != (want != 0u)) atomicXor(&T.syn[b >> 5], m);
+        if (((vmism[b >> 5] & m) != 0u) != (want != 0u)) atomicXor(&T.mism[b >> 5], m);
+    }
+    for (int k = lane; k < cd.P; k += 32) T.m[k * S + s] = L.lch_pos[k];
+    for (int i = lane; i < cd.N; i += 32) T.flips[i * S + s] = 0;
+    if (lane == 0) {
+        ss->kind = e->kind;
+        ss->kidx = e->kidx;
+        ss->shot = e->shot;
+        for (int j = 0; j < kMaxW; ++j) ss->phi[j] = e->phi[j];
+        ss->iter = 0;
+        ss->outcome = 0;
+        ss->limit = e->kind == 1 ? cd.max_iter : cd.short_iter;
+    }
+    __syncwarp();
+}
+
+template <bool DEBUG>
+__device__ __forceinline__ void team_service(const StreamDev &sd, const LayoutMem &L, const TeamMem &T, int S, int lgS,
+                                             int lane) {
+    const int stv = lane < S ? *vstate(&T.st[lane]) : kSlotRunning;
+    const bool obf = lane < S && *vflag(&T.ob[lane].full) != 0;
+    unsigned pm = __ballot_sync(FULLMASK, stv == kSlotPending && !obf);
+    if (pm) __threadfence_block();  // the manager's reads of the drained outboxes are done
+    while (pm) {
+        const int s = __ffs(pm) - 1;
+        pm &= pm - 1u;
+        team_pack<DEBUG>(sd, T, lgS, s, lane);
+        // team_pack set the outbox flag before the slot reads EMPTY (the
+        // manager's exit test reads the state first, then the outbox flag).
+        if (lane == 0) {
+            __threadfence_block();
+            *vstate(&T.st[s]) = kSlotEmpty;
+        }
+    }
+    __syncwarp();
+    const bool want = lane < S && *vstate(&T.st[lane]) == kSlotEmpty && *vflag(&T.ibf[lane]) != 0;
+    unsigned im = __ballot_sync(FULLMASK, want);
+    if (im) __threadfence_block();  // the inbox items are visible
+    while (im) {
+        const int s = __ffs(im) - 1;
+        im &= im - 1u;
+        const int kind = reinterpret_cast<const QEntry *>(T.ib + s * T.ibstride)->kind;
+        if (kind != 0) team_install(sd, L, T, S, s, lane);
+        __syncwarp();
+        if (lane == 0) {
+            // RUNNING before the inbox reads empty: the manager's exit test
+            // reads the inbox flag first, then the state.
+            __threadfence_block();
+            if (kind != 0) *vstate(&T.st[s]) = kSlotRunning;
+            __threadfence_block();
+            *vflag(&T.ibf[s]) = 0;
+        }
+        __syncwarp();
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Compute team loop.
 // ---------------------------------------------------------------------------
 template <int DC, int DVS, int DVX, bool DEBUG>
@@ -346,6 +488,7 @@ __device__ void team_loop(const StreamDev &sd, const LayoutMem &L, const TeamMem
     unsigned last_beat = 0;
     for (;;) {
         if (wt == 0) {
+            team_service<DEBUG>(sd, L, T, S, lgS, lane);
             SlotState *ss = &T.st[lane < S ? lane : 0];
             const int stv = lane < S ? *vstate(ss) : kSlotEmpty;
             const bool r = stv == kSlotRunning;
@@ -376,6 +519,7 @@ __device__ void team_loop(const StreamDev &sd, const LayoutMem &L, const TeamMem
                 T.ctl->init_mask = im;
                 T.ctl->exit = ex;
                 T.ctl->iters += (unsigned long long)__popc(run);
+                if (run) T.ctl->cap += (unsigned long long)S;
             }
         }
         team_sync(W, bar_id);
@@ -405,23 +549,8 @@ __device__ void team_loop(const StreamDev &sd, const LayoutMem &L, const TeamMem
                     done = true;
                 }
             }
-            // Pack the hard decision of each finished slot into words for the manager.
-            unsigned fm = __ballot_sync(FULLMASK, done);
-            while (fm) {
-                const int s = __ffs(fm) - 1;
-                fm &= fm - 1u;
-                for (int w = 0; w < Wn; ++w) {
-                    const int i = 32 * w + lane;
-                    const unsigned b = i < N ? ((unsigned)T.flips[(i << lgS) + s] >> 15) : 0u;
-                    const unsigned word = __ballot_sync(FULLMASK, b != 0u);
-                    if (lane == 0) T.ebits[s * Wn + w] = word;
-                }
-            }
-            __syncwarp();
-            if (done) {
-                __threadfence_block();
-                *vstate(&T.st[lane]) = kSlotFinished;
-            }
+            // Finished slots are packed by the service step at the next loop top.
+            if (done) *vstate(&T.st[lane]) = kSlotPending;
         }
     }
 }
@@ -450,8 +579,6 @@ __device__ __forceinline__ uint32_t *qsyn(QEntry *e) {
 // Word w of finished slot s's hard decision (packed by its team).
 __device__ __forceinline__ unsigned slot_word(const uint32_t *ebits, int Wn, int s, int w) { return ebits[s * Wn + w]; }
 
-// Flip count of (slot, variable) word f: bits 0..14 (bit 15 is the decision).
-__device__ __forceinline__ unsigned flip_count(uint16_t f) { return (unsigned)f & 0x7fffu; }
 
 __device__ __forceinline__ long long row_of(const StreamDev &sd, long long shot) {
     return (sd.flags & kServe) ? (shot % sd.serve.rows) : shot;
@@ -466,21 +593,19 @@ __device__ __forceinline__ void shot_complete(const StreamDev &sd, long long row
     st_release_sys_u32(sd.serve.row_done + row, (unsigned)(shot + 1));
 }
 
-// Lane-parallel write-out of finished slots that need no warp cooperation:
+// Lane-parallel write-out of outboxes that need no warp cooperation:
 // converged or uncorrectable initial runs, and trial runs.
 template <bool DEBUG>
 __device__ __forceinline__ void finalize_simple(const StreamDev &sd, TeamMem T, int s, MgrState &mg) {
     const CodeDev &cd = sd.code;
     const JobDev &job = sd.job;
-    SlotState *ss = &T.st[s];
+    const OutBox *ss = &T.ob[s];
     const int kind = ss->kind, iter = ss->iter;
     const bool conv = ss->outcome == 1;
     const long long shot = ss->shot;
     const long long row = row_of(sd, shot);
-    const int N = cd.N, Wn = cd.Wn;
+    const int Wn = cd.Wn;
     if (kind == 1) {
-        if (DEBUG && sd.dbg.flips)
-            for (int i = 0; i < N; ++i) sd.dbg.flips[shot * N + i] = (uint16_t)flip_count(T.flips[i * sd.S + s]);
         uint32_t *out = job.corr + row * job.corr_stride;
         for (int w = 0; w < Wn; ++w) out[w] = slot_word(T.ebits, Wn, s, w);
         job.conv[row] = conv ? 1 : 0;
@@ -538,52 +663,29 @@ __device__ __forceinline__ void finalize_simple(const StreamDev &sd, TeamMem T, 
 }
 
 // Failed initial run with trials (whole manager warp): provisional output,
-// Phi = top(flip_count, w), record, publication of its trials.
+// record (Phi from the outbox, the shot's syndrome from its input row) and
+// publication of its trials.
 template <bool DEBUG>
 __device__ __forceinline__ void finalize_failed(const StreamDev &sd, TeamMem T, int s, int lane, MgrState &mg) {
     const CodeDev &cd = sd.code;
     const JobDev &job = sd.job;
-    SlotState *ss = &T.st[s];
-    const long long shot = ss->shot;
+    const OutBox *ob = &T.ob[s];
+    const long long shot = ob->shot;
     const long long row = row_of(sd, shot);
-    const int N = cd.N, Wn = cd.Wn, Ws = cd.Ws, S = sd.S;
-    if (DEBUG && sd.dbg.flips)
-        for (int i = lane; i < N; i += 32) sd.dbg.flips[shot * N + i] = (uint16_t)flip_count(T.flips[i * S + s]);
+    const int Wn = cd.Wn, Ws = cd.Ws;
     uint32_t *out = job.corr + row * job.corr_stride;
     for (int w = lane; w < Wn; w += 32) out[w] = slot_word(T.ebits, Wn, s, w);
     if (lane == 0) {
         job.conv[row] = 0;
         job.iters[row] = (int16_t)cd.max_iter;
         if (job.stage) job.stage[row] = 2;
-    }
-    // Keys (count << 16 | 0xffff - i) are distinct, so each round takes the
-    // largest key below the previous one: count descending, index ascending.
-    unsigned thr = 0xffffffffu;
-    int my_phi = 0;
-    for (int r = 0; r < cd.w; ++r) {
-        unsigned best = 0;
-        for (int i = lane; i < N; i += 32) {
-            const unsigned key = (flip_count(T.flips[i * S + s]) << 16) | (0xffffu - (unsigned)i);
-            if (key < thr && key > best) best = key;
-        }
-        best = __reduce_max_sync(FULLMASK, best);
-        if (lane == r) my_phi = (int)(0xffffu - (best & 0xffffu));
-        thr = best;
-    }
-    if (lane == 0) {
         sd.rec.done[row] = 0u;
         sd.rec.best[row] = ~0ull;
     }
-    if (lane < cd.w) sd.rec.phi[row * cd.w + lane] = my_phi;
-    // The shot's syndrome, gathered from bits j*S + s of the team's words.
-    for (int w = 0; w < Ws; ++w) {
-        const int j = 32 * w + lane;
-        const int b = j * S + s;
-        const unsigned bit = j < cd.M ? (T.syn[b >> 5] >> (b & 31)) & 1u : 0u;
-        const unsigned word = __ballot_sync(FULLMASK, bit != 0u);
-        if (lane == 0) sd.rec.synd[row * Ws + w] = word;
-    }
-    if (DEBUG && sd.dbg.phi && lane < cd.w) sd.dbg.phi[shot * cd.w + lane] = my_phi;
+    if (lane < cd.w) sd.rec.phi[row * cd.w + lane] = ob->phi[lane];
+    const uint32_t *syn = job.synd + row * job.synd_stride;
+    for (int w = lane; w < Ws; w += 32) sd.rec.synd[row * Ws + w] = __ldcg(syn + w);
+    if (DEBUG && sd.dbg.phi && lane < cd.w) sd.dbg.phi[shot * cd.w + lane] = ob->phi[lane];
     __threadfence();
     __syncwarp();
     if (lane == 0) {
@@ -592,45 +694,6 @@ __device__ __forceinline__ void finalize_failed(const StreamDev &sd, TeamMem T, 
         sd.rec.qshot[qi] = shot;
         st_release_u64(sd.rec.qseq + qi, q + 1ull);
         mg.init_local += 1;
-    }
-    __syncwarp();
-}
-
-// Install ready-queue entry e into slot s (whole manager warp): the slot's
-// bits of the syndrome and residual-syndrome words, its V2C messages set to
-// the channel LLRs (the first C phase reads l_ch on every edge), its
-// decision and flip-count words zeroed.  Bits of other slots in the same
-// words may change meanwhile (the team's atomics on running slots), never
-// this slot's: only bits that differ are toggled, atomically.
-__device__ __forceinline__ void install(const StreamDev &sd, const LayoutMem &L, TeamMem T, int s, const QEntry *e,
-                                        int lane) {
-    const CodeDev &cd = sd.code;
-    const int S = sd.S;
-    SlotState *ss = &T.st[s];
-    const uint32_t *src = qsyn(const_cast<QEntry *>(e));
-    volatile uint32_t *vsyn = T.syn, *vmism = T.mism;
-    for (int j = lane; j < cd.M; j += 32) {
-        const unsigned want = (src[j >> 5] >> (j & 31)) & 1u;
-        const int b = j * S + s;
-        const unsigned m = 1u << (b & 31);
-        if (((vsyn[b >> 5] & m) != 0u) != (want != 0u)) atomicXor(&T.syn[b >> 5], m);
-        if (((vmism[b >> 5] & m) != 0u) != (want != 0u)) atomicXor(&T.mism[b >> 5], m);
-    }
-    for (int k = lane; k < cd.P; k += 32) T.m[k * S + s] = L.lch_pos[k];
-    for (int i = lane; i < cd.N; i += 32) T.flips[i * S + s] = 0;
-    if (lane == 0) {
-        ss->kind = e->kind;
-        ss->kidx = e->kidx;
-        ss->shot = e->shot;
-        for (int j = 0; j < kMaxW; ++j) ss->phi[j] = e->phi[j];
-        ss->iter = 0;
-        ss->outcome = 0;
-        ss->limit = e->kind == 1 ? cd.max_iter : cd.short_iter;
-    }
-    __syncwarp();
-    if (lane == 0) {
-        __threadfence_block();
-        *vstate(ss) = kSlotRunning;
     }
     __syncwarp();
 }
@@ -781,19 +844,19 @@ __device__ void manager_loop(const StreamDev &sd, const LayoutMem &L, unsigned c
     for (;;) {
         bool progress = false;
         bool busy = false;
-        int n_empty = 0;  // empty slots of the block (warp-uniform)
+        int n_empty = 0;  // idle slots of the block with an empty inbox (warp-uniform)
         if (lane == 0) hdr->heartbeat = hdr->heartbeat + 1u;
-        // (A) write out finished slots.
+        // (A) write out the outboxes the teams filled.
         for (int g0 = 0; g0 < nslots; g0 += 32) {
             const int g = g0 + lane;
             const bool inr = g < nslots;
             const int t = inr ? g / S : 0, s = inr ? g - t * S : 0;
             TeamMem T = team_mem(team_base + t * team_bytes, to);
             const int stv = inr ? *vstate(&T.st[s]) : kSlotEmpty;
+            const bool fin = inr && *vflag(&T.ob[s].full) != 0;
             __threadfence_block();
-            const bool fin = stv == kSlotFinished;
-            const bool coop = fin && T.st[s].kind == 1 && T.st[s].outcome == 2 && cd.w > 0;
-            if (__any_sync(FULLMASK, stv == kSlotRunning)) busy = true;
+            const bool coop = fin && T.ob[s].kind == 1 && T.ob[s].outcome == 2 && cd.w > 0;
+            if (__any_sync(FULLMASK, stv != kSlotEmpty)) busy = true;
             if (fin && !coop) finalize_simple<DEBUG>(sd, T, s, mg);
             unsigned cm = __ballot_sync(FULLMASK, coop);
             while (cm) {
@@ -803,33 +866,41 @@ __device__ void manager_loop(const StreamDev &sd, const LayoutMem &L, unsigned c
                 const int tt = gg / S, s2 = gg - tt * S;
                 finalize_failed<DEBUG>(sd, team_mem(team_base + tt * team_bytes, to), s2, lane, mg);
             }
-            if (fin) *vstate(&T.st[s]) = kSlotEmpty;
+            __syncwarp();
+            if (fin) {
+                __threadfence_block();
+                *vflag(&T.ob[s].full) = 0;
+            }
             if (__any_sync(FULLMASK, fin)) progress = true;
-            n_empty += __popc(__ballot_sync(FULLMASK, inr && (fin || stv == kSlotEmpty)));
         }
         __syncwarp();
-        // (B) refill empty slots from the ready queue.
-        for (int g0 = 0; g0 < nslots && mg.tail > mg.head; g0 += 32) {
-            const int g = g0 + lane;
-            const bool inr = g < nslots;
-            const int t = inr ? g / S : 0, s = inr ? g - t * S : 0;
-            TeamMem T = team_mem(team_base + t * team_bytes, to);
-            const bool empty = inr && *vstate(&T.st[s]) == kSlotEmpty;
-            unsigned em = __ballot_sync(FULLMASK, empty);
-            const int avail = mg.tail - mg.head;
-            const int used = __popc(em) < avail ? __popc(em) : avail;
-            // The first `used` empty slots take the next queue entries, in order.
-            for (int r = 0; r < used; ++r) {
-                const int l = __ffs(em) - 1;
-                em &= em - 1u;
-                const int gg = g0 + l;
-                const int tt = gg / S, s2 = gg - tt * S;
-                const QEntry *e = qentry(qbase, (mg.head + r) % Q, qstride);
-                if (e->kind != 0) install(sd, L, team_mem(team_base + tt * team_bytes, to), s2, e, lane);
+        // (B) fill empty inboxes from the ready queue: idle slots first (they
+        // start at once), then running ones (their next run).  Count the
+        // slots left idle with nothing in their inbox.
+        for (int pass = 0; pass < 2; ++pass) {
+            for (int g0 = 0; g0 < nslots && (pass == 1 || mg.tail > mg.head); g0 += 32) {
+                const int g = g0 + lane;
+                const bool inr = g < nslots;
+                const int t = inr ? g / S : 0, s = inr ? g - t * S : 0;
+                TeamMem T = team_mem(team_base + t * team_bytes, to);
+                const bool idle = inr && *vstate(&T.st[s]) == kSlotEmpty;
+                const bool open = inr && *vflag(&T.ibf[s]) == 0 && (pass == 1 || idle);
+                const unsigned om = __ballot_sync(FULLMASK, open);
+                const int rank = __popc(om & ((1u << lane) - 1u));
+                const int avail = mg.tail - mg.head;
+                const bool take = open && rank < avail;
+                if (take) {
+                    const uint4 *src = reinterpret_cast<const uint4 *>(qentry(qbase, (mg.head + rank) % Q, qstride));
+                    uint4 *dst = reinterpret_cast<uint4 *>(T.ib + s * T.ibstride);
+                    for (int k = 0; k < qstride / 16; ++k) dst[k] = src[k];
+                    __threadfence_block();
+                    *vflag(&T.ibf[s]) = 1;
+                }
+                const int used = __popc(om) < avail ? __popc(om) : avail;
+                mg.head += used;
+                if (used) progress = true;
+                if (pass == 1) n_empty += __popc(__ballot_sync(FULLMASK, open && !take && idle));
             }
-            mg.head += used;
-            n_empty -= used;
-            if (used) progress = true;
         }
         __syncwarp();
         // (C) claim work ahead.
@@ -848,14 +919,24 @@ __device__ void manager_loop(const StreamDev &sd, const LayoutMem &L, unsigned c
                 }
             }
         }
-        // (D) leave when nothing is running, queued or claimable.
+        // (D) leave when nothing is running, queued, boxed or claimable.
         if (!busy && !progress && mg.tail == mg.head) {
             bool any_slot = false;
             for (int g0 = 0; g0 < nslots; g0 += 32) {
                 const int g = g0 + lane;
                 const int t = g < nslots ? g / S : 0, s = g < nslots ? g - t * S : 0;
                 TeamMem T = team_mem(team_base + t * team_bytes, to);
-                const bool occ = g < nslots && *vstate(&T.st[s]) != kSlotEmpty;
+                // Read order matters: inbox flag, state, outbox flag (the
+                // team writes state before clearing the inbox flag, and the
+                // outbox flag before the state).
+                bool occ = false;
+                if (g < nslots) {
+                    occ = *vflag(&T.ibf[s]) != 0;
+                    __threadfence_block();
+                    occ = occ || *vstate(&T.st[s]) != kSlotEmpty;
+                    __threadfence_block();
+                    occ = occ || *vflag(&T.ob[s].full) != 0;
+                }
                 if (__any_sync(FULLMASK, occ)) any_slot = true;
             }
             // Nothing left for this code: hand the block back, which then
@@ -873,13 +954,16 @@ __device__ void manager_loop(const StreamDev &sd, const LayoutMem &L, unsigned c
             atomicAdd(&sd.ctr->init_done, (unsigned long long)init_tot);
         }
         if (trial_tot) atomicAdd(&sd.ctr->trial_runs, (unsigned long long)trial_tot);
-        unsigned long long it = 0;
+        unsigned long long it = 0, cap = 0;
         for (int t = 0; t < teams; ++t) {
             TeamMem T = team_mem(team_base + t * team_bytes, to);
             it += T.ctl->iters;
+            cap += T.ctl->cap;
             T.ctl->iters = 0;
+            T.ctl->cap = 0;
         }
         if (it) atomicAdd(&sd.ctr->iters_total, it);
+        if (cap) atomicAdd(&sd.ctr->slot_capacity, cap);
         __threadfence_block();
         hdr->exit = 1;
     }
@@ -998,17 +1082,21 @@ __global__ void __launch_bounds__(512, (DVX > 0 ? BPSF_MIN_BLOCKS : 1)) bpsf_per
             cur = sid;
         }
         // Every slot starts empty; teams start idle.
-        const TeamOffsets to = team_offsets(S, cd.M, cd.N, cd.P);
+        const TeamOffsets to = team_offsets(S, cd.M, cd.N, cd.P, cd.Ws);
         unsigned char *qbase = lay + lo.total;
         unsigned char *team_base = qbase + Q * qentry_bytes(cd.Ws);
         for (int k = tid; k < teams * S; k += blockDim.x) {
-            SlotState *ss = reinterpret_cast<SlotState *>(team_base + (k / S) * to.total + to.state) + (k % S);
+            unsigned char *tb = team_base + (k / S) * to.total;
+            SlotState *ss = reinterpret_cast<SlotState *>(tb + to.state) + (k % S);
             ss->state = kSlotEmpty;
             ss->kind = 0;
+            reinterpret_cast<OutBox *>(tb + to.outbox)[k % S].full = 0;
+            reinterpret_cast<int *>(tb + to.inflag)[k % S] = 0;
         }
         for (int t = tid; t < teams; t += blockDim.x) {
             TeamCtl *ctl = reinterpret_cast<TeamCtl *>(team_base + t * to.total + to.ctl);
             ctl->iters = 0;
+            ctl->cap = 0;
             ctl->exit = 0;
         }
         // Syndrome and residual-syndrome words start at zero: installs toggle

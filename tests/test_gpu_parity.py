@@ -288,6 +288,9 @@ def test_work_counters_are_consistent():
     assert w["trial_runs"] == w["failed_shots"] * 63
     assert w["edge_updates"] == w["iterations"] * 432
     assert w["iterations"] >= int(g["iters"][g["stage"] == 0].sum()) + 100 * w["failed_shots"]
+    # Slots offered while teams worked: at least the iterations run, at most all of them busy.
+    S = dec.tuning[1]
+    assert w["iterations"] <= w["slot_capacity"] and w["slot_capacity"] % S == 0
 
 
 # --------------------------------------------------------------------------
