@@ -198,6 +198,10 @@ __device__ __forceinline__ void c_compute_store(CTask<DC, REG> &t, int MS, float
 // Rows (C phase) and columns (V phase) a thread handles per step: their
 // loads are all issued before any of their stores, for instruction-level
 // parallelism (the tasks of one step touch disjoint messages).
+// Teams with S >= 2 slots run the paired phases (one lane per slot pair).
+#ifndef BPSF_PAIRS
+#define BPSF_PAIRS 1
+#endif
 #ifndef BPSF_CU
 #define BPSF_CU 1
 #endif
@@ -330,6 +334,152 @@ __device__ __forceinline__ void v_phase(const StreamDev &sd, const LayoutMem &L,
             v_load<DVS, DVX>(t[u], L, T, lgS, s, tau + u * nthreads, tau + u * nthreads < total);
 #pragma unroll
         for (int u = 0; u < BPSF_VU; ++u) v_compute_store<DVS, DVX, DEBUG>(t[u], sd, T, lgS, s, initm);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Paired phases (S >= 2): lane l serves the slot pair (2p, 2p+1), p = l mod
+// S/2.  The pair's items are adjacent words, so one 64-bit access moves both
+// slots' messages; column tables, LLRs, addresses and loop control are
+// shared, and both slots' residual-syndrome bits of a check sit in one word.
+// A slot of the pair that is not running is computed on its own stale data
+// and its messages are rewritten harmlessly (an install resets them); its
+// decision/flip word and syndrome bits are left alone.
+// ---------------------------------------------------------------------------
+template <int DC, bool REG>
+__device__ __forceinline__ void c_row_pair(const LayoutMem &L, const TeamMem &T, int MH, int lgH, int tau2,
+                                           float alpha) {
+    float2 *p2 = reinterpret_cast<float2 *>(T.m) + tau2;  // tau2 = j*(S/2) + p
+    const int deg = REG ? DC : (int)L.row_deg[tau2 >> lgH];
+    const unsigned sb = T.syn[(2 * tau2) >> 5] >> ((2 * tau2) & 31);
+    float2 v[DC];
+#pragma unroll
+    for (int k = 0; k < DC; ++k)
+        if (REG || k < deg) v[k] = p2[k * MH];
+    float m1x = __int_as_float(0x7f800000), m2x = m1x, m1y = m1x, m2y = m1x;
+    unsigned sx = (sb & 1u) << 31, sy = ((sb >> 1) & 1u) << 31;
+#pragma unroll
+    for (int k = 0; k < DC; ++k) {
+        if (REG || k < deg) {
+            const float ax = fabsf(v[k].x), ay = fabsf(v[k].y);
+            m2x = fminf(m2x, fmaxf(m1x, ax));
+            m1x = fminf(m1x, ax);
+            m2y = fminf(m2y, fmaxf(m1y, ay));
+            m1y = fminf(m1y, ay);
+            sx ^= __float_as_uint(v[k].x);
+            sy ^= __float_as_uint(v[k].y);
+        }
+    }
+    sx &= 0x80000000u;
+    sy &= 0x80000000u;
+    const unsigned g1x = __float_as_uint(__fmul_rn(alpha, m1x)) | sx, g2x = __float_as_uint(__fmul_rn(alpha, m2x)) | sx;
+    const unsigned g1y = __float_as_uint(__fmul_rn(alpha, m1y)) | sy, g2y = __float_as_uint(__fmul_rn(alpha, m2y)) | sy;
+#pragma unroll
+    for (int k = 0; k < DC; ++k) {
+        if (REG || k < deg) {
+            float2 o;
+            o.x = __uint_as_float(((fabsf(v[k].x) == m1x) ? g2x : g1x) ^ (__float_as_uint(v[k].x) & 0x80000000u));
+            o.y = __uint_as_float(((fabsf(v[k].y) == m1y) ? g2y : g1y) ^ (__float_as_uint(v[k].y) & 0x80000000u));
+            p2[k * MH] = o;
+        }
+    }
+}
+
+template <int DC, bool REG>
+__device__ __forceinline__ void c_phase_pair(const CodeDev &cd, const LayoutMem &L, const TeamMem &T, int lgS, int tid,
+                                             int nthreads) {
+    const int lgH = lgS - 1;
+    const int MH = cd.M << lgH;
+    const float alpha = cd.alpha;
+    for (int tau2 = tid; tau2 < MH; tau2 += nthreads) c_row_pair<DC, REG>(L, T, MH, lgH, tau2, alpha);
+}
+
+template <int DVS, int DVX, bool DEBUG>
+__device__ __forceinline__ void v_phase_pair(const StreamDev &sd, const LayoutMem &L, const TeamMem &T, int lgS,
+                                             bool on0, bool on1, unsigned initm, int tid, int nthreads) {
+    const CodeDev &cd = sd.code;
+    const int lgH = lgS - 1;
+    const int total = cd.N << lgH;
+    const int p = tid & ((1 << lgH) - 1);
+    const int s0 = 2 * p;
+    float2 *m2 = reinterpret_cast<float2 *>(T.m) + p;
+    uint32_t *f2 = reinterpret_cast<uint32_t *>(T.flips);
+    for (int tau2 = tid; tau2 < total; tau2 += nthreads) {
+        const int i = tau2 >> lgH;
+        uint16_t pos[DVS];
+        const uint16_t *vp = L.vpos + i * DVS;
+        if (DVS == 4) {
+            const uint2 raw = *reinterpret_cast<const uint2 *>(vp);
+            pos[0] = (uint16_t)(raw.x & 0xffffu);
+            pos[1] = (uint16_t)(raw.x >> 16);
+            pos[2] = (uint16_t)(raw.y & 0xffffu);
+            pos[3] = (uint16_t)(raw.y >> 16);
+        } else {
+#pragma unroll
+            for (int k = 0; k < DVS; ++k) pos[k] = vp[k];
+        }
+        const float lc = L.lch[i];
+        float2 r[DVS];
+#pragma unroll
+        for (int k = 0; k < DVS; ++k)
+            if (DVX > 0 ? (k < DVX) : (pos[k] != 0xffffu)) r[k] = m2[(int)pos[k] << lgH];
+        const unsigned f = f2[tau2];
+        float lox, loy;
+        if (DVX == 3) {
+            const float t0x = __fadd_rn(lc, r[0].x), t0y = __fadd_rn(lc, r[0].y);
+            const float q2x = __fadd_rn(t0x, r[1].x), q2y = __fadd_rn(t0y, r[1].y);
+            lox = __fadd_rn(q2x, r[2].x);
+            loy = __fadd_rn(q2y, r[2].y);
+            m2[(int)pos[0] << lgH] = make_float2(__fadd_rn(__fadd_rn(lc, r[1].x), r[2].x),
+                                                 __fadd_rn(__fadd_rn(lc, r[1].y), r[2].y));
+            m2[(int)pos[1] << lgH] = make_float2(__fadd_rn(t0x, r[2].x), __fadd_rn(t0y, r[2].y));
+            m2[(int)pos[2] << lgH] = make_float2(q2x, q2y);
+        } else {
+#pragma unroll
+            for (int k = 0; k < DVS; ++k) {
+                if (pos[k] != 0xffffu) {
+                    float ax = lc, ay = lc;
+#pragma unroll
+                    for (int k2 = 0; k2 < DVS; ++k2)
+                        if (k2 != k && pos[k2] != 0xffffu) {
+                            ax = __fadd_rn(ax, r[k2].x);
+                            ay = __fadd_rn(ay, r[k2].y);
+                        }
+                    m2[(int)pos[k] << lgH] = make_float2(ax, ay);
+                }
+            }
+            lox = lc;
+            loy = lc;
+#pragma unroll
+            for (int k = 0; k < DVS; ++k)
+                if (pos[k] != 0xffffu) {
+                    lox = __fadd_rn(lox, r[k].x);
+                    loy = __fadd_rn(loy, r[k].y);
+                }
+        }
+        const unsigned ebx = (lox <= 0.f) ? 1u : 0u, eby = (loy <= 0.f) ? 1u : 0u;
+        if (DEBUG && sd.dbg.lout) {
+            if (on0 && ((initm >> s0) & 1u)) sd.dbg.lout[T.st[s0].shot * cd.N + i] = lox;
+            if (on1 && ((initm >> (s0 + 1)) & 1u)) sd.dbg.lout[T.st[s0 + 1].shot * cd.N + i] = loy;
+        }
+        // Decision (bit 15) and flip count of each slot's 16-bit half.
+        const bool fx = on0 && ((f >> 15) & 1u) != ebx;
+        const bool fy = on1 && ((f >> 31) & 1u) != eby;
+        if (fx || fy) {
+            unsigned lo = f & 0xffffu, hi = f >> 16;
+            if (fx) lo = ((lo ^ 0x8000u) + 1u) & 0xffffu;
+            if (fy) hi = ((hi ^ 0x8000u) + 1u) & 0xffffu;
+            f2[tau2] = lo | (hi << 16);
+            const unsigned bm = (fx ? 1u : 0u) | (fy ? 2u : 0u);
+            const uint16_t *vc = cd.vchk + i * DVS;
+#pragma unroll
+            for (int k = 0; k < DVS; ++k) {
+                if (DVX > 0 ? (k < DVX) : (pos[k] != 0xffffu)) {
+                    const int b = ((int)__ldg(vc + k) << lgS) + s0;
+                    atomicXor(&T.mism[b >> 5], bm << (b & 31));
+                }
+            }
+        }
     }
 }
 
@@ -484,6 +634,7 @@ __device__ void team_loop(const StreamDev &sd, const LayoutMem &L, const TeamMem
     const int my_slot = lane & (S - 1);             // the slot this lane serves in every phase
     const int n_rwords = ((cd.M << lgS) + 31) >> 5;  // residual-syndrome words of the team
     const unsigned pat = slot_pattern(S) << (lane < S ? lane : 0);
+    constexpr bool kPairs = BPSF_PAIRS && DC <= 16;  // the widest rows keep one slot per lane (registers)
     unsigned long long idle_since = 0;
     unsigned last_beat = 0;
     for (;;) {
@@ -528,11 +679,20 @@ __device__ void team_loop(const StreamDev &sd, const LayoutMem &L, const TeamMem
         team_sync(W, bar_id);
         if (ex) break;
         if (run == 0u) continue;
-        const bool lane_on = (run >> my_slot) & 1u;
-        if (lane_on) c_phase<DC, (DVX > 0)>(cd, L, T, lgS, tid, nthreads);
-        team_sync(W, bar_id);
-        if (lane_on) v_phase<DVS, DVX, DEBUG>(sd, L, T, lgS, initm, tid, nthreads);
-        team_sync(W, bar_id);
+        if (kPairs && S >= 2) {
+            const int s0 = 2 * (lane & ((S >> 1) - 1));
+            const bool on0 = (run >> s0) & 1u, on1 = (run >> (s0 + 1)) & 1u;
+            if (on0 || on1) c_phase_pair<DC, (DVX > 0)>(cd, L, T, lgS, tid, nthreads);
+            team_sync(W, bar_id);
+            if (on0 || on1) v_phase_pair<DVS, DVX, DEBUG>(sd, L, T, lgS, on0, on1, initm, tid, nthreads);
+            team_sync(W, bar_id);
+        } else {
+            const bool lane_on = (run >> my_slot) & 1u;
+            if (lane_on) c_phase<DC, (DVX > 0)>(cd, L, T, lgS, tid, nthreads);
+            team_sync(W, bar_id);
+            if (lane_on) v_phase<DVS, DVX, DEBUG>(sd, L, T, lgS, initm, tid, nthreads);
+            team_sync(W, bar_id);
+        }
         if (wt == 0) {
             // Slot s owns bits s, s + S, s + 2S, ... of every residual-syndrome word.
             unsigned acc = 0;
