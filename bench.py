@@ -324,6 +324,7 @@ def run_gpu(args, rank, world, pool):
     if rank == 0 and not args.no_extras:
         extras["phenomenological"] = run_phenom(B, codes, torch)
         extras["mixed_one_launch"] = run_mixed(B, codes, torch)
+        extras["code_capacity_paper_setting"] = run_families(B, codes, torch, harness)
         extras["served"] = run_served(B, codes, torch, (1e4, 1e5, 1e6, 3.16e6, 1e7), seconds=args.serve_seconds,
                                       tuning=args.serve_tuning)
 
@@ -411,6 +412,49 @@ def run_phenom(B, codes, torch, n=100_000):
         out[str(p)] = {"shots": n, "shots_per_s": n / dt, "ms": dt * 1e3, "edge_updates_per_s": w["edge_updates"] / dt,
                        "stage_counts": st, "tuning": list(d.tuning)}
         d.close()
+    return out
+
+
+# The paper's code-capacity setting (Section V, Fig. capacity, the [[154]] study):
+# adaptive damping alpha_t = 1 - 2^-t, weight-1 trial vectors over |Phi| bits,
+# 50 iterations per run.
+FAMILY_SETTINGS = (("bb72", 4), ("bb144", 7), ("cbb126", 6), ("gb254", 13), ("cbb154", 8))
+
+
+def run_families(B, codes, torch, harness, n=100_000, p_list=(0.04, 0.06)):
+    """Code families under the paper's code-capacity setting, batched: shots/s and LER."""
+    import synth
+    out = {}
+    for k, (name, w) in enumerate(FAMILY_SETTINGS):
+        c = codes.bb(name)
+        hx, hz = c.dense(), codes.bb(name, 1).dense()
+        lx = harness.x_logicals(hx, hz)
+        res = {"n": c.N, "k": int(lx.shape[0]), "phi": w}
+        for j, p in enumerate(p_list):
+            d = B.Decoder(c.ptr, c.idx, c.M, c.N, np.full(c.N, p),
+                          B.Params(max_iter=50, alpha=0.0, w=w, w_max=1, short_iter=50))
+            e = synth.bernoulli_bits(6100 + k, j, 0, n, c.N, p)
+            synd = d.syndrome(_packed_errors_dev(torch, e, d.Wn))
+            o = d.outputs(n)
+            d.decode(synd, out=o)  # warm-up
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            d.decode(synd, out=o)
+            dt = time.perf_counter() - t0
+            wk = d.last_work()
+            # Shot fails iff not converged, or the residual e xor e_hat has a nonzero
+            # syndrome or logical (exact: integer sums < 2^24 in float32).
+            G = torch.from_numpy(np.vstack([hx, lx]).astype(np.float32)).cuda()
+            corr = torch.from_numpy(harness.unpack_rows(o["corr"].cpu().numpy().view(np.uint32), c.N)).cuda()
+            r = (torch.from_numpy(e).cuda() ^ corr).float()
+            f = (torch.remainder(r @ G.T, 2.0) > 0.5).any(dim=1) | (o["conv"] == 0)
+            L = float(f.float().mean().item())
+            res[str(p)] = {"shots_per_s": n / dt, "edge_updates_per_s": wk["edge_updates"] / dt,
+                           "ler": L, "sigma": (L * (1 - L) / n) ** 0.5,
+                           "stage_counts": np.bincount(o["stage"].cpu().numpy(), minlength=3).tolist(),
+                           "tuning": list(d.tuning)}
+            d.close()
+        out[name] = res
     return out
 
 

@@ -61,7 +61,12 @@ enum { BPSF_SELECT_MIN_WEIGHT = 0, BPSF_SELECT_FIRST = 1 };
  * Decoder parameters (Algorithm 1 inputs plus the min-sum settings of
  * Section II-B).
  *   max_iter   iterations of the initial run (i_max of Algorithm 1), 1..32767.
- *   alpha      normalisation factor of Eq. (c2v), finite and > 0.
+ *   alpha      normalisation factor of Eq. (c2v), finite and > 0; or 0 for
+ *              adaptive damping alpha_t = 1 - 2^-t at iteration t = 1, 2, ...
+ *              of every run (Section V's schedule, printed there as
+ *              "1 - 2^i"), rounded once to float.  C2V magnitudes are
+ *              clamped at 2^100 (never reached with a fixed alpha at the
+ *              configurations; with alpha_t -> 1 it keeps messages finite).
  *   w          |Phi|, the number of oscillating bits used for trials,
  *              0..16; 0 means plain BP with no post-processing.
  *   w_max      largest trial weight, 1..w; 0 means w (all 2^w - 1 subsets).

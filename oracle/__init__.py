@@ -156,6 +156,11 @@ BB_CODES = {
     "bb108": (9, 6, [(3, 0), (0, 1), (0, 2)], [(0, 3), (1, 0), (2, 0)]),
     "bb144": (12, 6, [(3, 0), (0, 1), (0, 2)], [(0, 3), (1, 0), (2, 0)]),
     "bb288": (12, 12, [(3, 0), (0, 2), (0, 7)], [(0, 3), (1, 0), (2, 0)]),
+    # Appendix "GB codes": [[254,28]], l = 127, m = 1 (polynomials in x only).
+    "gb254": (127, 1, [(0, 0), (15, 0), (20, 0), (28, 0), (66, 0)], [(0, 0), (58, 0), (59, 0), (100, 0), (121, 0)]),
+    # Appendix "Coprime-BB codes" (Table cbbcodes): polynomials in pi = x y.
+    "cbb126": (7, 9, [(0, 0), (1, 1), (58, 58)], [(0, 0), (13, 13), (41, 41)]),
+    "cbb154": (7, 11, [(0, 0), (1, 1), (31, 31)], [(0, 0), (19, 19), (53, 53)]),
 }
 
 

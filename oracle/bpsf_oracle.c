@@ -19,6 +19,13 @@
  *   - the V2C sum and the posterior sum are left folds that start at the
  *     channel LLR and add the C2V messages in ascending check index;
  *   - the normalised magnitude is one multiply alpha * min, then the sign;
+ *   - damping: alpha > 0 is fixed; alpha == 0 selects the adaptive factor
+ *     alpha_t = 1 - 2^-t at iteration t = 1, 2, ... of each run (the paper
+ *     prints it garbled as "1 - 2^i", i the iteration), computed in double
+ *     and rounded once to the mode's type;
+ *   - C2V magnitudes are clamped at 2^100.  With a fixed alpha <= 1/(dv-1)
+ *     messages grow at most geometrically by alpha*(dv-1) and never get
+ *     near it at the workloads; with alpha_t -> 1 the clamp keeps them finite;
  *   - hard decision: e_i = 1 iff l_out_i <= 0 (Section II-B, step 4);
  *   - oscillation counters start at zero with e_prev = 0 and are updated in
  *     every iteration of the initial run (Algorithm 1);

@@ -1,9 +1,12 @@
 """Codes the decoder is exercised on, built through libbpsf's own builders.
 
-Bivariate bicycle codes (Appendix "Code Construction", Table bbcodes) plus
-the two extra BB codes of the mixed-size batch, and the 12-round
-phenomenological detector matrix of the [[144,12,12]] code.  Terms are
-(power of x, power of y).
+Bivariate bicycle codes (Appendix "Code Construction", Table bbcodes), the
+two extra BB codes of the mixed-size batch, the [[254,28]] generalised
+bicycle code (Appendix "GB codes": m = 1, polynomials in x) and the
+coprime-BB codes [[126,12,10]] and [[154,6,16]] (Appendix "Coprime-BB
+codes": polynomials in pi = x y, so pi^e is the term (e, e)), and the
+12-round phenomenological detector matrix of the [[144,12,12]] code.  Terms
+are (power of x, power of y).
 """
 from __future__ import annotations
 
@@ -19,6 +22,9 @@ BB = {
     "bb108": (9, 6, ((3, 0), (0, 1), (0, 2)), ((0, 3), (1, 0), (2, 0))),
     "bb144": (12, 6, ((3, 0), (0, 1), (0, 2)), ((0, 3), (1, 0), (2, 0))),
     "bb288": (12, 12, ((3, 0), (0, 2), (0, 7)), ((0, 3), (1, 0), (2, 0))),
+    "gb254": (127, 1, ((0, 0), (15, 0), (20, 0), (28, 0), (66, 0)), ((0, 0), (58, 0), (59, 0), (100, 0), (121, 0))),
+    "cbb126": (7, 9, ((0, 0), (1, 1), (58, 58)), ((0, 0), (13, 13), (41, 41))),
+    "cbb154": (7, 11, ((0, 0), (1, 1), (31, 31)), ((0, 0), (19, 19), (53, 53))),
 }
 
 PHENOM_ROUNDS = 12

@@ -219,7 +219,8 @@ extern "C" bpsf_status bpsf_create(bpsf_ctx **out, int32_t M, int32_t N, int64_t
     const bpsf_params p = *params;
     if (p.flags != 0) return bpsf_fail(BPSF_EINVAL, "params.flags must be 0");
     if (p.max_iter < 1 || p.max_iter > 32767) return bpsf_fail(BPSF_EINVAL, "max_iter must be in 1..32767");
-    if (!(p.alpha > 0.f) || !std::isfinite(p.alpha)) return bpsf_fail(BPSF_EINVAL, "alpha must be finite and > 0");
+    if (!(p.alpha >= 0.f) || !std::isfinite(p.alpha))
+        return bpsf_fail(BPSF_EINVAL, "alpha must be finite and > 0, or 0 for adaptive damping");
     if (p.w < 0 || p.w > kMaxW) return bpsf_fail(BPSF_EINVAL, "w must be in 0..%d", kMaxW);
     if (p.w > N) return bpsf_fail(BPSF_EINVAL, "w must not exceed N");
     if (p.w > 0) {

@@ -141,6 +141,18 @@ __device__ __forceinline__ unsigned flip_count(uint16_t f) { return (unsigned)f 
 // an XOR of sign bits.  m2 = min(m2, max(m1, a)) keeps the second smallest
 // value branch-free, equal to m1 on ties.
 // ---------------------------------------------------------------------------
+// C2V magnitudes are clamped here (2^100): never reached with a fixed alpha at
+// the configurations; keeps messages finite when adaptive damping tends to 1.
+constexpr float kMagClamp = 0x1p100f;
+
+// Damping factor of iteration t (1-based) of a run: the fixed alpha, or the
+// adaptive 1 - 2^-t (alpha == 0), an exactly rounded float subtraction
+// (2^-t is exact; t >= 25 rounds to 1).
+__device__ __forceinline__ float damping(const CodeDev &cd, int t) {
+    const float tiny = __int_as_float((127 - min(t, 126)) << 23);
+    return cd.alpha > 0.f ? cd.alpha : __fsub_rn(1.0f, tiny);
+}
+
 template <int DC, bool REG>
 struct CTask {
     float v[DC];
@@ -184,8 +196,8 @@ __device__ __forceinline__ void c_compute_store(CTask<DC, REG> &t, int MS, float
     // The row's sign product goes into both magnitudes (they are >= 0); each
     // output then flips it by its own input's sign bit.
     sx &= 0x80000000u;
-    const unsigned g1 = __float_as_uint(__fmul_rn(alpha, m1)) | sx;
-    const unsigned g2 = __float_as_uint(__fmul_rn(alpha, m2)) | sx;
+    const unsigned g1 = __float_as_uint(fminf(__fmul_rn(alpha, m1), kMagClamp)) | sx;
+    const unsigned g2 = __float_as_uint(fminf(__fmul_rn(alpha, m2), kMagClamp)) | sx;
 #pragma unroll
     for (int k = 0; k < DC; ++k) {
         if (REG || k < t.deg) {
@@ -210,10 +222,9 @@ __device__ __forceinline__ void c_compute_store(CTask<DC, REG> &t, int MS, float
 #endif
 
 template <int DC, bool REG>
-__device__ __forceinline__ void c_phase(const CodeDev &cd, const LayoutMem &L, const TeamMem &T, int lgS,
+__device__ __forceinline__ void c_phase(const CodeDev &cd, const LayoutMem &L, const TeamMem &T, int lgS, float alpha,
                                         int tid, int nthreads) {
     const int MS = cd.M << lgS;
-    const float alpha = cd.alpha;
     for (int tau = tid; tau < MS; tau += BPSF_CU * nthreads) {
         CTask<DC, REG> t[BPSF_CU];
 #pragma unroll
@@ -348,7 +359,7 @@ __device__ __forceinline__ void v_phase(const StreamDev &sd, const LayoutMem &L,
 // ---------------------------------------------------------------------------
 template <int DC, bool REG>
 __device__ __forceinline__ void c_row_pair(const LayoutMem &L, const TeamMem &T, int MH, int lgH, int tau2,
-                                           float alpha) {
+                                           float alpha0, float alpha1) {
     float2 *p2 = reinterpret_cast<float2 *>(T.m) + tau2;  // tau2 = j*(S/2) + p
     const int deg = REG ? DC : (int)L.row_deg[tau2 >> lgH];
     const unsigned sb = T.syn[(2 * tau2) >> 5] >> ((2 * tau2) & 31);
@@ -372,8 +383,10 @@ __device__ __forceinline__ void c_row_pair(const LayoutMem &L, const TeamMem &T,
     }
     sx &= 0x80000000u;
     sy &= 0x80000000u;
-    const unsigned g1x = __float_as_uint(__fmul_rn(alpha, m1x)) | sx, g2x = __float_as_uint(__fmul_rn(alpha, m2x)) | sx;
-    const unsigned g1y = __float_as_uint(__fmul_rn(alpha, m1y)) | sy, g2y = __float_as_uint(__fmul_rn(alpha, m2y)) | sy;
+    const unsigned g1x = __float_as_uint(fminf(__fmul_rn(alpha0, m1x), kMagClamp)) | sx;
+    const unsigned g2x = __float_as_uint(fminf(__fmul_rn(alpha0, m2x), kMagClamp)) | sx;
+    const unsigned g1y = __float_as_uint(fminf(__fmul_rn(alpha1, m1y), kMagClamp)) | sy;
+    const unsigned g2y = __float_as_uint(fminf(__fmul_rn(alpha1, m2y), kMagClamp)) | sy;
 #pragma unroll
     for (int k = 0; k < DC; ++k) {
         if (REG || k < deg) {
@@ -386,12 +399,11 @@ __device__ __forceinline__ void c_row_pair(const LayoutMem &L, const TeamMem &T,
 }
 
 template <int DC, bool REG>
-__device__ __forceinline__ void c_phase_pair(const CodeDev &cd, const LayoutMem &L, const TeamMem &T, int lgS, int tid,
-                                             int nthreads) {
+__device__ __forceinline__ void c_phase_pair(const CodeDev &cd, const LayoutMem &L, const TeamMem &T, int lgS,
+                                             float alpha0, float alpha1, int tid, int nthreads) {
     const int lgH = lgS - 1;
     const int MH = cd.M << lgH;
-    const float alpha = cd.alpha;
-    for (int tau2 = tid; tau2 < MH; tau2 += nthreads) c_row_pair<DC, REG>(L, T, MH, lgH, tau2, alpha);
+    for (int tau2 = tid; tau2 < MH; tau2 += nthreads) c_row_pair<DC, REG>(L, T, MH, lgH, tau2, alpha0, alpha1);
 }
 
 template <int DVS, int DVX, bool DEBUG>
@@ -682,13 +694,15 @@ __device__ void team_loop(const StreamDev &sd, const LayoutMem &L, const TeamMem
         if (kPairs && S >= 2) {
             const int s0 = 2 * (lane & ((S >> 1) - 1));
             const bool on0 = (run >> s0) & 1u, on1 = (run >> (s0 + 1)) & 1u;
-            if (on0 || on1) c_phase_pair<DC, (DVX > 0)>(cd, L, T, lgS, tid, nthreads);
+            if (on0 || on1)
+                c_phase_pair<DC, (DVX > 0)>(cd, L, T, lgS, damping(cd, T.st[s0].iter + 1),
+                                            damping(cd, T.st[s0 + 1].iter + 1), tid, nthreads);
             team_sync(W, bar_id);
             if (on0 || on1) v_phase_pair<DVS, DVX, DEBUG>(sd, L, T, lgS, on0, on1, initm, tid, nthreads);
             team_sync(W, bar_id);
         } else {
             const bool lane_on = (run >> my_slot) & 1u;
-            if (lane_on) c_phase<DC, (DVX > 0)>(cd, L, T, lgS, tid, nthreads);
+            if (lane_on) c_phase<DC, (DVX > 0)>(cd, L, T, lgS, damping(cd, T.st[my_slot].iter + 1), tid, nthreads);
             team_sync(W, bar_id);
             if (lane_on) v_phase<DVS, DVX, DEBUG>(sd, L, T, lgS, initm, tid, nthreads);
             team_sync(W, bar_id);

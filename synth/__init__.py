@@ -36,6 +36,7 @@ SEEDS = {
     "mixed_counts": 4000,
     "mixed": (4001, 4002, 4003, 4004, 4005),
     "serve": 5001,
+    "families": (6001, 6002, 6003),
 }
 
 

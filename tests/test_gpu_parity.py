@@ -118,6 +118,33 @@ def test_bb72_workload_matches_oracle():
     assert (g["stage"] == 1).sum() > 0  # the trial path ran
 
 
+# The paper's code-capacity settings for its other code families (Section V,
+# Fig. capacity and the [[154]] study): adaptive damping alpha_t = 1 - 2^-t,
+# weight-1 trial vectors, |Phi| = 6 ([[126]]), 13 ([[254]]) and 8 ([[154]]),
+# 50 iterations per run.
+FAMILY_CASES = [("cbb126", 6, 0), ("gb254", 13, 1), ("cbb154", 8, 2)]
+
+
+@pytest.mark.parametrize("name,w,k", FAMILY_CASES)
+def test_code_families_match_oracle(name, w, k):
+    p = 0.06
+    P = B.Params(max_iter=50, alpha=0.0, w=w, w_max=1, short_iter=50)
+    oc, e, s = make_inputs(name, p, 3000, synth.SEEDS["families"][k])
+    dec = decoder(name, p, P)
+    g, (eo, co, io, so) = compare(oc, dec, s, p, P)
+    assert (g["stage"] == 1).sum() > 0  # the trial path ran
+    assert B.bpsf_num_trials(dec.handle) == w
+
+
+def test_adaptive_damping_matches_oracle():
+    """[[144,12,12]] at p = 0.06 with alpha_t = 1 - 2^-t instead of 0.625."""
+    p = 0.06
+    P = B.Params(max_iter=100, alpha=0.0, w=6, short_iter=20)
+    oc, e, s = make_inputs("bb144", p, 3000, synth.SEEDS["bb144_cc"][2], stream=1)
+    dec = decoder("bb144", p, P)
+    compare(oc, dec, s, p, P)
+
+
 @pytest.mark.parametrize("p_idx", range(4))
 def test_bb144_workload_matches_oracle(p_idx):
     """[[144,12,12]] at p in {0.02, 0.04, 0.06, 0.08}: max_iter 100, w 6, short_iter 20."""

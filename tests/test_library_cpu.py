@@ -43,7 +43,7 @@ def test_status_strings():
     assert L.bpsf_status_str(4) == b"timeout"
 
 
-@pytest.mark.parametrize("name", ["bb72", "bb90", "bb108", "bb144", "bb288"])
+@pytest.mark.parametrize("name", ["bb72", "bb90", "bb108", "bb144", "bb288", "gb254", "cbb126", "cbb154"])
 def test_bb_builder_matches_oracle(name):
     hx_o, hz_o = oracle.named_code(name)
     assert (codes.bb(name, 0).dense() == hx_o).all()
@@ -93,7 +93,7 @@ def test_create_rejects_bad_arguments_before_device_work():
         (dict(w=17), "w must"),
         (dict(w=4, w_max=5), "w_max"),
         (dict(short_iter=60), "short_iter"),
-        (dict(alpha=0.0), "alpha"),
+        (dict(alpha=-0.5), "alpha"),
         (dict(alpha=float("inf")), "alpha"),
         (dict(select=3), "select"),
     ]

@@ -255,6 +255,32 @@ def test_single_check_closed_form(fp32, s_bit):
     assert r["e"].tolist() == ([0, 0, 1, 0] if s_bit else [0, 0, 0, 0])
 
 
+@pytest.mark.parametrize("fp32", [False, True])
+def test_adaptive_damping_schedule_closed_form(fp32):
+    # alpha = 0 selects alpha_t = 1 - 2^-t (0.5, 0.75, 0.875, ...).  One check over
+    # two bits with s = 1: every iteration's V2C messages are the channel LLRs
+    # (each bit has no other check), so r_t = -alpha_t * (the other bit's LLR) and
+    # l_out_2(t) = L2 - alpha_t * L1.  With L2 / L1 = 0.8 the run converges at the
+    # first t with alpha_t >= 0.8, i.e. t = 3; a schedule shifted by one step, or
+    # 2^-t, or a fixed alpha would stop elsewhere or never.
+    H = np.ones((1, 2), dtype=np.uint8)
+    L1 = 4.0
+    L2 = 0.8 * L1
+    p = 1.0 / (1.0 + np.exp(np.array([L1, L2])))  # priors with these channel LLRs
+    code = Code(H)
+    r = code.bp(np.array([1], dtype=np.uint8), p, max_iter=10, alpha=0.0, fp32=fp32)
+    assert r["converged"] and r["iters"] == 3
+    assert r["e"].tolist() == [0, 1]
+    ty = np.float32 if fp32 else np.float64
+    l1, l2 = ty(np.log((1 - p[0]) / p[0])), ty(np.log((1 - p[1]) / p[1]))
+    a3 = ty(1.0 - 2.0 ** -3)
+    assert r["lout"][1] == l2 + (-(a3 * l1))
+    assert r["lout"][0] == l1 + (-(a3 * l2))
+    # Stopped one iteration early, alpha_2 = 0.75 leaves bit 2 positive.
+    r2 = code.bp(np.array([1], dtype=np.uint8), p, max_iter=2, alpha=0.0, fp32=fp32)
+    assert not r2["converged"] and r2["e"].tolist() == [0, 0]
+
+
 def test_two_check_chain_signs():
     # v0 - c0 - v1 - c1 - v2 with s = (1, 0): the unique lowest-cost solution flips v0 or v1.
     # Min-sum with alpha = 1 on this tree equals the min-cost difference (checked above); here
