@@ -78,14 +78,14 @@ def lib():
             fn.argtypes = [vp, rp, _u8p, C.c_int, rt, C.c_int, _u8p, vp, vp, C.POINTER(C.c_int)]
             fn.restype = C.c_int
             fn = getattr(L, "oracle_trials_" + sfx)
-            fn.argtypes = [vp, rp, _u8p, _i32p, C.c_int, C.c_int, C.c_int, rt, vp, vp, vp, vp]
+            fn.argtypes = [vp, rp, _u8p, _i32p, C.c_int, C.c_int, vp, C.c_int, C.c_int, rt, vp, vp, vp, vp]
             fn.restype = C.c_int
             fn = getattr(L, "oracle_bpsf_" + sfx)
-            fn.argtypes = [vp, rp, _u8p, C.c_int, rt, C.c_int, C.c_int, C.c_int, C.c_int, _u8p,
+            fn.argtypes = [vp, rp, _u8p, C.c_int, rt, C.c_int, C.c_int, vp, C.c_int, C.c_int, C.c_int, _u8p,
                            C.POINTER(C.c_int), C.POINTER(C.c_int), vp, vp]
             fn.restype = C.c_int
             fn = getattr(L, "oracle_bpsf_batch_" + sfx)
-            fn.argtypes = [vp, rp, C.c_int64, _u8p, C.c_int, rt, C.c_int, C.c_int, C.c_int, C.c_int,
+            fn.argtypes = [vp, rp, C.c_int64, _u8p, C.c_int, rt, C.c_int, C.c_int, vp, C.c_int, C.c_int, C.c_int,
                            _u8p, _u8p, _i32p, _u8p, C.c_int]
         L.oracle_bp_sumproduct.argtypes = [vp, _f64p, _u8p, C.c_int, _f64p]
         L.oracle_max_threads.restype = C.c_int
@@ -180,7 +180,8 @@ class Params:
     w: int = 4
     w_max: int = 0          # 0 -> w
     short_iter: int = 10
-    select: int = 0         # 0 min weight, 1 smallest converged mask
+    select: int = 0         # 0 min weight, 1 earliest converged trial of the list
+    trials: tuple = ()      # explicit trial list (subset masks over Phi); () -> weight <= w_max
 
 
 class Code:
@@ -238,11 +239,12 @@ class Code:
         return dict(e=e, converged=bool(conv), iters=it.value, lout=lout, flips=flips)
 
     def trials(self, s, priors, phi, params: Params, fp32=True):
-        """Every trial of one failed shot: (s', converged, iters, e' xor t), mask ascending."""
+        """Every trial of one failed shot: (s', converged, iters, e' xor t), in list order."""
         lch = self._lch(priors, fp32)
         w = len(phi)
         wm = w if params.w_max <= 0 or params.w_max > w else params.w_max
-        cap = 1 << w
+        masks, nm = _masks(params)
+        cap = max(1, nm if nm else sum(1 for m in range(1, 1 << w) if bin(m).count("1") <= wm))
         synd = np.zeros((cap, self.M), dtype=np.uint8)
         conv = np.zeros(cap, dtype=np.uint8)
         iters = np.zeros(cap, dtype=np.int32)
@@ -250,7 +252,7 @@ class Code:
         fn = lib().oracle_trials_f32 if fp32 else lib().oracle_trials_f64
         alpha_t = np.float32(params.alpha) if fp32 else float(params.alpha)
         n = fn(self._h, lch, np.ascontiguousarray(s, dtype=np.uint8), np.asarray(phi, dtype=np.int32), w, wm,
-               params.short_iter, alpha_t, _ptr(synd), _ptr(conv), _ptr(iters), _ptr(es))
+               _ptr(masks), nm, params.short_iter, alpha_t, _ptr(synd), _ptr(conv), _ptr(iters), _ptr(es))
         return synd[:n], conv[:n].astype(bool), iters[:n], es[:n]
 
     def bpsf(self, s, priors, params: Params, fp32=True):
@@ -262,9 +264,10 @@ class Code:
         flips = np.zeros(self.N, dtype=np.uint16)
         fn = lib().oracle_bpsf_f32 if fp32 else lib().oracle_bpsf_f64
         alpha_t = np.float32(params.alpha) if fp32 else float(params.alpha)
+        masks, nm = _masks(params)
         conv = fn(self._h, lch, np.ascontiguousarray(s, dtype=np.uint8), params.max_iter, alpha_t, params.w,
-                  params.w_max, params.short_iter, params.select, e, C.byref(it), C.byref(st), _ptr(phi),
-                  _ptr(flips))
+                  params.w_max, _ptr(masks), nm, params.short_iter, params.select, e, C.byref(it), C.byref(st),
+                  _ptr(phi), _ptr(flips))
         return dict(e=e, converged=bool(conv), iters=it.value, stage=st.value,
                     phi=phi[: params.w] if params.w > 0 else phi[:0], flips=flips)
 
@@ -279,8 +282,9 @@ class Code:
         stage = np.zeros(n, dtype=np.uint8)
         fn = lib().oracle_bpsf_batch_f32 if fp32 else lib().oracle_bpsf_batch_f64
         alpha_t = np.float32(params.alpha) if fp32 else float(params.alpha)
-        fn(self._h, lch, n, synd, params.max_iter, alpha_t, params.w, params.w_max, params.short_iter,
-           params.select, e, conv, iters, stage, int(threads))
+        masks, nm = _masks(params)
+        fn(self._h, lch, n, synd, params.max_iter, alpha_t, params.w, params.w_max, _ptr(masks), nm,
+           params.short_iter, params.select, e, conv, iters, stage, int(threads))
         return e, conv.astype(bool), iters, stage
 
     def sumproduct(self, s, priors, iters):
@@ -289,6 +293,14 @@ class Code:
         out = np.zeros(self.N, dtype=np.float64)
         lib().oracle_bp_sumproduct(self._h, lch, np.ascontiguousarray(s, dtype=np.uint8), int(iters), out)
         return out
+
+
+def _masks(params: Params):
+    """The explicit trial list of params as a uint64 array (None and 0 if default)."""
+    if not params.trials:
+        return None, 0
+    m = np.ascontiguousarray(np.asarray(params.trials, dtype=np.uint64))
+    return m, int(m.shape[0])
 
 
 def top(flips: np.ndarray, w: int) -> np.ndarray:

@@ -31,9 +31,11 @@
  *     every iteration of the initial run (Algorithm 1);
  *   - top(|Phi|) orders bits by (flip count descending, index ascending);
  *   - trial vectors are the non-empty subsets of Phi with weight <= w_max,
- *     visited in ascending subset mask (bit j of the mask selects Phi[j]);
+ *     visited in ascending subset mask (bit j of the mask selects Phi[j]),
+ *     or an explicit list of masks in list order (the sampled variant);
  *   - selection: minimum Hamming weight of the returned e xor t, ties to the
- *     smaller mask (select = 0), or the smallest converged mask (select = 1);
+ *     earlier trial of the list (select = 0), or the earliest converged trial
+ *     of the list (select = 1);
  *   - on total failure the initial run's e is returned with converged = 0.
  */
 #include <math.h>
@@ -356,6 +358,39 @@ void oracle_top(const uint16_t *flips, int N, int w, int *phi) {
     free(taken);
 }
 
+/*
+ * Trial list of Algorithm 1 as subset masks over Phi (bit j selects Phi[j]):
+ * the n_masks given masks in the given order, or, when n_masks == 0, every
+ * non-empty subset of weight <= w_max in ascending mask order (enumerated by
+ * counting, so only for w <= 24).  Returns the count (and *out, malloc'd),
+ * or -1.  The sampled variant of Section V (n_s random vectors per weight)
+ * is an explicit list.
+ */
+static int trial_count(int w, int w_max, int n_masks) {
+    if (n_masks > 0) return n_masks;
+    if (w <= 0) return 0;
+    if (w > 24) return -1;
+    int n = 0;
+    for (uint64_t m = 1; m < (1ull << w); m++)
+        if (__builtin_popcountll(m) <= w_max) n++;
+    return n;
+}
+
+static int trial_list(int w, int w_max, const uint64_t *masks, int n_masks, uint64_t **out) {
+    int n = trial_count(w, w_max, n_masks);
+    if (n < 0) return -1;
+    uint64_t *l = malloc(sizeof(uint64_t) * (size_t)(n + 1));
+    if (n_masks > 0) {
+        memcpy(l, masks, sizeof(uint64_t) * (size_t)n);
+    } else {
+        int k = 0;
+        for (uint64_t m = 1; w > 0 && m < (1ull << w); m++)
+            if (__builtin_popcountll(m) <= w_max) l[k++] = m;
+    }
+    *out = l;
+    return n;
+}
+
 /* ------------------------------------------------------------------------ */
 /* Normalised min-sum BP (Section II-B) with oscillation tracking            */
 /* (Algorithm 1, BP_with_oscillation); one body per floating-point mode.     */
@@ -429,8 +464,8 @@ int oracle_max_threads(void) {
 }
 
 void oracle_bpsf_batch_f32(const oracle_code *c, const float *lch, int64_t n, const uint8_t *synd, int max_iter,
-                           float alpha, int w, int w_max, int short_iter, int select, uint8_t *e_out,
-                           uint8_t *conv, int32_t *iters, uint8_t *stage, int threads) {
+                           float alpha, int w, int w_max, const uint64_t *masks, int n_masks, int short_iter,
+                           int select, uint8_t *e_out, uint8_t *conv, int32_t *iters, uint8_t *stage, int threads) {
 #ifdef _OPENMP
 #pragma omp parallel for schedule(dynamic, 8) num_threads(threads > 0 ? threads : 1)
 #else
@@ -438,16 +473,16 @@ void oracle_bpsf_batch_f32(const oracle_code *c, const float *lch, int64_t n, co
 #endif
     for (int64_t k = 0; k < n; k++) {
         int it = 0, st = 0;
-        conv[k] = (uint8_t)oracle_bpsf_f32(c, lch, synd + k * c->M, max_iter, alpha, w, w_max, short_iter, select,
-                                           e_out + k * c->N, &it, &st, NULL, NULL);
+        conv[k] = (uint8_t)oracle_bpsf_f32(c, lch, synd + k * c->M, max_iter, alpha, w, w_max, masks, n_masks,
+                                           short_iter, select, e_out + k * c->N, &it, &st, NULL, NULL);
         iters[k] = it;
         stage[k] = (uint8_t)st;
     }
 }
 
 void oracle_bpsf_batch_f64(const oracle_code *c, const double *lch, int64_t n, const uint8_t *synd, int max_iter,
-                           double alpha, int w, int w_max, int short_iter, int select, uint8_t *e_out,
-                           uint8_t *conv, int32_t *iters, uint8_t *stage, int threads) {
+                           double alpha, int w, int w_max, const uint64_t *masks, int n_masks, int short_iter,
+                           int select, uint8_t *e_out, uint8_t *conv, int32_t *iters, uint8_t *stage, int threads) {
 #ifdef _OPENMP
 #pragma omp parallel for schedule(dynamic, 8) num_threads(threads > 0 ? threads : 1)
 #else
@@ -455,8 +490,8 @@ void oracle_bpsf_batch_f64(const oracle_code *c, const double *lch, int64_t n, c
 #endif
     for (int64_t k = 0; k < n; k++) {
         int it = 0, st = 0;
-        conv[k] = (uint8_t)oracle_bpsf_f64(c, lch, synd + k * c->M, max_iter, alpha, w, w_max, short_iter, select,
-                                           e_out + k * c->N, &it, &st, NULL, NULL);
+        conv[k] = (uint8_t)oracle_bpsf_f64(c, lch, synd + k * c->M, max_iter, alpha, w, w_max, masks, n_masks,
+                                           short_iter, select, e_out + k * c->N, &it, &st, NULL, NULL);
         iters[k] = it;
         stage[k] = (uint8_t)st;
     }

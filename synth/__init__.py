@@ -133,3 +133,37 @@ def uniform_choice(seed: int, stream: int, count: int, n_choices: int,
     w = np.ones(n_choices) if weights is None else np.asarray(weights, dtype=np.float64)
     cdf = np.cumsum(w) / np.sum(w)
     return np.minimum(np.searchsorted(cdf, u, side="right"), n_choices - 1)
+
+
+def sample_trial_masks(seed: int, w: int, w_max: int, n_s: int) -> np.ndarray:
+    """Sampled trial set of BP-SF: for each weight k = 1..w_max, n_s distinct
+    k-subsets of the w oscillating bits (partial Fisher-Yates: position r
+    takes index r + (u mod (w - r)) of a counter-based draw u; a duplicate
+    subset is drawn again).  Returned as subset masks
+    over Phi (bit j selects Phi[j]), weight by weight, in draw order; a weight
+    with fewer than n_s subsets contributes all of them in ascending order."""
+    if not (1 <= w <= 64 and 1 <= w_max <= w and n_s >= 1):
+        raise ValueError("need 1 <= w_max <= w <= 64 and n_s >= 1")
+    from itertools import combinations
+    from math import comb
+    out = []
+    for k in range(1, w_max + 1):
+        if comb(w, k) <= n_s:
+            out.extend(sorted(sum(1 << b for b in c) for c in combinations(range(w), k)))
+            continue
+        key = stream_key(seed, k)
+        seen, ctr = set(), 0
+        while len(seen) < n_s:
+            u = draws(key, np.arange(ctr, ctr + k, dtype=np.uint64))
+            ctr += k
+            idx = list(range(w))
+            for r in range(k):  # partial Fisher-Yates: position r takes a uniform pick of the rest
+                j = r + int(u[r] % np.uint64(w - r))
+                idx[r], idx[j] = idx[j], idx[r]
+            m = 0
+            for b in idx[:k]:
+                m |= 1 << b
+            if m not in seen:
+                seen.add(m)
+                out.append(m)
+    return np.array(out, dtype=np.uint64)

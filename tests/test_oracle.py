@@ -373,6 +373,57 @@ def test_trials_and_winner_by_brute_force():
     assert failed > 10
 
 
+@pytest.mark.parametrize("select", [0, 1])
+def test_explicit_trial_list_by_brute_force(select):
+    # The sampled variant (Section V): an explicit list of trial masks over a
+    # larger Phi, decoded and selected in list order.
+    code, hx, hz, e, s = _bb72_shots(400, 0.1)
+    masks = synth.sample_trial_masks(11, 10, 3, 4)[::-1].copy()  # reversed: list order != mask order
+    P = Params(max_iter=50, alpha=0.625, w=10, w_max=3, short_iter=10, select=select, trials=tuple(int(m) for m in masks))
+    failed = 0
+    for k in range(400):
+        out = code.bpsf(s[k], 0.1, P, fp32=True)
+        if out["stage"] == 0:
+            continue
+        failed += 1
+        phi = out["phi"]
+        assert len(phi) == 10 and len(set(phi.tolist())) == 10
+        synd, conv, iters, es = code.trials(s[k], 0.1, phi, P, fp32=True)
+        assert len(synd) == len(masks)
+        best = None
+        for idx, m in enumerate(masks):
+            t = np.zeros(72, dtype=np.uint8)
+            for j in range(10):
+                if (int(m) >> j) & 1:
+                    t[phi[j]] = 1
+            assert (synd[idx] == (s[k].astype(np.int64) + hx.astype(np.int64) @ t) % 2).all()
+            if conv[idx]:
+                assert (((hx.astype(np.int64) @ es[idx]) % 2) == s[k]).all()
+                key = (int(es[idx].sum()), idx) if select == 0 else (0, idx)
+                if best is None or key < best:
+                    best = key
+        if best is None:
+            assert out["stage"] == 2
+        else:
+            assert out["stage"] == 1 and (out["e"] == es[best[1]]).all() and out["iters"] == iters[best[1]]
+    assert failed > 10
+
+
+def test_sampled_trial_masks():
+    m = synth.sample_trial_masks(5, 50, 6, 5)
+    assert m.dtype == np.uint64 and len(m) == 30
+    wts = [bin(int(x)).count("1") for x in m]
+    assert wts == [k for k in range(1, 7) for _ in range(5)]  # n_s per weight, weight by weight
+    assert len(set(int(x) for x in m)) == 30 and int(m.max()) < (1 << 50)
+    assert (synth.sample_trial_masks(5, 50, 6, 5) == m).all()  # counter-based: reproducible
+    assert not (synth.sample_trial_masks(6, 50, 6, 5) == m).all()
+    # A weight with at most n_s subsets contributes all of them.
+    assert synth.sample_trial_masks(1, 4, 2, 10).tolist() == [1, 2, 4, 8, 3, 5, 6, 9, 10, 12]
+    # Exactly n_s subsets of a weight: all of them.
+    big = synth.sample_trial_masks(9, 8, 1, 8)
+    assert sorted(int(x) for x in big) == [1 << b for b in range(8)]
+
+
 def test_select_first_and_w_max():
     code, hx, hz, e, s = _bb72_shots(400, 0.1)
     P1 = Params(max_iter=50, alpha=0.625, w=4, short_iter=10, select=1)
