@@ -68,13 +68,18 @@ enum { BPSF_SELECT_MIN_WEIGHT = 0, BPSF_SELECT_FIRST = 1 };
  *              clamped at 2^100 (never reached with a fixed alpha at the
  *              configurations; with alpha_t -> 1 it keeps messages finite).
  *   w          |Phi|, the number of oscillating bits used for trials,
- *              0..16; 0 means plain BP with no post-processing.
- *   w_max      largest trial weight, 1..w; 0 means w (all 2^w - 1 subsets).
+ *              0..64; 0 means plain BP with no post-processing.
+ *   w_max      largest trial weight, 1..min(w, 16); 0 means w.  The default
+ *              trial set is every non-empty subset of Phi of weight <= w_max;
+ *              bpsf_set_trials replaces it.  When that set would exceed 4096
+ *              trials it is left empty, and decoding (every form) returns
+ *              BPSF_EINVAL until a list is given.
  *   short_iter iterations of each trial run, 1..max_iter.
  *   select     BPSF_SELECT_MIN_WEIGHT: the converged trial whose e' xor t has
- *              the smallest Hamming weight, ties to the smaller subset mask;
- *              BPSF_SELECT_FIRST: the converged trial with the smallest mask
- *              (the paper's "first valid" rule made deterministic).
+ *              the smallest Hamming weight, ties to the earlier trial (the
+ *              default set is in ascending subset mask);
+ *              BPSF_SELECT_FIRST: the earliest converged trial (the paper's
+ *              "first valid" rule made deterministic).
  *   flags      reserved, must be 0.
  */
 typedef struct {
@@ -360,8 +365,21 @@ bpsf_status bpsf_decode_debug(bpsf_ctx *ctx, int64_t n_shots, const uint32_t *d_
  */
 bpsf_status bpsf_selftest_wait(bpsf_ctx *ctx, int64_t wait_us, void *stream);
 
-/* Number of trials per failed shot (masks with popcount <= w_max). */
+/* Number of trials per failed shot (the default set or the given list). */
 int32_t bpsf_num_trials(const bpsf_ctx *ctx);
+
+/*
+ * Replace the trial set of ctx (Algorithm 1's trial vectors t as subsets of
+ * Phi): n masks, bit j of mask k selects Phi[j] (j < w); each mask
+ * non-empty with at most 16 bits; n <= 4096.  Trials are decoded and
+ * selected in list order: the minimum-weight rule breaks ties, and the
+ * first-success rule picks, by list index.  The sampled variant of
+ * Section V (n_s random trial vectors per weight 1..w_max over a larger
+ * Phi) is such a list.  n = 0 restores the default set.  Host array,
+ * copied.  Not while a decode or a server uses ctx; the next decode
+ * re-sizes the failed-shot workspace.
+ */
+bpsf_status bpsf_set_trials(bpsf_ctx *ctx, int32_t n, const uint64_t *masks);
 
 /* Work counters of the last decode on ctx (after bpsf_sync): runs started,
  * failed shots (records), iterations and edge-updates (iterations x nnz

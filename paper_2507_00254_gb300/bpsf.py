@@ -26,7 +26,7 @@ EXPORTS = (
     "bpsf_sync", "bpsf_get_tuning", "bpsf_set_tuning", "bpsf_autotune", "bpsf_serve_start", "bpsf_serve_submit",
     "bpsf_serve_poll", "bpsf_serve_stop", "bpsf_bb_code", "bpsf_phenom_code", "bpsf_syndrome", "bpsf_decode_debug",
     "bpsf_num_trials", "bpsf_last_work", "bpsf_status_str", "bpsf_last_error", "bpsf_decode_noalloc",
-    "bpsf_noalloc_max_shots", "bpsf_selftest_wait", "bpsf_serve_replay",
+    "bpsf_noalloc_max_shots", "bpsf_selftest_wait", "bpsf_serve_replay", "bpsf_set_trials",
 )
 
 
@@ -105,6 +105,7 @@ def lib():
         "bpsf_syndrome": ([vp, i64, vp, i32, vp, i32, vp], st),
         "bpsf_decode_debug": ([vp, i64, vp, i32, vp, i32, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp], st),
         "bpsf_num_trials": ([vp], i32),
+        "bpsf_set_trials": ([vp, i32, vp], st),
         "bpsf_selftest_wait": ([vp, i64, vp], st),
         "bpsf_last_work": ([vp, C.POINTER(bpsf_work)], st),
         "bpsf_status_str": ([st], C.c_char_p),
@@ -205,6 +206,12 @@ def bpsf_syndrome(h, n, d_err, es, d_synd, ss, stream):
 
 def bpsf_num_trials(h) -> int:
     return int(lib().bpsf_num_trials(h))
+
+
+def bpsf_set_trials(h, masks) -> None:
+    """Trial list as subset masks over Phi (bit j selects Phi[j]); empty restores the default."""
+    m = np.ascontiguousarray(np.asarray(masks, dtype=np.uint64).reshape(-1))
+    check(lib().bpsf_set_trials(h, int(m.shape[0]), m.ctypes.data_as(C.c_void_p) if m.shape[0] else None))
 
 
 def bpsf_last_work(h) -> bpsf_work:
@@ -393,6 +400,10 @@ class Decoder:
 
     def autotune(self, p_sample=0.05, n_sample=1 << 16, stream=None):
         return bpsf_autotune(self.handle, p_sample, n_sample, _stream_handle(stream)).as_tuple()
+
+    def set_trials(self, masks) -> None:
+        """Replace the trial set (see bpsf_set_trials); () restores the default."""
+        bpsf_set_trials(self.handle, masks)
 
     def last_work(self):
         w = bpsf_last_work(self.handle)

@@ -72,6 +72,7 @@ extern "C" void bpsf_destroy(bpsf_ctx *c) {
     cudaSetDevice(c->device);
     free_workspace(c);
     if (c->d_code) cudaFree(c->d_code);
+    if (c->d_trials) cudaFree(c->d_trials);
     if (c->d_ctr) cudaFree(c->d_ctr);
     if (c->h_ctr) cudaFreeHost(c->h_ctr);
     if (c->h_flag) cudaFreeHost(c->h_flag);
@@ -207,6 +208,33 @@ static bpsf_tuning default_tuning(bpsf_ctx *c) {
 // Context creation
 // ---------------------------------------------------------------------------
 
+// Default trial list of Algorithm 1: every non-empty subset of Phi of weight
+// <= w_max, as masks (bit j selects Phi[j]) in ascending order.
+static long long default_trial_count(int w, int w_max) {
+    long long n = 0, c = 1;  // c = C(w, k)
+    for (int k = 1; k <= w_max && k <= w; ++k) {
+        c = c * (w - k + 1) / k;
+        n += c;
+        if (n > (1ll << 40)) break;
+    }
+    return n;
+}
+
+static void add_subsets(std::vector<unsigned long long> &out, int w, int k, int start, unsigned long long m) {
+    if (k == 0) {
+        if (m) out.push_back(m);
+        return;
+    }
+    for (int b = start; b <= w - k; ++b) add_subsets(out, w, k - 1, b + 1, m | (1ull << b));
+}
+
+static std::vector<unsigned long long> default_trials(int w, int w_max) {
+    std::vector<unsigned long long> out;
+    for (int k = 1; k <= w_max && k <= w; ++k) add_subsets(out, w, k, 0, 0ull);
+    std::sort(out.begin(), out.end());
+    return out;
+}
+
 extern "C" bpsf_status bpsf_create(bpsf_ctx **out, int32_t M, int32_t N, int64_t nnz, int32_t layout,
                                    const int32_t *ptr, const int32_t *idx, const double *priors,
                                    const bpsf_params *params) {
@@ -221,10 +249,12 @@ extern "C" bpsf_status bpsf_create(bpsf_ctx **out, int32_t M, int32_t N, int64_t
     if (p.max_iter < 1 || p.max_iter > 32767) return bpsf_fail(BPSF_EINVAL, "max_iter must be in 1..32767");
     if (!(p.alpha >= 0.f) || !std::isfinite(p.alpha))
         return bpsf_fail(BPSF_EINVAL, "alpha must be finite and > 0, or 0 for adaptive damping");
-    if (p.w < 0 || p.w > kMaxW) return bpsf_fail(BPSF_EINVAL, "w must be in 0..%d", kMaxW);
+    if (p.w < 0 || p.w > kMaxPhi) return bpsf_fail(BPSF_EINVAL, "w must be in 0..%d", kMaxPhi);
     if (p.w > N) return bpsf_fail(BPSF_EINVAL, "w must not exceed N");
     if (p.w > 0) {
         if (p.w_max < 0 || p.w_max > p.w) return bpsf_fail(BPSF_EINVAL, "w_max must be in 0..w");
+        if ((p.w_max == 0 ? p.w : p.w_max) > kMaxW)
+            return bpsf_fail(BPSF_EINVAL, "w_max must be at most %d (a trial flips at most %d bits)", kMaxW, kMaxW);
         if (p.short_iter < 1 || p.short_iter > p.max_iter)
             return bpsf_fail(BPSF_EINVAL, "short_iter must be in 1..max_iter");
     }
@@ -310,9 +340,9 @@ extern "C" bpsf_status bpsf_create(bpsf_ctx **out, int32_t M, int32_t N, int64_t
     for (int i = 0; i < N; ++i) lch[i] = (float)std::log((1.0 - priors[i]) / priors[i]);
     for (int j = 0; j < M; ++j)
         for (int k = 0; k < (int)rows[j].size(); ++k) lch_pos[(size_t)k * M + j] = lch[rows[j][k]];
-    std::vector<uint32_t> masks;
-    for (uint32_t k = 1; c->p.w > 0 && k < (1u << c->p.w); ++k)
-        if (__builtin_popcount(k) <= c->p.w_max) masks.push_back(k);
+    // A default set beyond kMaxTrials is left empty: decoding then needs a list.
+    std::vector<unsigned long long> masks;
+    if (default_trial_count(c->p.w, c->p.w_max) <= kMaxTrials) masks = default_trials(c->p.w, c->p.w_max);
     c->n_trials = (int)masks.size();
     if (masks.empty()) masks.push_back(0);
 
@@ -330,7 +360,7 @@ extern "C" bpsf_status bpsf_create(bpsf_ctx **out, int32_t M, int32_t N, int64_t
     const void *srcs[8] = {row_deg.data(), vpos.data(), vchk.data(), lch.data(),
                            lch_pos.data(), row_ptr.data(), csr_col.data(), masks.data()};
     const size_t sizes[8] = {(size_t)M, 2 * vpos.size(), 2 * vchk.size(), 4 * (size_t)N,
-                             4 * (size_t)P, 2 * (size_t)(M + 1), 2 * (size_t)nnz, 4 * masks.size()};
+                             4 * (size_t)P, 2 * (size_t)(M + 1), 2 * (size_t)nnz, 8 * masks.size()};
     size_t off[8], sz = 0;
     for (int k = 0; k < 8; ++k) {
         off[k] = sz;
@@ -369,7 +399,9 @@ extern "C" bpsf_status bpsf_create(bpsf_ctx **out, int32_t M, int32_t N, int64_t
     cd.lch_pos = (const float *)(base + off[4]);
     cd.row_ptr = (const uint16_t *)(base + off[5]);
     cd.csr_col = (const uint16_t *)(base + off[6]);
-    cd.trial_mask = (const uint32_t *)(base + off[7]);
+    cd.trial_mask = (const unsigned long long *)(base + off[7]);
+    c->default_masks = cd.trial_mask;
+    c->default_n_trials = c->n_trials;
     if (e == cudaSuccess) e = cudaMalloc((void **)&c->d_ctr, sizeof(StreamCounters));
     if (e == cudaSuccess) e = cudaMemset(c->d_ctr, 0, sizeof(StreamCounters));
     if (e == cudaSuccess) e = cudaMallocHost((void **)&c->h_ctr, sizeof(StreamCounters));
@@ -459,6 +491,7 @@ void bpsf_launch_plan(const bpsf_plan &pl, bool debug, StreamDev *sds, int n, in
 static bpsf_status check_io(const bpsf_ctx *c, int64_t n, const void *synd, int32_t ss, const void *corr, int32_t cs,
                             const void *conv, const void *iters) {
     if (!c) return bpsf_fail(BPSF_EINVAL, "ctx is NULL");
+    if (bpsf_check_trials(c) != BPSF_OK) return BPSF_EINVAL;
     if (n < 0) return bpsf_fail(BPSF_EINVAL, "n_shots must be >= 0");
     if (n > (1ll << 40)) return bpsf_fail(BPSF_EINVAL, "n_shots too large");
     if (n == 0) return BPSF_OK;
@@ -539,6 +572,42 @@ extern "C" bpsf_status bpsf_last_work(bpsf_ctx *c, bpsf_work *out) {
 }
 
 extern "C" int32_t bpsf_num_trials(const bpsf_ctx *c) { return c ? c->n_trials : -1; }
+
+extern "C" bpsf_status bpsf_set_trials(bpsf_ctx *c, int32_t n, const uint64_t *masks) {
+    if (!c) return bpsf_fail(BPSF_EINVAL, "ctx is NULL");
+    if (c->p.w <= 0) return bpsf_fail(BPSF_EINVAL, "the context has no trials (w = 0)");
+    if (n < 0 || n > kMaxTrials) return bpsf_fail(BPSF_EINVAL, "n must be in 0..%d", kMaxTrials);
+    if (n > 0 && !masks) return bpsf_fail(BPSF_EINVAL, "masks is NULL");
+    for (int k = 0; k < n; ++k) {
+        const unsigned long long m = masks[k];
+        if (m == 0ull) return bpsf_fail(BPSF_EINVAL, "mask %d is empty", k);
+        if (c->p.w < 64 && (m >> c->p.w) != 0ull) return bpsf_fail(BPSF_EINVAL, "mask %d selects a bit >= w", k);
+        if (__builtin_popcountll(m) > kMaxW) return bpsf_fail(BPSF_EINVAL, "mask %d has more than %d bits", k, kMaxW);
+    }
+    cudaSetDevice(c->device);
+    // Records hold per-trial rows: the workspace is re-sized at the next decode.
+    free_workspace(c);
+    if (c->d_trials) cudaFree(c->d_trials);
+    c->d_trials = nullptr;
+    if (n == 0) {
+        c->code.trial_mask = c->default_masks;
+        c->n_trials = c->default_n_trials;
+    } else {
+        cudaError_t e = cudaMalloc(&c->d_trials, 8 * (size_t)n);
+        if (e == cudaSuccess) e = cudaMemcpy(c->d_trials, masks, 8 * (size_t)n, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            if (c->d_trials) cudaFree(c->d_trials);
+            c->d_trials = nullptr;
+            c->code.trial_mask = c->default_masks;
+            c->n_trials = c->default_n_trials;
+            return bpsf_fail(BPSF_ENOMEM, "trial list: %s", cudaGetErrorString(e));
+        }
+        c->code.trial_mask = (const unsigned long long *)c->d_trials;
+        c->n_trials = n;
+    }
+    c->code.n_trials = c->n_trials;
+    return BPSF_OK;
+}
 
 // ---------------------------------------------------------------------------
 // Plain per-shot form: launch, synchronise, read the flag, launch the trial

@@ -14,6 +14,9 @@ struct bpsf_ctx {
     bpsf_params p{};
     std::vector<int32_t> csr_ptr, csr_col;  // host copy of H (CSR, ascending columns)
     void *d_code = nullptr;                 // one allocation for all code arrays
+    void *d_trials = nullptr;               // trial list set by bpsf_set_trials (else the default in d_code)
+    const unsigned long long *default_masks = nullptr;
+    int default_n_trials = 0;
     bpsf::CodeDev code{};
     bpsf::StreamCounters *d_ctr = nullptr;  // per-launch counters
     bpsf::StreamCounters *d_ctr_last = nullptr;  // counters of the most recent launch (read by bpsf_sync)
@@ -39,6 +42,13 @@ struct bpsf_plan {
 };
 
 bpsf_status bpsf_fail(bpsf_status s, const char *fmt, ...);
+
+// A context with trials (w > 0) decodes only with a non-empty trial set.
+inline bpsf_status bpsf_check_trials(const bpsf_ctx *c) {
+    if (c->p.w > 0 && c->n_trials == 0)
+        return bpsf_fail(BPSF_EINVAL, "the default trial set is too large; give a trial list (bpsf_set_trials)");
+    return BPSF_OK;
+}
 bpsf_status bpsf_ensure_workspace(bpsf_ctx *c, long long n);
 bpsf_status bpsf_ensure_kernel_attrs(int variant, int smem_optin);
 // Plan one launch over n_codes codes; tunes[k] is code k's team shape (a

@@ -5,7 +5,9 @@
 
 namespace bpsf {
 
-constexpr int kMaxW = 16;         // largest |Phi|
+constexpr int kMaxW = 16;         // most bits a trial vector flips (entries of a work item's bit list)
+constexpr int kMaxPhi = 64;       // |Phi|: trial masks are 64-bit
+constexpr int kMaxTrials = 4096;  // trials per failed shot
 constexpr int kMaxSlots = 32;     // work items per team
 constexpr int kMaxStreams = 16;   // codes per launch
 constexpr int kMaxComputeWarps = 15;  // plus one manager warp: <= 512 threads per block
@@ -45,7 +47,7 @@ struct CodeDev {
     const float *lch_pos;        // P, channel LLR of the variable at each position
     const uint16_t *row_ptr;     // M+1, CSR (syndrome kernel)
     const uint16_t *csr_col;     // nnz
-    const uint32_t *trial_mask;  // n_trials subset masks over Phi, ascending
+    const unsigned long long *trial_mask;  // n_trials subset masks over Phi (bit j selects Phi[j]), list order
 };
 
 // Per-launch counters of one stream (64 bytes, zeroed before a launch).
@@ -170,15 +172,16 @@ struct SlotState {
     int pad;
     long long shot;  // shot index in the job (global sequence number when serving)
     long long pad2;
-    uint16_t phi[kMaxW];
+    uint16_t phi[kMaxW];  // trial run: the bits its trial vector flips, 0xffff-terminated
 };
 static_assert(sizeof(SlotState) == 80, "slot state is 80 bytes");
 
 // A finished run's facts, handed from the team to the manager (64 bytes;
 // the packed hard decision goes with it in the team's ebits words).  The
 // team fills an outbox whose flag is 0 and then sets it; the manager writes
-// the results out and clears it.  phi: Phi = top(flip_count, w) for a failed
-// initial run, the trial's own Phi for a trial run.
+// the results out and clears it.  phi: a trial run's flipped bits
+// (0xffff-terminated); a failed initial run's Phi = top(flip_count, w) goes
+// to the shot's record directly.
 struct OutBox {
     int full;
     int kind;
@@ -206,7 +209,7 @@ struct QEntry {
     int kind;
     int kidx;
     long long shot;
-    uint16_t phi[kMaxW];
+    uint16_t phi[kMaxW];  // trial run: the bits its trial vector flips, 0xffff-terminated
 };
 static_assert(sizeof(QEntry) == 48, "queue entry header is 48 bytes");
 

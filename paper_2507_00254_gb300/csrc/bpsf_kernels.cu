@@ -529,6 +529,10 @@ __device__ __forceinline__ void team_pack(const StreamDev &sd, const TeamMem &T,
     }
     const int kind = ss->kind, outcome = ss->outcome;
     if (kind == 1 && outcome == 2 && cd.w > 0) {
+        // Phi goes straight to the shot's record (up to 64 entries); the
+        // manager publishes the record after this outbox, and the fence
+        // below orders these stores before the outbox flag.
+        const long long row = (sd.flags & kServe) ? (ss->shot % sd.serve.rows) : ss->shot;
         unsigned thr = 0xffffffffu;
         for (int r = 0; r < cd.w; ++r) {
             unsigned best = 0;
@@ -537,11 +541,16 @@ __device__ __forceinline__ void team_pack(const StreamDev &sd, const TeamMem &T,
                 if (key < thr && key > best) best = key;
             }
             best = __reduce_max_sync(FULLMASK, best);
-            if (lane == 0) ob->phi[r] = (uint16_t)(0xffffu - (best & 0xffffu));
+            const int phi_r = (int)(0xffffu - (best & 0xffffu));
+            if (lane == 0) {
+                sd.rec.phi[row * cd.w + r] = phi_r;
+                if (DEBUG && sd.dbg.phi) sd.dbg.phi[ss->shot * cd.w + r] = phi_r;
+            }
             thr = best;
         }
+        __threadfence();
     } else if (lane < kMaxW) {
-        ob->phi[lane] = ss->phi[lane];
+        ob->phi[lane] = ss->phi[lane];  // a trial's flipped bits, for the undo
     }
     if (DEBUG && kind == 1 && sd.dbg.flips)
         for (int i = lane; i < N; i += 32)
@@ -792,16 +801,14 @@ __device__ __forceinline__ void finalize_simple(const StreamDev &sd, TeamMem T, 
     // Trial run: undo the flip (Algorithm 1) and take part in the selection.
     const int C = cd.n_trials, kidx = ss->kidx;
     if (conv) {
-        const unsigned mask = __ldg(cd.trial_mask + kidx);
         unsigned wsum = 0;
         uint32_t *dst = sd.rec.corr + ((long long)row * C + kidx) * Wn;
         for (int w = 0; w < Wn; ++w) {
             unsigned v = slot_word(T.ebits, Wn, s, w);
-            for (int j = 0; j < cd.w; ++j) {
-                if ((mask >> j) & 1u) {
-                    const int b = ss->phi[j];
-                    if ((b >> 5) == w) v ^= 1u << (b & 31);
-                }
+            for (int j = 0; j < kMaxW; ++j) {  // the bits t flips, 0xffff-terminated
+                const int b = ss->phi[j];
+                if (b == 0xffff) break;
+                if ((b >> 5) == w) v ^= 1u << (b & 31);
             }
             dst[w] = v;
             wsum += __popc(v);
@@ -837,8 +844,8 @@ __device__ __forceinline__ void finalize_simple(const StreamDev &sd, TeamMem T, 
 }
 
 // Failed initial run with trials (whole manager warp): provisional output,
-// record (Phi from the outbox, the shot's syndrome from its input row) and
-// publication of its trials.
+// record (its Phi written by the team, the shot's syndrome copied from its
+// input row) and publication of its trials.
 template <bool DEBUG>
 __device__ __forceinline__ void finalize_failed(const StreamDev &sd, TeamMem T, int s, int lane, MgrState &mg) {
     const CodeDev &cd = sd.code;
@@ -856,10 +863,8 @@ __device__ __forceinline__ void finalize_failed(const StreamDev &sd, TeamMem T, 
         sd.rec.done[row] = 0u;
         sd.rec.best[row] = ~0ull;
     }
-    if (lane < cd.w) sd.rec.phi[row * cd.w + lane] = ob->phi[lane];
     const uint32_t *syn = job.synd + row * job.synd_stride;
     for (int w = lane; w < Ws; w += 32) sd.rec.synd[row * Ws + w] = __ldcg(syn + w);
-    if (DEBUG && sd.dbg.phi && lane < cd.w) sd.dbg.phi[shot * cd.w + lane] = ob->phi[lane];
     __threadfence();
     __syncwarp();
     if (lane == 0) {
@@ -934,20 +939,22 @@ __device__ __forceinline__ bool prefetch(const StreamDev &sd, unsigned char *qba
                 e->kind = 2;
                 e->kidx = kidx;
                 e->shot = shot;
-                for (int j = 0; j < kMaxW; ++j)
-                    e->phi[j] = j < cd.w ? (uint16_t)__ldcg(sd.rec.phi + row * cd.w + j) : (uint16_t)0;
+                // The trial vector t: the bits Phi[j] its mask selects (at most
+                // kMaxW), listed in the item and terminated by 0xffff.
+                const unsigned long long mask = __ldg(cd.trial_mask + kidx);
+                int cnt = 0;
+                for (int j = 0; j < cd.w; ++j)
+                    if (((mask >> j) & 1ull) && cnt < kMaxW) e->phi[cnt++] = (uint16_t)__ldcg(sd.rec.phi + row * cd.w + j);
+                for (int j = cnt; j < kMaxW; ++j) e->phi[j] = 0xffff;
                 uint32_t *sy = qsyn(e);
                 for (int w = 0; w < Ws; ++w) sy[w] = __ldcg(sd.rec.synd + row * Ws + w);
                 // s' = s xor t H^T (Algorithm 1): flip the checks of every selected bit.
-                const unsigned mask = __ldg(cd.trial_mask + kidx);
-                for (int j = 0; j < cd.w; ++j) {
-                    if ((mask >> j) & 1u) {
-                        const int v = e->phi[j];
-                        for (int k = 0; k < cd.vstride; ++k) {
-                            const int c = __ldg(cd.vchk + v * cd.vstride + k);
-                            if (c == 0xffff) break;
-                            sy[c >> 5] ^= 1u << (c & 31);
-                        }
+                for (int j = 0; j < cnt; ++j) {
+                    const int v = e->phi[j];
+                    for (int k = 0; k < cd.vstride; ++k) {
+                        const int c = __ldg(cd.vchk + v * cd.vstride + k);
+                        if (c == 0xffff) break;
+                        sy[c >> 5] ^= 1u << (c & 31);
                     }
                 }
                 if (DEBUG && sd.dbg.trial_synd)

@@ -75,6 +75,7 @@ extern "C" bpsf_status bpsf_decode_noalloc(bpsf_ctx *c, int64_t n, const uint32_
                                            int32_t cs, uint8_t *conv, int16_t *iters, uint8_t *stage, void *stream) {
     if (!c) return bpsf_fail(BPSF_EINVAL, "ctx is NULL");
     if (n < 0) return bpsf_fail(BPSF_EINVAL, "n_shots must be >= 0");
+    if (bpsf_check_trials(c) != BPSF_OK) return BPSF_EINVAL;
     if (n == 0) return BPSF_OK;
     if (!synd || !corr || !conv || !iters) return bpsf_fail(BPSF_EINVAL, "NULL input or output pointer");
     if (ss < c->Ws) return bpsf_fail(BPSF_EINVAL, "synd_stride_words %d < Ws = %d", ss, c->Ws);

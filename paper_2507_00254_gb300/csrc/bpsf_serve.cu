@@ -180,6 +180,7 @@ extern "C" bpsf_status bpsf_serve_start(bpsf_server **out, bpsf_ctx *const *code
         for (int q = 0; q < k; ++q)
             if (codes[q] == codes[k]) return bpsf_fail(BPSF_EINVAL, "a context appears twice");
         if (codes[k]->device != codes[0]->device) return bpsf_fail(BPSF_EINVAL, "contexts on different devices");
+        if (bpsf_check_trials(codes[k]) != BPSF_OK) return BPSF_EINVAL;
     }
     bpsf_server *s = new bpsf_server();
     s->device = codes[0]->device;

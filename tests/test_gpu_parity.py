@@ -136,6 +136,51 @@ def test_code_families_match_oracle(name, w, k):
     assert B.bpsf_num_trials(dec.handle) == w
 
 
+# The sampled variant (Section V): n_s random trial vectors per weight
+# 1..w_max over |Phi| = 50, the setting of the paper's complexity study
+# (w_max = 6, n_s = 5, 100 iterations per BP instance, adaptive damping).
+@pytest.mark.parametrize("name,p,n", [("bb144", 0.06, 2000), ("bb144_phenom", 0.008, 1500)])
+def test_sampled_trial_list_matches_oracle(name, p, n):
+    masks = synth.sample_trial_masks(7001, 50, 6, 5)
+    P = B.Params(max_iter=100, alpha=0.0, w=50, w_max=6, short_iter=100)
+    oc, e, s = make_inputs(name, p, n, 7002)
+    dec = decoder(name, p, P)
+    dec.set_trials(masks)
+    assert B.bpsf_num_trials(dec.handle) == 30
+    OP = oparams(P)
+    OP = OParams(OP.max_iter, OP.alpha, OP.w, OP.w_max, OP.short_iter, OP.select, tuple(int(m) for m in masks))
+    eo, co, io, so = oc.bpsf_batch(s, p, OP, fp32=True, threads=THREADS)
+    g = gpu_decode(dec, s)
+    eg = unpack(g["corr"], oc.N)
+    same = (eg == eo).all(axis=1)
+    assert same.mean() >= CORR_MATCH, same.mean()
+    for k, ref in (("conv", co), ("iters", io), ("stage", so)):
+        assert ((g[k] != 0) == ref if k == "conv" else g[k] == ref)[same].all(), k
+    assert (g["stage"] == 1).sum() > 0
+    # Weight <= 6 over 50 bits is far beyond 4096 trials: the create-time set is
+    # empty, and decoding without a list is refused.
+    dec.set_trials([])
+    assert B.bpsf_num_trials(dec.handle) == 0
+    with pytest.raises(B.BpsfError) as ei:
+        gpu_decode(dec, s[:4])
+    assert ei.value.status == B.BPSF_EINVAL
+
+
+def test_set_trials_rejects_bad_masks():
+    P = B.Params(max_iter=50, alpha=0.625, w=4, short_iter=10)
+    dec = decoder("bb72", 0.05, P)
+    n0 = B.bpsf_num_trials(dec.handle)
+    assert n0 == 15
+    for bad in ([0], [1 << 4], [(1 << 17) - 1]):
+        with pytest.raises(B.BpsfError) as ei:
+            dec.set_trials(np.array(bad, dtype=np.uint64))
+        assert ei.value.status == B.BPSF_EINVAL
+    dec.set_trials([3, 1])
+    assert B.bpsf_num_trials(dec.handle) == 2
+    dec.set_trials([])
+    assert B.bpsf_num_trials(dec.handle) == n0
+
+
 def test_adaptive_damping_matches_oracle():
     """[[144,12,12]] at p = 0.06 with alpha_t = 1 - 2^-t instead of 0.625."""
     p = 0.06

@@ -90,7 +90,8 @@ def test_create_rejects_bad_arguments_before_device_work():
         (dict(priors=0.6), "prior"),
         (dict(priors=0.0), "prior"),
         (dict(max_iter=0), "max_iter"),
-        (dict(w=17), "w must"),
+        (dict(w=65), "w must"),
+        (dict(w=17), "w_max must be at most 16"),
         (dict(w=4, w_max=5), "w_max"),
         (dict(short_iter=60), "short_iter"),
         (dict(alpha=-0.5), "alpha"),
