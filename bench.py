@@ -325,6 +325,7 @@ def run_gpu(args, rank, world, pool):
         extras["phenomenological"] = run_phenom(B, codes, torch)
         extras["mixed_one_launch"] = run_mixed(B, codes, torch)
         extras["code_capacity_paper_setting"] = run_families(B, codes, torch, harness)
+        extras["sampled_trials_complexity"] = run_sampled(B, codes, torch, harness)
         extras["served"] = run_served(B, codes, torch, (1e4, 1e5, 1e6, 3.16e6, 1e7), seconds=args.serve_seconds,
                                       tuning=args.serve_tuning)
 
@@ -455,6 +456,46 @@ def run_families(B, codes, torch, harness, n=100_000, p_list=(0.04, 0.06)):
                            "tuning": list(d.tuning)}
             d.close()
         out[name] = res
+    return out
+
+
+def run_sampled(B, codes, torch, harness, n=100_000, p=0.003):
+    """The paper's complexity study (Section V: |Phi| = 50, n_s trial vectors sampled per
+    weight 1..w_max, 100 iterations per BP instance, adaptive damping), on the 12-round
+    phenomenological [[144]] model at p = q = 0.003 standing in for the circuit-level model:
+    LER against BP iterations per shot counted serially, batched throughput."""
+    import synth
+    c = codes.phenom("bb144")
+    h0x, h0z = codes.bb("bb144", 0).dense(), codes.bb("bb144", 1).dense()
+    lx = harness.x_logicals(h0x, h0z)
+    G = torch.from_numpy(np.vstack([h0x, lx]).astype(np.float32)).cuda()
+    e = synth.phenom_error_bits(synth.SEEDS["bb144_phenom"][0], 7, 0, n, 144, 72, 12, p, p)
+    out = {"p": p, "shots": n}
+    for label, w_max in (("bp", 0), ("sf_wmax2", 2), ("sf_wmax4", 4), ("sf_wmax6", 6)):
+        params = B.Params(max_iter=100, alpha=0.0, w=50 if w_max else 0, w_max=w_max, short_iter=100)
+        d = B.Decoder(c.ptr, c.idx, c.M, c.N, np.full(c.N, p), params)
+        if w_max:
+            d.set_trials(synth.sample_trial_masks(7100 + w_max, 50, w_max, 5))
+        synd = d.syndrome(_packed_errors_dev(torch, e, d.Wn))
+        o = d.outputs(n)
+        d.decode(synd, out=o)  # warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        d.decode(synd, out=o)
+        dt = time.perf_counter() - t0
+        wk = d.last_work()
+        corr = torch.from_numpy(harness.unpack_rows(o["corr"].cpu().numpy().view(np.uint32), c.N)).cuda()
+        r = torch.from_numpy(e).cuda() ^ corr
+        folded = r[:, :144].clone()
+        for t in range(1, 12):
+            folded ^= r[:, t * 144:(t + 1) * 144]
+        f = (torch.remainder(folded.float() @ G.T, 2.0) > 0.5).any(dim=1) | (o["conv"] == 0)
+        L = float(f.float().mean().item())
+        out[label] = {"trials_per_failed_shot": B.bpsf_num_trials(d.handle), "ler": L, "sigma": (L * (1 - L) / n) ** 0.5,
+                      "bp_iterations_per_shot": wk["iterations"] / n, "shots_per_s": n / dt,
+                      "edge_updates_per_s": wk["edge_updates"] / dt,
+                      "stage_counts": np.bincount(o["stage"].cpu().numpy(), minlength=3).tolist()}
+        d.close()
     return out
 
 
