@@ -385,7 +385,10 @@ bpsf_status bpsf_set_trials(bpsf_ctx *ctx, int32_t n, const uint64_t *masks);
  * failed shots (records), iterations and edge-updates (iterations x nnz
  * summed over runs), and the slot-iterations the teams offered while they
  * had work (team iterations with a running slot x slots per team);
- * iterations / slot_capacity is the slot occupancy of the launch. */
+ * iterations / slot_capacity is the slot occupancy of the launch; and the
+ * trials cancelled because they could not win (first-success rule: a trial
+ * after the earliest converged one is not started, or is stopped at its
+ * next iteration); trial_runs counts the trials run to their end. */
 typedef struct {
     int64_t initial_runs;
     int64_t failed_shots;
@@ -393,6 +396,7 @@ typedef struct {
     int64_t iterations;
     int64_t edge_updates;
     int64_t slot_capacity;
+    int64_t trials_cancelled;
 } bpsf_work;
 bpsf_status bpsf_last_work(bpsf_ctx *ctx, bpsf_work *out);
 

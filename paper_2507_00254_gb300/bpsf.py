@@ -57,7 +57,8 @@ class bpsf_job(C.Structure):
 
 class bpsf_work(C.Structure):
     _fields_ = [("initial_runs", C.c_int64), ("failed_shots", C.c_int64), ("trial_runs", C.c_int64),
-                ("iterations", C.c_int64), ("edge_updates", C.c_int64), ("slot_capacity", C.c_int64)]
+                ("iterations", C.c_int64), ("edge_updates", C.c_int64), ("slot_capacity", C.c_int64),
+                ("trials_cancelled", C.c_int64)]
 
 
 class bpsf_serve_cfg(C.Structure):
@@ -408,7 +409,8 @@ class Decoder:
     def last_work(self):
         w = bpsf_last_work(self.handle)
         return dict(initial_runs=w.initial_runs, failed_shots=w.failed_shots, trial_runs=w.trial_runs,
-                    iterations=w.iterations, edge_updates=w.edge_updates, slot_capacity=w.slot_capacity)
+                    iterations=w.iterations, edge_updates=w.edge_updates, slot_capacity=w.slot_capacity,
+                    trials_cancelled=w.trials_cancelled)
 
 
 class Server:

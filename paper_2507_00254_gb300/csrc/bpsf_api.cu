@@ -554,6 +554,7 @@ extern "C" bpsf_status bpsf_sync(bpsf_ctx *c, void *stream) {
     c->last.iterations = (int64_t)k.iters_total;
     c->last.edge_updates = (int64_t)k.iters_total * c->nnz;
     c->last.slot_capacity = (int64_t)k.slot_capacity;
+    c->last.trials_cancelled = (int64_t)k.trials_cancelled;
     if (k.status) {
         const unsigned stv = k.status;
         cudaMemsetAsync(&dc->status, 0, sizeof(unsigned), (cudaStream_t)stream);
@@ -640,7 +641,7 @@ extern "C" bpsf_status bpsf_decode_plain(bpsf_ctx *c, int64_t n, const uint32_t 
     preset.init_done = 1;
     preset.rec_count = 1;
     *c->h_preset = preset;
-    long long iters_total = 0, trial_runs = 0, failed = 0, cap = 0;
+    long long iters_total = 0, trial_runs = 0, failed = 0, cap = 0, cancelled = 0;
     for (int64_t i = 0; i < n; ++i) {
         JobDev job{synd + i * ss, corr + i * cs, conv + i, iters + i, stage ? stage + i : nullptr, 1, ss, cs};
         cudaError_t e = cudaMemsetAsync(c->d_ctr, 0, sizeof(StreamCounters), s);
@@ -668,9 +669,10 @@ extern "C" bpsf_status bpsf_decode_plain(bpsf_ctx *c, int64_t n, const uint32_t 
             trial_runs += (long long)c->h_ctr->trial_runs;
             iters_total += (long long)c->h_ctr->iters_total;
             cap += (long long)c->h_ctr->slot_capacity;
+            cancelled += (long long)c->h_ctr->trials_cancelled;
         }
     }
-    c->last = bpsf_work{n, failed, trial_runs, iters_total, iters_total * c->nnz, cap};
+    c->last = bpsf_work{n, failed, trial_runs, iters_total, iters_total * c->nnz, cap, cancelled};
     c->d_ctr_last = c->d_ctr;
     return BPSF_OK;
 }

@@ -61,8 +61,10 @@ struct StreamCounters {
     unsigned int status;             // kDev* bits
     unsigned int pad0;
     unsigned long long slot_capacity;  // slot-iterations offered: team iterations with work x S
+    unsigned long long trials_cancelled; // trials not run, or stopped, because they could not win
+    unsigned long long pad[7];
 };
-static_assert(sizeof(StreamCounters) == 64, "counter block is one 64-byte line");
+static_assert(sizeof(StreamCounters) == 128, "counter block is two 64-byte lines");
 
 // Failed-shot records.  A record lives at the shot's row (its index in the
 // job, or its arena row when serving); the publication queue lists failed
@@ -165,13 +167,13 @@ struct SlotState {
     int state;       // kSlot*
     int kind;        // 1 initial run, 2 trial run
     int spare;
-    int outcome;     // 1 converged, 2 iteration cap (valid when PENDING)
+    int outcome;     // 1 converged, 2 iteration cap, 3 stopped (cannot win); valid when PENDING
     int iter;        // iterations completed
     int limit;       // iteration cap of this run
     int kidx;        // trial index (trial runs)
     int pad;
     long long shot;  // shot index in the job (global sequence number when serving)
-    long long pad2;
+    long long cancel;  // manager -> team: shot * n_trials + kidx + 1 of a trial run that cannot win
     uint16_t phi[kMaxW];  // trial run: the bits its trial vector flips, 0xffff-terminated
 };
 static_assert(sizeof(SlotState) == 80, "slot state is 80 bytes");

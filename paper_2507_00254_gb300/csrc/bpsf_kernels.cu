@@ -597,6 +597,7 @@ __device__ __forceinline__ void team_install(const StreamDev &sd, const LayoutMe
         for (int j = 0; j < kMaxW; ++j) ss->phi[j] = e->phi[j];
         ss->iter = 0;
         ss->outcome = 0;
+        ss->cancel = 0;
         ss->limit = e->kind == 1 ? cd.max_iter : cd.short_iter;
     }
     __syncwarp();
@@ -726,7 +727,11 @@ __device__ void team_loop(const StreamDev &sd, const LayoutMem &L, const TeamMem
                 SlotState *ss = &T.st[lane];
                 const int it = ss->iter + 1;
                 ss->iter = it;
-                const int oc = ((acc & pat) == 0u) ? 1 : (it >= ss->limit ? 2 : 0);
+                // A trial the manager found unable to win stops (first-success rule).
+                const bool stop = ss->kind == 2 &&
+                                  *reinterpret_cast<volatile long long *>(&ss->cancel) ==
+                                      ss->shot * (long long)cd.n_trials + ss->kidx + 1;
+                const int oc = ((acc & pat) == 0u) ? 1 : (stop ? 3 : (it >= ss->limit ? 2 : 0));
                 if (oc) {
                     ss->outcome = oc;
                     done = true;
@@ -749,6 +754,7 @@ struct MgrState {
     int head, tail;          // ready queue (ring of Q entries)
     unsigned init_local;     // finished initial runs not yet counted globally
     unsigned trials_local;   // finished trial runs not yet counted globally
+    unsigned trials_cancelled; // trials not run or stopped because they could not win
 };
 
 __device__ __forceinline__ QEntry *qentry(unsigned char *q, int idx, int stride) {
@@ -774,6 +780,39 @@ __device__ __forceinline__ void shot_complete(const StreamDev &sd, long long row
     if (!(sd.flags & kServe)) return;
     __threadfence_system();
     st_release_sys_u32(sd.serve.row_done + row, (unsigned)(shot + 1));
+}
+
+// One trial of a failed shot is over (run, or cancelled because it cannot
+// win): count it; the last one settles the winner (the minimum key of the
+// shot's converged trials) and completes the shot.
+__device__ __forceinline__ void trial_done(const StreamDev &sd, long long row, long long shot) {
+    const CodeDev &cd = sd.code;
+    const JobDev &job = sd.job;
+    const int C = cd.n_trials, Wn = cd.Wn;
+    __threadfence();
+    const unsigned d = atomicAdd(&sd.rec.done[row], 1u) + 1u;
+    if (d == (unsigned)C) {
+        __threadfence();
+        const unsigned long long best = atomicAdd(&sd.rec.best[row], 0ull);
+        if (best != ~0ull) {
+            const int kw = (int)(best & 0xffffffffu);
+            uint32_t *out = job.corr + row * job.corr_stride;
+            const uint32_t *src = sd.rec.corr + ((long long)row * C + kw) * Wn;
+            for (int w = 0; w < Wn; ++w) out[w] = __ldcg(src + w);
+            job.conv[row] = 1;
+            job.iters[row] = __ldcg(sd.rec.iters + (long long)row * C + kw);
+            if (job.stage) job.stage[row] = 1;
+        }
+        shot_complete(sd, row, shot);
+    }
+}
+
+// Under the first-success rule (select = 1) the winner is the earliest
+// converged trial: once trial k* has converged, no later trial can win.
+__device__ __forceinline__ bool trial_cannot_win(const StreamDev &sd, long long row, int kidx) {
+    if (sd.code.select != 1) return false;
+    const unsigned long long best = __ldcg(sd.rec.best + row);
+    return best != ~0ull && (long long)(best & 0xffffffffu) < (long long)kidx;
 }
 
 // Lane-parallel write-out of outboxes that need no warp cooperation:
@@ -823,24 +862,11 @@ __device__ __forceinline__ void finalize_simple(const StreamDev &sd, TeamMem T, 
         if (sd.dbg.trial_conv) sd.dbg.trial_conv[shot * C + kidx] = conv ? 1 : 0;
         if (sd.dbg.trial_iters) sd.dbg.trial_iters[shot * C + kidx] = (int16_t)iter;
     }
-    __threadfence();
-    const unsigned d = atomicAdd(&sd.rec.done[row], 1u) + 1u;
-    mg.trials_local += 1;
-    if (d == (unsigned)C) {
-        // Last trial of this shot: the winner is settled.
-        __threadfence();
-        const unsigned long long best = atomicAdd(&sd.rec.best[row], 0ull);
-        if (best != ~0ull) {
-            const int kw = (int)(best & 0xffffffffu);
-            uint32_t *out = job.corr + row * job.corr_stride;
-            const uint32_t *src = sd.rec.corr + ((long long)row * C + kw) * Wn;
-            for (int w = 0; w < Wn; ++w) out[w] = __ldcg(src + w);
-            job.conv[row] = 1;
-            job.iters[row] = __ldcg(sd.rec.iters + (long long)row * C + kw);
-            if (job.stage) job.stage[row] = 1;
-        }
-        shot_complete(sd, row, shot);
-    }
+    if (ss->outcome == 3)
+        mg.trials_cancelled += 1;  // stopped: it could not win
+    else
+        mg.trials_local += 1;
+    trial_done(sd, row, shot);
 }
 
 // Failed initial run with trials (whole manager warp): provisional output,
@@ -920,19 +946,25 @@ __device__ __forceinline__ bool prefetch(const StreamDev &sd, unsigned char *qba
             const unsigned long long qi = ticket / (unsigned long long)cd.n_trials;
             const int kidx = (int)(ticket - qi * (unsigned long long)cd.n_trials);
             const long long slot_q = (long long)(qi % (unsigned long long)sd.rec.cap);
-            bool ok = true;
+            bool ok = true, timed_out = false;
             if (ld_acquire_u64(sd.rec.qseq + slot_q) != qi + 1ull) {
                 const unsigned long long start = globaltimer_ns();
                 while (ld_acquire_u64(sd.rec.qseq + slot_q) != qi + 1ull) {
                     if (globaltimer_ns() - start > wait_ns) {
                         atomicOr(&sd.ctr->status, kDevReadyTimeout);
                         ok = false;
+                        timed_out = true;
                         break;
                     }
                     __nanosleep(64);
                 }
             }
             QEntry *e = qentry(qbase, (mg.tail + lane) % Q, qstride);
+            if (ok) {
+                const long long shot = __ldcg(sd.rec.qshot + slot_q);
+                const long long row = row_of(sd, shot);
+                if (trial_cannot_win(sd, row, kidx)) ok = false;  // early cancel: counted, not run
+            }
             if (ok) {
                 const long long shot = __ldcg(sd.rec.qshot + slot_q);
                 const long long row = row_of(sd, shot);
@@ -961,7 +993,14 @@ __device__ __forceinline__ bool prefetch(const StreamDev &sd, unsigned char *qba
                     for (int w = 0; w < Ws; ++w)
                         sd.dbg.trial_synd[(shot * cd.n_trials + kidx) * Ws + w] = sy[w];
             } else {
-                e->kind = 0;  // dropped: the record never settles, the device status reports it
+                // Dropped.  A trial that cannot win is counted as done now; after a
+                // timed-out wait the record never settles and the status reports it.
+                if (!timed_out) {
+                    const long long shot = __ldcg(sd.rec.qshot + slot_q);
+                    trial_done(sd, row_of(sd, shot), shot);
+                    ++mg.trials_cancelled;
+                }
+                e->kind = 0;
             }
         }
         __syncwarp();
@@ -1021,7 +1060,7 @@ __device__ void manager_loop(const StreamDev &sd, const LayoutMem &L, unsigned c
     const CodeDev &cd = sd.code;
     const int qstride = qentry_bytes(cd.Ws);
     const int nslots = teams * S;
-    MgrState mg{0, 0, 0u, 0u};
+    MgrState mg{0, 0, 0u, 0u, 0u};
     for (;;) {
         bool progress = false;
         bool busy = false;
@@ -1038,6 +1077,14 @@ __device__ void manager_loop(const StreamDev &sd, const LayoutMem &L, unsigned c
             __threadfence_block();
             const bool coop = fin && T.ob[s].kind == 1 && T.ob[s].outcome == 2 && cd.w > 0;
             if (__any_sync(FULLMASK, stv != kSlotEmpty)) busy = true;
+            // First-success rule: ask running trials that can no longer win to stop.
+            if (cd.select == 1 && stv == kSlotRunning && T.st[s].kind == 2) {
+                const long long shot = T.st[s].shot;
+                const int kidx = T.st[s].kidx;
+                const long long key = shot * (long long)cd.n_trials + kidx + 1;
+                if (T.st[s].cancel != key && trial_cannot_win(sd, row_of(sd, shot), kidx))
+                    *reinterpret_cast<volatile long long *>(&T.st[s].cancel) = key;
+            }
             if (fin && !coop) finalize_simple<DEBUG>(sd, T, s, mg);
             unsigned cm = __ballot_sync(FULLMASK, coop);
             while (cm) {
@@ -1129,12 +1176,14 @@ __device__ void manager_loop(const StreamDev &sd, const LayoutMem &L, unsigned c
     // Flush counters and release the teams.
     const unsigned init_tot = __reduce_add_sync(FULLMASK, mg.init_local);
     const unsigned trial_tot = __reduce_add_sync(FULLMASK, mg.trials_local);
+    const unsigned skip_tot = __reduce_add_sync(FULLMASK, mg.trials_cancelled);
     if (lane == 0) {
         if (init_tot) {
             __threadfence();
             atomicAdd(&sd.ctr->init_done, (unsigned long long)init_tot);
         }
         if (trial_tot) atomicAdd(&sd.ctr->trial_runs, (unsigned long long)trial_tot);
+        if (skip_tot) atomicAdd(&sd.ctr->trials_cancelled, (unsigned long long)skip_tot);
         unsigned long long it = 0, cap = 0;
         for (int t = 0; t < teams; ++t) {
             TeamMem T = team_mem(team_base + t * team_bytes, to);
@@ -1271,6 +1320,7 @@ __global__ void __launch_bounds__(512, (DVX > 0 ? BPSF_MIN_BLOCKS : 1)) bpsf_per
             SlotState *ss = reinterpret_cast<SlotState *>(tb + to.state) + (k % S);
             ss->state = kSlotEmpty;
             ss->kind = 0;
+            ss->cancel = 0;
             reinterpret_cast<OutBox *>(tb + to.outbox)[k % S].full = 0;
             reinterpret_cast<int *>(tb + to.inflag)[k % S] = 0;
         }

@@ -181,6 +181,25 @@ def test_set_trials_rejects_bad_masks():
     assert B.bpsf_num_trials(dec.handle) == n0
 
 
+def test_first_success_cancels_trials_that_cannot_win():
+    """Under the first-success rule trials after the earliest converged one are not run
+    (or are stopped); the results still equal the oracle's, which runs every trial."""
+    p = 0.06
+    P = B.Params(max_iter=100, alpha=0.625, w=6, short_iter=20, select=B.BPSF_SELECT_FIRST)
+    oc, e, s = make_inputs("bb144", p, 3000, synth.SEEDS["bb144_cc"][2], stream=2)
+    dec = decoder("bb144", p, P)
+    compare(oc, dec, s, p, P)
+    wf = dec.last_work()
+    assert wf["trials_cancelled"] > 0
+    assert wf["trial_runs"] + wf["trials_cancelled"] == 63 * wf["failed_shots"]
+    Pm = B.Params(max_iter=100, alpha=0.625, w=6, short_iter=20)
+    decm = decoder("bb144", p, Pm)
+    gpu_decode(decm, s)
+    wm = decm.last_work()
+    assert wm["trials_cancelled"] == 0 and wm["failed_shots"] == wf["failed_shots"]
+    assert wf["iterations"] < wm["iterations"]
+
+
 def test_adaptive_damping_matches_oracle():
     """[[144,12,12]] at p = 0.06 with alpha_t = 1 - 2^-t instead of 0.625."""
     p = 0.06

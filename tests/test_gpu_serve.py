@@ -79,6 +79,24 @@ def test_each_result_is_the_same_alone_and_in_the_mix(mix):
         srv.stop()
 
 
+def test_first_success_rule_served_equals_alone():
+    # Early cancel of trials that cannot win changes no result, served or alone.
+    c = codes.bb("bb144")
+    P = B.Params(max_iter=100, alpha=0.625, w=6, short_iter=20, select=B.BPSF_SELECT_FIRST)
+    d = B.Decoder(c.ptr, c.idx, c.M, c.N, np.full(c.N, 0.07), P)
+    srv = B.Server([d], max_inflight_shots=4096)
+    try:
+        reqs = []
+        for r, n in enumerate((1, 50, 700, 3)):
+            s = synd_host(c, d, 0.07, n, 7700 + r)
+            reqs.append((s, srv.submit(0, s)))
+        got = [(s, srv.poll(t, s.shape[0], 0)) for s, t in reqs]
+    finally:
+        srv.stop()
+    for s, g in got:
+        same(g, alone(d, s))
+
+
 def test_admission_backpressure_and_errors(mix):
     name, c, d, p = mix[0]
     srv = B.Server([d], max_inflight_shots=256)
