@@ -326,6 +326,7 @@ def run_gpu(args, rank, world, pool):
         extras["mixed_one_launch"] = run_mixed(B, codes, torch)
         extras["code_capacity_paper_setting"] = run_families(B, codes, torch, harness)
         extras["sampled_trials_complexity"] = run_sampled(B, codes, torch, harness)
+        extras["first_success_early_cancel"] = run_first_success(B, codes, torch)
         extras["served"] = run_served(B, codes, torch, (1e4, 1e5, 1e6, 3.16e6, 1e7), seconds=args.serve_seconds,
                                       tuning=args.serve_tuning)
 
@@ -495,6 +496,45 @@ def run_sampled(B, codes, torch, harness, n=100_000, p=0.003):
                       "bp_iterations_per_shot": wk["iterations"] / n, "shots_per_s": n / dt,
                       "edge_updates_per_s": wk["edge_updates"] / dt,
                       "stage_counts": np.bincount(o["stage"].cpu().numpy(), minlength=3).tolist()}
+        d.close()
+    return out
+
+
+def run_first_success(B, codes, torch, n=200_000, n_plain=300, p=0.07):
+    """First-success rule with early cancel vs the minimum-weight rule on [[144]] at p:
+    batched throughput and work, and the plain form's per-shot latency on failed shots
+    (the paper's latency argument: a shot ends when its deciding trial is settled)."""
+    import synth
+    c = codes.bb(CODE)
+    e = synth.bernoulli_bits(synth.SEEDS["bb144_cc"][3], 9, 0, n, c.N, p)
+    out = {"p": p, "shots": n}
+    for label, sel in (("min_weight", 0), ("first_success", 1)):
+        d = B.Decoder(c.ptr, c.idx, c.M, c.N, np.full(c.N, p),
+                      B.Params(max_iter=100, alpha=0.625, w=6, short_iter=20, select=sel))
+        synd = d.syndrome(_packed_errors_dev(torch, e, d.Wn))
+        o = d.outputs(n)
+        d.decode(synd, out=o)  # warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        d.decode(synd, out=o)
+        dt = time.perf_counter() - t0
+        wk = d.last_work()
+        stage = o["stage"].cpu().numpy()
+        failed = np.nonzero(stage != 0)[0][:n_plain]
+        lat = []
+        for i in failed:
+            s1 = synd[int(i):int(i) + 1].contiguous()
+            po = d.outputs(1)
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            d.decode(s1, out=po, plain=True)
+            lat.append(time.perf_counter() - t1)
+        lat = np.array(lat) * 1e3
+        out[label] = {"shots_per_s": n / dt, "iterations_per_shot": wk["iterations"] / n,
+                      "trial_runs": wk["trial_runs"], "trials_cancelled": wk["trials_cancelled"],
+                      "stage_counts": np.bincount(stage, minlength=3).tolist(),
+                      "plain_failed_shot_ms": {"n": int(lat.size), "p50": float(np.percentile(lat, 50)),
+                                               "p99": float(np.percentile(lat, 99))}}
         d.close()
     return out
 
