@@ -136,7 +136,7 @@ bpsf_status bpsf_make_plan(bpsf_ctx *const *codes, int n_codes, const bpsf_tunin
         B = std::max(B, tunes[k].warps_per_block);
         if (tunes[k].blocks_per_sm > 0) bps = bps > 0 ? std::min(bps, tunes[k].blocks_per_sm) : tunes[k].blocks_per_sm;
     }
-    const int variant = kernel_variant(all_regular ? -dc : dc, std::max(dv, 1));
+    int variant = kernel_variant(all_regular ? -dc : dc, std::max(dv, 1));
     if (variant < 0) return bpsf_fail(BPSF_EINVAL, "no kernel variant for row degree %d, column degree %d", dc, dv);
     const int vstride = kernel_variant_dv(variant);
     const bpsf_ctx *c0 = codes[0];
@@ -177,6 +177,20 @@ bpsf_status bpsf_make_plan(bpsf_ctx *const *codes, int n_codes, const bpsf_tunin
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, persistent_kernel_ptr(variant, debug), block, smem);
     if (e != cudaSuccess) return bpsf_fail(BPSF_ECUDA, "occupancy query: %s", cudaGetErrorString(e));
     if (bps > 0) occ = std::min(occ, bps);
+    // Fewer than two blocks per SM: the variant's full-register instance runs the
+    // same work with more registers per thread (and four slots per lane).
+    const int full = kernel_variant_full_regs(variant);
+    if (occ < 2 && full != variant) {
+        st = bpsf_ensure_kernel_attrs(full, c0->smem_optin);
+        if (st != BPSF_OK) return st;
+        int occ1 = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ1, persistent_kernel_ptr(full, debug), block, smem);
+        if (e != cudaSuccess) return bpsf_fail(BPSF_ECUDA, "occupancy query: %s", cudaGetErrorString(e));
+        if (occ1 >= 1) {
+            variant = full;
+            occ = 1;
+        }
+    }
     if (occ <= 0) return bpsf_fail(BPSF_EINVAL, "launch shape does not fit on an SM");
     out->variant = variant;
     out->Q = Q;

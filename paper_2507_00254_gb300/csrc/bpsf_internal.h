@@ -264,6 +264,7 @@ __host__ __device__ inline int block_smem_bytes(int M, int N, int P, int Ws, int
 // Kernel entry points (bpsf_kernels.cu).
 int kernel_variant(int dc_max, int dv_max);  // smallest variant that fits, -1 if none
 int kernel_variant_dv(int variant);          // column table width of a variant
+int kernel_variant_full_regs(int variant);   // its one-block, full-register instance
 const void *persistent_kernel_ptr(int variant, bool debug);
 void launch_persistent(int variant, bool debug, int grid, int block, int smem, const LaunchArgs &args,
                        void *stream);

@@ -210,9 +210,13 @@ __device__ __forceinline__ void c_compute_store(CTask<DC, REG> &t, int MS, float
 // Rows (C phase) and columns (V phase) a thread handles per step: their
 // loads are all issued before any of their stores, for instruction-level
 // parallelism (the tasks of one step touch disjoint messages).
-// Teams with S >= 2 slots run the paired phases (one lane per slot pair).
+// Teams with S >= 2 slots run the vector phases: a lane serves up to
+// BPSF_VEC adjacent slots (2 or 4); BPSF_PAIRS = 0 keeps one slot per lane.
 #ifndef BPSF_PAIRS
 #define BPSF_PAIRS 1
+#endif
+#ifndef BPSF_VEC
+#define BPSF_VEC 4
 #endif
 #ifndef BPSF_CU
 #define BPSF_CU 1
@@ -349,75 +353,100 @@ __device__ __forceinline__ void v_phase(const StreamDev &sd, const LayoutMem &L,
 }
 
 // ---------------------------------------------------------------------------
-// Paired phases (S >= 2): lane l serves the slot pair (2p, 2p+1), p = l mod
-// S/2.  The pair's items are adjacent words, so one 64-bit access moves both
-// slots' messages; column tables, LLRs, addresses and loop control are
-// shared, and both slots' residual-syndrome bits of a check sit in one word.
-// A slot of the pair that is not running is computed on its own stale data
-// and its messages are rewritten harmlessly (an install resets them); its
-// decision/flip word and syndrome bits are left alone.
+// Vector phases (S >= V, V = 2 or 4): lane l serves the V adjacent slots
+// V*q .. V*q + V-1, q = l mod S/V.  Their items are adjacent words, so one
+// 64- or 128-bit access moves all V slots' messages; column tables, LLRs,
+// addresses and loop control are shared, and the V slots' residual-syndrome
+// bits of a check sit in one word.  A slot of the group that is not running
+// is computed on its own stale data and its messages are rewritten
+// harmlessly (an install resets them); its decision/flip word and syndrome
+// bits are left alone.
 // ---------------------------------------------------------------------------
-template <int DC, bool REG>
-__device__ __forceinline__ void c_row_pair(const LayoutMem &L, const TeamMem &T, int MH, int lgH, int tau2,
-                                           float alpha0, float alpha1) {
-    float2 *p2 = reinterpret_cast<float2 *>(T.m) + tau2;  // tau2 = j*(S/2) + p
-    const int deg = REG ? DC : (int)L.row_deg[tau2 >> lgH];
-    const unsigned sb = T.syn[(2 * tau2) >> 5] >> ((2 * tau2) & 31);
-    float2 v[DC];
+template <int V> struct VecF;
+template <> struct VecF<2> { typedef float2 T; typedef uint32_t U; };  // U holds V 16-bit flip words
+template <> struct VecF<4> { typedef float4 T; typedef uint2 U; };
+
+template <int V>
+__device__ __forceinline__ float &comp(typename VecF<V>::T &v, int c) { return reinterpret_cast<float *>(&v)[c]; }
+template <int V>
+__device__ __forceinline__ float compc(const typename VecF<V>::T &v, int c) {
+    return reinterpret_cast<const float *>(&v)[c];
+}
+
+template <int DC, bool REG, int V>
+__device__ __forceinline__ void c_row_vec(const LayoutMem &L, const TeamMem &T, int MQ, int lgQ, int tauv,
+                                          const float (&alpha)[V]) {
+    typedef typename VecF<V>::T VT;
+    VT *pv = reinterpret_cast<VT *>(T.m) + tauv;  // tauv = j*(S/V) + q
+    const int deg = REG ? DC : (int)L.row_deg[tauv >> lgQ];
+    const unsigned sb = T.syn[(V * tauv) >> 5] >> ((V * tauv) & 31);
+    VT v[DC];
 #pragma unroll
     for (int k = 0; k < DC; ++k)
-        if (REG || k < deg) v[k] = p2[k * MH];
-    float m1x = __int_as_float(0x7f800000), m2x = m1x, m1y = m1x, m2y = m1x;
-    unsigned sx = (sb & 1u) << 31, sy = ((sb >> 1) & 1u) << 31;
+        if (REG || k < deg) v[k] = pv[k * MQ];
+    float m1[V], m2[V];
+    unsigned sx[V];
+#pragma unroll
+    for (int c = 0; c < V; ++c) {
+        m1[c] = __int_as_float(0x7f800000);
+        m2[c] = m1[c];
+        sx[c] = ((sb >> c) & 1u) << 31;
+    }
 #pragma unroll
     for (int k = 0; k < DC; ++k) {
         if (REG || k < deg) {
-            const float ax = fabsf(v[k].x), ay = fabsf(v[k].y);
-            m2x = fminf(m2x, fmaxf(m1x, ax));
-            m1x = fminf(m1x, ax);
-            m2y = fminf(m2y, fmaxf(m1y, ay));
-            m1y = fminf(m1y, ay);
-            sx ^= __float_as_uint(v[k].x);
-            sy ^= __float_as_uint(v[k].y);
+#pragma unroll
+            for (int c = 0; c < V; ++c) {
+                const float a = fabsf(compc<V>(v[k], c));
+                m2[c] = fminf(m2[c], fmaxf(m1[c], a));
+                m1[c] = fminf(m1[c], a);
+                sx[c] ^= __float_as_uint(compc<V>(v[k], c));
+            }
         }
     }
-    sx &= 0x80000000u;
-    sy &= 0x80000000u;
-    const unsigned g1x = __float_as_uint(fminf(__fmul_rn(alpha0, m1x), kMagClamp)) | sx;
-    const unsigned g2x = __float_as_uint(fminf(__fmul_rn(alpha0, m2x), kMagClamp)) | sx;
-    const unsigned g1y = __float_as_uint(fminf(__fmul_rn(alpha1, m1y), kMagClamp)) | sy;
-    const unsigned g2y = __float_as_uint(fminf(__fmul_rn(alpha1, m2y), kMagClamp)) | sy;
+    unsigned g1[V], g2[V];
+#pragma unroll
+    for (int c = 0; c < V; ++c) {
+        sx[c] &= 0x80000000u;
+        g1[c] = __float_as_uint(fminf(__fmul_rn(alpha[c], m1[c]), kMagClamp)) | sx[c];
+        g2[c] = __float_as_uint(fminf(__fmul_rn(alpha[c], m2[c]), kMagClamp)) | sx[c];
+    }
 #pragma unroll
     for (int k = 0; k < DC; ++k) {
         if (REG || k < deg) {
-            float2 o;
-            o.x = __uint_as_float(((fabsf(v[k].x) == m1x) ? g2x : g1x) ^ (__float_as_uint(v[k].x) & 0x80000000u));
-            o.y = __uint_as_float(((fabsf(v[k].y) == m1y) ? g2y : g1y) ^ (__float_as_uint(v[k].y) & 0x80000000u));
-            p2[k * MH] = o;
+            VT o;
+#pragma unroll
+            for (int c = 0; c < V; ++c) {
+                const float x = compc<V>(v[k], c);
+                comp<V>(o, c) = __uint_as_float(((fabsf(x) == m1[c]) ? g2[c] : g1[c]) ^ (__float_as_uint(x) & 0x80000000u));
+            }
+            pv[k * MQ] = o;
         }
     }
 }
 
-template <int DC, bool REG>
-__device__ __forceinline__ void c_phase_pair(const CodeDev &cd, const LayoutMem &L, const TeamMem &T, int lgS,
-                                             float alpha0, float alpha1, int tid, int nthreads) {
-    const int lgH = lgS - 1;
-    const int MH = cd.M << lgH;
-    for (int tau2 = tid; tau2 < MH; tau2 += nthreads) c_row_pair<DC, REG>(L, T, MH, lgH, tau2, alpha0, alpha1);
+template <int DC, bool REG, int V>
+__device__ __forceinline__ void c_phase_vec(const CodeDev &cd, const LayoutMem &L, const TeamMem &T, int lgS,
+                                            const float (&alpha)[V], int tid, int nthreads) {
+    const int lgQ = lgS - (V == 4 ? 2 : 1);
+    const int MQ = cd.M << lgQ;
+    for (int tauv = tid; tauv < MQ; tauv += nthreads) c_row_vec<DC, REG, V>(L, T, MQ, lgQ, tauv, alpha);
 }
 
-template <int DVS, int DVX, bool DEBUG>
-__device__ __forceinline__ void v_phase_pair(const StreamDev &sd, const LayoutMem &L, const TeamMem &T, int lgS,
-                                             bool on0, bool on1, unsigned initm, int tid, int nthreads) {
+template <int DVS, int DVX, bool DEBUG, int V>
+__device__ __forceinline__ void v_phase_vec(const StreamDev &sd, const LayoutMem &L, const TeamMem &T, int lgS,
+                                            unsigned onm, unsigned initm, int tid, int nthreads) {
+    typedef typename VecF<V>::T VT;
+    typedef typename VecF<V>::U UT;
     const CodeDev &cd = sd.code;
-    const int lgH = lgS - 1;
-    const int total = cd.N << lgH;
-    const int p = tid & ((1 << lgH) - 1);
-    const int s0 = 2 * p;
-    float2 *m2 = reinterpret_cast<float2 *>(T.m) + p;
-    uint32_t *f2 = reinterpret_cast<uint32_t *>(T.flips);
-    for (int tau2 = tid; tau2 < total; tau2 += nthreads) {
-        const int i = tau2 >> lgH;
+    const int lgQ = lgS - (V == 4 ? 2 : 1);
+    const int total = cd.N << lgQ;
+    const int q = tid & ((1 << lgQ) - 1);
+    const int s0 = V * q;
+    VT *mv = reinterpret_cast<VT *>(T.m) + q;
+    UT *fv = reinterpret_cast<UT *>(T.flips);
+    for (int tauv = tid; tauv < total; tauv += nthreads) {
+        const int i = tauv >> lgQ;
         uint16_t pos[DVS];
         const uint16_t *vp = L.vpos + i * DVS;
         if (DVS == 4) {
@@ -431,58 +460,66 @@ __device__ __forceinline__ void v_phase_pair(const StreamDev &sd, const LayoutMe
             for (int k = 0; k < DVS; ++k) pos[k] = vp[k];
         }
         const float lc = L.lch[i];
-        float2 r[DVS];
+        VT r[DVS];
 #pragma unroll
         for (int k = 0; k < DVS; ++k)
-            if (DVX > 0 ? (k < DVX) : (pos[k] != 0xffffu)) r[k] = m2[(int)pos[k] << lgH];
-        const unsigned f = f2[tau2];
-        float lox, loy;
+            if (DVX > 0 ? (k < DVX) : (pos[k] != 0xffffu)) r[k] = mv[(int)pos[k] << lgQ];
+        const UT fw = fv[tauv];
+        const uint16_t *fh = reinterpret_cast<const uint16_t *>(&fw);
+        float lo[V];
         if (DVX == 3) {
-            const float t0x = __fadd_rn(lc, r[0].x), t0y = __fadd_rn(lc, r[0].y);
-            const float q2x = __fadd_rn(t0x, r[1].x), q2y = __fadd_rn(t0y, r[1].y);
-            lox = __fadd_rn(q2x, r[2].x);
-            loy = __fadd_rn(q2y, r[2].y);
-            m2[(int)pos[0] << lgH] = make_float2(__fadd_rn(__fadd_rn(lc, r[1].x), r[2].x),
-                                                 __fadd_rn(__fadd_rn(lc, r[1].y), r[2].y));
-            m2[(int)pos[1] << lgH] = make_float2(__fadd_rn(t0x, r[2].x), __fadd_rn(t0y, r[2].y));
-            m2[(int)pos[2] << lgH] = make_float2(q2x, q2y);
+            VT q0, q1, q2;
+#pragma unroll
+            for (int c = 0; c < V; ++c) {
+                const float t0 = __fadd_rn(lc, compc<V>(r[0], c));
+                const float a2 = __fadd_rn(t0, compc<V>(r[1], c));
+                lo[c] = __fadd_rn(a2, compc<V>(r[2], c));
+                comp<V>(q0, c) = __fadd_rn(__fadd_rn(lc, compc<V>(r[1], c)), compc<V>(r[2], c));
+                comp<V>(q1, c) = __fadd_rn(t0, compc<V>(r[2], c));
+                comp<V>(q2, c) = a2;
+            }
+            mv[(int)pos[0] << lgQ] = q0;
+            mv[(int)pos[1] << lgQ] = q1;
+            mv[(int)pos[2] << lgQ] = q2;
         } else {
 #pragma unroll
             for (int k = 0; k < DVS; ++k) {
                 if (pos[k] != 0xffffu) {
-                    float ax = lc, ay = lc;
+                    VT acc;
+#pragma unroll
+                    for (int c = 0; c < V; ++c) comp<V>(acc, c) = lc;
 #pragma unroll
                     for (int k2 = 0; k2 < DVS; ++k2)
-                        if (k2 != k && pos[k2] != 0xffffu) {
-                            ax = __fadd_rn(ax, r[k2].x);
-                            ay = __fadd_rn(ay, r[k2].y);
-                        }
-                    m2[(int)pos[k] << lgH] = make_float2(ax, ay);
+                        if (k2 != k && pos[k2] != 0xffffu)
+#pragma unroll
+                            for (int c = 0; c < V; ++c) comp<V>(acc, c) = __fadd_rn(compc<V>(acc, c), compc<V>(r[k2], c));
+                    mv[(int)pos[k] << lgQ] = acc;
                 }
             }
-            lox = lc;
-            loy = lc;
+#pragma unroll
+            for (int c = 0; c < V; ++c) lo[c] = lc;
 #pragma unroll
             for (int k = 0; k < DVS; ++k)
-                if (pos[k] != 0xffffu) {
-                    lox = __fadd_rn(lox, r[k].x);
-                    loy = __fadd_rn(loy, r[k].y);
-                }
+                if (pos[k] != 0xffffu)
+#pragma unroll
+                    for (int c = 0; c < V; ++c) lo[c] = __fadd_rn(lo[c], compc<V>(r[k], c));
         }
-        const unsigned ebx = (lox <= 0.f) ? 1u : 0u, eby = (loy <= 0.f) ? 1u : 0u;
-        if (DEBUG && sd.dbg.lout) {
-            if (on0 && ((initm >> s0) & 1u)) sd.dbg.lout[T.st[s0].shot * cd.N + i] = lox;
-            if (on1 && ((initm >> (s0 + 1)) & 1u)) sd.dbg.lout[T.st[s0 + 1].shot * cd.N + i] = loy;
+        // Decision (bit 15) and flip count of each slot's 16-bit word.
+        unsigned bm = 0;
+#pragma unroll
+        for (int c = 0; c < V; ++c) {
+            const unsigned eb = (lo[c] <= 0.f) ? 1u : 0u;
+            if (((onm >> c) & 1u) && (((unsigned)fh[c] >> 15) & 1u) != eb) bm |= 1u << c;
+            if (DEBUG && sd.dbg.lout && ((onm >> c) & 1u) && ((initm >> (s0 + c)) & 1u))
+                sd.dbg.lout[T.st[s0 + c].shot * cd.N + i] = lo[c];
         }
-        // Decision (bit 15) and flip count of each slot's 16-bit half.
-        const bool fx = on0 && ((f >> 15) & 1u) != ebx;
-        const bool fy = on1 && ((f >> 31) & 1u) != eby;
-        if (fx || fy) {
-            unsigned lo = f & 0xffffu, hi = f >> 16;
-            if (fx) lo = ((lo ^ 0x8000u) + 1u) & 0xffffu;
-            if (fy) hi = ((hi ^ 0x8000u) + 1u) & 0xffffu;
-            f2[tau2] = lo | (hi << 16);
-            const unsigned bm = (fx ? 1u : 0u) | (fy ? 2u : 0u);
+        if (bm) {
+            UT nw = fw;
+            uint16_t *nh = reinterpret_cast<uint16_t *>(&nw);
+#pragma unroll
+            for (int c = 0; c < V; ++c)
+                if ((bm >> c) & 1u) nh[c] = (uint16_t)((((unsigned)nh[c]) ^ 0x8000u) + 1u);
+            fv[tauv] = nw;
             const uint16_t *vc = cd.vchk + i * DVS;
 #pragma unroll
             for (int k = 0; k < DVS; ++k) {
@@ -646,7 +683,7 @@ __device__ __forceinline__ void team_service(const StreamDev &sd, const LayoutMe
 // ---------------------------------------------------------------------------
 // Compute team loop.
 // ---------------------------------------------------------------------------
-template <int DC, int DVS, int DVX, bool DEBUG>
+template <int DC, int DVS, int DVX, bool DEBUG, int MINB>
 __device__ void team_loop(const StreamDev &sd, const LayoutMem &L, const TeamMem &T, BlockHdr *hdr, int S, int W,
                           int tid, int bar_id, unsigned long long wait_ns) {
     const int lane = tid & 31, wt = tid >> 5, nthreads = 32 * W;
@@ -656,7 +693,9 @@ __device__ void team_loop(const StreamDev &sd, const LayoutMem &L, const TeamMem
     const int my_slot = lane & (S - 1);             // the slot this lane serves in every phase
     const int n_rwords = ((cd.M << lgS) + 31) >> 5;  // residual-syndrome words of the team
     const unsigned pat = slot_pattern(S) << (lane < S ? lane : 0);
-    constexpr bool kPairs = BPSF_PAIRS && DC <= 16;  // the widest rows keep one slot per lane (registers)
+    constexpr bool kVec = BPSF_PAIRS && DC <= 16;  // the widest rows keep one slot per lane (registers)
+    // Four slots per lane: exact-degree rows with the full register budget (one block).
+    constexpr bool kVec4 = kVec && MINB == 1 && DVX == 3 && BPSF_VEC >= 4;
     unsigned long long idle_since = 0;
     unsigned last_beat = 0;
     for (;;) {
@@ -701,14 +740,25 @@ __device__ void team_loop(const StreamDev &sd, const LayoutMem &L, const TeamMem
         team_sync(W, bar_id);
         if (ex) break;
         if (run == 0u) continue;
-        if (kPairs && S >= 2) {
-            const int s0 = 2 * (lane & ((S >> 1) - 1));
-            const bool on0 = (run >> s0) & 1u, on1 = (run >> (s0 + 1)) & 1u;
-            if (on0 || on1)
-                c_phase_pair<DC, (DVX > 0)>(cd, L, T, lgS, damping(cd, T.st[s0].iter + 1),
-                                            damping(cd, T.st[s0 + 1].iter + 1), tid, nthreads);
+        if (kVec4 && S >= 4) {
+            const int s0 = 4 * (lane & ((S >> 2) - 1));
+            const unsigned onm = (run >> s0) & 0xfu;
+            float al[4];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) al[c] = damping(cd, T.st[s0 + c].iter + 1);
+            if (onm) c_phase_vec<DC, (DVX > 0), 4>(cd, L, T, lgS, al, tid, nthreads);
             team_sync(W, bar_id);
-            if (on0 || on1) v_phase_pair<DVS, DVX, DEBUG>(sd, L, T, lgS, on0, on1, initm, tid, nthreads);
+            if (onm) v_phase_vec<DVS, DVX, DEBUG, 4>(sd, L, T, lgS, onm, initm, tid, nthreads);
+            team_sync(W, bar_id);
+        } else if (kVec && S >= 2) {
+            const int s0 = 2 * (lane & ((S >> 1) - 1));
+            const unsigned onm = (run >> s0) & 0x3u;
+            float al[2];
+            al[0] = damping(cd, T.st[s0].iter + 1);
+            al[1] = damping(cd, T.st[s0 + 1].iter + 1);
+            if (onm) c_phase_vec<DC, (DVX > 0), 2>(cd, L, T, lgS, al, tid, nthreads);
+            team_sync(W, bar_id);
+            if (onm) v_phase_vec<DVS, DVX, DEBUG, 2>(sd, L, T, lgS, onm, initm, tid, nthreads);
             team_sync(W, bar_id);
         } else {
             const bool lane_on = (run >> my_slot) & 1u;
@@ -1207,17 +1257,18 @@ struct KernelParams {
     unsigned long long wait_ns;
 };
 
-// Minimum resident blocks per SM the register allocation must allow: two
-// caps registers at 64 per thread, so two 512-thread blocks (or three
-// smaller ones) fit on an SM.  Only the exact-degree variant takes it; the
-// others (wider rows, irregular codes whose shared-memory needs allow few
-// slots per SM anyway) keep the full register budget.
+// MINB: minimum resident blocks per SM the register allocation must allow.
+// Two caps registers at 64 per thread, so two 512-thread blocks (or three
+// smaller ones) fit on an SM; one keeps the full budget, which four slots
+// per lane need.  The exact-degree variant has both instances (the launch
+// plan picks by the blocks that fit); the others (wider rows, irregular
+// codes whose shared-memory needs allow few slots per SM anyway) have one.
 #ifndef BPSF_MIN_BLOCKS
 #define BPSF_MIN_BLOCKS 2
 #endif
 
-template <int DC, int DVS, int DVX, bool DEBUG>
-__global__ void __launch_bounds__(512, (DVX > 0 ? BPSF_MIN_BLOCKS : 1)) bpsf_persistent(const __grid_constant__ KernelParams kp) {
+template <int DC, int DVS, int DVX, bool DEBUG, int MINB>
+__global__ void __launch_bounds__(512, MINB) bpsf_persistent(const __grid_constant__ KernelParams kp) {
     extern __shared__ __align__(16) unsigned char smem[];
     BlockHdr *hdr = reinterpret_cast<BlockHdr *>(smem);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -1356,7 +1407,7 @@ __global__ void __launch_bounds__(512, (DVX > 0 ? BPSF_MIN_BLOCKS : 1)) bpsf_per
             const int team = (warp - 1) / W;
             if (team < teams) {
                 TeamMem T = team_mem(team_base + team * to.total, to);
-                team_loop<DC, DVS, DVX, DEBUG>(sd, L, T, hdr, S, W, tid - 32 - team * W * 32, 1 + team, kp.wait_ns);
+                team_loop<DC, DVS, DVX, DEBUG, MINB>(sd, L, T, hdr, S, W, tid - 32 - team * W * 32, 1 + team, kp.wait_ns);
             }
         }
         __syncthreads();
@@ -1370,7 +1421,9 @@ __global__ void __launch_bounds__(512, (DVX > 0 ? BPSF_MIN_BLOCKS : 1)) bpsf_per
 struct Variant {
     int dc, dvs, dvx;  // row-degree bound, column table width, exact column degree (0 = any)
 };
-static const Variant kVariants[] = {{6, 4, 3}, {6, 4, 0}, {8, 4, 0}, {16, 8, 0}, {32, 16, 0}};
+// Index 5 is the full-register instance of variant 0 (never chosen by
+// kernel_variant; see kernel_variant_full_regs).
+static const Variant kVariants[] = {{6, 4, 3}, {6, 4, 0}, {8, 4, 0}, {16, 8, 0}, {32, 16, 0}, {6, 4, 3}};
 static const int kNumVariants = 5;
 
 // Smallest variant that fits.  The exact-degree variant serves codes with
@@ -1394,20 +1447,25 @@ typedef void (*KernelFn)(KernelParams);
 
 static KernelFn kernel_fn(int variant, bool debug) {
     switch (variant * 2 + (debug ? 1 : 0)) {
-        case 0: return bpsf_persistent<6, 4, 3, false>;
-        case 1: return bpsf_persistent<6, 4, 3, true>;
-        case 2: return bpsf_persistent<6, 4, 0, false>;
-        case 3: return bpsf_persistent<6, 4, 0, true>;
-        case 4: return bpsf_persistent<8, 4, 0, false>;
-        case 5: return bpsf_persistent<8, 4, 0, true>;
-        case 6: return bpsf_persistent<16, 8, 0, false>;
-        case 7: return bpsf_persistent<16, 8, 0, true>;
-        case 8: return bpsf_persistent<32, 16, 0, false>;
-        default: return bpsf_persistent<32, 16, 0, true>;
+        case 0: return bpsf_persistent<6, 4, 3, false, BPSF_MIN_BLOCKS>;
+        case 1: return bpsf_persistent<6, 4, 3, true, BPSF_MIN_BLOCKS>;
+        case 2: return bpsf_persistent<6, 4, 0, false, 1>;
+        case 3: return bpsf_persistent<6, 4, 0, true, 1>;
+        case 4: return bpsf_persistent<8, 4, 0, false, 1>;
+        case 5: return bpsf_persistent<8, 4, 0, true, 1>;
+        case 6: return bpsf_persistent<16, 8, 0, false, 1>;
+        case 7: return bpsf_persistent<16, 8, 0, true, 1>;
+        case 8: return bpsf_persistent<32, 16, 0, false, 1>;
+        case 9: return bpsf_persistent<32, 16, 0, true, 1>;
+        case 10: return bpsf_persistent<6, 4, 3, false, 1>;
+        default: return bpsf_persistent<6, 4, 3, true, 1>;
     }
 }
 
 int kernel_variant_dv(int variant) { return kVariants[variant].dvs; }
+
+// The full-register instance of a variant (itself when it has only one).
+int kernel_variant_full_regs(int variant) { return variant == 0 ? 5 : variant; }
 
 const void *persistent_kernel_ptr(int variant, bool debug) {
     return reinterpret_cast<const void *>(kernel_fn(variant, debug));
