@@ -68,6 +68,9 @@ def lib():
         L.oracle_code_new.restype = vp
         L.oracle_code_free.argtypes = [vp]
         L.oracle_code_nnz.argtypes = [vp]
+        L.oracle_code_set_layered.argtypes = [vp, C.c_int]
+        L.oracle_code_layer.argtypes = [vp, C.c_int]
+        L.oracle_code_layer.restype = C.c_int
         L.oracle_code_nnz.restype = C.c_int
         L.oracle_syndrome.argtypes = [vp, _u8p, _u8p]
         L.oracle_llr_f64.argtypes = [_f64p, C.c_int, _f64p]
@@ -182,6 +185,7 @@ class Params:
     short_iter: int = 10
     select: int = 0         # 0 min weight, 1 earliest converged trial of the list
     trials: tuple = ()      # explicit trial list (subset masks over Phi); () -> weight <= w_max
+    layered: bool = False   # layered schedule (rows by greedy layer) instead of flooding
 
 
 class Code:
@@ -224,8 +228,18 @@ class Code:
         pri = np.broadcast_to(np.asarray(priors, dtype=np.float64), (self.N,))
         return self.llr(np.ascontiguousarray(pri), fp32)
 
-    def bp(self, s, priors, max_iter, alpha, fp32=True, stop_on_converge=True, track=False):
+    def schedule(self, layered: bool):
+        """Select the flooding (default) or the layered schedule for the runs that follow."""
+        lib().oracle_code_set_layered(self._h, int(bool(layered)))
+
+    def layers(self):
+        """Layer of every row under the layered schedule."""
+        self.schedule(True)
+        return np.array([lib().oracle_code_layer(self._h, j) for j in range(self.M)], dtype=np.int64)
+
+    def bp(self, s, priors, max_iter, alpha, fp32=True, stop_on_converge=True, track=False, layered=False):
         """One min-sum BP run; returns dict(e, converged, iters, lout, flips)."""
+        self.schedule(layered)
         lch = self._lch(priors, fp32)
         s = np.ascontiguousarray(s, dtype=np.uint8)
         e = np.zeros(self.N, dtype=np.uint8)
@@ -240,6 +254,7 @@ class Code:
 
     def trials(self, s, priors, phi, params: Params, fp32=True):
         """Every trial of one failed shot: (s', converged, iters, e' xor t), in list order."""
+        self.schedule(params.layered)
         lch = self._lch(priors, fp32)
         w = len(phi)
         wm = w if params.w_max <= 0 or params.w_max > w else params.w_max
@@ -257,6 +272,7 @@ class Code:
 
     def bpsf(self, s, priors, params: Params, fp32=True):
         """BP-SF of one syndrome (Algorithm 1); dict(e, converged, iters, stage, phi, flips)."""
+        self.schedule(params.layered)
         lch = self._lch(priors, fp32)
         e = np.zeros(self.N, dtype=np.uint8)
         it, st = C.c_int(0), C.c_int(0)
@@ -275,6 +291,7 @@ class Code:
         """BP-SF over a batch of syndromes (n, M) -> (e (n, N), converged, iters, stage)."""
         synd = np.ascontiguousarray(synd, dtype=np.uint8)
         n = synd.shape[0]
+        self.schedule(params.layered)
         lch = self._lch(priors, fp32)
         e = np.zeros((n, self.N), dtype=np.uint8)
         conv = np.zeros(n, dtype=np.uint8)

@@ -262,6 +262,9 @@ typedef struct {
     int *col_ptr;     /* N+1 */
     int *col_chk;     /* nnz: checks of column i in ascending order */
     int *col_edge;    /* nnz: the edge id (row-ordered) of that (check, column) pair */
+    int layered;      /* 0: flooding schedule; 1: layered schedule (rows by layer) */
+    int n_layers;
+    int *layer_of;    /* M: layer of each row (layered schedule) */
 } oracle_code;
 
 oracle_code *oracle_code_new(const uint8_t *H, int M, int N) {
@@ -305,6 +308,7 @@ oracle_code *oracle_code_new(const uint8_t *H, int M, int N) {
 void oracle_code_free(oracle_code *c) {
     if (!c) return;
     free(c->H); free(c->row_ptr); free(c->row_var); free(c->col_ptr); free(c->col_chk); free(c->col_edge);
+    free(c->layer_of);
     free(c);
 }
 
@@ -320,6 +324,35 @@ void oracle_syndrome(const oracle_code *c, const uint8_t *e, uint8_t *s) {
 }
 
 /* e H^T = s, row by row over the ones of each row. */
+/*
+ * Layered schedule: rows are coloured greedily in ascending order, each row
+ * taking the smallest layer not used by an earlier row that shares a
+ * variable with it; layers are then processed in order.  Rows of one layer
+ * share no variable, so their order within the layer does not matter.
+ */
+void oracle_code_set_layered(oracle_code *c, int on) {
+    c->layered = on ? 1 : 0;
+    if (!on || c->layer_of) return;
+    c->layer_of = malloc(sizeof(int) * (size_t)(c->M + 1));
+    uint8_t *used = malloc((size_t)c->M + 1);
+    c->n_layers = 0;
+    for (int j = 0; j < c->M; j++) {
+        memset(used, 0, (size_t)c->M + 1);
+        for (int k = 0; k < j; k++) {
+            int share = 0;
+            for (int i = 0; i < c->N && !share; i++) share = c->H[(size_t)j * c->N + i] && c->H[(size_t)k * c->N + i];
+            if (share) used[c->layer_of[k]] = 1;
+        }
+        int l = 0;
+        while (used[l]) l++;
+        c->layer_of[j] = l;
+        if (l + 1 > c->n_layers) c->n_layers = l + 1;
+    }
+    free(used);
+}
+
+int oracle_code_layer(const oracle_code *c, int j) { return c->layer_of ? c->layer_of[j] : -1; }
+
 static int satisfies(const oracle_code *c, const uint8_t *e, const uint8_t *s) {
     for (int j = 0; j < c->M; j++) {
         int acc = 0;

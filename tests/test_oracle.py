@@ -232,6 +232,77 @@ def test_min_sum_alpha_one_is_min_cost_on_trees(seed):
     assert np.allclose(r32["lout"], want, rtol=1e-5, atol=1e-4)
 
 
+# --------------------------------------------------------------------------
+# Layered schedule: rows by greedy layer, running posterior
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("seed", range(6))
+def test_layered_min_sum_alpha_one_is_min_cost_on_trees(seed):
+    # On a cycle-free graph the layered schedule reaches the same fixed point as
+    # flooding: min-sum with alpha = 1 gives the exact min-cost differences.
+    rng = np.random.default_rng(200 + seed)
+    n_var, n_chk = 10 + seed % 3, 4 + seed % 2
+    H = random_tree_H(rng, n_var, n_chk)
+    p = rng.uniform(0.02, 0.3, size=n_var)
+    e = (rng.random(n_var) < 0.3).astype(np.uint8)
+    s = ((H.astype(np.int64) @ e) % 2).astype(np.uint8)
+    code = Code(H)
+    lch = np.log((1 - p) / p)
+    want = brute_min_cost(H, lch, s)
+    r64 = code.bp(s, p, max_iter=n_var + n_chk + 2, alpha=1.0, fp32=False, stop_on_converge=False, layered=True)
+    assert np.allclose(r64["lout"], want, rtol=1e-9, atol=1e-9)
+
+
+def test_layers_are_the_greedy_colouring():
+    hx, _ = oracle.named_code("bb72")
+    code = Code(hx)
+    lay = code.layers()
+    share = (hx.astype(np.int64) @ hx.T.astype(np.int64)) > 0
+    for j in range(hx.shape[0]):
+        earlier = {int(lay[k]) for k in range(j) if share[j, k]}
+        mex = 0
+        while mex in earlier:
+            mex += 1
+        assert lay[j] == mex
+    for a in range(hx.shape[0]):  # rows of one layer share no variable
+        for b in range(a + 1, hx.shape[0]):
+            if lay[a] == lay[b]:
+                assert not share[a, b]
+
+
+@pytest.mark.parametrize("fp32", [False, True])
+def test_layered_single_check_equals_flooding(fp32):
+    H = np.ones((1, 4), dtype=np.uint8)
+    p = np.array([0.05, 0.05, 0.2, 0.05])
+    code = Code(H)
+    f = code.bp(np.array([1], dtype=np.uint8), p, max_iter=1, alpha=0.625, fp32=fp32, stop_on_converge=False)
+    g = code.bp(np.array([1], dtype=np.uint8), p, max_iter=1, alpha=0.625, fp32=fp32, stop_on_converge=False,
+                layered=True)
+    assert (f["lout"] == g["lout"]).all()
+
+
+def test_layered_chain_closed_form():
+    # v0 - c0 - v1 - c1 - v2, s = (1, 0), alpha = 1, one iteration.  c0 is layer 0 and
+    # c1 layer 1 (they share v1), so c1 already sees c0's new message through L1:
+    #   c0: q = (l0, l1); r00 = -l1, r01 = -l0; L0 = l0 - l1, L1 = l1 - l0
+    #   c1: q1 = L1 - 0, q2 = l2; r11 = +|l2|, r12 = sign(q1) |q1|; L1 += r11, L2 = l2 + r12
+    # Under flooding c1 would see q1 = l1 instead (and L2 = l2 + l1).
+    H = np.array([[1, 1, 0], [0, 1, 1]], dtype=np.uint8)
+    p = np.array([0.1, 0.2, 0.1])
+    code = Code(H)
+    assert code.layers().tolist() == [0, 1]
+    r = code.bp(np.array([1, 0], dtype=np.uint8), p, max_iter=1, alpha=1.0, fp32=False, stop_on_converge=False,
+                layered=True)
+    l0, l1, l2 = (float(np.log((1 - x) / x)) for x in p)
+    L0 = l0 + (-(1.0 * l1))
+    q1 = (l1 + (-(1.0 * l0))) - 0.0
+    L1 = q1 + (1.0 * abs(l2))
+    L2 = l2 + ((1.0 if q1 >= 0 else -1.0) * (1.0 * abs(q1)))
+    assert r["lout"].tolist() == [L0, L1, L2]
+    f = code.bp(np.array([1, 0], dtype=np.uint8), p, max_iter=1, alpha=1.0, fp32=False, stop_on_converge=False)
+    assert f["lout"][2] != r["lout"][2]
+
+
 @pytest.mark.parametrize("fp32", [False, True])
 @pytest.mark.parametrize("s_bit", [0, 1])
 def test_single_check_closed_form(fp32, s_bit):
