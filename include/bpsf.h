@@ -56,6 +56,7 @@ typedef enum {
 typedef enum { BPSF_CSR = 0, BPSF_CSC = 1 } bpsf_layout;
 
 enum { BPSF_SELECT_MIN_WEIGHT = 0, BPSF_SELECT_FIRST = 1 };
+enum { BPSF_FLAG_LAYERED = 1 };
 
 /*
  * Decoder parameters (Algorithm 1 inputs plus the min-sum settings of
@@ -80,7 +81,13 @@ enum { BPSF_SELECT_MIN_WEIGHT = 0, BPSF_SELECT_FIRST = 1 };
  *              default set is in ascending subset mask);
  *              BPSF_SELECT_FIRST: the earliest converged trial (the paper's
  *              "first valid" rule made deterministic).
- *   flags      reserved, must be 0.
+ *   flags      BPSF_FLAG_LAYERED: the layered schedule (the paper's variant for
+ *              the [[288]] code) instead of flooding: rows are coloured
+ *              greedily in ascending order into layers of rows that share no
+ *              variable; layer by layer, each row takes its V2C messages out
+ *              of the running posterior (q = L - r), computes its C2V
+ *              messages by Eq. (c2v) and puts them back (L = q + r).  Other
+ *              bits must be 0.
  */
 typedef struct {
     int32_t max_iter;

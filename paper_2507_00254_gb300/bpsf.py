@@ -19,6 +19,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libbpsf.so")
 BPSF_OK, BPSF_EINVAL, BPSF_ENOMEM, BPSF_ECUDA, BPSF_ETIMEOUT, BPSF_EBUSY, BPSF_ECLOSED, BPSF_EDEVICE = range(8)
 BPSF_CSR, BPSF_CSC = 0, 1
 BPSF_SELECT_MIN_WEIGHT, BPSF_SELECT_FIRST = 0, 1
+BPSF_FLAG_LAYERED = 1
 
 # Every symbol include/bpsf.h declares.
 EXPORTS = (
@@ -291,9 +292,11 @@ class Params:
     w_max: int = 0
     short_iter: int = 10
     select: int = BPSF_SELECT_MIN_WEIGHT
+    layered: bool = False
 
     def c(self) -> bpsf_params:
-        return bpsf_params(self.max_iter, self.alpha, self.w, self.w_max, self.short_iter, self.select, 0)
+        return bpsf_params(self.max_iter, self.alpha, self.w, self.w_max, self.short_iter, self.select,
+                           BPSF_FLAG_LAYERED if self.layered else 0)
 
 
 def _stream_handle(stream):

@@ -86,10 +86,10 @@ bpsf_status bpsf_ensure_kernel_attrs(int variant, int smem_optin) {
     static std::mutex mu;
     static bool done[64] = {false};
     std::lock_guard<std::mutex> lk(mu);
-    for (int dbg = 0; dbg < 2; ++dbg) {
-        const int k = variant * 2 + dbg;
+    for (int k4 = 0; k4 < 4; ++k4) {  // debug x layered instances
+        const int k = variant * 4 + k4;
         if (done[k]) continue;
-        cudaError_t e = cudaFuncSetAttribute(persistent_kernel_ptr(variant, dbg != 0),
+        cudaError_t e = cudaFuncSetAttribute(persistent_kernel_ptr(variant, (k4 & 1) != 0, (k4 & 2) != 0),
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin);
         if (e != cudaSuccess) return bpsf_fail(BPSF_ECUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(e));
         done[k] = true;
@@ -106,7 +106,7 @@ bpsf_status bpsf_ensure_kernel_attrs(int variant, int smem_optin) {
 static int plan_queue(int teams, int S) { return std::min(32, std::max(16, teams * S / 2)); }
 
 static int plan_smem(const bpsf_ctx *c, int vstride, int S, int teams, int Q) {
-    return block_smem_bytes(c->M, c->N, c->P, c->Ws, vstride, S, teams, Q);
+    return block_smem_bytes(c->M, c->N, c->P, c->Ws, vstride, S, teams, Q, c->code.layered);
 }
 
 static bpsf_status check_shape(const bpsf_tuning &t) {
@@ -124,8 +124,9 @@ static bpsf_status check_shape(const bpsf_tuning &t) {
 bpsf_status bpsf_make_plan(bpsf_ctx *const *codes, int n_codes, const bpsf_tuning *tunes, bool debug,
                            bpsf_plan *out, bool shrink) {
     // One kernel variant must fit every code of the launch.
-    bool all_regular = true;
+    bool all_regular = true, layered = false;
     int dc = 0, dv = 0, B = 0, bps = 0;
+    for (int k = 0; k < n_codes; ++k) layered = layered || codes[k]->code.layered;
     for (int k = 0; k < n_codes; ++k) {
         bpsf_status st = check_shape(tunes[k]);
         if (st != BPSF_OK) return st;
@@ -174,7 +175,8 @@ bpsf_status bpsf_make_plan(bpsf_ctx *const *codes, int n_codes, const bpsf_tunin
     if (st != BPSF_OK) return st;
     const int block = 32 * (B + 1);
     int occ = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, persistent_kernel_ptr(variant, debug), block, smem);
+    cudaError_t e =
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, persistent_kernel_ptr(variant, debug, layered), block, smem);
     if (e != cudaSuccess) return bpsf_fail(BPSF_ECUDA, "occupancy query: %s", cudaGetErrorString(e));
     if (bps > 0) occ = std::min(occ, bps);
     // Fewer than two blocks per SM: the variant's full-register instance runs the
@@ -184,7 +186,7 @@ bpsf_status bpsf_make_plan(bpsf_ctx *const *codes, int n_codes, const bpsf_tunin
         st = bpsf_ensure_kernel_attrs(full, c0->smem_optin);
         if (st != BPSF_OK) return st;
         int occ1 = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ1, persistent_kernel_ptr(full, debug), block, smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ1, persistent_kernel_ptr(full, debug, layered), block, smem);
         if (e != cudaSuccess) return bpsf_fail(BPSF_ECUDA, "occupancy query: %s", cudaGetErrorString(e));
         if (occ1 >= 1) {
             variant = full;
@@ -193,6 +195,7 @@ bpsf_status bpsf_make_plan(bpsf_ctx *const *codes, int n_codes, const bpsf_tunin
     }
     if (occ <= 0) return bpsf_fail(BPSF_EINVAL, "launch shape does not fit on an SM");
     out->variant = variant;
+    out->layered = layered;
     out->Q = Q;
     out->block = block;
     out->smem = smem;
@@ -259,7 +262,7 @@ extern "C" bpsf_status bpsf_create(bpsf_ctx **out, int32_t M, int32_t N, int64_t
     if (nnz < 1 || nnz > 65535) return bpsf_fail(BPSF_EINVAL, "nnz must be in 1..65535");
     if (layout != BPSF_CSR && layout != BPSF_CSC) return bpsf_fail(BPSF_EINVAL, "layout must be BPSF_CSR or BPSF_CSC");
     const bpsf_params p = *params;
-    if (p.flags != 0) return bpsf_fail(BPSF_EINVAL, "params.flags must be 0");
+    if (p.flags & ~(uint32_t)BPSF_FLAG_LAYERED) return bpsf_fail(BPSF_EINVAL, "params.flags: unknown bits");
     if (p.max_iter < 1 || p.max_iter > 32767) return bpsf_fail(BPSF_EINVAL, "max_iter must be in 1..32767");
     if (!(p.alpha >= 0.f) || !std::isfinite(p.alpha))
         return bpsf_fail(BPSF_EINVAL, "alpha must be finite and > 0, or 0 for adaptive damping");
@@ -370,13 +373,42 @@ extern "C" bpsf_status bpsf_create(bpsf_ctx **out, int32_t M, int32_t N, int64_t
     c->sm_count = prop.multiProcessorCount;
     c->smem_optin = (int)prop.sharedMemPerBlockOptin;
 
+    // Layered schedule: rows coloured greedily in ascending order, each taking the
+    // smallest layer not used by an earlier row that shares a variable with it.
+    std::vector<uint16_t> layer_ptr(1, 0), layer_rows;
+    int n_layers = 0;
+    if (p.flags & BPSF_FLAG_LAYERED) {
+        std::vector<int> layer(M, 0);
+        std::vector<char> used;
+        for (int j = 0; j < M; ++j) {
+            used.assign(M + 1, 0);
+            for (int v : rows[j])
+                for (const auto &ck : cols[v])
+                    if (ck.first < j) used[layer[ck.first]] = 1;
+            int l = 0;
+            while (used[l]) ++l;
+            layer[j] = l;
+            n_layers = std::max(n_layers, l + 1);
+        }
+        layer_ptr.assign(n_layers + 1, 0);
+        for (int j = 0; j < M; ++j) ++layer_ptr[layer[j] + 1];
+        for (int l = 0; l < n_layers; ++l) layer_ptr[l + 1] = (uint16_t)(layer_ptr[l + 1] + layer_ptr[l]);
+        layer_rows.assign(M, 0);
+        std::vector<int> fill(layer_ptr.begin(), layer_ptr.end() - 1);
+        for (int j = 0; j < M; ++j) layer_rows[fill[layer[j]]++] = (uint16_t)j;
+    } else {
+        layer_rows.assign(1, 0);
+    }
+
     // One allocation for all code arrays.
-    const void *srcs[8] = {row_deg.data(), vpos.data(), vchk.data(), lch.data(),
-                           lch_pos.data(), row_ptr.data(), csr_col.data(), masks.data()};
-    const size_t sizes[8] = {(size_t)M, 2 * vpos.size(), 2 * vchk.size(), 4 * (size_t)N,
-                             4 * (size_t)P, 2 * (size_t)(M + 1), 2 * (size_t)nnz, 8 * masks.size()};
-    size_t off[8], sz = 0;
-    for (int k = 0; k < 8; ++k) {
+    const void *srcs[10] = {row_deg.data(), vpos.data(), vchk.data(), lch.data(),
+                            lch_pos.data(), row_ptr.data(), csr_col.data(), masks.data(),
+                            layer_ptr.data(), layer_rows.data()};
+    const size_t sizes[10] = {(size_t)M, 2 * vpos.size(), 2 * vchk.size(), 4 * (size_t)N,
+                              4 * (size_t)P, 2 * (size_t)(M + 1), 2 * (size_t)nnz, 8 * masks.size(),
+                              2 * layer_ptr.size(), 2 * layer_rows.size()};
+    size_t off[10], sz = 0;
+    for (int k = 0; k < 10; ++k) {
         off[k] = sz;
         sz += align16(sizes[k]);
     }
@@ -386,7 +418,7 @@ extern "C" bpsf_status bpsf_create(bpsf_ctx **out, int32_t M, int32_t N, int64_t
         return bpsf_fail(BPSF_ENOMEM, "cudaMalloc(code): %s", cudaGetErrorString(e));
     }
     std::vector<unsigned char> hbuf(sz, 0);
-    for (int k = 0; k < 8; ++k) std::memcpy(hbuf.data() + off[k], srcs[k], sizes[k]);
+    for (int k = 0; k < 10; ++k) std::memcpy(hbuf.data() + off[k], srcs[k], sizes[k]);
     e = cudaMemcpy(c->d_code, hbuf.data(), sz, cudaMemcpyHostToDevice);
     unsigned char *base = (unsigned char *)c->d_code;
     CodeDev &cd = c->code;
@@ -415,6 +447,10 @@ extern "C" bpsf_status bpsf_create(bpsf_ctx **out, int32_t M, int32_t N, int64_t
     cd.csr_col = (const uint16_t *)(base + off[6]);
     cd.trial_mask = (const unsigned long long *)(base + off[7]);
     c->default_masks = cd.trial_mask;
+    cd.layered = (p.flags & BPSF_FLAG_LAYERED) ? 1 : 0;
+    cd.n_layers = n_layers;
+    cd.layer_ptr = (const uint16_t *)(base + off[8]);
+    cd.layer_rows = (const uint16_t *)(base + off[9]);
     c->default_n_trials = c->n_trials;
     if (e == cudaSuccess) e = cudaMalloc((void **)&c->d_ctr, sizeof(StreamCounters));
     if (e == cudaSuccess) e = cudaMemset(c->d_ctr, 0, sizeof(StreamCounters));
@@ -499,7 +535,7 @@ void bpsf_launch_plan(const bpsf_plan &pl, bool debug, StreamDev *sds, int n, in
         sds[k].teams = pl.teams_code[k];
     }
     LaunchArgs la{sds, n, pl.Q, kBpsfWaitNs};
-    launch_persistent(pl.variant, debug, grid, pl.block, pl.smem, la, stream);
+    launch_persistent(pl.variant, debug, pl.layered, grid, pl.block, pl.smem, la, stream);
 }
 
 static bpsf_status check_io(const bpsf_ctx *c, int64_t n, const void *synd, int32_t ss, const void *corr, int32_t cs,
@@ -924,7 +960,7 @@ extern "C" bpsf_status bpsf_selftest_wait(bpsf_ctx *c, int64_t wait_us, void *st
     sd.W = pl.W_code[0];
     sd.teams = pl.teams_code[0];
     LaunchArgs la{&sd, 1, pl.Q, (unsigned long long)wait_us * 1000ull};
-    launch_persistent(pl.variant, false, 1, pl.block, pl.smem, la, stream);
+    launch_persistent(pl.variant, false, pl.layered, 1, pl.block, pl.smem, la, stream);
     e = cudaGetLastError();
     if (e != cudaSuccess) return bpsf_fail(BPSF_ECUDA, "kernel launch: %s", cudaGetErrorString(e));
     c->d_ctr_last = c->d_ctr;

@@ -36,6 +36,7 @@ struct bpsf_ctx {
 // Launch plan of the persistent kernel for one or several codes.
 struct bpsf_plan {
     int variant = 0, Q = 0, block = 0, smem = 0, grid = 0;
+    bool layered = false;  // some code of the launch uses the layered schedule
     int S_code[bpsf::kMaxStreams] = {0};      // slots per team, per code of the launch
     int W_code[bpsf::kMaxStreams] = {0};      // warps per team, per code
     int teams_code[bpsf::kMaxStreams] = {0};  // teams per block, per code

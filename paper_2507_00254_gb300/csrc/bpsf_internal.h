@@ -48,6 +48,10 @@ struct CodeDev {
     const uint16_t *row_ptr;     // M+1, CSR (syndrome kernel)
     const uint16_t *csr_col;     // nnz
     const unsigned long long *trial_mask;  // n_trials subset masks over Phi (bit j selects Phi[j]), list order
+    int layered;                 // 1: layered schedule
+    int n_layers;
+    const uint16_t *layer_ptr;   // n_layers+1, rows of layer l are layer_rows[layer_ptr[l] .. layer_ptr[l+1])
+    const uint16_t *layer_rows;  // M, rows grouped by layer, ascending within a layer
 };
 
 // Per-launch counters of one stream (64 bytes, zeroed before a launch).
@@ -233,11 +237,13 @@ __host__ __device__ inline int qentry_bytes(int Ws) { return align_up(48 + 4 * W
 //   inbox     : S work items (qentry_bytes(Ws) each), filled by the manager
 //               ahead of time and installed by the team as soon as the slot
 //               is free, so a slot does not wait for the manager between runs
+//   post      : layered schedule only: float i*S + s = running posterior L_i
+//               of slot s (the message array then holds the C2V messages)
 struct TeamOffsets {
-    int ctl, state, syn, mism, ebits, flips, m, outbox, inflag, inbox, ibstride, total;
+    int ctl, state, syn, mism, ebits, flips, m, outbox, inflag, inbox, ibstride, post, total;
 };
 
-__host__ __device__ inline TeamOffsets team_offsets(int S, int M, int N, int P, int Ws) {
+__host__ __device__ inline TeamOffsets team_offsets(int S, int M, int N, int P, int Ws, int layered) {
     TeamOffsets o;
     const int sw = (S * M + 31) / 32;
     int p = 0;
@@ -252,21 +258,23 @@ __host__ __device__ inline TeamOffsets team_offsets(int S, int M, int N, int P, 
     o.inbox = p;   p += o.ibstride * S;
     o.flips = p;   p = align_up(p + 2 * S * N, 16);
     o.m = p;       p += 4 * S * P;
+    o.post = p;    p += layered ? 4 * S * N : 0;
     o.total = align_up(p, 16);
     return o;
 }
 
-__host__ __device__ inline int block_smem_bytes(int M, int N, int P, int Ws, int vstride, int S, int teams, int Q) {
+__host__ __device__ inline int block_smem_bytes(int M, int N, int P, int Ws, int vstride, int S, int teams, int Q,
+                                                int layered) {
     return kBlockHeaderBytes + layout_offsets(M, N, vstride, P).total + Q * qentry_bytes(Ws) +
-           teams * team_offsets(S, M, N, P, Ws).total;
+           teams * team_offsets(S, M, N, P, Ws, layered).total;
 }
 
 // Kernel entry points (bpsf_kernels.cu).
 int kernel_variant(int dc_max, int dv_max);  // smallest variant that fits, -1 if none
 int kernel_variant_dv(int variant);          // column table width of a variant
 int kernel_variant_full_regs(int variant);   // its one-block, full-register instance
-const void *persistent_kernel_ptr(int variant, bool debug);
-void launch_persistent(int variant, bool debug, int grid, int block, int smem, const LaunchArgs &args,
+const void *persistent_kernel_ptr(int variant, bool debug, bool layered);
+void launch_persistent(int variant, bool debug, bool layered, int grid, int block, int smem, const LaunchArgs &args,
                        void *stream);
 void launch_syndrome(const CodeDev &cd, long long n, const uint32_t *err, int err_stride, uint32_t *synd,
                      int synd_stride, void *stream);

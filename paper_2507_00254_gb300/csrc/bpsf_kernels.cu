@@ -104,6 +104,7 @@ struct TeamMem {
     int *ibf;           // per slot: 1 while the inbox holds an item
     unsigned char *ib;  // per slot: the next work item
     int ibstride;
+    float *post;        // layered schedule: running posterior per (variable, slot)
 };
 
 __device__ __forceinline__ TeamMem team_mem(unsigned char *tb, const TeamOffsets &to) {
@@ -119,6 +120,7 @@ __device__ __forceinline__ TeamMem team_mem(unsigned char *tb, const TeamOffsets
     T.ibf = reinterpret_cast<int *>(tb + to.inflag);
     T.ib = tb + to.inbox;
     T.ibstride = to.ibstride;
+    T.post = reinterpret_cast<float *>(tb + to.post);
     return T;
 }
 
@@ -532,6 +534,93 @@ __device__ __forceinline__ void v_phase_vec(const StreamDev &sd, const LayoutMem
     }
 }
 
+// ---------------------------------------------------------------------------
+// Layered schedule (one slot per lane).  Layer by layer (rows of a layer
+// share no variable, so they run in parallel and in any order), each row j
+// of slot s: q_k = L_i - r_k for its edges k (i = the k-th variable of the
+// row, r_k its C2V message from the previous iteration), new C2V messages
+// from the q_k by Eq. (c2v) as in the C phase, then L_i = q_k + r_k.  After
+// all layers L is the posterior: hard decision, flip counters and residual
+// syndrome as in the V phase.
+// ---------------------------------------------------------------------------
+template <int DC>
+__device__ __forceinline__ void layered_row(const CodeDev &cd, const LayoutMem &L, const TeamMem &T, int lgS, int j,
+                                            int s, float alpha) {
+    const int S = 1 << lgS, M = cd.M;
+    const int deg = (int)L.row_deg[j];
+    const int base = (int)__ldg(cd.row_ptr + j);
+    float q[DC];
+    int vi[DC];
+    float *mj = T.m + (j << lgS) + s;  // edge k of row j at ((k*M + j)*S + s)
+#pragma unroll
+    for (int k = 0; k < DC; ++k) {
+        if (k < deg) {
+            vi[k] = (int)__ldg(cd.csr_col + base + k);
+            q[k] = __fsub_rn(T.post[(vi[k] << lgS) + s], mj[k * M * S]);
+        }
+    }
+    float m1 = __int_as_float(0x7f800000), m2 = m1;
+    unsigned sx = ((T.syn[((j << lgS) + s) >> 5] >> (((j << lgS) + s) & 31)) & 1u) << 31;
+#pragma unroll
+    for (int k = 0; k < DC; ++k) {
+        if (k < deg) {
+            const float a = fabsf(q[k]);
+            m2 = fminf(m2, fmaxf(m1, a));
+            m1 = fminf(m1, a);
+            sx ^= __float_as_uint(q[k]);
+        }
+    }
+    sx &= 0x80000000u;
+    const unsigned g1 = __float_as_uint(fminf(__fmul_rn(alpha, m1), kMagClamp)) | sx;
+    const unsigned g2 = __float_as_uint(fminf(__fmul_rn(alpha, m2), kMagClamp)) | sx;
+#pragma unroll
+    for (int k = 0; k < DC; ++k) {
+        if (k < deg) {
+            const float r = __uint_as_float(((fabsf(q[k]) == m1) ? g2 : g1) ^ (__float_as_uint(q[k]) & 0x80000000u));
+            mj[k * M * S] = r;
+            T.post[(vi[k] << lgS) + s] = __fadd_rn(q[k], r);
+        }
+    }
+}
+
+template <int DC, int DVS, int DVX, bool DEBUG>
+__device__ __forceinline__ void layered_iteration(const StreamDev &sd, const LayoutMem &L, const TeamMem &T, int lgS,
+                                                  bool lane_on, float alpha, unsigned initm, int tid, int nthreads,
+                                                  int W, int bar_id) {
+    const CodeDev &cd = sd.code;
+    const int S = 1 << lgS;
+    const int s = tid & (S - 1);
+    for (int layer = 0; layer < cd.n_layers; ++layer) {
+        const int r0 = (int)__ldg(cd.layer_ptr + layer), r1 = (int)__ldg(cd.layer_ptr + layer + 1);
+        const int total = (r1 - r0) << lgS;
+        if (lane_on)
+            for (int tau = tid; tau < total; tau += nthreads)
+                layered_row<DC>(cd, L, T, lgS, (int)__ldg(cd.layer_rows + r0 + (tau >> lgS)), s, alpha);
+        team_sync(W, bar_id);
+    }
+    if (!lane_on) return;
+    const int N = cd.N;
+    for (int tau = tid; tau < (N << lgS); tau += nthreads) {
+        const int i = tau >> lgS;
+        const float lo = T.post[tau];
+        const unsigned ebit = (lo <= 0.f) ? 1u : 0u;
+        if (DEBUG && ((initm >> s) & 1u) && sd.dbg.lout) sd.dbg.lout[T.st[s].shot * N + i] = lo;
+        const unsigned f = (unsigned)T.flips[tau];
+        if ((f >> 15) != ebit) {
+            T.flips[tau] = (uint16_t)((f ^ 0x8000u) + 1u);
+            const uint16_t *vc = cd.vchk + i * DVS;
+#pragma unroll
+            for (int k = 0; k < DVS; ++k) {
+                const int c = (int)__ldg(vc + k);
+                if (DVX > 0 ? (k < DVX) : (c != 0xffff)) {
+                    const int b = (c << lgS) + s;
+                    atomicXor(&T.mism[b >> 5], 1u << (b & 31));
+                }
+            }
+        }
+    }
+}
+
 // Bits b of a 32-bit word with b = s (mod S): the residual-syndrome bits
 // of slot s when shifted left by s (S is a power of two dividing 32).
 __device__ __forceinline__ unsigned slot_pattern(int S) {
@@ -625,7 +714,13 @@ __device__ __forceinline__ void team_install(const StreamDev &sd, const LayoutMe
         if (((vsyn[b >> 5] & m) != 0u) != (want != 0u)) atomicXor(&T.syn[b >> 5], m);
         if (((vmism[b >> 5] & m) != 0u) != (want != 0u)) atomicXor(&T.mism[b >> 5], m);
     }
-    for (int k = lane; k < cd.P; k += 32) T.m[k * S + s] = L.lch_pos[k];
+    if (cd.layered) {
+        // Layered schedule: C2V messages start at zero, the posterior at l_ch.
+        for (int k = lane; k < cd.P; k += 32) T.m[k * S + s] = 0.f;
+        for (int i = lane; i < cd.N; i += 32) T.post[i * S + s] = L.lch[i];
+    } else {
+        for (int k = lane; k < cd.P; k += 32) T.m[k * S + s] = L.lch_pos[k];
+    }
     for (int i = lane; i < cd.N; i += 32) T.flips[i * S + s] = 0;
     if (lane == 0) {
         ss->kind = e->kind;
@@ -683,7 +778,7 @@ __device__ __forceinline__ void team_service(const StreamDev &sd, const LayoutMe
 // ---------------------------------------------------------------------------
 // Compute team loop.
 // ---------------------------------------------------------------------------
-template <int DC, int DVS, int DVX, bool DEBUG, int MINB>
+template <int DC, int DVS, int DVX, bool DEBUG, int MINB, bool LAY>
 __device__ void team_loop(const StreamDev &sd, const LayoutMem &L, const TeamMem &T, BlockHdr *hdr, int S, int W,
                           int tid, int bar_id, unsigned long long wait_ns) {
     const int lane = tid & 31, wt = tid >> 5, nthreads = 32 * W;
@@ -740,7 +835,12 @@ __device__ void team_loop(const StreamDev &sd, const LayoutMem &L, const TeamMem
         team_sync(W, bar_id);
         if (ex) break;
         if (run == 0u) continue;
-        if (kVec4 && S >= 4) {
+        if (LAY && cd.layered) {
+            const bool lane_on = (run >> my_slot) & 1u;
+            layered_iteration<DC, DVS, DVX, DEBUG>(sd, L, T, lgS, lane_on, damping(cd, T.st[my_slot].iter + 1), initm,
+                                                   tid, nthreads, W, bar_id);
+            team_sync(W, bar_id);
+        } else if (kVec4 && S >= 4) {
             const int s0 = 4 * (lane & ((S >> 2) - 1));
             const unsigned onm = (run >> s0) & 0xfu;
             float al[4];
@@ -1267,7 +1367,9 @@ struct KernelParams {
 #define BPSF_MIN_BLOCKS 2
 #endif
 
-template <int DC, int DVS, int DVX, bool DEBUG, int MINB>
+// LAY: the instance also runs codes with the layered schedule (a launch
+// with no such code uses the instance without that path and its registers).
+template <int DC, int DVS, int DVX, bool DEBUG, int MINB, bool LAY>
 __global__ void __launch_bounds__(512, MINB) bpsf_persistent(const __grid_constant__ KernelParams kp) {
     extern __shared__ __align__(16) unsigned char smem[];
     BlockHdr *hdr = reinterpret_cast<BlockHdr *>(smem);
@@ -1363,7 +1465,7 @@ __global__ void __launch_bounds__(512, MINB) bpsf_persistent(const __grid_consta
             cur = sid;
         }
         // Every slot starts empty; teams start idle.
-        const TeamOffsets to = team_offsets(S, cd.M, cd.N, cd.P, cd.Ws);
+        const TeamOffsets to = team_offsets(S, cd.M, cd.N, cd.P, cd.Ws, cd.layered);
         unsigned char *qbase = lay + lo.total;
         unsigned char *team_base = qbase + Q * qentry_bytes(cd.Ws);
         for (int k = tid; k < teams * S; k += blockDim.x) {
@@ -1407,7 +1509,7 @@ __global__ void __launch_bounds__(512, MINB) bpsf_persistent(const __grid_consta
             const int team = (warp - 1) / W;
             if (team < teams) {
                 TeamMem T = team_mem(team_base + team * to.total, to);
-                team_loop<DC, DVS, DVX, DEBUG, MINB>(sd, L, T, hdr, S, W, tid - 32 - team * W * 32, 1 + team, kp.wait_ns);
+                team_loop<DC, DVS, DVX, DEBUG, MINB, LAY>(sd, L, T, hdr, S, W, tid - 32 - team * W * 32, 1 + team, kp.wait_ns);
             }
         }
         __syncthreads();
@@ -1445,39 +1547,39 @@ int kernel_variant(int dc_max, int dv_max) {
 
 typedef void (*KernelFn)(KernelParams);
 
-static KernelFn kernel_fn(int variant, bool debug) {
-    switch (variant * 2 + (debug ? 1 : 0)) {
-        case 0: return bpsf_persistent<6, 4, 3, false, BPSF_MIN_BLOCKS>;
-        case 1: return bpsf_persistent<6, 4, 3, true, BPSF_MIN_BLOCKS>;
-        case 2: return bpsf_persistent<6, 4, 0, false, 1>;
-        case 3: return bpsf_persistent<6, 4, 0, true, 1>;
-        case 4: return bpsf_persistent<8, 4, 0, false, 1>;
-        case 5: return bpsf_persistent<8, 4, 0, true, 1>;
-        case 6: return bpsf_persistent<16, 8, 0, false, 1>;
-        case 7: return bpsf_persistent<16, 8, 0, true, 1>;
-        case 8: return bpsf_persistent<32, 16, 0, false, 1>;
-        case 9: return bpsf_persistent<32, 16, 0, true, 1>;
-        case 10: return bpsf_persistent<6, 4, 3, false, 1>;
-        default: return bpsf_persistent<6, 4, 3, true, 1>;
+#define BPSF_KERNELS_OF(DC, DVS, DVX, MINB)                                                     \
+    (debug ? (lay ? bpsf_persistent<DC, DVS, DVX, true, MINB, true> : bpsf_persistent<DC, DVS, DVX, true, MINB, false>) \
+           : (lay ? bpsf_persistent<DC, DVS, DVX, false, MINB, true> : bpsf_persistent<DC, DVS, DVX, false, MINB, false>))
+
+static KernelFn kernel_fn(int variant, bool debug, bool lay) {
+    switch (variant) {
+        case 0: return BPSF_KERNELS_OF(6, 4, 3, BPSF_MIN_BLOCKS);
+        case 1: return BPSF_KERNELS_OF(6, 4, 0, 1);
+        case 2: return BPSF_KERNELS_OF(8, 4, 0, 1);
+        case 3: return BPSF_KERNELS_OF(16, 8, 0, 1);
+        case 4: return BPSF_KERNELS_OF(32, 16, 0, 1);
+        default: return BPSF_KERNELS_OF(6, 4, 3, 1);
     }
 }
+#undef BPSF_KERNELS_OF
 
 int kernel_variant_dv(int variant) { return kVariants[variant].dvs; }
 
 // The full-register instance of a variant (itself when it has only one).
 int kernel_variant_full_regs(int variant) { return variant == 0 ? 5 : variant; }
 
-const void *persistent_kernel_ptr(int variant, bool debug) {
-    return reinterpret_cast<const void *>(kernel_fn(variant, debug));
+const void *persistent_kernel_ptr(int variant, bool debug, bool layered) {
+    return reinterpret_cast<const void *>(kernel_fn(variant, debug, layered));
 }
 
-void launch_persistent(int variant, bool debug, int grid, int block, int smem, const LaunchArgs &args, void *stream) {
+void launch_persistent(int variant, bool debug, bool layered, int grid, int block, int smem, const LaunchArgs &args,
+                       void *stream) {
     KernelParams kp;
     for (int k = 0; k < args.n_streams; ++k) kp.streams[k] = args.streams[k];
     kp.n_streams = args.n_streams;
     kp.Q = args.Q;
     kp.wait_ns = args.wait_ns;
-    kernel_fn(variant, debug)<<<grid, block, smem, (cudaStream_t)stream>>>(kp);
+    kernel_fn(variant, debug, layered)<<<grid, block, smem, (cudaStream_t)stream>>>(kp);
 }
 
 // ---------------------------------------------------------------------------

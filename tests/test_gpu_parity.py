@@ -79,7 +79,7 @@ def decoder(name, p, params):
 
 
 def oparams(P):
-    return OParams(P.max_iter, P.alpha, P.w, P.w_max, P.short_iter, P.select)
+    return OParams(P.max_iter, P.alpha, P.w, P.w_max, P.short_iter, P.select, layered=P.layered)
 
 
 def gpu_decode(dec, s_bits, **kw):
@@ -243,6 +243,37 @@ def test_mixed_codes_one_launch_match_oracle():
         eg = unpack(o["corr"].cpu().numpy(), oc.N)
         assert (eg == eo).all(axis=1).mean() >= CORR_MATCH
         assert (o["stage"].cpu().numpy() == so).mean() >= CORR_MATCH
+
+
+# --------------------------------------------------------------------------
+# Layered schedule (the paper's variant for [[288]])
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("name,p,n,alpha", [("bb144", 0.06, 2000, 0.625), ("bb288", 0.06, 1500, 0.0),
+                                            ("bb144_phenom", 0.006, 800, 0.625)])
+def test_layered_schedule_matches_oracle(name, p, n, alpha):
+    P = B.Params(max_iter=100, alpha=alpha, w=6, short_iter=20, layered=True)
+    oc, e, s = make_inputs(name, p, n, 7301)
+    dec = decoder(name, p, P)
+    g, (eo, co, io, so) = compare(oc, dec, s, p, P)
+    assert (g["stage"] != 0).sum() > 0
+
+
+def test_layered_and_flooding_codes_in_one_launch():
+    Pl = B.Params(max_iter=100, alpha=0.625, w=6, short_iter=20, layered=True)
+    Pf = B.Params(max_iter=100, alpha=0.625, w=6, short_iter=20)
+    decs, synds, cases = [], [], []
+    for k, (name, P) in enumerate((("bb144", Pl), ("bb72", Pf), ("bb288", Pl))):
+        oc, e, s = make_inputs(name, 0.05, 500 + 100 * k, 7400 + k)
+        decs.append(decoder(name, 0.05, P))
+        synds.append(dev(pack(s)))
+        cases.append((oc, s, P))
+    outs = B.decode_multi(decs, synds)
+    for (oc, s, P), o in zip(cases, outs):
+        eo, co, io, so = oc.bpsf_batch(s, 0.05, oparams(P), threads=THREADS)
+        eg = unpack(o["corr"].cpu().numpy(), oc.N)
+        assert (eg == eo).all(axis=1).mean() >= CORR_MATCH
+        assert (o["iters"].cpu().numpy() == io).mean() >= CORR_MATCH
 
 
 # --------------------------------------------------------------------------
