@@ -327,6 +327,7 @@ def run_gpu(args, rank, world, pool):
         extras["code_capacity_paper_setting"] = run_families(B, codes, torch, harness)
         extras["sampled_trials_complexity"] = run_sampled(B, codes, torch, harness)
         extras["first_success_early_cancel"] = run_first_success(B, codes, torch)
+        extras["layered_schedule_bb288"] = run_layered(B, codes, torch, harness)
         extras["served"] = run_served(B, codes, torch, (1e4, 1e5, 1e6, 3.16e6, 1e7), seconds=args.serve_seconds,
                                       tuning=args.serve_tuning)
 
@@ -536,6 +537,43 @@ def run_first_success(B, codes, torch, n=200_000, n_plain=300, p=0.07):
                       "plain_failed_shot_ms": {"n": int(lat.size), "p50": float(np.percentile(lat, 50)),
                                                "p99": float(np.percentile(lat, 99))}}
         d.close()
+    return out
+
+
+def run_layered(B, codes, torch, harness, n=100_000, p_list=(0.05, 0.07)):
+    """Flooding vs layered schedule on [[288,12,18]] under the paper's code-capacity setting
+    for that code (|Phi| = 20, weight-1 trials, 50 iterations per run, adaptive damping):
+    shots/s, LER and BP iterations per shot."""
+    import synth
+    c = codes.bb("bb288")
+    hx, hz = c.dense(), codes.bb("bb288", 1).dense()
+    lx = harness.x_logicals(hx, hz)
+    G = torch.from_numpy(np.vstack([hx, lx]).astype(np.float32)).cuda()
+    out = {}
+    for j, p in enumerate(p_list):
+        e = synth.bernoulli_bits(7500, j, 0, n, c.N, p)
+        res = {}
+        for label, lay in (("flooding", False), ("layered", True)):
+            d = B.Decoder(c.ptr, c.idx, c.M, c.N, np.full(c.N, p),
+                          B.Params(max_iter=50, alpha=0.0, w=20, w_max=1, short_iter=50, layered=lay))
+            synd = d.syndrome(_packed_errors_dev(torch, e, d.Wn))
+            o = d.outputs(n)
+            d.decode(synd, out=o)  # warm-up
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            d.decode(synd, out=o)
+            dt = time.perf_counter() - t0
+            wk = d.last_work()
+            corr = torch.from_numpy(harness.unpack_rows(o["corr"].cpu().numpy().view(np.uint32), c.N)).cuda()
+            r = (torch.from_numpy(e).cuda() ^ corr).float()
+            f = (torch.remainder(r @ G.T, 2.0) > 0.5).any(dim=1) | (o["conv"] == 0)
+            L = float(f.float().mean().item())
+            res[label] = {"shots_per_s": n / dt, "ler": L, "sigma": (L * (1 - L) / n) ** 0.5,
+                          "bp_iterations_per_shot": wk["iterations"] / n,
+                          "stage_counts": np.bincount(o["stage"].cpu().numpy(), minlength=3).tolist(),
+                          "tuning": list(d.tuning)}
+            d.close()
+        out[str(p)] = res
     return out
 
 
