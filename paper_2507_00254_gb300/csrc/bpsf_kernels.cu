@@ -16,22 +16,32 @@
 //             bumps the counter and toggles the slot's residual syndrome
 //             s xor H e at the column's checks by shared atomics;
 //   decide  : a slot whose residual syndrome is zero has converged, a slot at
-//             its iteration cap is exhausted; either has its decision packed
-//             into words and is handed to the manager.
+//             its iteration cap is exhausted (a trial the manager found
+//             unable to win under the first-success rule is stopped); the
+//             slot then waits for its team's service step.
 // Each message is read and written by exactly one thread in each phase, so
 // one array of P floats per slot holds V2C and C2V messages alternately.
 // The S slots of a team are interleaved item by item (S is a power of two):
-// lane l serves slot l mod S in both phases, task tau = j*S + s (row j) or
-// i*S + s (column i) addresses its data directly, and a warp's 32 lanes
-// touch consecutive words.  Installing a slot sets its messages to the
-// channel LLRs, so the phases have no first-iteration special case.
+// task tau = j*S + s (row j) or i*S + s (column i) addresses its data
+// directly and a warp's lanes touch consecutive words.  A lane serves one
+// slot, or 2 or 4 adjacent slots with 64- or 128-bit accesses (vector
+// phases).  Installing a slot sets its messages to the channel LLRs, so the
+// phases have no first-iteration special case.  With the layered schedule
+// the C and V phases are replaced by layer-by-layer row updates against a
+// running posterior (one slot per lane).
 //
-// The manager warp does everything that touches global memory: it writes
-// finished slots out, runs top(flip_count, w) for failed initial runs and
-// publishes their trials, resolves the winner of each failed shot (minimum
-// over converged trials of (weight, index), held in a per-shot atomicMin),
-// claims new shots and trial tickets ahead of time into a small ready queue
-// and refills empty slots from it.  Compute warps never wait on HBM.
+// Service (the team's warp 0, at the top of each iteration): a finished
+// slot packs its decision into words, its run's facts into its outbox and,
+// for a failed initial run, Phi = top(flip_count, w) into the shot's record;
+// then it installs the item the manager staged in its inbox and runs again
+// at once.
+//
+// The manager warp does the rest of the global-memory work: it writes the
+// outboxes out, publishes failed shots' trials, resolves the winner of each
+// failed shot (minimum over converged trials of (weight, index), held in a
+// per-shot atomicMin), claims new shots and trial tickets ahead of time into
+// a small ready queue and fills the inboxes from it.  Compute warps never
+// wait on HBM.
 #include <cuda_runtime.h>
 
 #include <cstdint>

@@ -105,6 +105,12 @@ def test_create_rejects_bad_arguments_before_device_work():
         with pytest.raises(B.BpsfError) as ei:
             _create(c.M, c.N, c.ptr, c.idx, priors, **kw)
         assert ei.value.status == B.BPSF_EINVAL and msg in str(ei.value), (over, str(ei.value))
+    # Only the layered-schedule bit of params.flags is defined.
+    p = B.Params(**good).c()
+    p.flags = 2
+    with pytest.raises(B.BpsfError) as ei:
+        B.bpsf_create(c.M, c.N, B.BPSF_CSR, c.ptr, c.idx, 0.05, p)
+    assert ei.value.status == B.BPSF_EINVAL and "flags" in str(ei.value)
 
 
 def test_create_rejects_bad_graphs():
