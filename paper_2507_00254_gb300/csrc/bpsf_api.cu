@@ -73,6 +73,7 @@ extern "C" void bpsf_destroy(bpsf_ctx *c) {
     free_workspace(c);
     if (c->d_code) cudaFree(c->d_code);
     if (c->d_trials) cudaFree(c->d_trials);
+    if (c->d_layouts) cudaFree(c->d_layouts);
     if (c->d_ctr) cudaFree(c->d_ctr);
     if (c->h_ctr) cudaFreeHost(c->h_ctr);
     if (c->h_flag) cudaFreeHost(c->h_flag);
@@ -106,7 +107,7 @@ bpsf_status bpsf_ensure_kernel_attrs(int variant, int smem_optin) {
 static int plan_queue(int teams, int S) { return std::min(32, std::max(16, teams * S / 2)); }
 
 static int plan_smem(const bpsf_ctx *c, int vstride, int S, int teams, int Q) {
-    return block_smem_bytes(c->M, c->N, c->P, c->Ws, vstride, S, teams, Q, c->code.layered);
+    return block_smem_bytes(c->M, c->N, c->code.lay[layout_index(S)].P, c->Ws, vstride, S, teams, Q, c->code.layered);
 }
 
 static bpsf_status check_shape(const bpsf_tuning &t) {
@@ -252,6 +253,99 @@ static std::vector<unsigned long long> default_trials(int w, int w_max) {
     return out;
 }
 
+// ---------------------------------------------------------------------------
+// Message layout per slot count (see LayoutS).  The column phase gathers the
+// messages of consecutive variables; with slots interleaved, the lanes of
+// one shared-memory access phase (32 lanes for 32-bit accesses, 16 for
+// 64-bit, 8 for 128-bit) hit bank group (chunk mod 32/V), chunk = (r*Mp + j)
+// * (S/V) + q for the q-th V-slot group.  Distinct chunks in one group
+// serialise.  A deterministic local search over the rank stride (M plus a
+// small pad) and the order of the edges within each row minimises the
+// number of wavefronts; any choice decodes identically.
+// ---------------------------------------------------------------------------
+struct LayoutSearch {
+    int M, N, dv, S, V, Q, lpp, G;
+    const std::vector<std::vector<int>> *rows;
+    const std::vector<std::vector<std::pair<int, int>>> *cols;  // (check, index in the sorted row)
+    std::vector<int> row_off;                                   // first edge id of each row
+    std::vector<int> edge_k;                                    // edge id -> its index in its column
+};
+
+// Wavefronts of one access phase: the k-th column edge of the lanes tau in
+// [ph, ph + lpp), lane tau serving V-slot group q = tau % Q of variable tau / Q.
+static int phase_cost(const LayoutSearch &L, const std::vector<int> &rank, int Mp, int k, int ph) {
+    int chunks[32][32];  // per bank group, the distinct chunks seen (at most lpp)
+    int cnt[32];
+    for (int g = 0; g < L.G; ++g) cnt[g] = 0;
+    int worst = 0;
+    const int end = std::min(ph + L.lpp, L.N * L.Q);
+    for (int tau = ph; tau < end; ++tau) {
+        const int i = tau / L.Q, q = tau % L.Q;
+        const auto &ci = (*L.cols)[i];
+        if (k >= (int)ci.size()) continue;
+        const int j = ci[k].first, e = L.row_off[j] + ci[k].second;
+        const int chunk = (rank[e] * Mp + j) * L.Q + q, g = chunk % L.G;
+        bool seen = false;
+        for (int a = 0; a < cnt[g]; ++a) seen = seen || chunks[g][a] == chunk;
+        if (!seen) chunks[g][cnt[g]++] = chunk;
+        worst = std::max(worst, cnt[g]);
+    }
+    return worst;
+}
+
+static void search_layout(const LayoutSearch &L, int max_pad_dc, int &Mp_out, std::vector<int> &rank_out) {
+    const int nnz = L.row_off.back();
+    std::vector<int> rank0(nnz);
+    for (int j = 0; j < L.M; ++j)
+        for (int t = 0; t < (int)(*L.rows)[j].size(); ++t) rank0[L.row_off[j] + t] = t;
+    Mp_out = L.M;
+    rank_out = rank0;
+    if (L.Q >= L.G || L.M < 2) return;  // a phase holds one variable's slots: no conflicts to remove
+    auto total = [&](const std::vector<int> &rk, int Mp) {
+        long long t = 0;
+        for (int k = 0; k < L.dv; ++k)
+            for (int ph = 0; ph < L.N * L.Q; ph += L.lpp) t += phase_cost(L, rk, Mp, k, ph);
+        return t;
+    };
+    long long best = total(rank0, L.M);
+    // A swap of two edges of one row moves exactly two messages, each read in
+    // one phase, so only those phases are re-costed.
+    const int iters = std::min(12000, 16 * nnz);
+    const int pads[] = {0, 1, 3, 5};
+    for (int pad : pads) {
+        const int Mp = L.M + pad;
+        if ((long long)max_pad_dc * Mp > 65534) continue;
+        std::vector<int> rk = rank0;
+        long long cur = total(rk, Mp);
+        unsigned long long x = 0x9E3779B97F4A7C15ull ^ (unsigned long long)(L.S * 131 + pad);
+        for (int it = 0; it < iters; ++it) {
+            x = x * 6364136223846793005ull + 1442695040888963407ull;
+            const int j = (int)((x >> 33) % (unsigned long long)L.M);
+            const int deg = (int)(*L.rows)[j].size();
+            x = x * 6364136223846793005ull + 1442695040888963407ull;
+            const int a = (int)((x >> 33) % (unsigned long long)deg);
+            int b = (int)((x >> 13) % (unsigned long long)(deg - 1));
+            if (b >= a) ++b;
+            const int ea = L.row_off[j] + a, eb = L.row_off[j] + b;
+            const int ka = L.edge_k[ea], kb = L.edge_k[eb];
+            const int pa = ((*L.rows)[j][a] * L.Q) / L.lpp * L.lpp, pb = ((*L.rows)[j][b] * L.Q) / L.lpp * L.lpp;
+            const bool same = ka == kb && pa == pb;
+            const int before = phase_cost(L, rk, Mp, ka, pa) + (same ? 0 : phase_cost(L, rk, Mp, kb, pb));
+            std::swap(rk[ea], rk[eb]);
+            const int after = phase_cost(L, rk, Mp, ka, pa) + (same ? 0 : phase_cost(L, rk, Mp, kb, pb));
+            if (after <= before)
+                cur += after - before;
+            else
+                std::swap(rk[ea], rk[eb]);
+        }
+        if (cur < best) {
+            best = cur;
+            Mp_out = Mp;
+            rank_out = rk;
+        }
+    }
+}
+
 extern "C" bpsf_status bpsf_create(bpsf_ctx **out, int32_t M, int32_t N, int64_t nnz, int32_t layout,
                                    const int32_t *ptr, const int32_t *idx, const double *priors,
                                    const bpsf_params *params) {
@@ -340,29 +434,18 @@ extern "C" bpsf_status bpsf_create(bpsf_ctx **out, int32_t M, int32_t N, int64_t
         for (int v : rows[j]) c->csr_col.push_back(v);
         c->csr_ptr[j + 1] = (int)c->csr_col.size();
     }
-    // Message position of the edge of rank k in row j: k * M + j.
+    // Check table per column (ascending check order); message positions are per layout below.
     std::vector<uint8_t> row_deg(M);
-    std::vector<uint16_t> vpos((size_t)N * vstride, 0xffff), vchk((size_t)N * vstride, 0xffff);
+    std::vector<uint16_t> vchk((size_t)N * vstride, 0xffff);
     std::vector<uint16_t> row_ptr(M + 1), csr_col(nnz);
-    std::vector<float> lch(N), lch_pos(P, 0.f);
+    std::vector<float> lch(N);
     for (int j = 0; j < M; ++j) row_deg[j] = (uint8_t)rows[j].size();
     for (int i = 0; i < N; ++i)
-        for (int k = 0; k < (int)cols[i].size(); ++k) {
-            vpos[(size_t)i * vstride + k] = (uint16_t)(cols[i][k].second * M + cols[i][k].first);
-            vchk[(size_t)i * vstride + k] = (uint16_t)cols[i][k].first;
-        }
+        for (int k = 0; k < (int)cols[i].size(); ++k) vchk[(size_t)i * vstride + k] = (uint16_t)cols[i][k].first;
     for (int j = 0; j <= M; ++j) row_ptr[j] = (uint16_t)c->csr_ptr[j];
     for (int e = 0; e < nnz; ++e) csr_col[e] = (uint16_t)c->csr_col[e];
     // Channel LLR (Section II-B, step 1) in double, rounded once to float.
     for (int i = 0; i < N; ++i) lch[i] = (float)std::log((1.0 - priors[i]) / priors[i]);
-    for (int j = 0; j < M; ++j)
-        for (int k = 0; k < (int)rows[j].size(); ++k) lch_pos[(size_t)k * M + j] = lch[rows[j][k]];
-    // A default set beyond kMaxTrials is left empty: decoding then needs a list.
-    std::vector<unsigned long long> masks;
-    if (default_trial_count(c->p.w, c->p.w_max) <= kMaxTrials) masks = default_trials(c->p.w, c->p.w_max);
-    c->n_trials = (int)masks.size();
-    if (masks.empty()) masks.push_back(0);
-
     cudaGetDevice(&c->device);
     cudaDeviceProp prop;
     cudaError_t e = cudaGetDeviceProperties(&prop, c->device);
@@ -372,6 +455,49 @@ extern "C" bpsf_status bpsf_create(bpsf_ctx **out, int32_t M, int32_t N, int64_t
     }
     c->sm_count = prop.multiProcessorCount;
     c->smem_optin = (int)prop.sharedMemPerBlockOptin;
+    // Per-slot-count layouts (LayoutS): rank stride and edge ranks from the search.
+    std::vector<int> row_off(M + 1, 0);
+    for (int j = 0; j < M; ++j) row_off[j + 1] = row_off[j] + (int)rows[j].size();
+    std::vector<int> edge_k(nnz);
+    for (int i = 0; i < N; ++i)
+        for (int k = 0; k < (int)cols[i].size(); ++k) edge_k[row_off[cols[i][k].first] + cols[i][k].second] = k;
+    std::vector<std::vector<uint16_t>> lay_vpos(kNumLayouts), lay_var(kNumLayouts);
+    std::vector<std::vector<float>> lay_lch(kNumLayouts);
+    int lay_Mp[kNumLayouts];
+    for (int li = 0; li < kNumLayouts; ++li) {
+        const int S = 1 << li;
+        // Slots per lane in the column phase: 4 for the exact-degree variant, 2 for
+        // rows up to 16 wide, else 1.
+        const int V = (variant == 0) ? std::min(S, 4) : (dc <= 16 ? std::min(S, 2) : 1);
+        LayoutSearch L;
+        L.M = M; L.N = N; L.dv = dv; L.S = S; L.V = V; L.Q = S / V; L.lpp = 32 / V; L.G = 32 / V;
+        L.rows = &rows; L.cols = &cols; L.row_off = row_off; L.edge_k = edge_k;
+        int Mp = M;
+        std::vector<int> rank;
+        search_layout(L, dc, Mp, rank);
+        lay_Mp[li] = Mp;
+        const size_t PS = (size_t)dc * Mp;
+        lay_vpos[li].assign((size_t)N * vstride, 0xffff);
+        lay_lch[li].assign(PS, 0.f);
+        lay_var[li].assign(PS, 0xffff);
+        for (int i = 0; i < N; ++i)
+            for (int k = 0; k < (int)cols[i].size(); ++k) {
+                const int j = cols[i][k].first, r = rank[row_off[j] + cols[i][k].second];
+                lay_vpos[li][(size_t)i * vstride + k] = (uint16_t)(r * Mp + j);
+            }
+        for (int j = 0; j < M; ++j)
+            for (int t = 0; t < (int)rows[j].size(); ++t) {
+                const size_t pos = (size_t)rank[row_off[j] + t] * Mp + j;
+                lay_lch[li][pos] = lch[rows[j][t]];
+                lay_var[li][pos] = (uint16_t)rows[j][t];
+            }
+    }
+    // A default set beyond kMaxTrials is left empty: decoding then needs a list.
+    std::vector<unsigned long long> masks;
+    if (default_trial_count(c->p.w, c->p.w_max) <= kMaxTrials) masks = default_trials(c->p.w, c->p.w_max);
+    c->n_trials = (int)masks.size();
+    if (masks.empty()) masks.push_back(0);
+
 
     // Layered schedule: rows coloured greedily in ascending order, each taking the
     // smallest layer not used by an earlier row that shares a variable with it.
@@ -401,14 +527,12 @@ extern "C" bpsf_status bpsf_create(bpsf_ctx **out, int32_t M, int32_t N, int64_t
     }
 
     // One allocation for all code arrays.
-    const void *srcs[10] = {row_deg.data(), vpos.data(), vchk.data(), lch.data(),
-                            lch_pos.data(), row_ptr.data(), csr_col.data(), masks.data(),
-                            layer_ptr.data(), layer_rows.data()};
-    const size_t sizes[10] = {(size_t)M, 2 * vpos.size(), 2 * vchk.size(), 4 * (size_t)N,
-                              4 * (size_t)P, 2 * (size_t)(M + 1), 2 * (size_t)nnz, 8 * masks.size(),
-                              2 * layer_ptr.size(), 2 * layer_rows.size()};
-    size_t off[10], sz = 0;
-    for (int k = 0; k < 10; ++k) {
+    const void *srcs[8] = {row_deg.data(), vchk.data(), lch.data(), row_ptr.data(), csr_col.data(),
+                           masks.data(), layer_ptr.data(), layer_rows.data()};
+    const size_t sizes[8] = {(size_t)M, 2 * vchk.size(), 4 * (size_t)N, 2 * (size_t)(M + 1), 2 * (size_t)nnz,
+                             8 * masks.size(), 2 * layer_ptr.size(), 2 * layer_rows.size()};
+    size_t off[8], sz = 0;
+    for (int k = 0; k < 8; ++k) {
         off[k] = sz;
         sz += align16(sizes[k]);
     }
@@ -418,7 +542,7 @@ extern "C" bpsf_status bpsf_create(bpsf_ctx **out, int32_t M, int32_t N, int64_t
         return bpsf_fail(BPSF_ENOMEM, "cudaMalloc(code): %s", cudaGetErrorString(e));
     }
     std::vector<unsigned char> hbuf(sz, 0);
-    for (int k = 0; k < 10; ++k) std::memcpy(hbuf.data() + off[k], srcs[k], sizes[k]);
+    for (int k = 0; k < 8; ++k) std::memcpy(hbuf.data() + off[k], srcs[k], sizes[k]);
     e = cudaMemcpy(c->d_code, hbuf.data(), sz, cudaMemcpyHostToDevice);
     unsigned char *base = (unsigned char *)c->d_code;
     CodeDev &cd = c->code;
@@ -439,19 +563,47 @@ extern "C" bpsf_status bpsf_create(bpsf_ctx **out, int32_t M, int32_t N, int64_t
     cd.select = p.select;
     cd.alpha = p.alpha;
     cd.row_deg = (const uint8_t *)(base + off[0]);
-    cd.vpos = (const uint16_t *)(base + off[1]);
-    cd.vchk = (const uint16_t *)(base + off[2]);
-    cd.lch = (const float *)(base + off[3]);
-    cd.lch_pos = (const float *)(base + off[4]);
-    cd.row_ptr = (const uint16_t *)(base + off[5]);
-    cd.csr_col = (const uint16_t *)(base + off[6]);
-    cd.trial_mask = (const unsigned long long *)(base + off[7]);
+    cd.vchk = (const uint16_t *)(base + off[1]);
+    cd.lch = (const float *)(base + off[2]);
+    cd.row_ptr = (const uint16_t *)(base + off[3]);
+    cd.csr_col = (const uint16_t *)(base + off[4]);
+    cd.trial_mask = (const unsigned long long *)(base + off[5]);
     c->default_masks = cd.trial_mask;
     cd.layered = (p.flags & BPSF_FLAG_LAYERED) ? 1 : 0;
     cd.n_layers = n_layers;
-    cd.layer_ptr = (const uint16_t *)(base + off[8]);
-    cd.layer_rows = (const uint16_t *)(base + off[9]);
+    cd.layer_ptr = (const uint16_t *)(base + off[6]);
+    cd.layer_rows = (const uint16_t *)(base + off[7]);
     c->default_n_trials = c->n_trials;
+    // The per-slot-count layouts: one allocation.
+    {
+        size_t lsz = 0;
+        size_t lo[kNumLayouts][3];
+        for (int li = 0; li < kNumLayouts; ++li) {
+            lo[li][0] = lsz; lsz += align16(2 * lay_vpos[li].size());
+            lo[li][1] = lsz; lsz += align16(4 * lay_lch[li].size());
+            lo[li][2] = lsz; lsz += align16(2 * lay_var[li].size());
+        }
+        if (e == cudaSuccess) e = cudaMalloc(&c->d_layouts, lsz);
+        if (e == cudaSuccess) {
+            std::vector<unsigned char> lb(lsz, 0);
+            for (int li = 0; li < kNumLayouts; ++li) {
+                std::memcpy(lb.data() + lo[li][0], lay_vpos[li].data(), 2 * lay_vpos[li].size());
+                std::memcpy(lb.data() + lo[li][1], lay_lch[li].data(), 4 * lay_lch[li].size());
+                std::memcpy(lb.data() + lo[li][2], lay_var[li].data(), 2 * lay_var[li].size());
+            }
+            e = cudaMemcpy(c->d_layouts, lb.data(), lsz, cudaMemcpyHostToDevice);
+            unsigned char *lbase = (unsigned char *)c->d_layouts;
+            for (int li = 0; li < kNumLayouts; ++li) {
+                LayoutS &ly = cd.lay[li];
+                ly.Mp = lay_Mp[li];
+                ly.P = (int)lay_lch[li].size();
+                ly.vpos = (const uint16_t *)(lbase + lo[li][0]);
+                ly.lch_pos = (const float *)(lbase + lo[li][1]);
+                ly.pos_var = (const uint16_t *)(lbase + lo[li][2]);
+            }
+            bpsf_activate_layout(cd, 1);
+        }
+    }
     if (e == cudaSuccess) e = cudaMalloc((void **)&c->d_ctr, sizeof(StreamCounters));
     if (e == cudaSuccess) e = cudaMemset(c->d_ctr, 0, sizeof(StreamCounters));
     if (e == cudaSuccess) e = cudaMallocHost((void **)&c->h_ctr, sizeof(StreamCounters));
@@ -531,6 +683,7 @@ StreamDev bpsf_make_stream(const bpsf_ctx *c, const JobDev &job, const DebugDev 
 void bpsf_launch_plan(const bpsf_plan &pl, bool debug, StreamDev *sds, int n, int grid, void *stream) {
     for (int k = 0; k < n; ++k) {
         sds[k].S = pl.S_code[k];
+        bpsf_activate_layout(sds[k].code, pl.S_code[k]);
         sds[k].W = pl.W_code[k];
         sds[k].teams = pl.teams_code[k];
     }
@@ -957,6 +1110,7 @@ extern "C" bpsf_status bpsf_selftest_wait(bpsf_ctx *c, int64_t wait_us, void *st
                reinterpret_cast<int16_t *>(c->rec.done), nullptr, 1, c->Ws, c->Wn};
     StreamDev sd = bpsf_make_stream(c, job, nullptr, 0);
     sd.S = pl.S_code[0];
+    bpsf_activate_layout(sd.code, pl.S_code[0]);
     sd.W = pl.W_code[0];
     sd.teams = pl.teams_code[0];
     LaunchArgs la{&sd, 1, pl.Q, (unsigned long long)wait_us * 1000ull};

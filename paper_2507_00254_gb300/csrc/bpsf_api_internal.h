@@ -15,6 +15,7 @@ struct bpsf_ctx {
     std::vector<int32_t> csr_ptr, csr_col;  // host copy of H (CSR, ascending columns)
     void *d_code = nullptr;                 // one allocation for all code arrays
     void *d_trials = nullptr;               // trial list set by bpsf_set_trials (else the default in d_code)
+    void *d_layouts = nullptr;              // per-slot-count message layouts (CodeDev::lay)
     const unsigned long long *default_masks = nullptr;
     int default_n_trials = 0;
     bpsf::CodeDev code{};
@@ -43,6 +44,23 @@ struct bpsf_plan {
 };
 
 bpsf_status bpsf_fail(bpsf_status s, const char *fmt, ...);
+
+// Index of the layout for S slots per team (S a power of two, 1..32).
+inline int layout_index(int S) {
+    int i = 0;
+    while ((1 << i) < S && i < bpsf::kNumLayouts - 1) ++i;
+    return i;
+}
+
+// Make the layout for S slots per team the active one of a code descriptor.
+inline void bpsf_activate_layout(bpsf::CodeDev &cd, int S) {
+    const bpsf::LayoutS &ly = cd.lay[layout_index(S)];
+    cd.Mp = ly.Mp;
+    cd.P = ly.P;
+    cd.vpos = ly.vpos;
+    cd.lch_pos = ly.lch_pos;
+    cd.pos_var = ly.pos_var;
+}
 
 // A context with trials (w > 0) decodes only with a non-empty trial set.
 inline bpsf_status bpsf_check_trials(const bpsf_ctx *c) {

@@ -34,6 +34,19 @@ enum : unsigned {
 // stride M (one word per bank for consecutive rows).  vpos lists, for each
 // column, the positions of its edges in ascending check order (the order the
 // V2C and posterior sums are folded in).
+// Message layout for one slot count S = 1 << index: edge of row j with
+// rank r sits at position r*Mp + j (Mp >= M, P = dc_max * Mp positions); the
+// rank stride and the rank of each edge within its row are chosen at create
+// so that the column phase's gathered accesses meet few shared-memory bank
+// conflicts for that S (the row phase is exact for any rank order).
+struct LayoutS {
+    int Mp, P;
+    const uint16_t *vpos;     // N x vstride positions
+    const float *lch_pos;     // P, channel LLR of the variable at each position
+    const uint16_t *pos_var;  // P, variable at each position (0xffff: unused)
+};
+constexpr int kNumLayouts = 6;  // S = 1, 2, 4, 8, 16, 32
+
 struct CodeDev {
     int M, N, nnz, Ws, Wn;
     int DC, dv_max, P, regular;  // regular: every row has DC ones, every column dv_max
@@ -41,13 +54,16 @@ struct CodeDev {
     int max_iter, short_iter, w, n_trials, select;
     float alpha;
     const uint8_t *row_deg;      // M, ones per row
-    const uint16_t *vpos;        // N x vstride, message positions (0xffff padding)
+    const uint16_t *vpos;        // N x vstride, message positions (0xffff padding), active layout
     const uint16_t *vchk;        // N x vstride, check indices
     const float *lch;            // N, channel LLRs (FP32)
-    const float *lch_pos;        // P, channel LLR of the variable at each position
+    const float *lch_pos;        // P, channel LLR of the variable at each position, active layout
     const uint16_t *row_ptr;     // M+1, CSR (syndrome kernel)
     const uint16_t *csr_col;     // nnz
     const unsigned long long *trial_mask;  // n_trials subset masks over Phi (bit j selects Phi[j]), list order
+    int Mp;                      // rank stride of the active layout (see LayoutS)
+    const uint16_t *pos_var;     // active layout: variable at each position
+    LayoutS lay[kNumLayouts];    // per slot count; a launch activates the one of its S
     int layered;                 // 1: layered schedule
     int n_layers;
     const uint16_t *layer_ptr;   // n_layers+1, rows of layer l are layer_rows[layer_ptr[l] .. layer_ptr[l+1])

@@ -240,11 +240,12 @@ __device__ __forceinline__ void c_compute_store(CTask<DC, REG> &t, int MS, float
 template <int DC, bool REG>
 __device__ __forceinline__ void c_phase(const CodeDev &cd, const LayoutMem &L, const TeamMem &T, int lgS, float alpha,
                                         int tid, int nthreads) {
-    const int MS = cd.M << lgS;
-    for (int tau = tid; tau < MS; tau += BPSF_CU * nthreads) {
+    const int MS = cd.Mp << lgS;  // rank stride of the active layout
+    const int nt = cd.M << lgS;   // row tasks (rows M..Mp-1 of the stride are padding)
+    for (int tau = tid; tau < nt; tau += BPSF_CU * nthreads) {
         CTask<DC, REG> t[BPSF_CU];
 #pragma unroll
-        for (int u = 0; u < BPSF_CU; ++u) c_load<DC, REG>(t[u], L, T, MS, lgS, tau + u * nthreads, tau + u * nthreads < MS);
+        for (int u = 0; u < BPSF_CU; ++u) c_load<DC, REG>(t[u], L, T, MS, lgS, tau + u * nthreads, tau + u * nthreads < nt);
 #pragma unroll
         for (int u = 0; u < BPSF_CU; ++u) c_compute_store<DC, REG>(t[u], MS, alpha);
     }
@@ -441,8 +442,9 @@ template <int DC, bool REG, int V>
 __device__ __forceinline__ void c_phase_vec(const CodeDev &cd, const LayoutMem &L, const TeamMem &T, int lgS,
                                             const float (&alpha)[V], int tid, int nthreads) {
     const int lgQ = lgS - (V == 4 ? 2 : 1);
-    const int MQ = cd.M << lgQ;
-    for (int tauv = tid; tauv < MQ; tauv += nthreads) c_row_vec<DC, REG, V>(L, T, MQ, lgQ, tauv, alpha);
+    const int MQ = cd.Mp << lgQ;  // rank stride of the active layout, in V-slot groups
+    const int nt = cd.M << lgQ;   // row tasks (rows M..Mp-1 of the stride are padding)
+    for (int tauv = tid; tauv < nt; tauv += nthreads) c_row_vec<DC, REG, V>(L, T, MQ, lgQ, tauv, alpha);
 }
 
 template <int DVS, int DVX, bool DEBUG, int V>
@@ -556,16 +558,15 @@ __device__ __forceinline__ void v_phase_vec(const StreamDev &sd, const LayoutMem
 template <int DC>
 __device__ __forceinline__ void layered_row(const CodeDev &cd, const LayoutMem &L, const TeamMem &T, int lgS, int j,
                                             int s, float alpha) {
-    const int S = 1 << lgS, M = cd.M;
+    const int S = 1 << lgS, M = cd.Mp;  // rank stride of the active layout
     const int deg = (int)L.row_deg[j];
-    const int base = (int)__ldg(cd.row_ptr + j);
     float q[DC];
     int vi[DC];
     float *mj = T.m + (j << lgS) + s;  // edge k of row j at ((k*M + j)*S + s)
 #pragma unroll
     for (int k = 0; k < DC; ++k) {
         if (k < deg) {
-            vi[k] = (int)__ldg(cd.csr_col + base + k);
+            vi[k] = (int)__ldg(cd.pos_var + k * M + j);
             q[k] = __fsub_rn(T.post[(vi[k] << lgS) + s], mj[k * M * S]);
         }
     }
