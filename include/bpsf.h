@@ -184,6 +184,19 @@ typedef struct {
 bpsf_status bpsf_decode_multi(int32_t n_jobs, const bpsf_job *jobs, void *stream);
 
 /*
+ * End-to-end mixed-code batch with HOST buffers: the jobs' five array fields
+ * hold host addresses here (pinned memory gives full copy bandwidth).  Each
+ * job's syndromes are copied into its context's device staging buffer, all
+ * jobs decode in ONE bpsf_decode_multi launch, and the results are copied
+ * back, all on `stream`; the call returns when the results are in the host
+ * buffers.  Same limits and results as bpsf_decode_multi; jobs with
+ * n_shots = 0 are checked and then left out of the launch.  A context's
+ * staging buffer is shared with bpsf_decode_host: calls on one context must
+ * not overlap.
+ */
+bpsf_status bpsf_decode_multi_host(int32_t n_jobs, const bpsf_job *jobs, void *stream);
+
+/*
  * Batched decode that allocates nothing.  The paper has no counterpart: this
  * serves callers that cannot allocate device memory when they decode (a
  * control loop with a hard deadline that must not block in the CUDA

@@ -28,6 +28,7 @@ EXPORTS = (
     "bpsf_serve_poll", "bpsf_serve_stop", "bpsf_bb_code", "bpsf_phenom_code", "bpsf_syndrome", "bpsf_decode_debug",
     "bpsf_num_trials", "bpsf_last_work", "bpsf_status_str", "bpsf_last_error", "bpsf_decode_noalloc",
     "bpsf_noalloc_max_shots", "bpsf_selftest_wait", "bpsf_serve_replay", "bpsf_set_trials",
+    "bpsf_decode_multi_host",
 )
 
 
@@ -93,6 +94,7 @@ def lib():
         "bpsf_noalloc_max_shots": ([vp], i64),
         "bpsf_decode_host": ([vp, i64, vp, i32, vp, i32, vp, vp, vp, vp], st),
         "bpsf_decode_multi": ([i32, C.POINTER(bpsf_job), vp], st),
+        "bpsf_decode_multi_host": ([i32, C.POINTER(bpsf_job), vp], st),
         "bpsf_sync": ([vp, vp], st),
         "bpsf_get_tuning": ([vp, C.POINTER(bpsf_tuning)], st),
         "bpsf_set_tuning": ([vp, C.POINTER(bpsf_tuning)], st),
@@ -174,6 +176,11 @@ def bpsf_decode_host(h, n, h_synd, ss, h_corr, cs, h_conv, h_iters, h_stage, str
 def bpsf_decode_multi(jobs, stream):
     arr = (bpsf_job * len(jobs))(*jobs)
     check(lib().bpsf_decode_multi(len(jobs), arr, stream))
+
+
+def bpsf_decode_multi_host(jobs, stream):
+    arr = (bpsf_job * len(jobs))(*jobs)
+    check(lib().bpsf_decode_multi_host(len(jobs), arr, stream))
 
 
 def bpsf_decode_debug(h, n, d_synd, ss, d_corr, cs, d_conv, d_iters, d_stage, d_lout, d_flips, d_phi, d_tsynd,
@@ -468,6 +475,21 @@ class Server:
             self.stop()
         except Exception:
             pass
+
+
+def decode_multi_host(decoders, synds, stream=None):
+    """End-to-end form of decode_multi: host (numpy) syndromes in, numpy outputs out, one launch."""
+    synds = [np.ascontiguousarray(s) for s in synds]
+    outs, jobs = [], []
+    for d, s in zip(decoders, synds):
+        n = int(s.shape[0])
+        o = dict(corr=np.zeros((n, d.Wn), dtype=np.uint32), conv=np.zeros(n, dtype=np.uint8),
+                 iters=np.zeros(n, dtype=np.int16), stage=np.zeros(n, dtype=np.uint8))
+        outs.append(o)
+        jobs.append(bpsf_job(d.handle, n, _np_ptr(s), int(s.shape[1]), _np_ptr(o["corr"]), d.Wn, _np_ptr(o["conv"]),
+                             _np_ptr(o["iters"]), _np_ptr(o["stage"])))
+    bpsf_decode_multi_host(jobs, _stream_handle(stream))
+    return outs
 
 
 def decode_multi(decoders, synds, outs=None, stream=None, sync=True):

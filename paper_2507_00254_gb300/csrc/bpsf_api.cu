@@ -884,14 +884,23 @@ extern "C" bpsf_status bpsf_decode_plain(bpsf_ctx *c, int64_t n, const uint32_t 
 // Host-buffer form.
 // ---------------------------------------------------------------------------
 
-extern "C" bpsf_status bpsf_decode_host(bpsf_ctx *c, int64_t n, const uint32_t *h_synd, int32_t ss, uint32_t *h_corr,
-                                        int32_t cs, uint8_t *h_conv, int16_t *h_iters, uint8_t *h_stage,
-                                        void *stream) {
-    bpsf_status st = check_io(c, n, h_synd, ss, h_corr, cs, h_conv, h_iters);
-    if (st != BPSF_OK || n == 0) return st;
-    cudaSetDevice(c->device);
-    const size_t b_synd = 4 * (size_t)n * ss, b_corr = 4 * (size_t)n * cs, b_conv = (size_t)n, b_it = 2 * (size_t)n;
-    const size_t need = align16(b_synd) + align16(b_corr) + align16(b_conv) + align16(b_it) + align16(b_conv);
+// Device staging for a host-buffer call: syndromes, corrections, converged
+// flags, iterations and stages of n shots, in the context's own buffer
+// (grown when too small, kept for the next call).
+struct HostStage {
+    uint32_t *synd, *corr;
+    uint8_t *conv, *stage;
+    int16_t *it;
+    size_t b_synd, b_corr, b_conv, b_it;
+};
+
+static bpsf_status host_stage(bpsf_ctx *c, int64_t n, int32_t ss, int32_t cs, HostStage *h) {
+    h->b_synd = 4 * (size_t)n * ss;
+    h->b_corr = 4 * (size_t)n * cs;
+    h->b_conv = (size_t)n;
+    h->b_it = 2 * (size_t)n;
+    const size_t need = align16(h->b_synd) + align16(h->b_corr) + align16(h->b_conv) + align16(h->b_it) +
+                        align16(h->b_conv);
     if (need > c->host_stage_bytes) {
         if (c->d_host_stage) cudaFree(c->d_host_stage);
         c->d_host_stage = nullptr;
@@ -901,26 +910,93 @@ extern "C" bpsf_status bpsf_decode_host(bpsf_ctx *c, int64_t n, const uint32_t *
         c->host_stage_bytes = need;
     }
     unsigned char *p = (unsigned char *)c->d_host_stage;
-    uint32_t *d_synd = (uint32_t *)p;
-    p += align16(b_synd);
-    uint32_t *d_corr = (uint32_t *)p;
-    p += align16(b_corr);
-    uint8_t *d_conv = p;
-    p += align16(b_conv);
-    int16_t *d_it = (int16_t *)p;
-    p += align16(b_it);
-    uint8_t *d_stage = p;
-    cudaStream_t s = (cudaStream_t)stream;
-    cudaError_t e = cudaMemcpyAsync(d_synd, h_synd, b_synd, cudaMemcpyHostToDevice, s);
-    if (e != cudaSuccess) return bpsf_fail(BPSF_ECUDA, "H2D: %s", cudaGetErrorString(e));
-    st = decode_impl(c, n, d_synd, ss, d_corr, cs, d_conv, d_it, d_stage, nullptr, stream);
-    if (st != BPSF_OK) return st;
-    e = cudaMemcpyAsync(h_corr, d_corr, b_corr, cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(h_conv, d_conv, b_conv, cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(h_iters, d_it, b_it, cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess && h_stage) e = cudaMemcpyAsync(h_stage, d_stage, b_conv, cudaMemcpyDeviceToHost, s);
+    h->synd = (uint32_t *)p;
+    p += align16(h->b_synd);
+    h->corr = (uint32_t *)p;
+    p += align16(h->b_corr);
+    h->conv = p;
+    p += align16(h->b_conv);
+    h->it = (int16_t *)p;
+    p += align16(h->b_it);
+    h->stage = p;
+    return BPSF_OK;
+}
+
+static bpsf_status host_results(const HostStage &h, uint32_t *h_corr, uint8_t *h_conv, int16_t *h_iters,
+                                uint8_t *h_stage, cudaStream_t s) {
+    cudaError_t e = cudaMemcpyAsync(h_corr, h.corr, h.b_corr, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h_conv, h.conv, h.b_conv, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h_iters, h.it, h.b_it, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && h_stage) e = cudaMemcpyAsync(h_stage, h.stage, h.b_conv, cudaMemcpyDeviceToHost, s);
     if (e != cudaSuccess) return bpsf_fail(BPSF_ECUDA, "D2H: %s", cudaGetErrorString(e));
+    return BPSF_OK;
+}
+
+extern "C" bpsf_status bpsf_decode_host(bpsf_ctx *c, int64_t n, const uint32_t *h_synd, int32_t ss, uint32_t *h_corr,
+                                        int32_t cs, uint8_t *h_conv, int16_t *h_iters, uint8_t *h_stage,
+                                        void *stream) {
+    bpsf_status st = check_io(c, n, h_synd, ss, h_corr, cs, h_conv, h_iters);
+    if (st != BPSF_OK || n == 0) return st;
+    cudaSetDevice(c->device);
+    HostStage h;
+    st = host_stage(c, n, ss, cs, &h);
+    if (st != BPSF_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaMemcpyAsync(h.synd, h_synd, h.b_synd, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return bpsf_fail(BPSF_ECUDA, "H2D: %s", cudaGetErrorString(e));
+    st = decode_impl(c, n, h.synd, ss, h.corr, cs, h.conv, h.it, h.stage, nullptr, stream);
+    if (st != BPSF_OK) return st;
+    st = host_results(h, h_corr, h_conv, h_iters, h_stage, s);
+    if (st != BPSF_OK) return st;
     return bpsf_sync(c, stream);
+}
+
+extern "C" bpsf_status bpsf_decode_multi_host(int32_t n_jobs, const bpsf_job *jobs, void *stream) {
+    if (n_jobs < 1 || n_jobs > kMaxStreams || !jobs) return bpsf_fail(BPSF_EINVAL, "n_jobs must be in 1..%d", kMaxStreams);
+    for (int k = 0; k < n_jobs; ++k) {
+        const bpsf_job &j = jobs[k];
+        bpsf_status st = check_io(j.ctx, j.n_shots, j.d_synd, j.synd_stride_words, j.d_corr, j.corr_stride_words,
+                                  j.d_converged, j.d_iters);
+        if (st != BPSF_OK) return st;
+        for (int q = 0; q < k; ++q)
+            if (jobs[q].ctx == j.ctx) return bpsf_fail(BPSF_EINVAL, "a context appears twice in one launch");
+        if (j.ctx->device != jobs[0].ctx->device) return bpsf_fail(BPSF_EINVAL, "contexts on different devices");
+    }
+    cudaSetDevice(jobs[0].ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    // Stage every non-empty job's syndromes, then one launch over the device copies.
+    std::vector<HostStage> hs(n_jobs);
+    std::vector<bpsf_job> dj;
+    std::vector<int> live;
+    for (int k = 0; k < n_jobs; ++k) {
+        const bpsf_job &j = jobs[k];
+        if (j.n_shots == 0) continue;  // empty jobs take no part in the launch
+        bpsf_status st = host_stage(j.ctx, j.n_shots, j.synd_stride_words, j.corr_stride_words, &hs[k]);
+        if (st != BPSF_OK) return st;
+        cudaError_t e = cudaMemcpyAsync(hs[k].synd, j.d_synd, hs[k].b_synd, cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) return bpsf_fail(BPSF_ECUDA, "H2D: %s", cudaGetErrorString(e));
+        bpsf_job d = j;
+        d.d_synd = hs[k].synd;
+        d.d_corr = hs[k].corr;
+        d.d_converged = hs[k].conv;
+        d.d_iters = hs[k].it;
+        d.d_stage = hs[k].stage;
+        dj.push_back(d);
+        live.push_back(k);
+    }
+    if (dj.empty()) return BPSF_OK;
+    bpsf_status st = bpsf_decode_multi((int32_t)dj.size(), dj.data(), stream);
+    if (st != BPSF_OK) return st;
+    for (int k : live) {
+        const bpsf_job &j = jobs[k];
+        st = host_results(hs[k], j.d_corr, j.d_converged, j.d_iters, j.d_stage, s);
+        if (st != BPSF_OK) return st;
+    }
+    for (int k : live) {
+        st = bpsf_sync(jobs[k].ctx, stream);
+        if (st != BPSF_OK) return st;
+    }
+    return BPSF_OK;
 }
 
 // ---------------------------------------------------------------------------

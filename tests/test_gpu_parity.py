@@ -345,6 +345,34 @@ def test_host_buffer_form_equals_device_form():
     assert (h["conv"] == a["conv"]).all() and (h["iters"] == a["iters"]).all() and (h["stage"] == a["stage"]).all()
 
 
+def test_multi_host_form_equals_device_multi_and_oracle():
+    """bpsf_decode_multi_host: one launch over host buffers of several codes,
+    including an empty job; results equal the device-buffer multi launch and
+    the oracle."""
+    P = B.Params(max_iter=100, alpha=0.625, w=6, short_iter=20)
+    names = ["bb72", "bb144", "bb288", "bb90"]
+    sizes = [700, 1200, 400, 0]
+    decs, host_synds, cases = [], [], []
+    for k, (name, n) in enumerate(zip(names, sizes)):
+        oc, e, s = make_inputs(name, 0.06, max(n, 1), synth.SEEDS["mixed"][k])
+        s = s[:n]
+        decs.append(decoder(name, 0.06, P))
+        host_synds.append(pack(s))
+        cases.append((oc, s))
+    h = B.decode_multi_host(decs, host_synds)
+    live = [k for k, n in enumerate(sizes) if n > 0]
+    d = B.decode_multi([decs[k] for k in live], [dev(host_synds[k]) for k in live])
+    for k, o in zip(live, d):
+        assert (h[k]["corr"].view(np.int32) == o["corr"].cpu().numpy()).all()
+        for f in ("conv", "iters", "stage"):
+            assert (h[k][f] == o[f].cpu().numpy()).all()
+        oc, s = cases[k]
+        eo, co, io, so = oc.bpsf_batch(s, 0.06, oparams(P), threads=THREADS)
+        assert (unpack(h[k]["corr"].view(np.int32), oc.N) == eo).all(axis=1).mean() >= CORR_MATCH
+        assert (h[k]["stage"] == so).mean() >= CORR_MATCH
+    assert h[3]["corr"].shape == (0, decs[3].Wn)
+
+
 # --------------------------------------------------------------------------
 # Variants and edge cases
 # --------------------------------------------------------------------------
