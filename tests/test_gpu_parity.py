@@ -317,11 +317,27 @@ def test_launch_shape_does_not_change_results():
     dec = decoder("bb144", 0.07, P)
     ref = gpu_decode(dec, s)
     for t in [(1, 1, 4, 0), (1, 16, 4, 0), (2, 2, 8, 0), (4, 1, 8, 1), (1, 8, 4, 0), (1, 2, 15, 0), (8, 1, 8, 0),
-              (1, 32, 2, 0), (8, 32, 8, 0), (4, 16, 12, 0)]:
+              (1, 32, 2, 0), (8, 32, 8, 0), (4, 16, 12, 0), (1, 4, 12, 0), (2, 4, 8, 0)]:
         dec.tuning = t
         got = gpu_decode(dec, s)
         for key in ("corr", "conv", "iters", "stage"):
             assert (got[key] == ref[key]).all(), (t, key)
+
+
+def test_launch_shape_irregular_code():
+    """Every slot count has its own message layout (rank stride and edge order);
+    for the irregular-row [[254,28]] code the strides differ from M at some slot
+    counts.  Results equal the oracle at each of them."""
+    P = B.Params(max_iter=60, alpha=0.625, w=5, short_iter=15)
+    oc, e, s = make_inputs("gb254", 0.03, 600, 6)
+    dec = decoder("gb254", 0.03, P)
+    eo, co, io, so = oc.bpsf_batch(s, 0.03, oparams(P), threads=THREADS)
+    for t in [(1, 1, 8, 0), (1, 2, 8, 0), (1, 4, 8, 0), (1, 8, 4, 0), (2, 16, 2, 0)]:
+        dec.tuning = t
+        got = gpu_decode(dec, s)
+        assert (unpack(got["corr"], oc.N) == eo).all(axis=1).mean() >= CORR_MATCH, t
+        assert (got["stage"] == so).mean() >= CORR_MATCH, t
+        assert (got["iters"] == io).mean() >= CORR_MATCH, t
 
 
 def test_plain_form_equals_batched_form():
