@@ -122,6 +122,29 @@ static bpsf_status check_shape(const bpsf_tuning &t) {
     return BPSF_OK;
 }
 
+// Resident blocks per SM of a kernel instance at a block size and shared
+// memory size, queried once and remembered: a plan made while a stream is
+// being captured into a CUDA graph then makes no query.
+static cudaError_t blocks_per_sm(const void *fn, int block, int smem, int *occ) {
+    static std::mutex mu;
+    static std::map<std::tuple<const void *, int, int>, int> cache;
+    const auto key = std::make_tuple(fn, block, smem);
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        auto it = cache.find(key);
+        if (it != cache.end()) {
+            *occ = it->second;
+            return cudaSuccess;
+        }
+    }
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, fn, block, smem);
+    if (e == cudaSuccess) {
+        std::lock_guard<std::mutex> lk(mu);
+        cache[key] = *occ;
+    }
+    return e;
+}
+
 bpsf_status bpsf_make_plan(bpsf_ctx *const *codes, int n_codes, const bpsf_tuning *tunes, bool debug,
                            bpsf_plan *out, bool shrink) {
     // One kernel variant must fit every code of the launch.
@@ -176,8 +199,7 @@ bpsf_status bpsf_make_plan(bpsf_ctx *const *codes, int n_codes, const bpsf_tunin
     if (st != BPSF_OK) return st;
     const int block = 32 * (B + 1);
     int occ = 0;
-    cudaError_t e =
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, persistent_kernel_ptr(variant, debug, layered), block, smem);
+    cudaError_t e = blocks_per_sm(persistent_kernel_ptr(variant, debug, layered), block, smem, &occ);
     if (e != cudaSuccess) return bpsf_fail(BPSF_ECUDA, "occupancy query: %s", cudaGetErrorString(e));
     if (bps > 0) occ = std::min(occ, bps);
     // Fewer than two blocks per SM: the variant's full-register instance runs the
@@ -187,7 +209,7 @@ bpsf_status bpsf_make_plan(bpsf_ctx *const *codes, int n_codes, const bpsf_tunin
         st = bpsf_ensure_kernel_attrs(full, c0->smem_optin);
         if (st != BPSF_OK) return st;
         int occ1 = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ1, persistent_kernel_ptr(full, debug, layered), block, smem);
+        e = blocks_per_sm(persistent_kernel_ptr(full, debug, layered), block, smem, &occ1);
         if (e != cudaSuccess) return bpsf_fail(BPSF_ECUDA, "occupancy query: %s", cudaGetErrorString(e));
         if (occ1 >= 1) {
             variant = full;

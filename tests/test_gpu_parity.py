@@ -340,6 +340,51 @@ def test_launch_shape_irregular_code():
         assert (got["iters"] == io).mean() >= CORR_MATCH, t
 
 
+def test_cuda_graph_replay_equals_eager():
+    """A decode recorded into a CUDA graph after a warm-up call (counter and
+    queue resets plus the persistent launch) replays to the eager results,
+    also after new syndromes are written into the recorded input buffer; the
+    same for a mixed-code launch."""
+    P = B.Params(max_iter=100, alpha=0.625, w=6, short_iter=20)
+    n = 3000
+    _, _, s1 = make_inputs("bb144", 0.07, n, 21)
+    _, _, s2 = make_inputs("bb144", 0.07, n, 22)
+    dec = decoder("bb144", 0.07, P)
+    refs = [gpu_decode(dec, s) for s in (s1, s2)]
+    synd = dev(pack(s1))
+    out = dec.outputs(n)
+    dec.decode(synd, out=out)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        dec.decode(synd, out=out, sync=False)
+    for s, ref in zip((s1, s2), refs):
+        synd.copy_(dev(pack(s)))
+        for v in out.values():
+            v.zero_()
+        g.replay()
+        torch.cuda.synchronize()
+        for key in ("corr", "conv", "iters", "stage"):
+            assert (out[key].cpu().numpy() == ref[key]).all(), key
+    # Two codes in one recorded launch.
+    _, _, s3 = make_inputs("bb72", 0.06, 1500, 23)
+    dec72 = decoder("bb72", 0.06, P)
+    synds = [dev(pack(s1)), dev(pack(s3))]
+    ref = B.decode_multi([dec, dec72], synds)
+    ref = [{k: v.clone() for k, v in o.items()} for o in ref]
+    outs = B.decode_multi([dec, dec72], synds)
+    g2 = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g2):
+        B.decode_multi([dec, dec72], synds, outs=outs, sync=False)
+    for o in outs:
+        for v in o.values():
+            v.zero_()
+    g2.replay()
+    torch.cuda.synchronize()
+    for o, r in zip(outs, ref):
+        for key in r:
+            assert torch.equal(o[key], r[key]), key
+
+
 def test_plain_form_equals_batched_form():
     P = B.Params(max_iter=100, alpha=0.625, w=6, short_iter=20)
     oc, e, s = make_inputs("bb144", 0.07, 300, 6)
