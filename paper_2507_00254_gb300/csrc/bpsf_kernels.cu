@@ -632,6 +632,129 @@ __device__ __forceinline__ void layered_iteration(const StreamDev &sd, const Lay
     }
 }
 
+// Layered schedule with V adjacent slots per lane (the slots' words are
+// adjacent in the interleaved layout): the same row and posterior updates as
+// layered_row, on V slots at once with vector loads and stores.  Slots of the
+// group that are not running compute on stale values; their results are
+// never read (a slot's messages and posterior are set up again when it takes
+// its next item).
+template <int DC, int V>
+__device__ __forceinline__ void layered_row_vec(const CodeDev &cd, const LayoutMem &L, const TeamMem &T, int lgQ, int j,
+                                                int q, const float (&alpha)[V]) {
+    typedef typename VecF<V>::T VT;
+    const int M = cd.Mp, MQ = cd.Mp << lgQ;  // rank stride of the active layout (in V-slot groups: MQ)
+    const int deg = (int)L.row_deg[j];
+    VT *mj = reinterpret_cast<VT *>(T.m) + (j << lgQ) + q;  // edge k of row j at (k*M + j)*Q + q
+    VT *pv = reinterpret_cast<VT *>(T.post) + q;             // posterior of variable i at i*Q + q
+    VT qv[DC];
+#pragma unroll
+    for (int k = 0; k < DC; ++k) {
+        if (k < deg) {
+            const VT lp = pv[(int)__ldg(cd.pos_var + k * M + j) << lgQ], r = mj[k * MQ];
+#pragma unroll
+            for (int c = 0; c < V; ++c) comp<V>(qv[k], c) = __fsub_rn(compc<V>(lp, c), compc<V>(r, c));
+        }
+    }
+    const int b0 = (j << (lgQ + (V == 4 ? 2 : 1))) + V * q;  // syndrome bit of row j, first slot of the group
+    const unsigned sb = T.syn[b0 >> 5] >> (b0 & 31);
+    float m1[V], m2[V];
+    unsigned sx[V];
+#pragma unroll
+    for (int c = 0; c < V; ++c) {
+        m1[c] = __int_as_float(0x7f800000);
+        m2[c] = m1[c];
+        sx[c] = ((sb >> c) & 1u) << 31;
+    }
+#pragma unroll
+    for (int k = 0; k < DC; ++k) {
+        if (k < deg) {
+#pragma unroll
+            for (int c = 0; c < V; ++c) {
+                const float a = fabsf(compc<V>(qv[k], c));
+                m2[c] = fminf(m2[c], fmaxf(m1[c], a));
+                m1[c] = fminf(m1[c], a);
+                sx[c] ^= __float_as_uint(compc<V>(qv[k], c));
+            }
+        }
+    }
+    unsigned g1[V], g2[V];
+#pragma unroll
+    for (int c = 0; c < V; ++c) {
+        sx[c] &= 0x80000000u;
+        g1[c] = __float_as_uint(fminf(__fmul_rn(alpha[c], m1[c]), kMagClamp)) | sx[c];
+        g2[c] = __float_as_uint(fminf(__fmul_rn(alpha[c], m2[c]), kMagClamp)) | sx[c];
+    }
+#pragma unroll
+    for (int k = 0; k < DC; ++k) {
+        if (k < deg) {
+            VT r, np;
+#pragma unroll
+            for (int c = 0; c < V; ++c) {
+                const float x = compc<V>(qv[k], c);
+                comp<V>(r, c) = __uint_as_float(((fabsf(x) == m1[c]) ? g2[c] : g1[c]) ^ (__float_as_uint(x) & 0x80000000u));
+                comp<V>(np, c) = __fadd_rn(x, compc<V>(r, c));
+            }
+            mj[k * MQ] = r;
+            pv[(int)__ldg(cd.pos_var + k * M + j) << lgQ] = np;  // the variable is read again: fewer live registers
+        }
+    }
+}
+
+template <int DC, int DVS, int DVX, bool DEBUG, int V>
+__device__ __forceinline__ void layered_iteration_vec(const StreamDev &sd, const LayoutMem &L, const TeamMem &T,
+                                                      int lgS, unsigned onm, const float (&alpha)[V], unsigned initm,
+                                                      int tid, int nthreads, int W, int bar_id) {
+    typedef typename VecF<V>::T VT;
+    typedef typename VecF<V>::U UT;
+    const CodeDev &cd = sd.code;
+    const int lgQ = lgS - (V == 4 ? 2 : 1);
+    const int q = tid & ((1 << lgQ) - 1);  // the lane's slot group: slots V*q .. V*q + V-1
+    const int s0 = V * q;
+    for (int layer = 0; layer < cd.n_layers; ++layer) {
+        const int r0 = (int)__ldg(cd.layer_ptr + layer), r1 = (int)__ldg(cd.layer_ptr + layer + 1);
+        const int total = (r1 - r0) << lgQ;
+        if (onm)
+            for (int tauv = tid; tauv < total; tauv += nthreads)
+                layered_row_vec<DC, V>(cd, L, T, lgQ, (int)__ldg(cd.layer_rows + r0 + (tauv >> lgQ)), q, alpha);
+        team_sync(W, bar_id);
+    }
+    if (!onm) return;
+    const int N = cd.N;
+    const VT *pv = reinterpret_cast<const VT *>(T.post);
+    UT *fv = reinterpret_cast<UT *>(T.flips);
+    for (int tauv = tid; tauv < (N << lgQ); tauv += nthreads) {
+        const int i = tauv >> lgQ;
+        const VT lo = pv[tauv];
+        const UT fw = fv[tauv];
+        const uint16_t *fh = reinterpret_cast<const uint16_t *>(&fw);
+        unsigned bm = 0;
+#pragma unroll
+        for (int c = 0; c < V; ++c) {
+            const unsigned eb = (compc<V>(lo, c) <= 0.f) ? 1u : 0u;
+            if (((onm >> c) & 1u) && (((unsigned)fh[c] >> 15) & 1u) != eb) bm |= 1u << c;
+            if (DEBUG && sd.dbg.lout && ((onm >> c) & 1u) && ((initm >> (s0 + c)) & 1u))
+                sd.dbg.lout[T.st[s0 + c].shot * N + i] = compc<V>(lo, c);
+        }
+        if (bm) {
+            UT nw = fw;
+            uint16_t *nh = reinterpret_cast<uint16_t *>(&nw);
+#pragma unroll
+            for (int c = 0; c < V; ++c)
+                if ((bm >> c) & 1u) nh[c] = (uint16_t)((((unsigned)nh[c]) ^ 0x8000u) + 1u);
+            fv[tauv] = nw;
+            const uint16_t *vc = cd.vchk + i * DVS;
+#pragma unroll
+            for (int k = 0; k < DVS; ++k) {
+                const int c = (int)__ldg(vc + k);
+                if (DVX > 0 ? (k < DVX) : (c != 0xffff)) {
+                    const int b = (c << lgS) + s0;
+                    atomicXor(&T.mism[b >> 5], bm << (b & 31));
+                }
+            }
+        }
+    }
+}
+
 // Bits b of a 32-bit word with b = s (mod S): the residual-syndrome bits
 // of slot s when shifted left by s (S is a power of two dividing 32).
 __device__ __forceinline__ unsigned slot_pattern(int S) {
@@ -802,6 +925,8 @@ __device__ void team_loop(const StreamDev &sd, const LayoutMem &L, const TeamMem
     constexpr bool kVec = BPSF_PAIRS && DC <= 16;  // the widest rows keep one slot per lane (registers)
     // Four slots per lane: exact-degree rows with the full register budget (one block).
     constexpr bool kVec4 = kVec && MINB == 1 && DVX == 3 && BPSF_VEC >= 4;
+    // Layered schedule: vector lanes in the full-register instances only.
+    constexpr bool kLayV2 = LAY && kVec && MINB == 1 && DC <= 6, kLayV4 = kLayV2 && kVec4;
     unsigned long long idle_since = 0;
     unsigned last_beat = 0;
     for (;;) {
@@ -847,9 +972,25 @@ __device__ void team_loop(const StreamDev &sd, const LayoutMem &L, const TeamMem
         if (ex) break;
         if (run == 0u) continue;
         if (LAY && cd.layered) {
-            const bool lane_on = (run >> my_slot) & 1u;
-            layered_iteration<DC, DVS, DVX, DEBUG>(sd, L, T, lgS, lane_on, damping(cd, T.st[my_slot].iter + 1), initm,
-                                                   tid, nthreads, W, bar_id);
+            if (kLayV4 && S >= 4) {
+                const int s0 = 4 * (lane & ((S >> 2) - 1));
+                float al[4];
+#pragma unroll
+                for (int c = 0; c < 4; ++c) al[c] = damping(cd, T.st[s0 + c].iter + 1);
+                layered_iteration_vec<DC, DVS, DVX, DEBUG, 4>(sd, L, T, lgS, (run >> s0) & 0xfu, al, initm, tid,
+                                                              nthreads, W, bar_id);
+            } else if (kLayV2 && S >= 2) {
+                const int s0 = 2 * (lane & ((S >> 1) - 1));
+                float al[2];
+                al[0] = damping(cd, T.st[s0].iter + 1);
+                al[1] = damping(cd, T.st[s0 + 1].iter + 1);
+                layered_iteration_vec<DC, DVS, DVX, DEBUG, 2>(sd, L, T, lgS, (run >> s0) & 0x3u, al, initm, tid,
+                                                              nthreads, W, bar_id);
+            } else {
+                const bool lane_on = (run >> my_slot) & 1u;
+                layered_iteration<DC, DVS, DVX, DEBUG>(sd, L, T, lgS, lane_on, damping(cd, T.st[my_slot].iter + 1),
+                                                       initm, tid, nthreads, W, bar_id);
+            }
             team_sync(W, bar_id);
         } else if (kVec4 && S >= 4) {
             const int s0 = 4 * (lane & ((S >> 2) - 1));
