@@ -131,3 +131,14 @@ def test_null_context_is_rejected():
     assert L.bpsf_decode(None, 1, None, 1, None, 1, None, None, None, None) == B.BPSF_EINVAL
     assert L.bpsf_sync(None, None) == B.BPSF_EINVAL
     assert L.bpsf_num_trials(None) == -1
+
+
+def test_multi_job_calls_reject_bad_job_lists():
+    """bpsf_decode_multi and bpsf_decode_multi_host check the job list before any device work."""
+    L = B.lib()
+    for fn in (L.bpsf_decode_multi, L.bpsf_decode_multi_host):
+        assert fn(0, None, None) == B.BPSF_EINVAL
+        one = (B.bpsf_job * 1)(B.bpsf_job(None, 1, None, 1, None, 1, None, None, None))
+        assert fn(1, one, None) == B.BPSF_EINVAL  # NULL context
+        many = (B.bpsf_job * 17)()
+        assert fn(17, many, None) == B.BPSF_EINVAL  # more than 16 jobs
