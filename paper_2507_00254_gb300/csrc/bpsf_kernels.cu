@@ -379,6 +379,21 @@ template <int V> struct VecF;
 template <> struct VecF<2> { typedef float2 T; typedef uint32_t U; };  // U holds V 16-bit flip words
 template <> struct VecF<4> { typedef float4 T; typedef uint2 U; };
 
+// Decision bits (bit 15 of each 16-bit word) of packed flip words, as a mask
+// with bit c for slot c.
+__device__ __forceinline__ unsigned decision_mask(uint32_t w) { return ((w >> 15) & 1u) | ((w >> 30) & 2u); }
+__device__ __forceinline__ unsigned decision_mask(uint2 w) { return decision_mask(w.x) | (decision_mask(w.y) << 2); }
+
+// Toggle the decision and add one flip in the words selected by mask bm.  A
+// count is below max_iter <= 32767 before the increment, so no carry leaves
+// its 15 bits.
+__device__ __forceinline__ uint32_t flip_words(uint32_t w, unsigned bm) {
+    return (w ^ (((bm & 1u) << 15) | ((bm & 2u) << 30))) + ((bm & 1u) | ((bm & 2u) << 15));
+}
+__device__ __forceinline__ uint2 flip_words(uint2 w, unsigned bm) {
+    return make_uint2(flip_words(w.x, bm & 3u), flip_words(w.y, bm >> 2));
+}
+
 template <int V>
 __device__ __forceinline__ float &comp(typename VecF<V>::T &v, int c) { return reinterpret_cast<float *>(&v)[c]; }
 template <int V>
@@ -479,7 +494,6 @@ __device__ __forceinline__ void v_phase_vec(const StreamDev &sd, const LayoutMem
         for (int k = 0; k < DVS; ++k)
             if (DVX > 0 ? (k < DVX) : (pos[k] != 0xffffu)) r[k] = mv[(int)pos[k] << lgQ];
         const UT fw = fv[tauv];
-        const uint16_t *fh = reinterpret_cast<const uint16_t *>(&fw);
         float lo[V];
         if (DVX == 3) {
             VT q0, q1, q2;
@@ -518,22 +532,18 @@ __device__ __forceinline__ void v_phase_vec(const StreamDev &sd, const LayoutMem
 #pragma unroll
                     for (int c = 0; c < V; ++c) lo[c] = __fadd_rn(lo[c], compc<V>(r[k], c));
         }
-        // Decision (bit 15) and flip count of each slot's 16-bit word.
-        unsigned bm = 0;
+        // Decision (bit 15) and flip count of each slot's 16-bit word: the
+        // running slots whose decision changed, as a mask.
+        unsigned em = 0;
 #pragma unroll
         for (int c = 0; c < V; ++c) {
-            const unsigned eb = (lo[c] <= 0.f) ? 1u : 0u;
-            if (((onm >> c) & 1u) && (((unsigned)fh[c] >> 15) & 1u) != eb) bm |= 1u << c;
+            em |= ((lo[c] <= 0.f) ? 1u : 0u) << c;
             if (DEBUG && sd.dbg.lout && ((onm >> c) & 1u) && ((initm >> (s0 + c)) & 1u))
                 sd.dbg.lout[T.st[s0 + c].shot * cd.N + i] = lo[c];
         }
+        const unsigned bm = (em ^ decision_mask(fw)) & onm;
         if (bm) {
-            UT nw = fw;
-            uint16_t *nh = reinterpret_cast<uint16_t *>(&nw);
-#pragma unroll
-            for (int c = 0; c < V; ++c)
-                if ((bm >> c) & 1u) nh[c] = (uint16_t)((((unsigned)nh[c]) ^ 0x8000u) + 1u);
-            fv[tauv] = nw;
+            fv[tauv] = flip_words(fw, bm);
             const uint16_t *vc = cd.vchk + i * DVS;
 #pragma unroll
             for (int k = 0; k < DVS; ++k) {
@@ -726,22 +736,16 @@ __device__ __forceinline__ void layered_iteration_vec(const StreamDev &sd, const
         const int i = tauv >> lgQ;
         const VT lo = pv[tauv];
         const UT fw = fv[tauv];
-        const uint16_t *fh = reinterpret_cast<const uint16_t *>(&fw);
-        unsigned bm = 0;
+        unsigned em = 0;
 #pragma unroll
         for (int c = 0; c < V; ++c) {
-            const unsigned eb = (compc<V>(lo, c) <= 0.f) ? 1u : 0u;
-            if (((onm >> c) & 1u) && (((unsigned)fh[c] >> 15) & 1u) != eb) bm |= 1u << c;
+            em |= ((compc<V>(lo, c) <= 0.f) ? 1u : 0u) << c;
             if (DEBUG && sd.dbg.lout && ((onm >> c) & 1u) && ((initm >> (s0 + c)) & 1u))
                 sd.dbg.lout[T.st[s0 + c].shot * N + i] = compc<V>(lo, c);
         }
+        const unsigned bm = (em ^ decision_mask(fw)) & onm;
         if (bm) {
-            UT nw = fw;
-            uint16_t *nh = reinterpret_cast<uint16_t *>(&nw);
-#pragma unroll
-            for (int c = 0; c < V; ++c)
-                if ((bm >> c) & 1u) nh[c] = (uint16_t)((((unsigned)nh[c]) ^ 0x8000u) + 1u);
-            fv[tauv] = nw;
+            fv[tauv] = flip_words(fw, bm);
             const uint16_t *vc = cd.vchk + i * DVS;
 #pragma unroll
             for (int k = 0; k < DVS; ++k) {
