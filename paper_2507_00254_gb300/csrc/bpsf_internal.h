@@ -28,12 +28,12 @@ enum : unsigned {
 };
 
 // One code's Tanner graph in the order the kernels read it, plus the
-// decoder constants.  Messages of one work item live in one array of
-// P = DC * M floats: the edge of rank k in row j (CSR order) sits at
-// position k * M + j, so a check-node thread reads and writes its row at
-// stride M (one word per bank for consecutive rows).  vpos lists, for each
-// column, the positions of its edges in ascending check order (the order the
-// V2C and posterior sums are folded in).
+// decoder constants.  Messages of one work item live in one array of P
+// floats, one position per edge, given by the layout of the launch's slot
+// count (LayoutS): a check-node thread reads and writes its row at stride Mp
+// (one word per bank for consecutive rows).  vpos lists, for each column,
+// the positions of its edges in ascending check order (the order the V2C and
+// posterior sums are folded in).
 // Message layout for one slot count S = 1 << index: edge of row j with
 // rank r sits at position r*Mp + j (Mp >= M, P = dc_max * Mp positions); the
 // rank stride and the rank of each edge within its row are chosen at create

@@ -260,7 +260,7 @@ __device__ __forceinline__ void c_phase(const CodeDev &cd, const LayoutMem &L, c
 // ---------------------------------------------------------------------------
 template <int DVS>
 struct VTask {
-    uint16_t pos[DVS];  // edge positions k*M + j of the column's checks
+    uint16_t pos[DVS];  // edge positions r*Mp + j of the column's checks
     float r[DVS];
     float lc;
     unsigned f;  // decision (bit 15) and flip count of (variable, slot)
