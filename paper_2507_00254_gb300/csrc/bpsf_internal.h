@@ -285,6 +285,14 @@ __host__ __device__ inline int block_smem_bytes(int M, int N, int P, int Ws, int
            teams * team_offsets(S, M, N, P, Ws, layered).total;
 }
 
+// Arguments of one persistent launch: the streams (codes) it serves, by value.
+struct KernelParams {
+    StreamDev streams[kMaxStreams];
+    int n_streams;
+    int Q;
+    unsigned long long wait_ns;
+};
+
 // Kernel entry points (bpsf_kernels.cu).
 int kernel_variant(int dc_max, int dv_max);  // smallest variant that fits, -1 if none
 int kernel_variant_dv(int variant);          // column table width of a variant
