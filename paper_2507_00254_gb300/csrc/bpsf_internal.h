@@ -194,16 +194,16 @@ struct SlotState {
     int pad;
     long long shot;  // shot index in the job (global sequence number when serving)
     long long cancel;  // manager -> team: shot * n_trials + kidx + 1 of a trial run that cannot win
-    uint16_t phi[kMaxW];  // trial run: the bits its trial vector flips, 0xffff-terminated
 };
-static_assert(sizeof(SlotState) == 80, "slot state is 80 bytes");
+static_assert(sizeof(SlotState) == 48, "slot state is 48 bytes");
 
-// A finished run's facts, handed from the team to the manager (64 bytes;
+// A finished run's facts, handed from the team to the manager (32 bytes;
 // the packed hard decision goes with it in the team's ebits words).  The
 // team fills an outbox whose flag is 0 and then sets it; the manager writes
-// the results out and clears it.  phi: a trial run's flipped bits
-// (0xffff-terminated); a failed initial run's Phi = top(flip_count, w) goes
-// to the shot's record directly.
+// the results out and clears it.  A failed initial run's Phi =
+// top(flip_count, w) goes to the shot's record directly; a trial's flipped
+// bits are the record's Phi[j] that the trial mask selects, so neither the
+// items nor the outboxes carry them.
 struct OutBox {
     int full;
     int kind;
@@ -212,9 +212,8 @@ struct OutBox {
     int iter;
     int pad;
     long long shot;
-    uint16_t phi[kMaxW];
 };
-static_assert(sizeof(OutBox) == 64, "outbox is 64 bytes");
+static_assert(sizeof(OutBox) == 32, "outbox is 32 bytes");
 
 // Team control block (32 bytes).
 struct TeamCtl {
@@ -224,18 +223,17 @@ struct TeamCtl {
     unsigned long long cap;    // team iterations with a running slot, times S
 };
 
-// Work items of the manager's ready queue and of the slots' inboxes: 48
-// bytes of fields plus Ws syndrome words.  kind 1 = initial run of a shot,
+// Work items of the manager's ready queue and of the slots' inboxes: 16
+// bytes of fields plus Ws syndrome words (a trial's words are s' = s xor t H^T).  kind 1 = initial run of a shot,
 // 2 = trial run, 0 = nothing to run (an item dropped after a timed-out wait).
 struct QEntry {
     int kind;
     int kidx;
     long long shot;
-    uint16_t phi[kMaxW];  // trial run: the bits its trial vector flips, 0xffff-terminated
 };
-static_assert(sizeof(QEntry) == 48, "queue entry header is 48 bytes");
+static_assert(sizeof(QEntry) == 16, "queue entry header is 16 bytes");
 
-__host__ __device__ inline int qentry_bytes(int Ws) { return align_up(48 + 4 * Ws, 16); }
+__host__ __device__ inline int qentry_bytes(int Ws) { return align_up((int)sizeof(QEntry) + 4 * Ws, 16); }
 
 // Per-team shared memory.  The S slots of a team (S a power of two <= 32)
 // are interleaved: item x of slot s sits at x*S + s, so lane l always serves
@@ -264,8 +262,8 @@ __host__ __device__ inline TeamOffsets team_offsets(int S, int M, int N, int P, 
     const int sw = (S * M + 31) / 32;
     int p = 0;
     o.ctl = p;     p += 32;
-    o.state = p;   p += 80 * S;
-    o.outbox = p;  p += 64 * S;
+    o.state = p;   p += (int)sizeof(SlotState) * S;
+    o.outbox = p;  p += (int)sizeof(OutBox) * S;
     o.syn = p;     p += 4 * sw;
     o.mism = p;    p += 4 * sw;
     o.ebits = p;   p += 4 * S * ((N + 31) / 32);

@@ -817,8 +817,6 @@ __device__ __forceinline__ void team_pack(const StreamDev &sd, const TeamMem &T,
             thr = best;
         }
         __threadfence();
-    } else if (lane < kMaxW) {
-        ob->phi[lane] = ss->phi[lane];  // a trial's flipped bits, for the undo
     }
     if (DEBUG && kind == 1 && sd.dbg.flips)
         for (int i = lane; i < N; i += 32)
@@ -846,7 +844,7 @@ __device__ __forceinline__ void team_install(const StreamDev &sd, const LayoutMe
                                              int lane) {
     const CodeDev &cd = sd.code;
     const QEntry *e = reinterpret_cast<const QEntry *>(T.ib + s * T.ibstride);
-    const uint32_t *src = reinterpret_cast<const uint32_t *>(T.ib + s * T.ibstride + 48);
+    const uint32_t *src = reinterpret_cast<const uint32_t *>(T.ib + s * T.ibstride + sizeof(QEntry));
     SlotState *ss = &T.st[s];
     volatile uint32_t *vsyn = T.syn, *vmism = T.mism;
     for (int j = lane; j < cd.M; j += 32) {
@@ -868,7 +866,6 @@ __device__ __forceinline__ void team_install(const StreamDev &sd, const LayoutMe
         ss->kind = e->kind;
         ss->kidx = e->kidx;
         ss->shot = e->shot;
-        for (int j = 0; j < kMaxW; ++j) ss->phi[j] = e->phi[j];
         ss->iter = 0;
         ss->outcome = 0;
         ss->cancel = 0;
@@ -1072,7 +1069,7 @@ __device__ __forceinline__ QEntry *qentry(unsigned char *q, int idx, int stride)
 }
 
 __device__ __forceinline__ uint32_t *qsyn(QEntry *e) {
-    return reinterpret_cast<uint32_t *>(reinterpret_cast<unsigned char *>(e) + 48);
+    return reinterpret_cast<uint32_t *>(reinterpret_cast<unsigned char *>(e) + sizeof(QEntry));
 }
 
 // Word w of finished slot s's hard decision (packed by its team).
@@ -1150,18 +1147,17 @@ __device__ __forceinline__ void finalize_simple(const StreamDev &sd, TeamMem T, 
     // Trial run: undo the flip (Algorithm 1) and take part in the selection.
     const int C = cd.n_trials, kidx = ss->kidx;
     if (conv) {
-        unsigned wsum = 0;
+        // e' xor t: t flips the record's Phi[j] for the bits j of the trial's mask.
         uint32_t *dst = sd.rec.corr + ((long long)row * C + kidx) * Wn;
-        for (int w = 0; w < Wn; ++w) {
-            unsigned v = slot_word(T.ebits, Wn, s, w);
-            for (int j = 0; j < kMaxW; ++j) {  // the bits t flips, 0xffff-terminated
-                const int b = ss->phi[j];
-                if (b == 0xffff) break;
-                if ((b >> 5) == w) v ^= 1u << (b & 31);
-            }
-            dst[w] = v;
-            wsum += __popc(v);
+        for (int w = 0; w < Wn; ++w) dst[w] = slot_word(T.ebits, Wn, s, w);
+        const unsigned long long mask = __ldg(cd.trial_mask + kidx);
+        for (int j = 0; j < cd.w; ++j) {
+            if (!((mask >> j) & 1ull)) continue;
+            const int b = __ldcg(sd.rec.phi + row * cd.w + j);
+            dst[b >> 5] ^= 1u << (b & 31);
         }
+        unsigned wsum = 0;
+        for (int w = 0; w < Wn; ++w) wsum += __popc(dst[w]);
         sd.rec.iters[(long long)row * C + kidx] = (int16_t)iter;
         __threadfence();
         const unsigned long long key =
@@ -1281,18 +1277,14 @@ __device__ __forceinline__ bool prefetch(const StreamDev &sd, unsigned char *qba
                 e->kind = 2;
                 e->kidx = kidx;
                 e->shot = shot;
-                // The trial vector t: the bits Phi[j] its mask selects (at most
-                // kMaxW), listed in the item and terminated by 0xffff.
+                // The trial vector t: the bits Phi[j] its mask selects.
                 const unsigned long long mask = __ldg(cd.trial_mask + kidx);
-                int cnt = 0;
-                for (int j = 0; j < cd.w; ++j)
-                    if (((mask >> j) & 1ull) && cnt < kMaxW) e->phi[cnt++] = (uint16_t)__ldcg(sd.rec.phi + row * cd.w + j);
-                for (int j = cnt; j < kMaxW; ++j) e->phi[j] = 0xffff;
                 uint32_t *sy = qsyn(e);
                 for (int w = 0; w < Ws; ++w) sy[w] = __ldcg(sd.rec.synd + row * Ws + w);
                 // s' = s xor t H^T (Algorithm 1): flip the checks of every selected bit.
-                for (int j = 0; j < cnt; ++j) {
-                    const int v = e->phi[j];
+                for (int j = 0; j < cd.w; ++j) {
+                    if (!((mask >> j) & 1ull)) continue;
+                    const int v = __ldcg(sd.rec.phi + row * cd.w + j);
                     for (int k = 0; k < cd.vstride; ++k) {
                         const int c = __ldg(cd.vchk + v * cd.vstride + k);
                         if (c == 0xffff) break;
@@ -1351,7 +1343,6 @@ __device__ __forceinline__ bool prefetch(const StreamDev &sd, unsigned char *qba
             e->kind = 1;
             e->kidx = 0;
             e->shot = shot;
-            for (int j = 0; j < kMaxW; ++j) e->phi[j] = 0;
             const uint32_t *src = sd.job.synd + row * sd.job.synd_stride;
             uint32_t *sy = qsyn(e);
             for (int w = 0; w < Ws; ++w) sy[w] = __ldcg(src + w);
