@@ -90,8 +90,9 @@ bpsf_status bpsf_ensure_kernel_attrs(int variant, int smem_optin) {
     for (int k4 = 0; k4 < 4; ++k4) {  // debug x layered instances
         const int k = variant * 4 + k4;
         if (done[k]) continue;
-        cudaError_t e = cudaFuncSetAttribute(persistent_kernel_ptr(variant, (k4 & 1) != 0, (k4 & 2) != 0),
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin);
+        const void *fn = persistent_kernel_ptr(variant, (k4 & 1) != 0, (k4 & 2) != 0);
+        if (!fn) continue;  // an instance the variant does not have
+        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin);
         if (e != cudaSuccess) return bpsf_fail(BPSF_ECUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(e));
         done[k] = true;
     }
@@ -106,8 +107,9 @@ bpsf_status bpsf_ensure_kernel_attrs(int variant, int smem_optin) {
 // queue only covers claim batches.
 static int plan_queue(int teams, int S) { return std::min(32, std::max(16, teams * S / 2)); }
 
-static int plan_smem(const bpsf_ctx *c, int vstride, int S, int teams, int Q) {
-    return block_smem_bytes(c->M, c->N, c->code.lay[layout_index(S)].P, c->Ws, vstride, S, teams, Q, c->code.layered);
+static int plan_smem(const bpsf_ctx *c, int vstride, int S, int teams, int Q, int fb = 2) {
+    return block_smem_bytes(c->M, c->N, c->code.lay[layout_index(S)].P, c->Ws, vstride, S, teams, Q, c->code.layered,
+                            fb);
 }
 
 static bpsf_status check_shape(const bpsf_tuning &t) {
@@ -169,32 +171,50 @@ bpsf_status bpsf_make_plan(bpsf_ctx *const *codes, int n_codes, const bpsf_tunin
     for (int k = 0; k < n_codes; ++k)
         Q = std::max(Q, plan_queue(tunes[k].warps_per_block / tunes[k].warps_per_team, tunes[k].slots_per_team));
     // Team shape per code: its own tuning; when shrinking, fewer slots per
-    // team first, then fewer teams, until the code's block fits.
+    // team first, then fewer teams, until the code's block fits.  fb: bytes
+    // per flip word of the instance the sizes are for.
     int smem = 0;
-    for (int k = 0; k < n_codes; ++k) {
+    for (int k = 0; k < n_codes; ++k)
         if (codes[k]->vstride != vstride)
             return bpsf_fail(BPSF_EINVAL, "codes of one launch need the same column table width (%d vs %d)",
                              codes[k]->vstride, vstride);
-        const int W = tunes[k].warps_per_team;
-        int S = tunes[k].slots_per_team, teams = tunes[k].warps_per_block / W;
-        while (shrink && plan_smem(codes[k], vstride, S, teams, Q) > c0->smem_optin) {
-            if (S > 1)
-                S >>= 1;
-            else if (teams > 1)
-                --teams;
-            else
-                break;
+    auto size_codes = [&](int fb, bool allow_shrink) -> bool {
+        smem = 0;
+        for (int k = 0; k < n_codes; ++k) {
+            const int W = tunes[k].warps_per_team;
+            int S = tunes[k].slots_per_team, teams = tunes[k].warps_per_block / W;
+            while (allow_shrink && plan_smem(codes[k], vstride, S, teams, Q, fb) > c0->smem_optin) {
+                if (S > 1)
+                    S >>= 1;
+                else if (teams > 1)
+                    --teams;
+                else
+                    break;
+            }
+            const int need = plan_smem(codes[k], vstride, S, teams, Q, fb);
+            if (need > c0->smem_optin) return false;
+            out->S_code[k] = S;
+            out->W_code[k] = W;
+            out->teams_code[k] = teams;
+            smem = std::max(smem, need);
         }
-        const int need = plan_smem(codes[k], vstride, S, teams, Q);
-        if (need > c0->smem_optin)
-            return bpsf_fail(BPSF_EINVAL, "launch shape needs %d bytes of shared memory (limit %d)", need,
-                             c0->smem_optin);
-        if (W > 1 && teams > kMaxNamedTeams) return bpsf_fail(BPSF_EINVAL, "too many multi-warp teams");
-        out->S_code[k] = S;
-        out->W_code[k] = W;
-        out->teams_code[k] = teams;
-        smem = std::max(smem, need);
+        return true;
+    };
+    // One-byte flip words fit a shape that two-byte words do not: every code is
+    // of the exact (6, 4, 3) variant with max_iter <= 127 and none is layered.
+    bool byte_flips_ok = kernel_variant_byte_flips(variant) >= 0 && !layered;
+    for (int k = 0; k < n_codes; ++k) byte_flips_ok = byte_flips_ok && codes[k]->p.max_iter <= 127;
+    bool byte_flips = false;
+    if (!size_codes(2, false)) {
+        if (byte_flips_ok && size_codes(1, false))
+            byte_flips = true;
+        else if (!(shrink && size_codes(2, true)))
+            return bpsf_fail(BPSF_EINVAL, "launch shape needs more than %d bytes of shared memory", c0->smem_optin);
     }
+    for (int k = 0; k < n_codes; ++k)
+        if (out->W_code[k] > 1 && out->teams_code[k] > kMaxNamedTeams)
+            return bpsf_fail(BPSF_EINVAL, "too many multi-warp teams");
+    if (byte_flips) variant = kernel_variant_byte_flips(variant);
     bpsf_status st = bpsf_ensure_kernel_attrs(variant, c0->smem_optin);
     if (st != BPSF_OK) return st;
     const int block = 32 * (B + 1);
@@ -1137,7 +1157,7 @@ extern "C" bpsf_status bpsf_autotune(bpsf_ctx *c, double p_sample, int64_t n_sam
     bpsf_status st = BPSF_OK;
     const int Ws_[] = {1, 2, 4, 8};
     const int Ss_[] = {1, 2, 4, 8, 16, 32};
-    const int Bs_[] = {1, 2, 3, 4, 6, 7, 8, 10, 12, 14, 15};
+    const int Bs_[] = {1, 2, 3, 4, 6, 7, 8, 10, 12, 13, 14, 15};
     bpsf_ctx *cs1[1] = {c};
     for (int W : Ws_)
         for (int S : Ss_)

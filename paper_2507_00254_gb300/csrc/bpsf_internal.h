@@ -242,10 +242,10 @@ __host__ __device__ inline int qentry_bytes(int Ws) { return align_up((int)sizeo
 //               of slot s, in (S*M + 31)/32 words each
 //   ebits     : S x Wn words, the hard decision of a finished run, packed
 //               (part of the slot's outbox)
-//   flips     : 16-bit word i*S + s = decision (bit 15) and flip count of
-//               variable i in slot s
-//   m         : float k*S + s = the message of edge position k = r*M + j
-//               (r-th edge of row j) in slot s: V2C and C2V alternately
+//   flips     : flip word i*S + s (fb bytes) = decision (top bit) and flip
+//               count of variable i in slot s
+//   m         : float k*S + s = the message of edge position k = r*Mp + j
+//               (edge of row j with rank r) in slot s: V2C and C2V alternately
 //   outbox    : S OutBox entries
 //   inflag    : S flags, 1 while the slot's inbox holds an item
 //   inbox     : S work items (qentry_bytes(Ws) each), filled by the manager
@@ -257,7 +257,7 @@ struct TeamOffsets {
     int ctl, state, syn, mism, ebits, flips, m, outbox, inflag, inbox, ibstride, post, total;
 };
 
-__host__ __device__ inline TeamOffsets team_offsets(int S, int M, int N, int P, int Ws, int layered) {
+__host__ __device__ inline TeamOffsets team_offsets(int S, int M, int N, int P, int Ws, int layered, int fb = 2) {
     TeamOffsets o;
     const int sw = (S * M + 31) / 32;
     int p = 0;
@@ -270,7 +270,7 @@ __host__ __device__ inline TeamOffsets team_offsets(int S, int M, int N, int P, 
     o.inflag = p;  p = align_up(p + 4 * S, 16);
     o.ibstride = qentry_bytes(Ws);
     o.inbox = p;   p += o.ibstride * S;
-    o.flips = p;   p = align_up(p + 2 * S * N, 16);
+    o.flips = p;   p = align_up(p + fb * S * N, 16);
     o.m = p;       p += 4 * S * P;
     o.post = p;    p += layered ? 4 * S * N : 0;
     o.total = align_up(p, 16);
@@ -278,9 +278,9 @@ __host__ __device__ inline TeamOffsets team_offsets(int S, int M, int N, int P, 
 }
 
 __host__ __device__ inline int block_smem_bytes(int M, int N, int P, int Ws, int vstride, int S, int teams, int Q,
-                                                int layered) {
+                                                int layered, int fb = 2) {
     return kBlockHeaderBytes + layout_offsets(M, N, vstride, P).total + Q * qentry_bytes(Ws) +
-           teams * team_offsets(S, M, N, P, Ws, layered).total;
+           teams * team_offsets(S, M, N, P, Ws, layered, fb).total;
 }
 
 // Arguments of one persistent launch: the streams (codes) it serves, by value.
@@ -295,6 +295,7 @@ struct KernelParams {
 int kernel_variant(int dc_max, int dv_max);  // smallest variant that fits, -1 if none
 int kernel_variant_dv(int variant);          // column table width of a variant
 int kernel_variant_full_regs(int variant);   // its one-block, full-register instance
+int kernel_variant_byte_flips(int variant);  // its one-block instance with one-byte flip words, -1 if none
 const void *persistent_kernel_ptr(int variant, bool debug, bool layered);
 void launch_persistent(int variant, bool debug, bool layered, int grid, int block, int smem, const LaunchArgs &args,
                        void *stream);

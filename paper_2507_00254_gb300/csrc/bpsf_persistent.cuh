@@ -112,7 +112,7 @@ struct TeamMem {
     TeamCtl *ctl;
     SlotState *st;
     uint32_t *syn, *mism, *ebits;
-    uint16_t *flips;
+    unsigned char *flips;  // flip words, FB bytes each (see FlipW)
     float *m;
     OutBox *ob;         // per slot: a finished run's facts for the manager
     int *ibf;           // per slot: 1 while the inbox holds an item
@@ -128,7 +128,7 @@ __device__ __forceinline__ TeamMem team_mem(unsigned char *tb, const TeamOffsets
     T.syn = reinterpret_cast<uint32_t *>(tb + to.syn);
     T.mism = reinterpret_cast<uint32_t *>(tb + to.mism);
     T.ebits = reinterpret_cast<uint32_t *>(tb + to.ebits);
-    T.flips = reinterpret_cast<uint16_t *>(tb + to.flips);
+    T.flips = tb + to.flips;
     T.m = reinterpret_cast<float *>(tb + to.m);
     T.ob = reinterpret_cast<OutBox *>(tb + to.outbox);
     T.ibf = reinterpret_cast<int *>(tb + to.inflag);
@@ -141,8 +141,22 @@ __device__ __forceinline__ TeamMem team_mem(unsigned char *tb, const TeamOffsets
 __device__ __forceinline__ volatile int *vstate(SlotState *s) { return reinterpret_cast<volatile int *>(&s->state); }
 __device__ __forceinline__ volatile int *vflag(int *f) { return reinterpret_cast<volatile int *>(f); }
 
-// Flip count of a (variable, slot) word: bits 0..14 (bit 15 is the decision).
-__device__ __forceinline__ unsigned flip_count(uint16_t f) { return (unsigned)f & 0x7fffu; }
+// Flip words: FB bytes per (variable, slot).  The top bit is the current hard
+// decision, the bits below it count its flips (Algorithm 1): up to 32767 in
+// two bytes, up to 127 in one (used only when max_iter <= 127).  Installing
+// a slot zeroes them (e = 0, count 0).
+template <int FB> struct FlipW;
+template <> struct FlipW<2> { typedef uint16_t W; };
+template <> struct FlipW<1> { typedef uint8_t W; };
+template <int FB>
+__device__ __forceinline__ typename FlipW<FB>::W *flipw(const TeamMem &T) {
+    return reinterpret_cast<typename FlipW<FB>::W *>(T.flips);
+}
+template <int FB> __device__ __forceinline__ unsigned flip_dec(unsigned f) { return (f >> (8 * FB - 1)) & 1u; }
+template <int FB> __device__ __forceinline__ unsigned flip_count(unsigned f) { return f & ((1u << (8 * FB - 1)) - 1u); }
+// Toggle the decision and count one flip (the count is below max_iter before
+// the increment, so no carry reaches the decision bit).
+template <int FB> __device__ __forceinline__ unsigned flip_bump(unsigned f) { return (f ^ (1u << (8 * FB - 1))) + 1u; }
 
 // ---------------------------------------------------------------------------
 // C phase: check-node update, Eq. (c2v).  For row j with V2C inputs q_k:
@@ -274,7 +288,7 @@ struct VTask {
 
 // Task tau = i*S + s of the interleaved team layout: column i of slot s
 // (s is the lane's fixed slot).
-template <int DVS, int DVX>
+template <int DVS, int DVX, int FB>
 __device__ __forceinline__ void v_load(VTask<DVS> &t, const LayoutMem &L, const TeamMem &T, int lgS, int s, int tau,
                                        bool on) {
     t.on = on;
@@ -298,10 +312,10 @@ __device__ __forceinline__ void v_load(VTask<DVS> &t, const LayoutMem &L, const 
     for (int k = 0; k < DVS; ++k)
         if (DVX > 0 ? (k < DVX) : true)
             t.r[k] = (DVX > 0 || t.pos[k] != 0xffffu) ? ms[(int)t.pos[k] << lgS] : 0.f;
-    t.f = (unsigned)T.flips[tau];
+    t.f = (unsigned)flipw<FB>(T)[tau];
 }
 
-template <int DVS, int DVX, bool DEBUG>
+template <int DVS, int DVX, bool DEBUG, int FB>
 __device__ __forceinline__ void v_compute_store(const VTask<DVS> &t, const StreamDev &sd, const TeamMem &T, int lgS,
                                                 int s, unsigned initm) {
     if (!t.on) return;
@@ -336,11 +350,9 @@ __device__ __forceinline__ void v_compute_store(const VTask<DVS> &t, const Strea
     const unsigned ebit = (lo <= 0.f) ? 1u : 0u;
     const int i = t.tau >> lgS;
     if (DEBUG && ((initm >> s) & 1u) && sd.dbg.lout) sd.dbg.lout[T.st[s].shot * sd.code.N + i] = lo;
-    // One 16-bit word per (variable, slot): bit 15 is the current hard
-    // decision, bits 0..14 count its flips (Algorithm 1; at most
-    // max_iter <= 32767).  Installing a slot zeroes them (e = 0, count 0).
-    if ((t.f >> 15) != ebit) {
-        T.flips[t.tau] = (uint16_t)((t.f ^ 0x8000u) + 1u);
+    // The (variable, slot) flip word: decision and flip count (FlipW).
+    if (flip_dec<FB>(t.f) != ebit) {
+        flipw<FB>(T)[t.tau] = (typename FlipW<FB>::W)flip_bump<FB>(t.f);
         // The residual syndrome s xor H e toggles at this column's checks
         // (bit c*S + s of the team's residual-syndrome words).
         const uint16_t *vc = sd.code.vchk + i * DVS;
@@ -354,7 +366,7 @@ __device__ __forceinline__ void v_compute_store(const VTask<DVS> &t, const Strea
     }
 }
 
-template <int DVS, int DVX, bool DEBUG>
+template <int DVS, int DVX, bool DEBUG, int FB>
 __device__ __forceinline__ void v_phase(const StreamDev &sd, const LayoutMem &L, const TeamMem &T, int lgS,
                                         unsigned initm, int tid, int nthreads) {
     const int total = sd.code.N << lgS;
@@ -363,9 +375,9 @@ __device__ __forceinline__ void v_phase(const StreamDev &sd, const LayoutMem &L,
         VTask<DVS> t[BPSF_VU];
 #pragma unroll
         for (int u = 0; u < BPSF_VU; ++u)
-            v_load<DVS, DVX>(t[u], L, T, lgS, s, tau + u * nthreads, tau + u * nthreads < total);
+            v_load<DVS, DVX, FB>(t[u], L, T, lgS, s, tau + u * nthreads, tau + u * nthreads < total);
 #pragma unroll
-        for (int u = 0; u < BPSF_VU; ++u) v_compute_store<DVS, DVX, DEBUG>(t[u], sd, T, lgS, s, initm);
+        for (int u = 0; u < BPSF_VU; ++u) v_compute_store<DVS, DVX, DEBUG, FB>(t[u], sd, T, lgS, s, initm);
     }
 }
 
@@ -380,23 +392,52 @@ __device__ __forceinline__ void v_phase(const StreamDev &sd, const LayoutMem &L,
 // bits are left alone.
 // ---------------------------------------------------------------------------
 template <int V> struct VecF;
-template <> struct VecF<2> { typedef float2 T; typedef uint32_t U; };  // U holds V 16-bit flip words
-template <> struct VecF<4> { typedef float4 T; typedef uint2 U; };
+template <> struct VecF<2> { typedef float2 T; };
+template <> struct VecF<4> { typedef float4 T; };
 
-// Decision bits (bit 15 of each 16-bit word) of packed flip words, as a mask
-// with bit c for slot c.
-__device__ __forceinline__ unsigned decision_mask(uint32_t w) { return ((w >> 15) & 1u) | ((w >> 30) & 2u); }
-__device__ __forceinline__ unsigned decision_mask(uint2 w) { return decision_mask(w.x) | (decision_mask(w.y) << 2); }
-
-// Toggle the decision and add one flip in the words selected by mask bm.  A
-// count is below max_iter <= 32767 before the increment, so no carry leaves
-// its 15 bits.
-__device__ __forceinline__ uint32_t flip_words(uint32_t w, unsigned bm) {
-    return (w ^ (((bm & 1u) << 15) | ((bm & 2u) << 30))) + ((bm & 1u) | ((bm & 2u) << 15));
-}
-__device__ __forceinline__ uint2 flip_words(uint2 w, unsigned bm) {
-    return make_uint2(flip_words(w.x, bm & 3u), flip_words(w.y, bm >> 2));
-}
+// The flip words of V adjacent slots packed in one integer U (slot c in the
+// c-th FB-byte field).  dmask: their decision bits as a mask with bit c for
+// slot c.  bump: toggle the decision and add one flip in the fields selected
+// by mask bm; a count is below max_iter before the increment, so no carry
+// leaves its field.
+template <int FB, int V> struct FlipPack;
+template <> struct FlipPack<2, 2> {
+    typedef uint32_t U;
+    static __device__ __forceinline__ unsigned dmask(U w) { return ((w >> 15) & 1u) | ((w >> 30) & 2u); }
+    static __device__ __forceinline__ U bump(U w, unsigned bm) {
+        return (w ^ (((bm & 1u) << 15) | ((bm & 2u) << 30))) + ((bm & 1u) | ((bm & 2u) << 15));
+    }
+};
+template <> struct FlipPack<2, 4> {
+    typedef uint2 U;
+    static __device__ __forceinline__ unsigned dmask(U w) {
+        return FlipPack<2, 2>::dmask(w.x) | (FlipPack<2, 2>::dmask(w.y) << 2);
+    }
+    static __device__ __forceinline__ U bump(U w, unsigned bm) {
+        return make_uint2(FlipPack<2, 2>::bump(w.x, bm & 3u), FlipPack<2, 2>::bump(w.y, bm >> 2));
+    }
+};
+template <> struct FlipPack<1, 2> {
+    typedef uint16_t U;
+    static __device__ __forceinline__ unsigned dmask(U w) {
+        const unsigned x = w;
+        return ((x >> 7) & 1u) | ((x >> 14) & 2u);
+    }
+    static __device__ __forceinline__ U bump(U w, unsigned bm) {
+        const unsigned sp = (bm & 1u) | ((bm & 2u) << 7);
+        return (U)(((unsigned)w ^ (sp << 7)) + sp);
+    }
+};
+template <> struct FlipPack<1, 4> {
+    typedef uint32_t U;
+    static __device__ __forceinline__ unsigned dmask(U w) {
+        return ((w >> 7) & 1u) | ((w >> 14) & 2u) | ((w >> 21) & 4u) | ((w >> 28) & 8u);
+    }
+    static __device__ __forceinline__ U bump(U w, unsigned bm) {
+        const unsigned sp = (bm & 1u) | ((bm & 2u) << 7) | ((bm & 4u) << 14) | ((bm & 8u) << 21);
+        return (w ^ (sp << 7)) + sp;
+    }
+};
 
 template <int V>
 __device__ __forceinline__ float &comp(typename VecF<V>::T &v, int c) { return reinterpret_cast<float *>(&v)[c]; }
@@ -466,11 +507,11 @@ __device__ __forceinline__ void c_phase_vec(const CodeDev &cd, const LayoutMem &
     for (int tauv = tid; tauv < nt; tauv += nthreads) c_row_vec<DC, REG, V>(L, T, MQ, lgQ, tauv, alpha);
 }
 
-template <int DVS, int DVX, bool DEBUG, int V>
+template <int DVS, int DVX, bool DEBUG, int V, int FB>
 __device__ __forceinline__ void v_phase_vec(const StreamDev &sd, const LayoutMem &L, const TeamMem &T, int lgS,
                                             unsigned onm, unsigned initm, int tid, int nthreads) {
     typedef typename VecF<V>::T VT;
-    typedef typename VecF<V>::U UT;
+    typedef typename FlipPack<FB, V>::U UT;
     const CodeDev &cd = sd.code;
     const int lgQ = lgS - (V == 4 ? 2 : 1);
     const int total = cd.N << lgQ;
@@ -545,9 +586,9 @@ __device__ __forceinline__ void v_phase_vec(const StreamDev &sd, const LayoutMem
             if (DEBUG && sd.dbg.lout && ((onm >> c) & 1u) && ((initm >> (s0 + c)) & 1u))
                 sd.dbg.lout[T.st[s0 + c].shot * cd.N + i] = lo[c];
         }
-        const unsigned bm = (em ^ decision_mask(fw)) & onm;
+        const unsigned bm = (em ^ FlipPack<FB, V>::dmask(fw)) & onm;
         if (bm) {
-            fv[tauv] = flip_words(fw, bm);
+            fv[tauv] = FlipPack<FB, V>::bump(fw, bm);
             const uint16_t *vc = cd.vchk + i * DVS;
 #pragma unroll
             for (int k = 0; k < DVS; ++k) {
@@ -608,7 +649,7 @@ __device__ __forceinline__ void layered_row(const CodeDev &cd, const LayoutMem &
     }
 }
 
-template <int DC, int DVS, int DVX, bool DEBUG>
+template <int DC, int DVS, int DVX, bool DEBUG, int FB>
 __device__ __forceinline__ void layered_iteration(const StreamDev &sd, const LayoutMem &L, const TeamMem &T, int lgS,
                                                   bool lane_on, float alpha, unsigned initm, int tid, int nthreads,
                                                   int W, int bar_id) {
@@ -630,9 +671,9 @@ __device__ __forceinline__ void layered_iteration(const StreamDev &sd, const Lay
         const float lo = T.post[tau];
         const unsigned ebit = (lo <= 0.f) ? 1u : 0u;
         if (DEBUG && ((initm >> s) & 1u) && sd.dbg.lout) sd.dbg.lout[T.st[s].shot * N + i] = lo;
-        const unsigned f = (unsigned)T.flips[tau];
-        if ((f >> 15) != ebit) {
-            T.flips[tau] = (uint16_t)((f ^ 0x8000u) + 1u);
+        const unsigned f = (unsigned)flipw<FB>(T)[tau];
+        if (flip_dec<FB>(f) != ebit) {
+            flipw<FB>(T)[tau] = (typename FlipW<FB>::W)flip_bump<FB>(f);
             const uint16_t *vc = cd.vchk + i * DVS;
 #pragma unroll
             for (int k = 0; k < DVS; ++k) {
@@ -714,12 +755,12 @@ __device__ __forceinline__ void layered_row_vec(const CodeDev &cd, const LayoutM
     }
 }
 
-template <int DC, int DVS, int DVX, bool DEBUG, int V>
+template <int DC, int DVS, int DVX, bool DEBUG, int V, int FB>
 __device__ __forceinline__ void layered_iteration_vec(const StreamDev &sd, const LayoutMem &L, const TeamMem &T,
                                                       int lgS, unsigned onm, const float (&alpha)[V], unsigned initm,
                                                       int tid, int nthreads, int W, int bar_id) {
     typedef typename VecF<V>::T VT;
-    typedef typename VecF<V>::U UT;
+    typedef typename FlipPack<FB, V>::U UT;
     const CodeDev &cd = sd.code;
     const int lgQ = lgS - (V == 4 ? 2 : 1);
     const int q = tid & ((1 << lgQ) - 1);  // the lane's slot group: slots V*q .. V*q + V-1
@@ -747,9 +788,9 @@ __device__ __forceinline__ void layered_iteration_vec(const StreamDev &sd, const
             if (DEBUG && sd.dbg.lout && ((onm >> c) & 1u) && ((initm >> (s0 + c)) & 1u))
                 sd.dbg.lout[T.st[s0 + c].shot * N + i] = compc<V>(lo, c);
         }
-        const unsigned bm = (em ^ decision_mask(fw)) & onm;
+        const unsigned bm = (em ^ FlipPack<FB, V>::dmask(fw)) & onm;
         if (bm) {
-            fv[tauv] = flip_words(fw, bm);
+            fv[tauv] = FlipPack<FB, V>::bump(fw, bm);
             const uint16_t *vc = cd.vchk + i * DVS;
 #pragma unroll
             for (int k = 0; k < DVS; ++k) {
@@ -783,7 +824,7 @@ __device__ __forceinline__ unsigned slot_pattern(int S) {
 // run's facts, and for a failed initial run Phi = top(flip_count, w) (keys
 // (count << 16 | 0xffff - i) are distinct, so each round takes the largest
 // key below the previous one: count descending, index ascending).
-template <bool DEBUG>
+template <bool DEBUG, int FB>
 __device__ __forceinline__ void team_pack(const StreamDev &sd, const TeamMem &T, int lgS, int s, int lane) {
     const CodeDev &cd = sd.code;
     const int N = cd.N, Wn = cd.Wn;
@@ -791,7 +832,7 @@ __device__ __forceinline__ void team_pack(const StreamDev &sd, const TeamMem &T,
     OutBox *ob = &T.ob[s];
     for (int w = 0; w < Wn; ++w) {
         const int i = 32 * w + lane;
-        const unsigned b = i < N ? ((unsigned)T.flips[(i << lgS) + s] >> 15) : 0u;
+        const unsigned b = i < N ? flip_dec<FB>((unsigned)flipw<FB>(T)[(i << lgS) + s]) : 0u;
         const unsigned word = __ballot_sync(FULLMASK, b != 0u);
         if (lane == 0) T.ebits[s * Wn + w] = word;
     }
@@ -805,7 +846,8 @@ __device__ __forceinline__ void team_pack(const StreamDev &sd, const TeamMem &T,
         for (int r = 0; r < cd.w; ++r) {
             unsigned best = 0;
             for (int i = lane; i < N; i += 32) {
-                const unsigned key = (flip_count(T.flips[(i << lgS) + s]) << 16) | (0xffffu - (unsigned)i);
+                const unsigned key =
+                    (flip_count<FB>((unsigned)flipw<FB>(T)[(i << lgS) + s]) << 16) | (0xffffu - (unsigned)i);
                 if (key < thr && key > best) best = key;
             }
             best = __reduce_max_sync(FULLMASK, best);
@@ -820,7 +862,7 @@ __device__ __forceinline__ void team_pack(const StreamDev &sd, const TeamMem &T,
     }
     if (DEBUG && kind == 1 && sd.dbg.flips)
         for (int i = lane; i < N; i += 32)
-            sd.dbg.flips[ss->shot * N + i] = (uint16_t)flip_count(T.flips[(i << lgS) + s]);
+            sd.dbg.flips[ss->shot * N + i] = (uint16_t)flip_count<FB>((unsigned)flipw<FB>(T)[(i << lgS) + s]);
     if (lane == 0) {
         ob->kind = kind;
         ob->kidx = ss->kidx;
@@ -840,6 +882,7 @@ __device__ __forceinline__ void team_pack(const StreamDev &sd, const TeamMem &T,
 // residual-syndrome words (atomic toggles of the bits that differ: lanes
 // share words), its V2C messages set to the channel LLRs (the first C phase
 // reads l_ch on every edge), its decision and flip-count words zeroed.
+template <int FB>
 __device__ __forceinline__ void team_install(const StreamDev &sd, const LayoutMem &L, const TeamMem &T, int S, int s,
                                              int lane) {
     const CodeDev &cd = sd.code;
@@ -861,7 +904,7 @@ __device__ __forceinline__ void team_install(const StreamDev &sd, const LayoutMe
     } else {
         for (int k = lane; k < cd.P; k += 32) T.m[k * S + s] = L.lch_pos[k];
     }
-    for (int i = lane; i < cd.N; i += 32) T.flips[i * S + s] = 0;
+    for (int i = lane; i < cd.N; i += 32) flipw<FB>(T)[i * S + s] = 0;
     if (lane == 0) {
         ss->kind = e->kind;
         ss->kidx = e->kidx;
@@ -874,7 +917,7 @@ __device__ __forceinline__ void team_install(const StreamDev &sd, const LayoutMe
     __syncwarp();
 }
 
-template <bool DEBUG>
+template <bool DEBUG, int FB>
 __device__ __forceinline__ void team_service(const StreamDev &sd, const LayoutMem &L, const TeamMem &T, int S, int lgS,
                                              int lane) {
     const int stv = lane < S ? *vstate(&T.st[lane]) : kSlotRunning;
@@ -884,7 +927,7 @@ __device__ __forceinline__ void team_service(const StreamDev &sd, const LayoutMe
     while (pm) {
         const int s = __ffs(pm) - 1;
         pm &= pm - 1u;
-        team_pack<DEBUG>(sd, T, lgS, s, lane);
+        team_pack<DEBUG, FB>(sd, T, lgS, s, lane);
         // team_pack set the outbox flag before the slot reads EMPTY (the
         // manager's exit test reads the state first, then the outbox flag).
         if (lane == 0) {
@@ -900,7 +943,7 @@ __device__ __forceinline__ void team_service(const StreamDev &sd, const LayoutMe
         const int s = __ffs(im) - 1;
         im &= im - 1u;
         const int kind = reinterpret_cast<const QEntry *>(T.ib + s * T.ibstride)->kind;
-        if (kind != 0) team_install(sd, L, T, S, s, lane);
+        if (kind != 0) team_install<FB>(sd, L, T, S, s, lane);
         __syncwarp();
         if (lane == 0) {
             // RUNNING before the inbox reads empty: the manager's exit test
@@ -917,7 +960,7 @@ __device__ __forceinline__ void team_service(const StreamDev &sd, const LayoutMe
 // ---------------------------------------------------------------------------
 // Compute team loop.
 // ---------------------------------------------------------------------------
-template <int DC, int DVS, int DVX, bool DEBUG, int MINB, bool LAY>
+template <int DC, int DVS, int DVX, bool DEBUG, int MINB, bool LAY, int FB>
 __device__ void team_loop(const StreamDev &sd, const LayoutMem &L, const TeamMem &T, BlockHdr *hdr, int S, int W,
                           int tid, int bar_id, unsigned long long wait_ns) {
     const int lane = tid & 31, wt = tid >> 5, nthreads = 32 * W;
@@ -936,7 +979,7 @@ __device__ void team_loop(const StreamDev &sd, const LayoutMem &L, const TeamMem
     unsigned last_beat = 0;
     for (;;) {
         if (wt == 0) {
-            team_service<DEBUG>(sd, L, T, S, lgS, lane);
+            team_service<DEBUG, FB>(sd, L, T, S, lgS, lane);
             SlotState *ss = &T.st[lane < S ? lane : 0];
             const int stv = lane < S ? *vstate(ss) : kSlotEmpty;
             const bool r = stv == kSlotRunning;
@@ -982,18 +1025,18 @@ __device__ void team_loop(const StreamDev &sd, const LayoutMem &L, const TeamMem
                 float al[4];
 #pragma unroll
                 for (int c = 0; c < 4; ++c) al[c] = damping(cd, T.st[s0 + c].iter + 1);
-                layered_iteration_vec<DC, DVS, DVX, DEBUG, 4>(sd, L, T, lgS, (run >> s0) & 0xfu, al, initm, tid,
+                layered_iteration_vec<DC, DVS, DVX, DEBUG, 4, FB>(sd, L, T, lgS, (run >> s0) & 0xfu, al, initm, tid,
                                                               nthreads, W, bar_id);
             } else if (kLayV2 && S >= 2) {
                 const int s0 = 2 * (lane & ((S >> 1) - 1));
                 float al[2];
                 al[0] = damping(cd, T.st[s0].iter + 1);
                 al[1] = damping(cd, T.st[s0 + 1].iter + 1);
-                layered_iteration_vec<DC, DVS, DVX, DEBUG, 2>(sd, L, T, lgS, (run >> s0) & 0x3u, al, initm, tid,
+                layered_iteration_vec<DC, DVS, DVX, DEBUG, 2, FB>(sd, L, T, lgS, (run >> s0) & 0x3u, al, initm, tid,
                                                               nthreads, W, bar_id);
             } else {
                 const bool lane_on = (run >> my_slot) & 1u;
-                layered_iteration<DC, DVS, DVX, DEBUG>(sd, L, T, lgS, lane_on, damping(cd, T.st[my_slot].iter + 1),
+                layered_iteration<DC, DVS, DVX, DEBUG, FB>(sd, L, T, lgS, lane_on, damping(cd, T.st[my_slot].iter + 1),
                                                        initm, tid, nthreads, W, bar_id);
             }
             team_sync(W, bar_id);
@@ -1005,7 +1048,7 @@ __device__ void team_loop(const StreamDev &sd, const LayoutMem &L, const TeamMem
             for (int c = 0; c < 4; ++c) al[c] = damping(cd, T.st[s0 + c].iter + 1);
             if (onm) c_phase_vec<DC, (DVX > 0), 4>(cd, L, T, lgS, al, tid, nthreads);
             team_sync(W, bar_id);
-            if (onm) v_phase_vec<DVS, DVX, DEBUG, 4>(sd, L, T, lgS, onm, initm, tid, nthreads);
+            if (onm) v_phase_vec<DVS, DVX, DEBUG, 4, FB>(sd, L, T, lgS, onm, initm, tid, nthreads);
             team_sync(W, bar_id);
         } else if (kVec && S >= 2) {
             const int s0 = 2 * (lane & ((S >> 1) - 1));
@@ -1015,13 +1058,13 @@ __device__ void team_loop(const StreamDev &sd, const LayoutMem &L, const TeamMem
             al[1] = damping(cd, T.st[s0 + 1].iter + 1);
             if (onm) c_phase_vec<DC, (DVX > 0), 2>(cd, L, T, lgS, al, tid, nthreads);
             team_sync(W, bar_id);
-            if (onm) v_phase_vec<DVS, DVX, DEBUG, 2>(sd, L, T, lgS, onm, initm, tid, nthreads);
+            if (onm) v_phase_vec<DVS, DVX, DEBUG, 2, FB>(sd, L, T, lgS, onm, initm, tid, nthreads);
             team_sync(W, bar_id);
         } else {
             const bool lane_on = (run >> my_slot) & 1u;
             if (lane_on) c_phase<DC, (DVX > 0)>(cd, L, T, lgS, damping(cd, T.st[my_slot].iter + 1), tid, nthreads);
             team_sync(W, bar_id);
-            if (lane_on) v_phase<DVS, DVX, DEBUG>(sd, L, T, lgS, initm, tid, nthreads);
+            if (lane_on) v_phase<DVS, DVX, DEBUG, FB>(sd, L, T, lgS, initm, tid, nthreads);
             team_sync(W, bar_id);
         }
         if (wt == 0) {
@@ -1513,7 +1556,9 @@ __device__ void manager_loop(const StreamDev &sd, const LayoutMem &L, unsigned c
 
 // LAY: the instance also runs codes with the layered schedule (a launch
 // with no such code uses the instance without that path and its registers).
-template <int DC, int DVS, int DVX, bool DEBUG, int MINB, bool LAY>
+// FB: bytes per flip word (FlipW): 2, or 1 for launches whose codes all have
+// max_iter <= 127 (an instance that leaves more shared memory for slots).
+template <int DC, int DVS, int DVX, bool DEBUG, int MINB, bool LAY, int FB = 2>
 __global__ void __launch_bounds__(512, MINB) bpsf_persistent(const __grid_constant__ KernelParams kp) {
     extern __shared__ __align__(16) unsigned char smem[];
     BlockHdr *hdr = reinterpret_cast<BlockHdr *>(smem);
@@ -1609,7 +1654,7 @@ __global__ void __launch_bounds__(512, MINB) bpsf_persistent(const __grid_consta
             cur = sid;
         }
         // Every slot starts empty; teams start idle.
-        const TeamOffsets to = team_offsets(S, cd.M, cd.N, cd.P, cd.Ws, cd.layered);
+        const TeamOffsets to = team_offsets(S, cd.M, cd.N, cd.P, cd.Ws, cd.layered, FB);
         unsigned char *qbase = lay + lo.total;
         unsigned char *team_base = qbase + Q * qentry_bytes(cd.Ws);
         for (int k = tid; k < teams * S; k += blockDim.x) {
@@ -1653,7 +1698,7 @@ __global__ void __launch_bounds__(512, MINB) bpsf_persistent(const __grid_consta
             const int team = (warp - 1) / W;
             if (team < teams) {
                 TeamMem T = team_mem(team_base + team * to.total, to);
-                team_loop<DC, DVS, DVX, DEBUG, MINB, LAY>(sd, L, T, hdr, S, W, tid - 32 - team * W * 32, 1 + team, kp.wait_ns);
+                team_loop<DC, DVS, DVX, DEBUG, MINB, LAY, FB>(sd, L, T, hdr, S, W, tid - 32 - team * W * 32, 1 + team, kp.wait_ns);
             }
         }
         __syncthreads();

@@ -324,6 +324,31 @@ def test_launch_shape_does_not_change_results():
             assert (got[key] == ref[key]).all(), (t, key)
 
 
+def test_one_byte_flip_words():
+    """Thirteen teams of 8 slots fit on an SM only with one-byte flip words
+    (max_iter <= 127): results, flip counts, Phi and posteriors equal those of
+    the two-byte shape; with max_iter > 127 the shape is refused."""
+    P = B.Params(max_iter=100, alpha=0.625, w=6, short_iter=20)
+    oc, e, s = make_inputs("bb144", 0.07, 3000, 31)
+    dec = decoder("bb144", 0.07, P)
+    dec.tuning = (1, 8, 12, 0)
+    ref = gpu_decode(dec, s)
+    ref_dbg = {k: v.cpu().numpy() for k, v in dec.decode_debug(dev(pack(s[:400]))).items()}
+    dec.tuning = (1, 8, 13, 0)
+    got = gpu_decode(dec, s)
+    for key in ("corr", "conv", "iters", "stage"):
+        assert (got[key] == ref[key]).all(), key
+    dbg = {k: v.cpu().numpy() for k, v in dec.decode_debug(dev(pack(s[:400]))).items()}
+    for key in ("flips", "phi", "lout", "trial_conv", "trial_iters", "corr"):
+        assert (dbg[key] == ref_dbg[key]).all(), key
+    eo, co, io, so = oc.bpsf_batch(s, 0.07, oparams(P), threads=THREADS)
+    assert (unpack(got["corr"], oc.N) == eo).all(axis=1).mean() >= CORR_MATCH
+    long_runs = decoder("bb144", 0.07, B.Params(max_iter=200, alpha=0.625, w=6, short_iter=20))
+    with pytest.raises(B.BpsfError) as ei:
+        long_runs.tuning = (1, 8, 13, 0)
+    assert ei.value.status == B.BPSF_EINVAL
+
+
 def test_launch_shape_irregular_code():
     """Every slot count has its own message layout (rank stride and edge order);
     for the irregular-row [[254,28]] code the strides differ from M at some slot
