@@ -28,8 +28,8 @@ sys.path.insert(0, ROOT)
 
 P_LIST = (0.02, 0.04, 0.06, 0.08)
 SHOTS_PER_P = 1_000_000
-# ncu, one launch of 4 x 200k shots: 88.8 MB read + 78.6 MB written.
-DRAM_BYTES_PER_SHOT = 167.4e6 / 800_000
+# ncu, one launch of 4 x 200k shots: 109.2 MB read + 76.1 MB written.
+DRAM_BYTES_PER_SHOT = 185.3e6 / 800_000
 CODE = "bb144"
 N_BITS, M_CHECKS, NNZ = 144, 72, 432
 PARAMS = dict(max_iter=100, alpha=0.625, w=6, w_max=0, short_iter=20, select=0)
