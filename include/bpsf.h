@@ -235,7 +235,12 @@ bpsf_status bpsf_sync(bpsf_ctx *ctx, void *stream);
  * items in lock step (interleaved in shared memory, so each lane serves one
  * fixed slot); warps_per_block / warps_per_team teams share a block
  * together with one manager warp that writes results and refills slots;
- * blocks_per_sm blocks per SM (0 = as many as fit).
+ * blocks_per_sm blocks per SM (0 = as many as fit).  bpsf_set_tuning
+ * returns BPSF_EINVAL for a shape whose block does not fit in shared memory.
+ * For codes of row weight 6 and column weight 3 with max_iter <= 127 and no
+ * layered schedule, a kernel instance with one-byte flip counters makes
+ * room for shapes that two-byte counters do not fit (for example 13 teams of
+ * 8 slots on [[144,12,12]]).
  */
 typedef struct {
     int32_t warps_per_team;  /* 1, 2, 4 or 8 */
