@@ -202,8 +202,9 @@ class Code:
         if h and _lib is not None:
             _lib.oracle_code_free(h)
 
-    # s = H e (mod 2)
-    def syndrome(self, e: np.ndarray) -> np.ndarray:
+    # s = H e (mod 2) (Section II-B, e H^T = s): the dense GF(2) mat-vec of the C
+    # oracle, one shot at a time.
+    def syndrome_matvec(self, e: np.ndarray) -> np.ndarray:
         e = np.ascontiguousarray(np.atleast_2d(e), dtype=np.uint8)
         out = np.zeros((e.shape[0], self.M), dtype=np.uint8)
         for k in range(e.shape[0]):
@@ -212,6 +213,18 @@ class Code:
             lib().oracle_syndrome(self._h, row, tmp)
             out[k] = tmp
         return out
+
+    # The same s = H e (mod 2) for a batch, as one library matrix product: the
+    # integer counts (at most the row weight) are exact in float32, and their
+    # parity is the syndrome bit.
+    def syndrome(self, e: np.ndarray) -> np.ndarray:
+        e = np.atleast_2d(np.asarray(e))
+        if e.shape[0] <= 8:
+            return self.syndrome_matvec(e)
+        if not hasattr(self, "_hT32"):
+            self._hT32 = np.ascontiguousarray(self.H.T, dtype=np.float32)
+        cnt = e.astype(np.float32) @ self._hT32
+        return (cnt.astype(np.int64) & 1).astype(np.uint8)
 
     @staticmethod
     def llr(priors, fp32: bool):

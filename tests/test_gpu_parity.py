@@ -219,12 +219,19 @@ def test_bb144_workload_matches_oracle(p_idx):
     compare(oc, dec, s, p, P)
 
 
-def test_phenomenological_matches_oracle():
-    """12-round phenomenological [[144]] (864 x 2592), p = q = 0.004, max_iter 200, w 5, short_iter 30."""
+@pytest.mark.parametrize("p,n,seed_idx,min_sf,min_fail", [(0.002, 20000, 0, 1, 0), (0.004, 30000, 1, 50, 10),
+                                                        (0.010, 3000, 1, 50, 10)])
+def test_phenomenological_matches_oracle(p, n, seed_idx, min_sf, min_fail):
+    """12-round phenomenological [[144]] (864 x 2592), p = q: max_iter 200, w 5 (31 trials), short_iter 30.
+
+    Enough shots that the trial path (stage 1) and the total-failure output
+    (stage 2, 31 failed trials) are both compared many times."""
     P = B.Params(max_iter=200, alpha=0.625, w=5, short_iter=30)
-    oc, e, s = make_inputs("bb144_phenom", 0.004, 150, synth.SEEDS["bb144_phenom"][1])
-    dec = decoder("bb144_phenom", 0.004, P)
-    compare(oc, dec, s, 0.004, P)
+    oc, e, s = make_inputs("bb144_phenom", p, n, synth.SEEDS["bb144_phenom"][seed_idx])
+    dec = decoder("bb144_phenom", p, P)
+    g, (eo, co, io, so) = compare(oc, dec, s, p, P)
+    assert (so == 1).sum() >= min_sf and (so == 2).sum() >= min_fail
+    assert (g["stage"] == so).all() and (g["iters"] == io).all()
 
 
 def test_mixed_codes_one_launch_match_oracle():
@@ -241,8 +248,11 @@ def test_mixed_codes_one_launch_match_oracle():
     for (oc, s), o in zip(cases, outs):
         eo, co, io, so = oc.bpsf_batch(s, 0.05, oparams(P), threads=THREADS)
         eg = unpack(o["corr"].cpu().numpy(), oc.N)
-        assert (eg == eo).all(axis=1).mean() >= CORR_MATCH
-        assert (o["stage"].cpu().numpy() == so).mean() >= CORR_MATCH
+        same = (eg == eo).all(axis=1)
+        assert same.mean() >= CORR_MATCH
+        assert ((o["conv"].cpu().numpy() != 0) == co)[same].all()
+        assert (o["iters"].cpu().numpy() == io)[same].all()
+        assert (o["stage"].cpu().numpy() == so)[same].all()
 
 
 # --------------------------------------------------------------------------
@@ -280,16 +290,25 @@ def test_layered_and_flooding_codes_in_one_launch():
 # Step-level parity through the debug dump
 # --------------------------------------------------------------------------
 
-def test_internal_values_match_oracle_bit_for_bit():
+# (code, p, shots, params, least failed shots): the [[72]] workload's settings,
+# the [[144]] benchmark settings at its highest p, and the phenomenological
+# settings on the row-weight-8 kernel variant.
+DUMP_CASES = [("bb72", 0.09, 1500, (50, 4, 10), 20), ("bb144", 0.08, 800, (100, 6, 20), 100),
+              ("bb144_phenom", 0.010, 1500, (200, 5, 30), 15)]
+
+
+@pytest.mark.parametrize("name,p,n,prm,min_failed", DUMP_CASES)
+def test_internal_values_match_oracle_bit_for_bit(name, p, n, prm, min_failed):
     """LLRs, flip counts, Phi, trial syndromes and trial outcomes on a failure-heavy batch."""
-    P = B.Params(max_iter=50, alpha=0.625, w=4, short_iter=10)
-    oc, e, s = make_inputs("bb72", 0.09, 1500, 77)
-    dec = decoder("bb72", 0.09, P)
+    max_iter, w, short_iter = prm
+    P = B.Params(max_iter=max_iter, alpha=0.625, w=w, short_iter=short_iter)
+    oc, e, s = make_inputs(name, p, n, 77)
+    dec = decoder(name, p, P)
     g = dec.decode_debug(dev(pack(s)))
     g = {k: v.cpu().numpy() for k, v in g.items()}
-    n_failed = 0
+    n_failed = n_trial_conv = 0
     for k in range(s.shape[0]):
-        r = oc.bp(s[k], 0.09, P.max_iter, P.alpha, fp32=True, track=True)
+        r = oc.bp(s[k], p, P.max_iter, P.alpha, fp32=True, track=True)
         L = r["lout"].astype(np.float64)
         d = np.abs(g["lout"][k].astype(np.float64) - L)
         assert (d <= LLR_TOL * np.maximum(1.0, np.abs(L))).all()
@@ -299,12 +318,13 @@ def test_internal_values_match_oracle_bit_for_bit():
         n_failed += 1
         phi = oracle.top(r["flips"], P.w)
         assert (g["phi"][k] == phi).all()
-        synd, conv, iters, es = oc.trials(s[k], 0.09, phi, oparams(P))
+        synd, conv, iters, es = oc.trials(s[k], p, phi, oparams(P))
         tsyn = unpack(g["trial_synd"][k].reshape(len(synd), -1), oc.M)
         assert (tsyn == synd).all()
         assert (g["trial_conv"][k] == conv).all()
         assert (g["trial_iters"][k] == iters).all()
-    assert n_failed > 20
+        n_trial_conv += int(conv.sum())
+    assert n_failed >= min_failed and n_trial_conv > 0
 
 
 # --------------------------------------------------------------------------
@@ -569,3 +589,50 @@ def test_full_size_bb144_p008_sampled_parity_and_ler():
     fg = oracle.logical_failures(hx, lx, e[idx], eg, conv.cpu().numpy()[idx]).mean()
     sigma = np.sqrt(max(f64 * (1 - f64), 1e-12) / len(idx))
     assert abs(fg - f64) <= sigma + 1e-12
+
+
+@pytest.mark.parametrize("p_idx", range(4))
+def test_ler_within_one_sigma_of_fp64_oracle(p_idx):
+    """[[144,12,12]] benchmark settings, 10^5 shots per p: the GPU's logical error
+    rate lies within the binomial 1-sigma of the FP64 oracle on the same shots."""
+    p = (0.02, 0.04, 0.06, 0.08)[p_idx]
+    n = 100_000
+    P = B.Params(max_iter=100, alpha=0.625, w=6, short_iter=20)
+    oc, e, s = make_inputs("bb144", p, n, synth.SEEDS["bb144_cc"][p_idx])
+    dec = decoder("bb144", p, P)
+    g = gpu_decode(dec, s)
+    eg = unpack(g["corr"], oc.N)
+    e64, c64, _, _ = oc.bpsf_batch(s, p, oparams(P), fp32=False, threads=THREADS)
+    hx, hz = oracle.named_code("bb144")
+    lx = oracle.logicals(hx, hz)
+    f64 = oracle.logical_failures(hx, lx, e, e64, c64).mean()
+    fg = oracle.logical_failures(hx, lx, e, eg, g["conv"] != 0).mean()
+    sigma = np.sqrt(max(f64 * (1 - f64), 1e-12) / n)
+    assert abs(fg - f64) <= sigma + 1e-12, (fg, f64, sigma)
+    assert (eg == e64).all(axis=1).mean() >= CORR_MATCH
+
+
+def test_c2v_clamp_where_it_fires_matches_oracle():
+    """H = [[1,1],[1,1],[1,1]], s = (1,0,0) never converges; with alpha_t -> 1 the
+    messages grow by half a bit per iteration until the 2^100 clamp holds them.
+    The kernel's posteriors equal the FP32 oracle's bit for bit before, at and
+    after saturation."""
+    H = np.array([[1, 1], [1, 1], [1, 1]], dtype=np.uint8)
+    ptr = np.array([0, 2, 4, 6], dtype=np.int32)
+    idx = np.array([0, 1, 0, 1, 0, 1], dtype=np.int32)
+    oc = Code(H)
+    s = np.array([[1, 0, 0]] * 4, dtype=np.uint8)
+    for T in (100, 260, 401):
+        P = B.Params(max_iter=T, alpha=0.0, w=2, short_iter=10)
+        dec = B.Decoder(ptr, idx, 3, 2, np.full(2, 0.1), P)
+        g = dec.decode_debug(dev(pack(s)))
+        r = oc.bp(s[0], 0.1, T, 0.0, fp32=True, track=True)
+        lg = g["lout"].cpu().numpy()
+        assert (lg == r["lout"][None, :]).all()
+        assert np.isfinite(lg).all()
+        if T >= 260:
+            assert (np.abs(lg) >= 2.0 ** 100).all()
+        assert (g["stage"].cpu().numpy() == 2).all() and (g["iters"].cpu().numpy() == T).all()
+        eo, co, io, so = oc.bpsf_batch(s, 0.1, oparams(P), threads=1)
+        assert (unpack(g["corr"].cpu().numpy(), 2) == eo).all()
+        dec.close()

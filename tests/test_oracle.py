@@ -6,6 +6,7 @@ tiny inputs, and invariants of Algorithm 1.  A plausible slip in the oracle (a
 dropped term, a wrong sign or index, a transposed operand) fails one of them.
 """
 import itertools
+import math
 
 import numpy as np
 import pytest
@@ -362,6 +363,70 @@ def test_two_check_chain_signs():
     r = code.bp(np.array([1, 0], dtype=np.uint8), p, max_iter=5, alpha=1.0, fp32=False, stop_on_converge=False)
     assert r["e"].tolist() == [1, 0, 0]
     assert r["converged"]
+
+
+def _clamp_toy_reduced(T, p, clamp=2.0 ** 100):
+    """Posterior after T iterations on H = [[1,1],[1,1],[1,1]], s = (1,0,0),
+    alpha_t = 1 - 2^-t, reduced by symmetry to two numbers: both variables
+    carry the same V2C message a to check 0 and b to checks 1 and 2 (which
+    stay equal), a check of degree two passes the other variable's message
+    scaled and signed, so a' = l + 2 r_b, b' = l + r_a + r_b with
+    r_a = -sign(a) min(alpha |a|, clamp), r_b = sign(b) min(alpha |b|, clamp)."""
+    l = math.log((1 - p) / p)
+    a = b = l
+    lout = l
+    for t in range(1, T + 1):
+        al = 1.0 - math.ldexp(1.0, -t)
+        ra = min(al * abs(a), clamp) if a < 0 else -min(al * abs(a), clamp)
+        rb = -min(al * abs(b), clamp) if b < 0 else min(al * abs(b), clamp)
+        lout = ((l + ra) + rb) + rb
+        a, b = (l + rb) + rb, (l + ra) + rb
+    return lout
+
+
+def test_c2v_clamp_where_it_fires():
+    """Messages that grow without bound, and the 2^100 clamp that keeps them finite.
+
+    On H = [[1,1],[1,1],[1,1]] with s = (1,0,0) no e satisfies the syndrome
+    (every check sees the same parity), so BP never stops.  With alpha_t -> 1
+    the reduced map (a, b) -> (2b, b - a) has eigenvalues (1 +- i sqrt 7) / 2 of
+    modulus sqrt 2: magnitudes grow by half a bit per iteration until the
+    clamp at 2^100 holds them, after which every posterior is a small multiple
+    of 2^100 (the channel LLR is far below its last place)."""
+    H = np.array([[1, 1], [1, 1], [1, 1]], dtype=np.uint8)
+    code = Code(H)
+    s = np.array([1, 0, 0], dtype=np.uint8)
+    p = 0.1
+    growth = []
+    for T in (20, 60, 100, 140, 180, 220, 260, 300, 333, 400, 401, 402):
+        r64 = code.bp(s, p, T, 0.0, fp32=False)
+        r32 = code.bp(s, p, T, 0.0, fp32=True)
+        assert not r64["converged"] and r64["iters"] == T and r32["iters"] == T
+        assert r64["lout"][0] == r64["lout"][1] and np.isfinite(r32["lout"]).all()
+        # FP64 equals the hand-reduced two-number recursion at every length.
+        assert r64["lout"][0] == _clamp_toy_reduced(T, p)
+        growth.append((T, math.log2(abs(r64["lout"][0]))))
+        if T >= 260:
+            # Saturated: |r| = 2^100 on every edge, posteriors are +-2^100 or 2^101.
+            for v in (r64["lout"][0], float(r32["lout"][0])):
+                assert abs(v) in (2.0 ** 100, 2.0 ** 101)
+            assert float(r32["lout"][0]) == r64["lout"][0]
+    # Before the clamp: half a bit per iteration (|lambda| = sqrt 2).
+    slope = (growth[4][1] - growth[1][1]) / (growth[4][0] - growth[1][0])
+    assert abs(slope - 0.5) < 0.03
+    # Without the clamp the same recursion leaves FP32's range long before 400.
+    assert abs(_clamp_toy_reduced(400, p, clamp=float("inf"))) > 2.0 ** 128
+
+
+def test_batch_syndrome_equals_the_matvec_and_the_columns():
+    for H in (oracle.named_code("bb144")[0], oracle.phenom_code(oracle.named_code("bb72")[0], 3)):
+        code = Code(H)
+        rng = np.random.default_rng(5)
+        e = (rng.random((40, code.N)) < 0.1).astype(np.uint8)
+        assert (code.syndrome(e) == code.syndrome_matvec(e)).all()
+        # Unit errors give the columns of H.
+        eye = np.eye(code.N, dtype=np.uint8)[:50]
+        assert (code.syndrome(eye) == H[:, :50].T).all()
 
 
 def test_zero_syndrome_is_trivial():
