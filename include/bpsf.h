@@ -200,8 +200,8 @@ bpsf_status bpsf_decode_multi_host(int32_t n_jobs, const bpsf_job *jobs, void *s
  * Batched decode that allocates nothing.  The paper has no counterpart: this
  * serves callers that cannot allocate device memory when they decode (a
  * control loop with a hard deadline that must not block in the CUDA
- * allocator, a runtime that owns the whole device heap, work being recorded
- * into a CUDA graph).  It runs the same kernel as bpsf_decode with the same
+ * allocator, or a runtime whose own allocator owns the whole device heap).
+ * It runs the same kernel as bpsf_decode with the same
  * arguments and results, but the kernel's scratch (launch counters and the
  * records of failed shots) lives in one static 32 MiB device array that
  * every GPU loading this library holds until the process exits.
@@ -215,7 +215,10 @@ bpsf_status bpsf_decode_multi_host(int32_t n_jobs, const bpsf_job *jobs, void *s
  *     GPU (on different streams, or from several contexts) race on the
  *     array: order them on one stream.
  *   - The context must already exist (bpsf_create allocates at set-up).
- * bpsf_sync(ctx, stream) reports device-side errors of the call as usual.
+ * After the kernel, the call copies its launch counters into ctx's own
+ * counter block on `stream` (a device-to-device copy), so bpsf_sync(ctx,
+ * stream) and bpsf_last_work report this call's device-side errors and work
+ * even when further no-allocation calls have been queued since.
  */
 bpsf_status bpsf_decode_noalloc(bpsf_ctx *ctx, int64_t n_shots, const uint32_t *d_synd, int32_t synd_stride_words,
                                 uint32_t *d_corr, int32_t corr_stride_words, uint8_t *d_converged, int16_t *d_iters,

@@ -1,8 +1,7 @@
 // bpsf_decode_noalloc: the batched decode for callers that cannot allocate
 // device memory when they decode -- a control loop with a hard deadline that
-// must never block inside the CUDA allocator, a host runtime that hands the
-// whole device heap to another framework, or code that records its work
-// into a CUDA graph where a cudaMalloc would break the capture.  Such callers
+// must never block inside the CUDA allocator, or a host runtime that hands
+// the whole device heap to another framework's allocator.  Such callers
 // create their context once at set-up and then decode without any further
 // allocation: the kernel's scratch (launch counters and failed-shot records)
 // lives in one statically sized device array defined in this file, which
@@ -59,6 +58,8 @@ size_t noalloc_bytes(const bpsf_ctx *c, long long n) {
 
 extern "C" int64_t bpsf_noalloc_max_shots(const bpsf_ctx *c) {
     if (!c) return -1;
+    // Every shot takes at least 24 bytes of records, so the answer is below
+    // 2^21 and the doubling stops long before any product could wrap.
     long long lo = 0, hi = 1;
     while (noalloc_bytes(c, hi) <= kNoallocScratchBytes) hi *= 2;
     while (hi - lo > 1) {
@@ -75,17 +76,19 @@ extern "C" bpsf_status bpsf_decode_noalloc(bpsf_ctx *c, int64_t n, const uint32_
                                            int32_t cs, uint8_t *conv, int16_t *iters, uint8_t *stage, void *stream) {
     if (!c) return bpsf_fail(BPSF_EINVAL, "ctx is NULL");
     if (n < 0) return bpsf_fail(BPSF_EINVAL, "n_shots must be >= 0");
+    // The bound comes first: the size arithmetic below is only done for
+    // batches known to fit, so no product can wrap.
+    const long long max_n = bpsf_noalloc_max_shots(c);
+    if (n > max_n)
+        return bpsf_fail(BPSF_EINVAL,
+                         "n_shots = %lld does not fit the static scratch of %zu bytes "
+                         "(at most %lld shots of this code per call)",
+                         (long long)n, kNoallocScratchBytes, max_n);
     if (bpsf_check_trials(c) != BPSF_OK) return BPSF_EINVAL;
     if (n == 0) return BPSF_OK;
     if (!synd || !corr || !conv || !iters) return bpsf_fail(BPSF_EINVAL, "NULL input or output pointer");
     if (ss < c->Ws) return bpsf_fail(BPSF_EINVAL, "synd_stride_words %d < Ws = %d", ss, c->Ws);
     if (cs < c->Wn) return bpsf_fail(BPSF_EINVAL, "corr_stride_words %d < Wn = %d", cs, c->Wn);
-    const size_t need = noalloc_bytes(c, n);
-    if (need > kNoallocScratchBytes)
-        return bpsf_fail(BPSF_EINVAL,
-                         "n_shots = %lld needs %zu bytes of scratch; the static scratch holds %zu bytes "
-                         "(at most %lld shots of this code per call)",
-                         (long long)n, need, kNoallocScratchBytes, (long long)bpsf_noalloc_max_shots(c));
     cudaError_t e = cudaSetDevice(c->device);
     if (e != cudaSuccess) return bpsf_fail(BPSF_ECUDA, "cudaSetDevice: %s", cudaGetErrorString(e));
     unsigned char *base = nullptr;
@@ -132,7 +135,13 @@ extern "C" bpsf_status bpsf_decode_noalloc(bpsf_ctx *c, int64_t n, const uint32_
     bpsf_launch_plan(pl, false, &sd, 1, pl.grid, stream);
     e = cudaGetLastError();
     if (e != cudaSuccess) return bpsf_fail(BPSF_ECUDA, "kernel launch: %s", cudaGetErrorString(e));
-    c->d_ctr_last = ctr;
+    // The next call reuses the array's counters, so this call's counters go
+    // to the context's own block, in stream order after the kernel (a copy
+    // between device buffers, no allocation); bpsf_sync reads them there
+    // even when another no-allocation call has run since.
+    e = cudaMemcpyAsync(c->d_ctr, ctr, sizeof(StreamCounters), cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) return bpsf_fail(BPSF_ECUDA, "counter copy: %s", cudaGetErrorString(e));
+    c->d_ctr_last = c->d_ctr;
     c->last_launch_n = n;
     return BPSF_OK;
 }
