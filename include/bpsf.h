@@ -238,7 +238,8 @@ bpsf_status bpsf_sync(bpsf_ctx *ctx, void *stream);
  * items in lock step (interleaved in shared memory, so each lane serves one
  * fixed slot); warps_per_block / warps_per_team teams share a block
  * together with one manager warp that writes results and refills slots;
- * blocks_per_sm blocks per SM (0 = as many as fit).  bpsf_set_tuning
+ * blocks_per_sm blocks per SM (0 = as many as fit); iter_chunk bounds how
+ * often a team stops to refill finished slots.  bpsf_set_tuning
  * returns BPSF_EINVAL for a shape whose block does not fit in shared memory.
  * For codes of row weight 6 and column weight 3 with max_iter <= 127 and no
  * layered schedule, a kernel instance with one-byte flip counters makes
@@ -250,6 +251,11 @@ typedef struct {
     int32_t slots_per_team;  /* 1, 2, 4, 8, 16 or 32 */
     int32_t warps_per_block; /* compute warps: a multiple of warps_per_team, <= 15 */
     int32_t blocks_per_sm;   /* 0 = occupancy limit */
+    int32_t iter_chunk;      /* 0 or 1: refill a finished slot after the iteration it finished in; k in 2..64:
+                                a team refills its finished slots at most every k iterations (finished slots
+                                wait, the team's other slots keep iterating).  Every run still stops at the
+                                first iteration whose decision satisfies its syndrome, so results do not
+                                depend on it. */
 } bpsf_tuning;
 
 bpsf_status bpsf_get_tuning(const bpsf_ctx *ctx, bpsf_tuning *out);
@@ -257,9 +263,12 @@ bpsf_status bpsf_set_tuning(bpsf_ctx *ctx, const bpsf_tuning *t);
 
 /*
  * Autotuner: times bpsf_decode over candidate launch shapes on n_sample
- * syndromes of random errors drawn at rate p_sample (device generator),
- * keeps the fastest, and caches it per code shape (M, N, nnz, degrees) for
- * the process.  Synchronises `stream`.  chosen is nullable.
+ * syndromes of random errors drawn at rate p_sample (device generator):
+ * threads per shot (warps per team over slots per team), shots per block
+ * (slots per team x teams), then the iteration chunk for the fastest shape.
+ * Keeps the fastest, sets it on ctx and caches it per code shape (M, N, nnz,
+ * degrees, parameters) for the process; a context created later for the same
+ * code shape starts with it.  Synchronises `stream`.  chosen is nullable.
  */
 bpsf_status bpsf_autotune(bpsf_ctx *ctx, double p_sample, int64_t n_sample, void *stream, bpsf_tuning *chosen);
 
@@ -270,11 +279,15 @@ bpsf_status bpsf_autotune(bpsf_ctx *ctx, double p_sample, int64_t n_sample, void
 /*
  * A server keeps one persistent decode loop on the device over several codes
  * (the paper's streaming setting: syndromes arrive one request at a time,
- * Section VI).  Each code has an arena of max_inflight_shots device rows; a
- * request takes consecutive rows and is admitted only when they are free
- * (admission by device memory).  Shots of requests that arrive while others
- * run join the same device work pool as slots free up; results are written
- * to host-mapped rows and each request's completion is posted by the device.
+ * Section VI).  Each code has max_inflight_shots rows, each with its shot's
+ * device-side records (the state of a failed shot's trials); a request takes
+ * consecutive rows and is admitted only when they are free (admission by
+ * device memory).  Submitting writes the syndromes into a host-mapped input
+ * arena and publishes them with a release store that the device reads with
+ * system-scope acquire loads: no copy and no driver call per request.  Shots
+ * of requests that arrive while others run join the same device work pool as
+ * slots free up; results are written to host-mapped rows and each request's
+ * completion is posted by the device.
  * The device loop leaves after idle_exit_us without work and a host thread
  * relaunches it when admitted work is pending, so no device wait is unbounded.
  * While the loop runs it holds the SMs: other kernels on the same device wait.
@@ -325,10 +338,30 @@ bpsf_status bpsf_serve_poll(bpsf_server *s, uint64_t ticket, int64_t timeout_us,
  * starts, by one host thread, while another polls every outstanding request;
  * results are dropped.  On return latency_s[i] = completion time - scheduled
  * arrival of request i, and *span_s (nullable) = time from the start to the
- * last completion.
+ * last completion.  arrival_s NULL replays the trace closed loop instead:
+ * request i is submitted when request i - 1 has completed, and latency_s[i]
+ * is its own submit-to-results time.  Times come from the host's monotonic
+ * clock (std::chrono::steady_clock), as in bpsf_plain_replay.
  */
 bpsf_status bpsf_serve_replay(bpsf_server *s, int64_t n_req, const double *arrival_s, const int32_t *code,
                               const int64_t *n_shots, const uint32_t *const *synd, double *latency_s, double *span_s);
+
+/*
+ * The plain per-shot form serving the same kind of trace, on the same clock:
+ * one host thread takes request i (code index code[i] into codes[], n_shots[i]
+ * host rows at synd[i]) at arrival_s[i] (or, with arrival_s NULL, when request
+ * i - 1 is done), copies its syndromes to the device, decodes its shots one at
+ * a time with bpsf_decode_plain (each shot: initial-run launch, synchronise,
+ * read the flag, on failure the trial-sweep launch, synchronise) and copies
+ * the results back.  latency_s[i] = completion - scheduled arrival (closed
+ * loop: its own service time); *span_s (nullable) = start to last completion.
+ * Requests wait in arrival order while earlier ones are decoded, so an
+ * offered load above the form's rate shows as growing latency.  Allocates
+ * its staging buffers for the call.  codes: 1..16 contexts on one device.
+ */
+bpsf_status bpsf_plain_replay(bpsf_ctx *const *codes, int32_t n_codes, int64_t n_req, const double *arrival_s,
+                              const int32_t *code, const int64_t *n_shots, const uint32_t *const *synd,
+                              double *latency_s, double *span_s);
 
 /* Stop: new submits get BPSF_ECLOSED, admitted requests finish on the device
  * (bounded wait), the device loop ends and the server is freed.  Results not

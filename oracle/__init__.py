@@ -89,7 +89,7 @@ def lib():
             fn.restype = C.c_int
             fn = getattr(L, "oracle_bpsf_batch_" + sfx)
             fn.argtypes = [vp, rp, C.c_int64, _u8p, C.c_int, rt, C.c_int, C.c_int, vp, C.c_int, C.c_int, C.c_int,
-                           _u8p, _u8p, _i32p, _u8p, C.c_int]
+                           _u8p, _u8p, _i32p, _u8p, C.c_int, vp]
         L.oracle_bp_sumproduct.argtypes = [vp, _f64p, _u8p, C.c_int, _f64p]
         L.oracle_max_threads.restype = C.c_int
         _lib = L
@@ -300,8 +300,9 @@ class Code:
         return dict(e=e, converged=bool(conv), iters=it.value, stage=st.value,
                     phi=phi[: params.w] if params.w > 0 else phi[:0], flips=flips)
 
-    def bpsf_batch(self, synd, priors, params: Params, fp32=True, threads=1):
-        """BP-SF over a batch of syndromes (n, M) -> (e (n, N), converged, iters, stage)."""
+    def bpsf_batch(self, synd, priors, params: Params, fp32=True, threads=1, shot_s=None):
+        """BP-SF over a batch of syndromes (n, M) -> (e (n, N), converged, iters, stage).
+        shot_s: optional float64 array of n, filled with each shot's wall time in seconds."""
         synd = np.ascontiguousarray(synd, dtype=np.uint8)
         n = synd.shape[0]
         self.schedule(params.layered)
@@ -313,8 +314,10 @@ class Code:
         fn = lib().oracle_bpsf_batch_f32 if fp32 else lib().oracle_bpsf_batch_f64
         alpha_t = np.float32(params.alpha) if fp32 else float(params.alpha)
         masks, nm = _masks(params)
+        if shot_s is not None:
+            assert shot_s.dtype == np.float64 and shot_s.shape == (n,) and shot_s.flags["C_CONTIGUOUS"]
         fn(self._h, lch, n, synd, params.max_iter, alpha_t, params.w, params.w_max, _ptr(masks), nm,
-           params.short_iter, params.select, e, conv, iters, stage, int(threads))
+           params.short_iter, params.select, e, conv, iters, stage, int(threads), _ptr(shot_s))
         return e, conv.astype(bool), iters, stage
 
     def sumproduct(self, s, priors, iters):

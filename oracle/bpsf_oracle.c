@@ -38,10 +38,12 @@
  *     of the list (select = 1);
  *   - on total failure the initial run's e is returned with converged = 0.
  */
+#define _POSIX_C_SOURCE 199309L
 #include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#include <time.h>
 #ifdef _OPENMP
 #include <omp.h>
 #endif
@@ -488,6 +490,14 @@ void oracle_bp_sumproduct(const oracle_code *c, const double *lch, const uint8_t
 /* loop over shots may run on several host threads.                          */
 /* ------------------------------------------------------------------------ */
 
+/* Monotonic wall time in seconds (per-shot times of the CPU baseline; shot_s
+ * of the batch drivers is nullable and changes nothing else). */
+static double wall_s(void) {
+    struct timespec ts;
+    clock_gettime(CLOCK_MONOTONIC, &ts);
+    return (double)ts.tv_sec + 1e-9 * (double)ts.tv_nsec;
+}
+
 int oracle_max_threads(void) {
 #ifdef _OPENMP
     return omp_get_max_threads();
@@ -498,7 +508,8 @@ int oracle_max_threads(void) {
 
 void oracle_bpsf_batch_f32(const oracle_code *c, const float *lch, int64_t n, const uint8_t *synd, int max_iter,
                            float alpha, int w, int w_max, const uint64_t *masks, int n_masks, int short_iter,
-                           int select, uint8_t *e_out, uint8_t *conv, int32_t *iters, uint8_t *stage, int threads) {
+                           int select, uint8_t *e_out, uint8_t *conv, int32_t *iters, uint8_t *stage, int threads,
+                           double *shot_s) {
 #ifdef _OPENMP
 #pragma omp parallel for schedule(dynamic, 8) num_threads(threads > 0 ? threads : 1)
 #else
@@ -506,16 +517,19 @@ void oracle_bpsf_batch_f32(const oracle_code *c, const float *lch, int64_t n, co
 #endif
     for (int64_t k = 0; k < n; k++) {
         int it = 0, st = 0;
+        const double t0 = shot_s ? wall_s() : 0.0;
         conv[k] = (uint8_t)oracle_bpsf_f32(c, lch, synd + k * c->M, max_iter, alpha, w, w_max, masks, n_masks,
                                            short_iter, select, e_out + k * c->N, &it, &st, NULL, NULL);
         iters[k] = it;
         stage[k] = (uint8_t)st;
+        if (shot_s) shot_s[k] = wall_s() - t0;
     }
 }
 
 void oracle_bpsf_batch_f64(const oracle_code *c, const double *lch, int64_t n, const uint8_t *synd, int max_iter,
                            double alpha, int w, int w_max, const uint64_t *masks, int n_masks, int short_iter,
-                           int select, uint8_t *e_out, uint8_t *conv, int32_t *iters, uint8_t *stage, int threads) {
+                           int select, uint8_t *e_out, uint8_t *conv, int32_t *iters, uint8_t *stage, int threads,
+                           double *shot_s) {
 #ifdef _OPENMP
 #pragma omp parallel for schedule(dynamic, 8) num_threads(threads > 0 ? threads : 1)
 #else
@@ -523,9 +537,11 @@ void oracle_bpsf_batch_f64(const oracle_code *c, const double *lch, int64_t n, c
 #endif
     for (int64_t k = 0; k < n; k++) {
         int it = 0, st = 0;
+        const double t0 = shot_s ? wall_s() : 0.0;
         conv[k] = (uint8_t)oracle_bpsf_f64(c, lch, synd + k * c->M, max_iter, alpha, w, w_max, masks, n_masks,
                                            short_iter, select, e_out + k * c->N, &it, &st, NULL, NULL);
         iters[k] = it;
         stage[k] = (uint8_t)st;
+        if (shot_s) shot_s[k] = wall_s() - t0;
     }
 }

@@ -28,7 +28,7 @@ EXPORTS = (
     "bpsf_serve_poll", "bpsf_serve_stop", "bpsf_bb_code", "bpsf_phenom_code", "bpsf_syndrome", "bpsf_decode_debug",
     "bpsf_num_trials", "bpsf_last_work", "bpsf_status_str", "bpsf_last_error", "bpsf_decode_noalloc",
     "bpsf_noalloc_max_shots", "bpsf_selftest_wait", "bpsf_serve_replay", "bpsf_set_trials",
-    "bpsf_decode_multi_host",
+    "bpsf_decode_multi_host", "bpsf_plain_replay",
 )
 
 
@@ -45,10 +45,10 @@ class bpsf_params(C.Structure):
 
 class bpsf_tuning(C.Structure):
     _fields_ = [("warps_per_team", C.c_int32), ("slots_per_team", C.c_int32), ("warps_per_block", C.c_int32),
-                ("blocks_per_sm", C.c_int32)]
+                ("blocks_per_sm", C.c_int32), ("iter_chunk", C.c_int32)]
 
     def as_tuple(self):
-        return (self.warps_per_team, self.slots_per_team, self.warps_per_block, self.blocks_per_sm)
+        return (self.warps_per_team, self.slots_per_team, self.warps_per_block, self.blocks_per_sm, self.iter_chunk)
 
 
 class bpsf_job(C.Structure):
@@ -104,6 +104,7 @@ def lib():
         "bpsf_serve_poll": ([vp, C.c_uint64, i64, vp, vp, vp, vp], st),
         "bpsf_serve_stop": ([vp], st),
         "bpsf_serve_replay": ([vp, i64, vp, vp, vp, vp, vp, C.POINTER(C.c_double)], st),
+        "bpsf_plain_replay": ([C.POINTER(vp), i32, i64, vp, vp, vp, vp, vp, C.POINTER(C.c_double)], st),
         "bpsf_bb_code": ([i32, i32, i32, vp, vp, i32, vp, vp, i32, vp, vp, i64, C.POINTER(i64)], st),
         "bpsf_phenom_code": ([i32, i32, vp, vp, i32, vp, vp, i64, C.POINTER(i64)], st),
         "bpsf_syndrome": ([vp, i64, vp, i32, vp, i32, vp], st),
@@ -452,18 +453,8 @@ class Server:
         return dict(corr=corr, conv=conv, iters=iters, stage=stage)
 
     def replay(self, arrival_s, codes, synds):
-        """Open-loop replay; returns (per-request latency in s, span in s)."""
-        n = len(arrival_s)
-        arr = np.ascontiguousarray(arrival_s, dtype=np.float64)
-        cd = np.ascontiguousarray(codes, dtype=np.int32)
-        synds = [np.ascontiguousarray(x).view(np.uint32) for x in synds]
-        ns = np.array([x.shape[0] for x in synds], dtype=np.int64)
-        ptrs = (C.c_void_p * n)(*[x.ctypes.data for x in synds])
-        lat = np.zeros(n, dtype=np.float64)
-        span = C.c_double(0.0)
-        check(lib().bpsf_serve_replay(self.handle, n, _np_ptr(arr), _np_ptr(cd), _np_ptr(ns), ptrs, _np_ptr(lat),
-                                      C.byref(span)))
-        return lat, span.value
+        """Open-loop replay (arrival_s None: closed loop); returns (per-request latency in s, span in s)."""
+        return _replay(lambda *a: lib().bpsf_serve_replay(self.handle, *a), arrival_s, codes, synds)
 
     def stop(self):
         h, self.handle = self.handle, None
@@ -475,6 +466,31 @@ class Server:
             self.stop()
         except Exception:
             pass
+
+
+def _trace_args(arrival_s, codes, synds):
+    n = len(codes)
+    arr = None if arrival_s is None else np.ascontiguousarray(arrival_s, dtype=np.float64)
+    cd = np.ascontiguousarray(codes, dtype=np.int32)
+    synds = [np.ascontiguousarray(x).view(np.uint32) for x in synds]
+    ns = np.array([x.shape[0] for x in synds], dtype=np.int64)
+    ptrs = (C.c_void_p * n)(*[x.ctypes.data for x in synds])
+    return n, arr, cd, synds, ns, ptrs
+
+
+def _replay(fn, arrival_s, codes, synds):
+    n, arr, cd, synds, ns, ptrs = _trace_args(arrival_s, codes, synds)
+    lat = np.zeros(n, dtype=np.float64)
+    span = C.c_double(0.0)
+    check(fn(n, None if arr is None else _np_ptr(arr), _np_ptr(cd), _np_ptr(ns), ptrs, _np_ptr(lat), C.byref(span)))
+    return lat, span.value
+
+
+def plain_replay(decoders, arrival_s, codes, synds):
+    """bpsf_plain_replay: the plain per-shot form serving a trace (arrival_s None: closed
+    loop); returns (per-request latency in s, span in s)."""
+    hs = (C.c_void_p * len(decoders))(*[d.handle for d in decoders])
+    return _replay(lambda *a: lib().bpsf_plain_replay(hs, len(decoders), *a), arrival_s, codes, synds)
 
 
 def decode_multi_host(decoders, synds, stream=None):

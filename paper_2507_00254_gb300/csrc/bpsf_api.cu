@@ -121,6 +121,7 @@ static bpsf_status check_shape(const bpsf_tuning &t) {
         return bpsf_fail(BPSF_EINVAL, "warps_per_block must be a multiple of warps_per_team, at most %d",
                          kMaxComputeWarps);
     if (t.blocks_per_sm < 0) return bpsf_fail(BPSF_EINVAL, "blocks_per_sm must be >= 0");
+    if (t.iter_chunk < 0 || t.iter_chunk > 64) return bpsf_fail(BPSF_EINVAL, "iter_chunk must be in 0..64");
     return BPSF_OK;
 }
 
@@ -196,6 +197,7 @@ bpsf_status bpsf_make_plan(bpsf_ctx *const *codes, int n_codes, const bpsf_tunin
             out->S_code[k] = S;
             out->W_code[k] = W;
             out->teams_code[k] = teams;
+            out->chunk_code[k] = std::max(1, tunes[k].iter_chunk);
             smem = std::max(smem, need);
         }
         return true;
@@ -215,6 +217,13 @@ bpsf_status bpsf_make_plan(bpsf_ctx *const *codes, int n_codes, const bpsf_tunin
         if (out->W_code[k] > 1 && out->teams_code[k] > kMaxNamedTeams)
             return bpsf_fail(BPSF_EINVAL, "too many multi-warp teams");
     if (byte_flips) variant = kernel_variant_byte_flips(variant);
+    // Exact (6, 4, 3) codes in a launch that needs wider rows keep their own path.
+    if (!all_regular && !layered && kernel_variant_mixed(variant) >= 0) {
+        bool any_exact = false;
+        for (int k = 0; k < n_codes; ++k)
+            any_exact = any_exact || (codes[k]->regular && codes[k]->dc_max == 6 && codes[k]->dv_max == 3);
+        if (any_exact) variant = kernel_variant_mixed(variant);
+    }
     bpsf_status st = bpsf_ensure_kernel_attrs(variant, c0->smem_optin);
     if (st != BPSF_OK) return st;
     const int block = 32 * (B + 1);
@@ -728,6 +737,7 @@ void bpsf_launch_plan(const bpsf_plan &pl, bool debug, StreamDev *sds, int n, in
         bpsf_activate_layout(sds[k].code, pl.S_code[k]);
         sds[k].W = pl.W_code[k];
         sds[k].teams = pl.teams_code[k];
+        sds[k].chunk = pl.chunk_code[k];
     }
     LaunchArgs la{sds, n, pl.Q, kBpsfWaitNs};
     launch_persistent(pl.variant, debug, pl.layered, grid, pl.block, pl.smem, la, stream);
@@ -871,7 +881,7 @@ extern "C" bpsf_status bpsf_decode_plain(bpsf_ctx *c, int64_t n, const uint32_t 
     bpsf_ctx *cs1[1] = {c};
     // Launch A: one block, one team, one slot, the initial run of one shot.
     bpsf_plan plA, plB;
-    bpsf_tuning tA{c->tune.warps_per_team, 1, c->tune.warps_per_team, 0};
+    bpsf_tuning tA{c->tune.warps_per_team, 1, c->tune.warps_per_team, 0, 1};
     st = bpsf_make_plan(cs1, 1, &tA, false, &plA);
     if (st != BPSF_OK) return st;
     // Launch B: the shot's trials spread over blocks of the tuned shape.
@@ -1109,11 +1119,15 @@ extern "C" bpsf_status bpsf_set_tuning(bpsf_ctx *c, const bpsf_tuning *t) {
     return BPSF_OK;
 }
 
-typedef std::tuple<int, int, int, int, int> ShapeKey;  // M, N, nnz, dc, dv
+// Cache key: the code's shape and the parameters that set the work per shot.
+typedef std::tuple<int, int, int, int, int, int, int, int, int, unsigned> ShapeKey;
 static std::mutex g_tune_mu;
 static std::map<ShapeKey, bpsf_tuning> g_tune_cache;
 
-static ShapeKey shape_key(const bpsf_ctx *c) { return ShapeKey(c->M, c->N, c->nnz, c->dc_max, c->dv_max); }
+static ShapeKey shape_key(const bpsf_ctx *c) {
+    return ShapeKey(c->M, c->N, c->nnz, c->dc_max, c->dv_max, c->p.max_iter, c->p.w, c->n_trials, c->p.short_iter,
+                    c->p.flags);
+}
 
 bool bpsf_tuning_cache_lookup(const bpsf_ctx *c, bpsf_tuning *out) {
     std::lock_guard<std::mutex> lk(g_tune_mu);
@@ -1155,34 +1169,52 @@ extern "C" bpsf_status bpsf_autotune(bpsf_ctx *c, double p_sample, int64_t n_sam
     bpsf_tuning best = saved;
     float best_ms = 1e30f;
     bpsf_status st = BPSF_OK;
+    bpsf_ctx *cs1[1] = {c};
+    // Time one shape: the best of two decodes after a warm-up decode.
+    auto time_shape = [&](const bpsf_tuning &t) -> float {
+        c->tune = t;
+        float ms_min = 1e30f;
+        for (int rep = 0; rep < 3 && st == BPSF_OK; ++rep) {
+            cudaEventRecord(e0, s);
+            st = bpsf_decode(c, n_sample, synd, c->Ws, corr, c->Wn, conv, it, nullptr, stream);
+            cudaEventRecord(e1, s);
+            if (st == BPSF_OK) st = bpsf_sync(c, stream);
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (rep > 0) ms_min = std::min(ms_min, ms);
+        }
+        return ms_min;
+    };
+    // Threads per shot and shots per block: warps per team, slots per team and
+    // compute warps per block, every shape that fits.
     const int Ws_[] = {1, 2, 4, 8};
     const int Ss_[] = {1, 2, 4, 8, 16, 32};
     const int Bs_[] = {1, 2, 3, 4, 6, 7, 8, 10, 12, 13, 14, 15};
-    bpsf_ctx *cs1[1] = {c};
     for (int W : Ws_)
         for (int S : Ss_)
             for (int B : Bs_) {
-                bpsf_tuning t{W, S, B, 0};
+                if (st != BPSF_OK) break;
+                bpsf_tuning t{W, S, B, 0, 1};
                 if (B % W) continue;
                 bpsf_plan pl;
                 if (bpsf_make_plan(cs1, 1, &t, false, &pl) != BPSF_OK) continue;
-                c->tune = t;
-                float ms_min = 1e30f;
-                for (int rep = 0; rep < 3 && st == BPSF_OK; ++rep) {
-                    cudaEventRecord(e0, s);
-                    st = bpsf_decode(c, n_sample, synd, c->Ws, corr, c->Wn, conv, it, nullptr, stream);
-                    cudaEventRecord(e1, s);
-                    if (st == BPSF_OK) st = bpsf_sync(c, stream);
-                    float ms = 0;
-                    cudaEventElapsedTime(&ms, e0, e1);
-                    if (rep > 0) ms_min = std::min(ms_min, ms);
-                }
-                if (st != BPSF_OK) break;
-                if (ms_min < best_ms) {
-                    best_ms = ms_min;
+                const float ms = time_shape(t);
+                if (st == BPSF_OK && ms < best_ms) {
+                    best_ms = ms;
                     best = t;
                 }
             }
+    // The iteration chunk of the fastest shape.
+    for (int k : {2, 4, 8}) {
+        if (st != BPSF_OK || best_ms >= 1e30f) break;
+        bpsf_tuning t = best;
+        t.iter_chunk = k;
+        const float ms = time_shape(t);
+        if (st == BPSF_OK && ms < best_ms) {
+            best_ms = ms;
+            best = t;
+        }
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaFree(buf);
@@ -1231,6 +1263,7 @@ extern "C" bpsf_status bpsf_selftest_wait(bpsf_ctx *c, int64_t wait_us, void *st
     bpsf_activate_layout(sd.code, pl.S_code[0]);
     sd.W = pl.W_code[0];
     sd.teams = pl.teams_code[0];
+    sd.chunk = pl.chunk_code[0];
     LaunchArgs la{&sd, 1, pl.Q, (unsigned long long)wait_us * 1000ull};
     launch_persistent(pl.variant, false, pl.layered, 1, pl.block, pl.smem, la, stream);
     e = cudaGetLastError();

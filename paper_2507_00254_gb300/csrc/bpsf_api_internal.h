@@ -41,6 +41,7 @@ struct bpsf_plan {
     int S_code[bpsf::kMaxStreams] = {0};      // slots per team, per code of the launch
     int W_code[bpsf::kMaxStreams] = {0};      // warps per team, per code
     int teams_code[bpsf::kMaxStreams] = {0};  // teams per block, per code
+    int chunk_code[bpsf::kMaxStreams] = {0};  // iterations between refills, per code
 };
 
 bpsf_status bpsf_fail(bpsf_status s, const char *fmt, ...);

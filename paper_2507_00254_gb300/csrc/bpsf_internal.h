@@ -121,12 +121,13 @@ struct DebugDev {
 };
 
 // Serving: shots carry global sequence numbers g; shot g uses arena row
-// g % rows.  The host copies a request's syndromes into its rows and then,
-// on the same copy stream, the new published count (so the count never runs
-// ahead of the rows); the device posts g + 1 to the row's completion word
+// g % rows.  The host writes a request's syndromes into its rows of the
+// host-mapped arena and then stores the new published count with release
+// semantics; the device reads the count with system-scope acquire loads
+// before it reads the rows, and posts g + 1 to the row's completion word
 // once the shot's results are in the host-mapped output rows.
 struct ServeDev {
-    volatile long long *published;   // shots published for this code (device memory)
+    volatile long long *published;   // shots published for this code (host-mapped)
     volatile int *stop;              // host asks the loop to end (host-mapped)
     volatile unsigned *row_done;     // rows: (g + 1) once the shot's results are out (host-mapped)
     long long rows;                  // arena rows
@@ -142,7 +143,7 @@ struct StreamDev {
     ServeDev serve;
     unsigned flags;  // kNoTickets, kServe
     int S, W, teams; // team shape for this code: teams of W warps with S slots each
-    int pad;
+    int chunk;       // team iterations between refills of finished slots (>= 1)
 };
 
 // Launch: the team shape is set per stream (StreamDev::S, W, teams); each
@@ -186,7 +187,7 @@ enum : int { kSlotEmpty = 0, kSlotRunning = 1, kSlotPending = 2 };
 struct SlotState {
     int state;       // kSlot*
     int kind;        // 1 initial run, 2 trial run
-    int spare;
+    int start;       // team iteration at which the current run's first iteration ran
     int outcome;     // 1 converged, 2 iteration cap, 3 stopped (cannot win); valid when PENDING
     int iter;        // iterations completed
     int limit;       // iteration cap of this run
@@ -215,13 +216,21 @@ struct OutBox {
 };
 static_assert(sizeof(OutBox) == 32, "outbox is 32 bytes");
 
-// Team control block (32 bytes).
+// Team control block (48 bytes).  run_mask, init_mask and exit are written
+// by the team's warp 0 at a service step and read by the whole team after the
+// barrier that follows; stop_mask[t & 1] holds the slots whose run ends after
+// team iteration t whatever its syndrome (iteration cap, or a trial asked to
+// stop), written by warp 0 before the iteration's first barrier and read by
+// every warp after its last, so consecutive iterations use different words.
 struct TeamCtl {
-    unsigned run_mask, spare, init_mask;
+    unsigned run_mask, init_mask;
     int exit;
+    unsigned stop_mask[2];
+    unsigned pad;
     unsigned long long iters;  // iterations run by this team (all slots)
     unsigned long long cap;    // team iterations with a running slot, times S
 };
+static_assert(sizeof(TeamCtl) <= 48, "team control block fits its 48 bytes");
 
 // Work items of the manager's ready queue and of the slots' inboxes: 16
 // bytes of fields plus Ws syndrome words (a trial's words are s' = s xor t H^T).  kind 1 = initial run of a shot,
@@ -261,7 +270,7 @@ __host__ __device__ inline TeamOffsets team_offsets(int S, int M, int N, int P, 
     TeamOffsets o;
     const int sw = (S * M + 31) / 32;
     int p = 0;
-    o.ctl = p;     p += 32;
+    o.ctl = p;     p += 48;
     o.state = p;   p += (int)sizeof(SlotState) * S;
     o.outbox = p;  p += (int)sizeof(OutBox) * S;
     o.syn = p;     p += 4 * sw;
@@ -296,6 +305,7 @@ int kernel_variant(int dc_max, int dv_max);  // smallest variant that fits, -1 i
 int kernel_variant_dv(int variant);          // column table width of a variant
 int kernel_variant_full_regs(int variant);   // its one-block, full-register instance
 int kernel_variant_byte_flips(int variant);  // its one-block instance with one-byte flip words, -1 if none
+int kernel_variant_mixed(int variant);       // its instance with the exact (6, 4, 3) path as well, -1 if none
 const void *persistent_kernel_ptr(int variant, bool debug, bool layered);
 void launch_persistent(int variant, bool debug, bool layered, int grid, int block, int smem, const LaunchArgs &args,
                        void *stream);

@@ -20,6 +20,7 @@ KernelFn kernel_fn_v3(bool debug, bool lay);
 KernelFn kernel_fn_v4(bool debug, bool lay);
 KernelFn kernel_fn_v5(bool debug, bool lay);
 KernelFn kernel_fn_v6(bool debug, bool lay);
+KernelFn kernel_fn_v7(bool debug, bool lay);
 
 // ---------------------------------------------------------------------------
 // Variants and launch helpers.
@@ -29,9 +30,12 @@ struct Variant {
     int dc, dvs, dvx;  // row-degree bound, column table width, exact column degree (0 = any)
 };
 // Index 5 is the full-register instance of variant 0 and index 6 the same
-// with one-byte flip words (neither is chosen by kernel_variant; see
-// kernel_variant_full_regs and kernel_variant_byte_flips).
-static const Variant kVariants[] = {{6, 4, 3}, {6, 4, 0}, {8, 4, 0}, {16, 8, 0}, {32, 16, 0}, {6, 4, 3}, {6, 4, 3}};
+// with one-byte flip words; index 7 is variant 2 with the exact (6, 4, 3)
+// path for the codes that have it (none is chosen by kernel_variant; see
+// kernel_variant_full_regs, kernel_variant_byte_flips and
+// kernel_variant_mixed).
+static const Variant kVariants[] = {{6, 4, 3}, {6, 4, 0}, {8, 4, 0}, {16, 8, 0}, {32, 16, 0}, {6, 4, 3}, {6, 4, 3},
+                                    {8, 4, 0}};
 static const int kNumVariants = 5;
 
 // Smallest variant that fits.  The exact-degree variant serves codes with
@@ -59,7 +63,8 @@ static KernelFn kernel_fn(int variant, bool debug, bool lay) {
         case 3: return kernel_fn_v3(debug, lay);
         case 4: return kernel_fn_v4(debug, lay);
         case 5: return kernel_fn_v5(debug, lay);
-        default: return kernel_fn_v6(debug, lay);
+        case 6: return kernel_fn_v6(debug, lay);
+        default: return kernel_fn_v7(debug, lay);
     }
 }
 
@@ -70,6 +75,10 @@ int kernel_variant_full_regs(int variant) { return variant == 0 ? 5 : variant; }
 
 // The instance with one-byte flip words (full registers, no layered path), or -1.
 int kernel_variant_byte_flips(int variant) { return (variant == 0 || variant == 5) ? 6 : -1; }
+
+// The instance that runs variant 2's codes together with exact (6, 4, 3)
+// codes on their own path, or -1.
+int kernel_variant_mixed(int variant) { return variant == 2 ? 7 : -1; }
 
 const void *persistent_kernel_ptr(int variant, bool debug, bool layered) {
     return reinterpret_cast<const void *>(kernel_fn(variant, debug, layered));

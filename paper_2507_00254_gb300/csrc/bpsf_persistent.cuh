@@ -804,14 +804,6 @@ __device__ __forceinline__ void layered_iteration_vec(const StreamDev &sd, const
     }
 }
 
-// Bits b of a 32-bit word with b = s (mod S): the residual-syndrome bits
-// of slot s when shifted left by s (S is a power of two dividing 32).
-__device__ __forceinline__ unsigned slot_pattern(int S) {
-    unsigned p = 1u;
-    for (int w = S; w < 32; w <<= 1) p |= p << w;
-    return p;
-}
-
 // ---------------------------------------------------------------------------
 // Team-side slot service (warp 0 of the team, all lanes).  A finished slot
 // (PENDING) hands its facts to its outbox as soon as the manager has drained
@@ -910,6 +902,7 @@ __device__ __forceinline__ void team_install(const StreamDev &sd, const LayoutMe
         ss->kidx = e->kidx;
         ss->shot = e->shot;
         ss->iter = 0;
+        ss->start = -1;  // set by the team at the service that starts the run
         ss->outcome = 0;
         ss->cancel = 0;
         ss->limit = e->kind == 1 ? cd.max_iter : cd.short_iter;
@@ -959,137 +952,198 @@ __device__ __forceinline__ void team_service(const StreamDev &sd, const LayoutMe
 
 // ---------------------------------------------------------------------------
 // Compute team loop.
+//
+// A team iteration is: C phase, barrier, V phase, barrier, decision.  The
+// decision needs no further barrier: every warp reads the residual-syndrome
+// words (stable until the next V phase, which lies beyond the next barrier)
+// and the iteration's stop mask (written by warp 0 before the first barrier,
+// one word per iteration parity), so all warps agree on which slots are done.
+// The service step (a barrier, warp 0 packs finished slots and installs new
+// items, a barrier) runs only after an iteration in which a slot finished, or
+// while a slot is empty, and with an iteration chunk k > 1 at most every k
+// iterations while some slot still runs; a team whose slots all keep running
+// goes from one iteration to the next with two barriers.
 // ---------------------------------------------------------------------------
 template <int DC, int DVS, int DVX, bool DEBUG, int MINB, bool LAY, int FB>
 __device__ void team_loop(const StreamDev &sd, const LayoutMem &L, const TeamMem &T, BlockHdr *hdr, int S, int W,
                           int tid, int bar_id, unsigned long long wait_ns) {
     const int lane = tid & 31, wt = tid >> 5, nthreads = 32 * W;
     const CodeDev &cd = sd.code;
-    const int Wn = cd.Wn, N = cd.N;
     const int lgS = __ffs(S) - 1;
     const int my_slot = lane & (S - 1);             // the slot this lane serves in every phase
     const int n_rwords = ((cd.M << lgS) + 31) >> 5;  // residual-syndrome words of the team
-    const unsigned pat = slot_pattern(S) << (lane < S ? lane : 0);
+    const unsigned full = S >= 32 ? 0xffffffffu : ((1u << S) - 1u);
     constexpr bool kVec = BPSF_PAIRS && DC <= 16;  // the widest rows keep one slot per lane (registers)
     // Four slots per lane: exact-degree rows with the full register budget (one block).
     constexpr bool kVec4 = kVec && MINB == 1 && DVX == 3 && BPSF_VEC >= 4;
     // Layered schedule: vector lanes in the full-register instances only.
     constexpr bool kLayV2 = LAY && kVec && MINB == 1 && DC <= 6, kLayV4 = kLayV2 && kVec4;
+    const bool lay = LAY && cd.layered;
+    // Slots per lane in the phases (vs) and the lane's first slot (s0).
+    const int vs = lay ? ((kLayV4 && S >= 4) ? 4 : ((kLayV2 && S >= 2) ? 2 : 1))
+                       : ((kVec4 && S >= 4) ? 4 : ((kVec && S >= 2) ? 2 : 1));
+    const int s0 = vs * (lane & ((S / vs) - 1));
     unsigned long long idle_since = 0;
     unsigned last_beat = 0;
+    unsigned run = 0u, initm = 0u;
+    int tt = 0;                   // team iterations run (the same in every warp)
+    int start[4] = {0, 0, 0, 0};  // team iteration of the first iteration of the lane's slots' runs
+    // Every warp, lane l < S: slot l's first team iteration and iteration cap.
+    int l_start = 0, l_lim = 0;
+    // Warp 0, lane s < S: slot s's stop key (first-success rule).
+    long long w_key = 0;
+    // Warp 0, lane 0: iterations run and slot-iterations offered since the
+    // last service (added to the control block at the next service).
+    unsigned long long n_iters = 0, n_cap = 0;
+    const bool first_rule = cd.select == 1;
+    bool svc = true;
+    const int chunk = sd.chunk > 1 ? sd.chunk : 1;  // iterations between refills of finished slots
+    int since = 0;                                  // team iterations since the last service
     for (;;) {
-        if (wt == 0) {
-            team_service<DEBUG, FB>(sd, L, T, S, lgS, lane);
-            SlotState *ss = &T.st[lane < S ? lane : 0];
-            const int stv = lane < S ? *vstate(ss) : kSlotEmpty;
-            const bool r = stv == kSlotRunning;
-            __threadfence_block();
-            const unsigned run = __ballot_sync(FULLMASK, r);
-            const unsigned im = __ballot_sync(FULLMASK, r && ss->kind == 1);
-            int ex = 0;
-            if (run == 0u) {
-                if (hdr->exit) {
-                    ex = 1;
-                } else {
-                    // Never wait forever: give up only if the manager has made
-                    // no pass for twice the bound on any of its own waits.
-                    const unsigned long long now = globaltimer_ns();
-                    const unsigned beat = hdr->heartbeat;
-                    if (idle_since == 0 || beat != last_beat) {
-                        idle_since = now;
-                        last_beat = beat;
-                    }
-                    if (now - idle_since > 2 * wait_ns) ex = 1;
-                    __nanosleep(100);
+        if (svc) {
+            // Every warp has made the previous decision (read the residual
+            // words, which an install rewrites) and has read the control
+            // block of the previous service.
+            team_sync(W, bar_id);
+            if (wt == 0) {
+                // The work counters first: the manager adds them up once every
+                // slot of the block reads empty, which the service below may make so.
+                if (lane == 0 && n_cap) {
+                    T.ctl->iters += n_iters;
+                    T.ctl->cap += n_cap;
+                    n_iters = n_cap = 0;
                 }
-            } else {
-                idle_since = 0;
+                team_service<DEBUG, FB>(sd, L, T, S, lgS, lane);
+                SlotState *ss = &T.st[lane < S ? lane : 0];
+                const int stv = lane < S ? *vstate(ss) : kSlotEmpty;
+                const bool r = stv == kSlotRunning;
+                __threadfence_block();
+                const unsigned rm = __ballot_sync(FULLMASK, r);
+                const unsigned im = __ballot_sync(FULLMASK, r && ss->kind == 1);
+                if (r) {
+                    // A run installed at this service starts with the next iteration.
+                    if (ss->start < 0) ss->start = tt;
+                    w_key = ss->kind == 2 ? ss->shot * (long long)cd.n_trials + ss->kidx + 1 : 0;
+                }
+                int ex = 0;
+                if (rm == 0u) {
+                    if (hdr->exit) {
+                        ex = 1;
+                    } else {
+                        // Never wait forever: give up only if the manager has made
+                        // no pass for twice the bound on any of its own waits.
+                        const unsigned long long now = globaltimer_ns();
+                        const unsigned beat = hdr->heartbeat;
+                        if (idle_since == 0 || beat != last_beat) {
+                            idle_since = now;
+                            last_beat = beat;
+                        }
+                        if (now - idle_since > 2 * wait_ns) ex = 1;
+                        __nanosleep(100);
+                    }
+                } else {
+                    idle_since = 0;
+                }
+                if (lane == 0) {
+                    T.ctl->run_mask = rm;
+                    T.ctl->init_mask = im;
+                    T.ctl->exit = ex;
+                }
             }
-            if (lane == 0) {
-                T.ctl->run_mask = run;
-                T.ctl->init_mask = im;
-                T.ctl->exit = ex;
-                T.ctl->iters += (unsigned long long)__popc(run);
-                if (run) T.ctl->cap += (unsigned long long)S;
+            team_sync(W, bar_id);
+            run = T.ctl->run_mask;
+            initm = T.ctl->init_mask;
+            const int ex = T.ctl->exit;
+            if (ex) break;
+            if (run == 0u) continue;
+            for (int c = 0; c < vs; ++c) start[c] = T.st[s0 + c].start;
+            if (lane < S) {
+                l_start = T.st[lane].start;
+                l_lim = T.st[lane].limit;
             }
+            svc = false;
+            since = 0;
         }
-        team_sync(W, bar_id);
-        const unsigned run = T.ctl->run_mask, initm = T.ctl->init_mask;
-        const int ex = T.ctl->exit;
-        team_sync(W, bar_id);
-        if (ex) break;
-        if (run == 0u) continue;
-        if (LAY && cd.layered) {
-            if (kLayV4 && S >= 4) {
-                const int s0 = 4 * (lane & ((S >> 2) - 1));
-                float al[4];
+        // First-success rule: warp 0 publishes the trials the manager asked to
+        // stop (they cannot win), read by every warp after this iteration.
+        if (first_rule && wt == 0) {
+            const bool cancel = lane < S && ((run >> lane) & 1u) && w_key != 0 &&
+                                *reinterpret_cast<volatile long long *>(&T.st[lane].cancel) == w_key;
+            const unsigned cm = __ballot_sync(FULLMASK, cancel);
+            if (lane == 0) T.ctl->stop_mask[tt & 1] = cm;
+        }
+        // Damping of iteration it = tt - start + 1 of each of the lane's slots.
+        float al[4];
 #pragma unroll
-                for (int c = 0; c < 4; ++c) al[c] = damping(cd, T.st[s0 + c].iter + 1);
-                layered_iteration_vec<DC, DVS, DVX, DEBUG, 4, FB>(sd, L, T, lgS, (run >> s0) & 0xfu, al, initm, tid,
+        for (int c = 0; c < 4; ++c) al[c] = damping(cd, tt - start[c] + 1);
+        if (lay) {
+            if (kLayV4 && vs == 4) {
+                float a4[4] = {al[0], al[1], al[2], al[3]};
+                layered_iteration_vec<DC, DVS, DVX, DEBUG, 4, FB>(sd, L, T, lgS, (run >> s0) & 0xfu, a4, initm, tid,
                                                               nthreads, W, bar_id);
-            } else if (kLayV2 && S >= 2) {
-                const int s0 = 2 * (lane & ((S >> 1) - 1));
-                float al[2];
-                al[0] = damping(cd, T.st[s0].iter + 1);
-                al[1] = damping(cd, T.st[s0 + 1].iter + 1);
-                layered_iteration_vec<DC, DVS, DVX, DEBUG, 2, FB>(sd, L, T, lgS, (run >> s0) & 0x3u, al, initm, tid,
+            } else if (kLayV2 && vs == 2) {
+                float a2[2] = {al[0], al[1]};
+                layered_iteration_vec<DC, DVS, DVX, DEBUG, 2, FB>(sd, L, T, lgS, (run >> s0) & 0x3u, a2, initm, tid,
                                                               nthreads, W, bar_id);
             } else {
                 const bool lane_on = (run >> my_slot) & 1u;
-                layered_iteration<DC, DVS, DVX, DEBUG, FB>(sd, L, T, lgS, lane_on, damping(cd, T.st[my_slot].iter + 1),
-                                                       initm, tid, nthreads, W, bar_id);
+                layered_iteration<DC, DVS, DVX, DEBUG, FB>(sd, L, T, lgS, lane_on, al[0], initm, tid, nthreads, W,
+                                                       bar_id);
             }
             team_sync(W, bar_id);
-        } else if (kVec4 && S >= 4) {
-            const int s0 = 4 * (lane & ((S >> 2) - 1));
+        } else if (kVec4 && vs == 4) {
             const unsigned onm = (run >> s0) & 0xfu;
-            float al[4];
-#pragma unroll
-            for (int c = 0; c < 4; ++c) al[c] = damping(cd, T.st[s0 + c].iter + 1);
-            if (onm) c_phase_vec<DC, (DVX > 0), 4>(cd, L, T, lgS, al, tid, nthreads);
+            float a4[4] = {al[0], al[1], al[2], al[3]};
+            if (onm) c_phase_vec<DC, (DVX > 0), 4>(cd, L, T, lgS, a4, tid, nthreads);
             team_sync(W, bar_id);
             if (onm) v_phase_vec<DVS, DVX, DEBUG, 4, FB>(sd, L, T, lgS, onm, initm, tid, nthreads);
             team_sync(W, bar_id);
-        } else if (kVec && S >= 2) {
-            const int s0 = 2 * (lane & ((S >> 1) - 1));
+        } else if (kVec && vs == 2) {
             const unsigned onm = (run >> s0) & 0x3u;
-            float al[2];
-            al[0] = damping(cd, T.st[s0].iter + 1);
-            al[1] = damping(cd, T.st[s0 + 1].iter + 1);
-            if (onm) c_phase_vec<DC, (DVX > 0), 2>(cd, L, T, lgS, al, tid, nthreads);
+            float a2[2] = {al[0], al[1]};
+            if (onm) c_phase_vec<DC, (DVX > 0), 2>(cd, L, T, lgS, a2, tid, nthreads);
             team_sync(W, bar_id);
             if (onm) v_phase_vec<DVS, DVX, DEBUG, 2, FB>(sd, L, T, lgS, onm, initm, tid, nthreads);
             team_sync(W, bar_id);
         } else {
             const bool lane_on = (run >> my_slot) & 1u;
-            if (lane_on) c_phase<DC, (DVX > 0)>(cd, L, T, lgS, damping(cd, T.st[my_slot].iter + 1), tid, nthreads);
+            if (lane_on) c_phase<DC, (DVX > 0)>(cd, L, T, lgS, al[0], tid, nthreads);
             team_sync(W, bar_id);
             if (lane_on) v_phase<DVS, DVX, DEBUG, FB>(sd, L, T, lgS, initm, tid, nthreads);
             team_sync(W, bar_id);
         }
+        // Decision, in every warp: slot s owns bits s, s + S, s + 2S, ... of
+        // every residual-syndrome word, so OR-folding the words down to S
+        // bits leaves bit s set iff slot s's residual syndrome is not zero.
+        unsigned acc = 0;
+        for (int w = lane; w < n_rwords; w += 32) acc |= T.mism[w];
+        acc = __reduce_or_sync(FULLMASK, acc);
+        for (int sh = 16; sh >= S; sh >>= 1) acc |= acc >> sh;
+        const unsigned nconv = acc & full;
+        // Runs at their iteration cap (every warp knows every slot's cap), and
+        // trials asked to stop.
+        const int it = tt - l_start + 1;  // lane l: this iteration's number in slot l's run
+        const unsigned capped = __ballot_sync(FULLMASK, lane < S && it >= l_lim);
+        const unsigned cancelled = first_rule ? T.ctl->stop_mask[tt & 1] : 0u;
+        const unsigned done = run & (~nconv | capped | cancelled);
         if (wt == 0) {
-            // Slot s owns bits s, s + S, s + 2S, ... of every residual-syndrome word.
-            unsigned acc = 0;
-            for (int w = lane; w < n_rwords; w += 32) acc |= T.mism[w];
-            acc = __reduce_or_sync(FULLMASK, acc);
-            bool done = false;
-            if (lane < S && ((run >> lane) & 1u)) {
+            if ((done >> lane) & 1u) {
                 SlotState *ss = &T.st[lane];
-                const int it = ss->iter + 1;
                 ss->iter = it;
-                // A trial the manager found unable to win stops (first-success rule).
-                const bool stop = ss->kind == 2 &&
-                                  *reinterpret_cast<volatile long long *>(&ss->cancel) ==
-                                      ss->shot * (long long)cd.n_trials + ss->kidx + 1;
-                const int oc = ((acc & pat) == 0u) ? 1 : (stop ? 3 : (it >= ss->limit ? 2 : 0));
-                if (oc) {
-                    ss->outcome = oc;
-                    done = true;
-                }
+                ss->outcome = !((nconv >> lane) & 1u) ? 1 : (((cancelled >> lane) & 1u) ? 3 : 2);
+                // Finished slots are packed by the next service step.
+                *vstate(ss) = kSlotPending;
             }
-            // Finished slots are packed by the service step at the next loop top.
-            if (done) *vstate(&T.st[lane]) = kSlotPending;
+            n_iters += (unsigned long long)__popc(run);
+            n_cap += (unsigned long long)S;
         }
+        // Finished slots leave the run mask at once (their decisions and flip
+        // counts stay as they were) and wait for the next service, which comes
+        // after the iteration chunk, or at once when no slot is left running.
+        ++tt;
+        ++since;
+        run &= ~done;
+        svc = run == 0u || (since >= chunk && run != full);
     }
 }
 
@@ -1379,6 +1433,10 @@ __device__ __forceinline__ bool prefetch(const StreamDev &sd, unsigned char *qba
         }
         c0 = __shfl_sync(FULLMASK, c0, 0);
         got = __shfl_sync(FULLMASK, got, 0);
+        // Lane 0's acquire of the published count orders the other lanes'
+        // reads of the rows too (when serving, the host writes the rows
+        // before it publishes them).
+        __syncwarp();
         if (lane < got) {
             const long long shot = c0 + lane;
             const long long row = row_of(sd, shot);
@@ -1558,7 +1616,11 @@ __device__ void manager_loop(const StreamDev &sd, const LayoutMem &L, unsigned c
 // with no such code uses the instance without that path and its registers).
 // FB: bytes per flip word (FlipW): 2, or 1 for launches whose codes all have
 // max_iter <= 127 (an instance that leaves more shared memory for slots).
-template <int DC, int DVS, int DVX, bool DEBUG, int MINB, bool LAY, int FB = 2>
+// MIX: the instance also carries the exact (6, 4, 3) team loop and runs it
+// for codes with exactly six ones per row and three per column, so such codes
+// keep their specialised path in a launch that mixes them with codes of
+// wider rows (the layouts agree: both have column tables of width DVS).
+template <int DC, int DVS, int DVX, bool DEBUG, int MINB, bool LAY, int FB = 2, bool MIX = false>
 __global__ void __launch_bounds__(512, MINB) bpsf_persistent(const __grid_constant__ KernelParams kp) {
     extern __shared__ __align__(16) unsigned char smem[];
     BlockHdr *hdr = reinterpret_cast<BlockHdr *>(smem);
@@ -1698,7 +1760,11 @@ __global__ void __launch_bounds__(512, MINB) bpsf_persistent(const __grid_consta
             const int team = (warp - 1) / W;
             if (team < teams) {
                 TeamMem T = team_mem(team_base + team * to.total, to);
-                team_loop<DC, DVS, DVX, DEBUG, MINB, LAY, FB>(sd, L, T, hdr, S, W, tid - 32 - team * W * 32, 1 + team, kp.wait_ns);
+                const int ttid = tid - 32 - team * W * 32;
+                if (MIX && cd.regular && cd.DC == 6 && cd.dv_max == 3)
+                    team_loop<6, DVS, 3, DEBUG, MINB, LAY, FB>(sd, L, T, hdr, S, W, ttid, 1 + team, kp.wait_ns);
+                else
+                    team_loop<DC, DVS, DVX, DEBUG, MINB, LAY, FB>(sd, L, T, hdr, S, W, ttid, 1 + team, kp.wait_ns);
             }
         }
         __syncthreads();

@@ -2,11 +2,13 @@
 // several codes.
 //
 // Each code owns an arena of `rows` shot rows.  A request of n shots takes n
-// consecutive rows of its code's ring (admission by device memory: a request
-// waits until rows are free).  Submitting stages the syndromes in pinned
-// memory and enqueues, on one copy stream, the copy of those rows into the
-// device arena followed by the copy of the code's new published shot count,
-// so the count never runs ahead of the rows (no host synchronisation).  The
+// consecutive rows of its code's ring (admission by arena rows: a request
+// waits until rows are free).  The arena and the code's published shot count
+// live in host memory mapped into the device's address space: submitting
+// writes the syndromes into the rows and then stores the new count with
+// release semantics, and the device reads the count with system-scope
+// acquire loads before it reads the rows, so a request reaches the device
+// without a copy, a stream operation or a driver call.  The
 // persistent kernel (the batched kernel with kServe streams) claims published
 // shots as slots free up, so requests that arrive while others run join the
 // same device work pool; trial tickets of failed shots keep priority over new
@@ -40,10 +42,9 @@ size_t a16(size_t x) { return (x + 15) & ~size_t(15); }
 struct SrvCode {
     bpsf_ctx *ctx = nullptr;
     long long rows = 0;
-    uint32_t *d_synd = nullptr;                      // rows x Ws, device arena
-    uint32_t *h_stage = nullptr;                     // rows x Ws, pinned staging
-    long long *d_pub = nullptr;                      // published shot count (device)
-    long long *h_pub_stage = nullptr;                // per request slot: the count to copy (pinned)
+    void *h_in = nullptr;                            // mapped input block: published count, then the arena
+    long long *h_pub = nullptr, *m_pub = nullptr;    // published shot count (host / device address)
+    uint32_t *h_synd = nullptr, *m_synd = nullptr;   // rows x Ws arena (host / device address)
     void *h_out = nullptr;                           // mapped output rows
     uint32_t *h_corr = nullptr, *m_corr = nullptr;
     uint8_t *h_conv = nullptr, *m_conv = nullptr;
@@ -76,7 +77,7 @@ struct bpsf_server {
     std::vector<int> free_slots;
     std::map<uint64_t, int> by_ticket;
     uint64_t next_ticket = 1;
-    cudaStream_t kstream = nullptr, cstream = nullptr;
+    cudaStream_t kstream = nullptr;
     cudaEvent_t kdone = nullptr;
     bool launched = false;
     long long idle_ns = 0;
@@ -133,10 +134,7 @@ static void pump_loop(bpsf_server *s) {
 static void free_server(bpsf_server *s) {
     for (int k = 0; k < s->n_codes; ++k) {
         SrvCode &c = s->codes[k];
-        if (c.d_synd) cudaFree(c.d_synd);
-        if (c.h_stage) cudaFreeHost(c.h_stage);
-        if (c.d_pub) cudaFree(c.d_pub);
-        if (c.h_pub_stage) cudaFreeHost(c.h_pub_stage);
+        if (c.h_in) cudaFreeHost(c.h_in);
         if (c.h_out) cudaFreeHost(c.h_out);
         if (c.d_ctr) cudaFree(c.d_ctr);
         if (c.d_rec) cudaFree(c.d_rec);
@@ -144,7 +142,6 @@ static void free_server(bpsf_server *s) {
     if (s->h_stop) cudaFreeHost(s->h_stop);
     if (s->kdone) cudaEventDestroy(s->kdone);
     if (s->kstream) cudaStreamDestroy(s->kstream);
-    if (s->cstream) cudaStreamDestroy(s->cstream);
     delete s;
 }
 
@@ -200,7 +197,6 @@ extern "C" bpsf_status bpsf_serve_start(bpsf_server **out, bpsf_ctx *const *code
     s->grid = c.blocks > 0 ? std::min(c.blocks, s->plan.grid) : s->plan.grid;
     cudaError_t e = cudaSuccess;
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->kstream, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->cstream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->kdone, cudaEventDisableTiming);
     if (e == cudaSuccess) e = host_mapped(&s->h_stop, &s->m_stop, 64);
     for (int k = 0; k < n_codes && e == cudaSuccess; ++k) {
@@ -209,12 +205,17 @@ extern "C" bpsf_status bpsf_serve_start(bpsf_server **out, bpsf_ctx *const *code
         sc.ctx = x;
         sc.rows = c.max_inflight_shots;
         const size_t R = (size_t)sc.rows;
-        e = cudaMalloc((void **)&sc.d_synd, 4 * R * x->Ws);
-        if (e == cudaSuccess) e = cudaMallocHost((void **)&sc.h_stage, 4 * R * x->Ws);
-        if (e == cudaSuccess) e = cudaMalloc((void **)&sc.d_pub, 64);
-        if (e == cudaSuccess) e = cudaMemset(sc.d_pub, 0, 64);
-        if (e == cudaSuccess) e = cudaMallocHost((void **)&sc.h_pub_stage, 8 * (size_t)s->max_req);
-        if (e != cudaSuccess) break;
+        // Mapped inputs: the published count (its own 128-byte line), then the arena.
+        {
+            unsigned char *h = nullptr, *m = nullptr;
+            e = host_mapped(&h, &m, 128 + 4 * R * x->Ws);
+            if (e != cudaSuccess) break;
+            sc.h_in = h;
+            sc.h_pub = reinterpret_cast<long long *>(h);
+            sc.m_pub = reinterpret_cast<long long *>(m);
+            sc.h_synd = reinterpret_cast<uint32_t *>(h + 128);
+            sc.m_synd = reinterpret_cast<uint32_t *>(m + 128);
+        }
         // Mapped outputs: corr | conv | iters | stage | completion words.
         const size_t o_corr = 0, o_conv = a16(o_corr + 4 * R * x->Wn), o_it = a16(o_conv + R), o_st = a16(o_it + 2 * R),
                      o_dn = a16(o_st + R), total = a16(o_dn + 4 * R);
@@ -263,11 +264,11 @@ extern "C" bpsf_status bpsf_serve_start(bpsf_server **out, bpsf_ctx *const *code
         sc.rec.cap = (long long)R;
         e = cudaMemset(sc.rec.qseq, 0, 8 * R);
         // The serving stream of this code.
-        JobDev job{sc.d_synd, sc.m_corr, sc.m_conv, sc.m_iters, sc.m_stage8, 0, x->Ws, x->Wn};
+        JobDev job{sc.m_synd, sc.m_corr, sc.m_conv, sc.m_iters, sc.m_stage8, 0, x->Ws, x->Wn};
         StreamDev sd = bpsf_make_stream(x, job, nullptr, kServe);
         sd.rec = sc.rec;
         sd.ctr = sc.d_ctr;
-        sd.serve.published = sc.d_pub;
+        sd.serve.published = sc.m_pub;
         sd.serve.stop = s->m_stop;
         sd.serve.row_done = sc.m_done;
         sd.serve.rows = sc.rows;
@@ -300,7 +301,7 @@ extern "C" bpsf_status bpsf_serve_submit(bpsf_server *s, int32_t code, int64_t n
         if (s->closing.load()) return bpsf_fail(BPSF_ECLOSED, "server is stopping");
         if (timeout_us <= 0 || s->cv.wait_until(lk, deadline) == std::cv_status::timeout) {
             if (fits()) break;
-            return bpsf_fail(BPSF_EBUSY, "no room for %lld shots (admission by device rows)", (long long)n);
+            return bpsf_fail(BPSF_EBUSY, "no room for %lld shots (admission by arena rows)", (long long)n);
         }
     }
     cudaSetDevice(s->device);
@@ -308,21 +309,13 @@ extern "C" bpsf_status bpsf_serve_submit(bpsf_server *s, int32_t code, int64_t n
     s->free_slots.pop_back();
     const long long g0 = sc.next_g;
     const int Ws = sc.ctx->Ws;
-    // Stage (the caller's buffer is free on return), then copy rows, then the count.
+    // Rows first, then the count with release semantics: a device thread that
+    // reads the new count (system-scope acquire) then sees the rows.  The
+    // caller's buffer is free on return.
     const long long r0 = g0 % sc.rows, first = std::min<long long>(n, sc.rows - r0);
-    std::memcpy(sc.h_stage + r0 * Ws, h_synd, 4 * (size_t)first * Ws);
-    if (first < n) std::memcpy(sc.h_stage, h_synd + first * Ws, 4 * (size_t)(n - first) * Ws);
-    cudaError_t e = cudaMemcpyAsync(sc.d_synd + r0 * Ws, sc.h_stage + r0 * Ws, 4 * (size_t)first * Ws,
-                                    cudaMemcpyHostToDevice, s->cstream);
-    if (e == cudaSuccess && first < n)
-        e = cudaMemcpyAsync(sc.d_synd, sc.h_stage, 4 * (size_t)(n - first) * Ws, cudaMemcpyHostToDevice, s->cstream);
-    sc.h_pub_stage[q] = g0 + n;
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(sc.d_pub, sc.h_pub_stage + q, 8, cudaMemcpyHostToDevice, s->cstream);
-    if (e != cudaSuccess) {
-        s->free_slots.push_back(q);
-        return bpsf_fail(BPSF_ECUDA, "request copy: %s", cudaGetErrorString(e));
-    }
+    std::memcpy(sc.h_synd + r0 * Ws, h_synd, 4 * (size_t)first * Ws);
+    if (first < n) std::memcpy(sc.h_synd, h_synd + first * Ws, 4 * (size_t)(n - first) * Ws);
+    __atomic_store_n(sc.h_pub, g0 + n, __ATOMIC_RELEASE);
     SrvReq &r = s->reqs[q];
     r.code = code;
     r.g0 = g0;
@@ -421,7 +414,6 @@ extern "C" bpsf_status bpsf_serve_stop(bpsf_server *s) {
     std::atomic_thread_fence(std::memory_order_seq_cst);
     cudaSetDevice(s->device);
     cudaError_t e = cudaStreamSynchronize(s->kstream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s->cstream);
     if (e != cudaSuccess && st == BPSF_OK) st = bpsf_fail(BPSF_ECUDA, "serving kernel: %s", cudaGetErrorString(e));
     for (int k = 0; k < s->n_codes && st == BPSF_OK; ++k) {
         StreamCounters h;
@@ -435,17 +427,41 @@ extern "C" bpsf_status bpsf_serve_stop(bpsf_server *s) {
 // Open-loop trace replay for latency measurement: one thread submits request
 // i at its scheduled arrival time, another polls every outstanding request
 // and stamps its completion, so neither side waits on the other.
+// Arguments shared by the two replays: codes in range, shots >= 1, arrivals
+// non-decreasing (arrival_s NULL: closed loop).
+static bpsf_status check_trace(int n_codes, int64_t n_req, const double *arrival_s, const int32_t *code,
+                               const int64_t *n_shots, const uint32_t *const *synd, const double *latency_s) {
+    if (n_req < 1 || !code || !n_shots || !synd || !latency_s) return bpsf_fail(BPSF_EINVAL, "bad replay arguments");
+    for (int64_t i = 0; i < n_req; ++i) {
+        if (code[i] < 0 || code[i] >= n_codes || n_shots[i] < 1 || !synd[i])
+            return bpsf_fail(BPSF_EINVAL, "bad request %lld", (long long)i);
+        if (arrival_s && i > 0 && arrival_s[i] < arrival_s[i - 1])
+            return bpsf_fail(BPSF_EINVAL, "arrivals must not decrease");
+    }
+    return BPSF_OK;
+}
+
 extern "C" bpsf_status bpsf_serve_replay(bpsf_server *s, int64_t n_req, const double *arrival_s, const int32_t *code,
                                          const int64_t *n_shots, const uint32_t *const *synd, double *latency_s,
                                          double *span_s) {
-    if (!s || n_req < 1 || !arrival_s || !code || !n_shots || !synd || !latency_s)
-        return bpsf_fail(BPSF_EINVAL, "bad replay arguments");
-    for (int64_t i = 0; i < n_req; ++i) {
-        if (code[i] < 0 || code[i] >= s->n_codes || n_shots[i] < 1 || !synd[i])
-            return bpsf_fail(BPSF_EINVAL, "bad request %lld", (long long)i);
-        if (i > 0 && arrival_s[i] < arrival_s[i - 1]) return bpsf_fail(BPSF_EINVAL, "arrivals must not decrease");
-    }
+    if (!s) return bpsf_fail(BPSF_EINVAL, "server is NULL");
+    bpsf_status cst = check_trace(s->n_codes, n_req, arrival_s, code, n_shots, synd, latency_s);
+    if (cst != BPSF_OK) return cst;
     using clk = std::chrono::steady_clock;
+    if (!arrival_s) {
+        // Closed loop: request i is submitted once request i - 1 is done.
+        const clk::time_point t0 = clk::now();
+        for (int64_t i = 0; i < n_req; ++i) {
+            const clk::time_point a = clk::now();
+            uint64_t t = 0;
+            bpsf_status st = bpsf_serve_submit(s, code[i], n_shots[i], synd[i], 60000000, &t);
+            if (st == BPSF_OK) st = bpsf_serve_poll(s, t, 60000000, nullptr, nullptr, nullptr, nullptr);
+            if (st != BPSF_OK) return st;
+            latency_s[i] = std::chrono::duration<double>(clk::now() - a).count();
+        }
+        if (span_s) *span_s = std::chrono::duration<double>(clk::now() - t0).count();
+        return BPSF_OK;
+    }
     std::vector<uint64_t> tickets((size_t)n_req, 0);
     std::vector<std::atomic<int>> submitted((size_t)n_req);
     for (auto &a : submitted) a.store(0);
@@ -504,4 +520,88 @@ extern "C" bpsf_status bpsf_serve_replay(bpsf_server *s, int64_t n_req, const do
     if (st != BPSF_OK) return st;
     if (span_s) *span_s = std::chrono::duration<double>(last - t0).count();
     return BPSF_OK;
+}
+
+// ---------------------------------------------------------------------------
+// The plain per-shot form as a request server, for latency comparisons on the
+// same trace and the same clock as bpsf_serve_replay.
+// ---------------------------------------------------------------------------
+
+extern "C" bpsf_status bpsf_plain_replay(bpsf_ctx *const *codes, int32_t n_codes, int64_t n_req,
+                                         const double *arrival_s, const int32_t *code, const int64_t *n_shots,
+                                         const uint32_t *const *synd, double *latency_s, double *span_s) {
+    if (!codes || n_codes < 1 || n_codes > kMaxStreams) return bpsf_fail(BPSF_EINVAL, "n_codes must be in 1..%d", kMaxStreams);
+    for (int k = 0; k < n_codes; ++k)
+        if (!codes[k]) return bpsf_fail(BPSF_EINVAL, "code %d is NULL", k);
+    bpsf_status st = check_trace(n_codes, n_req, arrival_s, code, n_shots, synd, latency_s);
+    if (st != BPSF_OK) return st;
+    cudaSetDevice(codes[0]->device);
+    // Per code: device rows for its largest request, and pinned host rows.
+    std::vector<int64_t> max_n(n_codes, 0);
+    for (int64_t i = 0; i < n_req; ++i) max_n[code[i]] = std::max(max_n[code[i]], n_shots[i]);
+    struct Buf {
+        void *d = nullptr, *h = nullptr;
+        uint32_t *d_synd = nullptr, *d_corr = nullptr, *h_synd = nullptr, *h_corr = nullptr;
+        uint8_t *d_conv = nullptr, *d_stage = nullptr, *h_small = nullptr;
+        int16_t *d_it = nullptr;
+    };
+    std::vector<Buf> bufs(n_codes);
+    cudaStream_t strm = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&strm, cudaStreamNonBlocking);
+    for (int k = 0; k < n_codes && e == cudaSuccess; ++k) {
+        if (max_n[k] == 0) continue;
+        const bpsf_ctx *c = codes[k];
+        const size_t n = (size_t)max_n[k];
+        const size_t b_s = a16(4 * n * c->Ws), b_c = a16(4 * n * c->Wn), b_1 = a16(n), b_2 = a16(2 * n);
+        Buf &b = bufs[k];
+        e = cudaMalloc(&b.d, b_s + b_c + 2 * b_1 + b_2);
+        if (e == cudaSuccess) e = cudaMallocHost(&b.h, b_s + b_c + 4 * n);
+        if (e != cudaSuccess) break;
+        unsigned char *p = (unsigned char *)b.d;
+        b.d_synd = (uint32_t *)p;
+        b.d_corr = (uint32_t *)(p + b_s);
+        b.d_conv = p + b_s + b_c;
+        b.d_stage = p + b_s + b_c + b_1;
+        b.d_it = (int16_t *)(p + b_s + b_c + 2 * b_1);
+        unsigned char *h = (unsigned char *)b.h;
+        b.h_synd = (uint32_t *)h;
+        b.h_corr = (uint32_t *)(h + b_s);
+        b.h_small = h + b_s + b_c;
+    }
+    using clk = std::chrono::steady_clock;
+    const clk::time_point t0 = clk::now();
+    clk::time_point last = t0;
+    for (int64_t i = 0; i < n_req && e == cudaSuccess && st == BPSF_OK; ++i) {
+        clk::time_point a = clk::now();
+        if (arrival_s) {
+            a = t0 + std::chrono::nanoseconds((long long)(arrival_s[i] * 1e9));
+            while (clk::now() < a) {
+            }
+        }
+        bpsf_ctx *c = codes[code[i]];
+        Buf &b = bufs[code[i]];
+        const int64_t n = n_shots[i];
+        std::memcpy(b.h_synd, synd[i], 4 * (size_t)n * c->Ws);
+        e = cudaMemcpyAsync(b.d_synd, b.h_synd, 4 * (size_t)n * c->Ws, cudaMemcpyHostToDevice, strm);
+        if (e != cudaSuccess) break;
+        st = bpsf_decode_plain(c, n, b.d_synd, c->Ws, b.d_corr, c->Wn, b.d_conv, b.d_it, b.d_stage, strm);
+        if (st != BPSF_OK) break;
+        e = cudaMemcpyAsync(b.h_corr, b.d_corr, 4 * (size_t)n * c->Wn, cudaMemcpyDeviceToHost, strm);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(b.h_small, b.d_conv, (size_t)n, cudaMemcpyDeviceToHost, strm);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(b.h_small + n, b.d_it, 2 * (size_t)n, cudaMemcpyDeviceToHost, strm);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(strm);
+        last = clk::now();
+        latency_s[i] = std::chrono::duration<double>(last - a).count();
+    }
+    if (e != cudaSuccess && st == BPSF_OK) st = bpsf_fail(BPSF_ECUDA, "plain replay: %s", cudaGetErrorString(e));
+    if (strm) {
+        cudaStreamSynchronize(strm);
+        cudaStreamDestroy(strm);
+    }
+    for (Buf &b : bufs) {
+        if (b.d) cudaFree(b.d);
+        if (b.h) cudaFreeHost(b.h);
+    }
+    if (st == BPSF_OK && span_s) *span_s = std::chrono::duration<double>(last - t0).count();
+    return st;
 }

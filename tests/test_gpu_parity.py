@@ -336,12 +336,35 @@ def test_launch_shape_does_not_change_results():
     oc, e, s = make_inputs("bb144", 0.07, 4000, 5)
     dec = decoder("bb144", 0.07, P)
     ref = gpu_decode(dec, s)
+    # (W, S, B, blocks per SM, iteration chunk): the chunk delays refills only.
     for t in [(1, 1, 4, 0), (1, 16, 4, 0), (2, 2, 8, 0), (4, 1, 8, 1), (1, 8, 4, 0), (1, 2, 15, 0), (8, 1, 8, 0),
-              (1, 32, 2, 0), (8, 32, 8, 0), (4, 16, 12, 0), (1, 4, 12, 0), (2, 4, 8, 0)]:
+              (1, 32, 2, 0), (8, 32, 8, 0), (4, 16, 12, 0), (1, 4, 12, 0), (2, 4, 8, 0), (1, 8, 12, 0, 4),
+              (1, 4, 15, 0, 8), (2, 8, 8, 0, 2), (4, 1, 12, 0, 3), (1, 32, 3, 0, 64)]:
         dec.tuning = t
         got = gpu_decode(dec, s)
         for key in ("corr", "conv", "iters", "stage"):
             assert (got[key] == ref[key]).all(), (t, key)
+    with pytest.raises(B.BpsfError):
+        dec.tuning = (1, 8, 12, 0, 65)
+
+
+def test_autotune_result_is_accepted_cached_and_decodes_like_the_oracle():
+    """bpsf_autotune picks a shape (threads per shot, shots per block,
+    iteration chunk) that bpsf_set_tuning accepts; a second context of the
+    same code and parameters starts with it from the cache; decoding under it
+    equals the oracle."""
+    P = B.Params(max_iter=50, alpha=0.625, w=4, short_iter=10)
+    dec = decoder("bb72", 0.06, P)
+    chosen = dec.autotune(p_sample=0.06, n_sample=1 << 13)
+    assert dec.tuning == chosen
+    W, S, Bw, bps, chunk = chosen
+    assert W in (1, 2, 4, 8) and S in (1, 2, 4, 8, 16, 32) and Bw % W == 0 and 1 <= max(chunk, 1) <= 8
+    fresh = decoder("bb72", 0.06, P)
+    assert fresh.tuning == chosen  # from the cache: same code shape and parameters
+    fresh.tuning = (1, 1, 1, 0)
+    fresh.tuning = chosen  # accepted by bpsf_set_tuning
+    oc, e, s = make_inputs("bb72", 0.06, 3000, 41)
+    compare(oc, fresh, s, 0.06, P)
 
 
 def test_one_byte_flip_words():

@@ -195,3 +195,44 @@ def test_bounded_device_wait_reports_instead_of_spinning(mix):
     # The context stays usable.
     s = synd_host(c, d, p, 100, 15)
     alone(d, s)
+
+
+def test_request_that_wraps_the_ring(mix):
+    # Rows are a ring: a request that runs past the last row continues at row 0.
+    name, c, d, p = mix[1]
+    srv = B.Server([d], max_inflight_shots=100)
+    try:
+        for r, n in enumerate((70, 70, 55, 100)):
+            s = synd_host(c, d, p, n, 7900 + r)
+            same(srv.poll(srv.submit(0, s), n, 0), alone(d, s))
+    finally:
+        srv.stop()
+
+
+def test_replays_time_both_forms_on_one_clock(mix):
+    """bpsf_serve_replay and bpsf_plain_replay on the same requests, open loop
+    and closed loop: every request gets a finite, positive latency on the
+    library's monotonic clock, and the open-loop latency counts from the
+    scheduled arrival."""
+    decs = [d for _, _, d, _ in mix]
+    reqs, which = [], []
+    for r in range(24):
+        k = r % len(mix)
+        name, c, d, p = mix[k]
+        reqs.append(synd_host(c, d, p, 1 + (r % 3), 8100 + r))
+        which.append(k)
+    arrivals = np.cumsum(np.full(len(reqs), 2e-4))
+    lat_p, span_p = B.plain_replay(decs, arrivals, which, reqs)
+    lat_pc, _ = B.plain_replay(decs, None, which, reqs)
+    assert (lat_p > 0).all() and (lat_pc > 0).all() and np.isfinite(lat_p).all()
+    assert span_p >= arrivals[-1]
+    srv = B.Server(decs, max_inflight_shots=1024)
+    try:
+        lat_s, span_s = srv.replay(arrivals, which, reqs)
+        lat_sc, _ = srv.replay(None, which, reqs)
+    finally:
+        srv.stop()
+    assert (lat_s > 0).all() and (lat_sc > 0).all() and np.isfinite(lat_s).all()
+    assert span_s >= arrivals[-1]
+    with pytest.raises(B.BpsfError):
+        B.plain_replay(decs, arrivals[::-1].copy(), which, reqs)  # arrivals must not decrease
