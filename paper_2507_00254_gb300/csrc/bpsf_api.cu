@@ -679,35 +679,13 @@ extern "C" bpsf_status bpsf_create(bpsf_ctx **out, int32_t M, int32_t N, int64_t
 bpsf_status bpsf_ensure_workspace(bpsf_ctx *c, long long n) {
     if (n <= c->rec_cap) return BPSF_OK;
     const long long cap = std::max<long long>(n, 1);
-    const int w = std::max(c->p.w, 1), T = std::max(c->n_trials, 1);
-    const size_t sz[8] = {align16(8 * (size_t)cap),      align16(8 * (size_t)cap),
-                          align16(4 * (size_t)cap),      align16(8 * (size_t)cap),
-                          align16(4 * (size_t)cap * w),  align16(4 * (size_t)cap * c->Ws),
-                          align16(4 * (size_t)cap * T * c->Wn), align16(2 * (size_t)cap * T)};
-    size_t total = 0;
-    for (size_t s : sz) total += s;
+    const size_t total = bpsf_records_bytes(cap, c->p.w, c->Ws, c->Wn, 16);
     free_workspace(c);
     void *mem = nullptr;
     cudaError_t e = cudaMalloc(&mem, total);
     if (e != cudaSuccess) return bpsf_fail(BPSF_ENOMEM, "workspace of %zu bytes: %s", total, cudaGetErrorString(e));
-    unsigned char *p = (unsigned char *)mem;
     c->d_rec = mem;
-    c->rec.qseq = (unsigned long long *)p;
-    p += sz[0];
-    c->rec.qshot = (long long *)p;
-    p += sz[1];
-    c->rec.done = (unsigned *)p;
-    p += sz[2];
-    c->rec.best = (unsigned long long *)p;
-    p += sz[3];
-    c->rec.phi = (int32_t *)p;
-    p += sz[4];
-    c->rec.synd = (uint32_t *)p;
-    p += sz[5];
-    c->rec.corr = (uint32_t *)p;
-    p += sz[6];
-    c->rec.iters = (int16_t *)p;
-    c->rec.cap = cap;
+    c->rec = bpsf_records_carve(mem, cap, c->p.w, c->Ws, c->Wn, 16);
     c->rec_cap = cap;
     return BPSF_OK;
 }
@@ -1256,7 +1234,7 @@ extern "C" bpsf_status bpsf_selftest_wait(bpsf_ctx *c, int64_t wait_us, void *st
     if (e == cudaSuccess) e = cudaMemsetAsync(c->rec.qseq, 0, 8, s);
     if (e != cudaSuccess) return bpsf_fail(BPSF_ECUDA, "self test set-up: %s", cudaGetErrorString(e));
     // Outputs of the (never settled) shot go to the workspace's own rows.
-    JobDev job{c->rec.synd, c->rec.corr, reinterpret_cast<uint8_t *>(c->rec.done),
+    JobDev job{c->rec.synd, reinterpret_cast<uint32_t *>(c->rec.win), reinterpret_cast<uint8_t *>(c->rec.done),
                reinterpret_cast<int16_t *>(c->rec.done), nullptr, 1, c->Ws, c->Wn};
     StreamDev sd = bpsf_make_stream(c, job, nullptr, 0);
     sd.S = pl.S_code[0];

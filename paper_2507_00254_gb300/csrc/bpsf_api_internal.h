@@ -46,6 +46,35 @@ struct bpsf_plan {
 
 bpsf_status bpsf_fail(bpsf_status s, const char *fmt, ...);
 
+// Failed-shot records of `rows` rows in one block of memory, each array
+// aligned to `al` bytes: bytes needed, and the arrays carved from `base`.
+inline size_t bpsf_records_bytes(long long rows, int w, int Ws, int Wn, size_t al) {
+    const size_t r = (size_t)(rows > 0 ? rows : 1), ww = (size_t)(w > 0 ? w : 1);
+    auto A = [al](size_t x) { return (x + al - 1) / al * al; };
+    return A(8 * r) + A(8 * r) + A(4 * r) + A(8 * r) + A(8 * r * (size_t)Wn) + A(4 * r * ww) + A(4 * r * (size_t)Ws);
+}
+inline bpsf::Records bpsf_records_carve(void *base, long long rows, int w, int Ws, int Wn, size_t al) {
+    const size_t r = (size_t)(rows > 0 ? rows : 1), ww = (size_t)(w > 0 ? w : 1);
+    auto A = [al](size_t x) { return (x + al - 1) / al * al; };
+    unsigned char *p = static_cast<unsigned char *>(base);
+    bpsf::Records rec;
+    rec.qseq = reinterpret_cast<unsigned long long *>(p);
+    p += A(8 * r);
+    rec.qshot = reinterpret_cast<long long *>(p);
+    p += A(8 * r);
+    rec.done = reinterpret_cast<unsigned *>(p);
+    p += A(4 * r);
+    rec.best = reinterpret_cast<unsigned long long *>(p);
+    p += A(8 * r);
+    rec.win = reinterpret_cast<unsigned long long *>(p);
+    p += A(8 * r * (size_t)Wn);
+    rec.phi = reinterpret_cast<int32_t *>(p);
+    p += A(4 * r * ww);
+    rec.synd = reinterpret_cast<uint32_t *>(p);
+    rec.cap = (long long)r;
+    return rec;
+}
+
 // Index of the layout for S slots per team (S a power of two, 1..32).
 inline int layout_index(int S) {
     int i = 0;

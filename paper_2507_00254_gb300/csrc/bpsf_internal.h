@@ -89,17 +89,25 @@ static_assert(sizeof(StreamCounters) == 128, "counter block is two 64-byte lines
 // Failed-shot records.  A record lives at the shot's row (its index in the
 // job, or its arena row when serving); the publication queue lists failed
 // shots in the order they failed, and trial tickets walk that queue.
+//
+// Only the winning trial's correction is kept.  A converged trial's
+// selection key (kSelKeyBits bits: weight << 12 | list index, or the list
+// index under the first-success rule; unique per trial) goes into the top
+// half of 64-bit words merged with atomicMin: best = key << 32 | iterations,
+// and word w of the correction as key << 32 | (e' xor t)_w.  Each word's
+// minimum is then the smallest key's own word, whatever order the trials
+// finish in, with no lock.
 struct Records {
     unsigned long long *qseq;   // cap, (queue index + 1) once the entry is written
     long long *qshot;           // cap, shot of the queue entry
     unsigned int *done;         // rows, trials finished
-    unsigned long long *best;   // rows, min over converged trials of the selection key
+    unsigned long long *best;   // rows, min over converged trials of key << 32 | iterations
+    unsigned long long *win;    // rows x Wn, min over converged trials of key << 32 | correction word
     int32_t *phi;               // rows x w
     uint32_t *synd;             // rows x Ws, the shot's syndrome
-    uint32_t *corr;             // rows x n_trials x Wn, e' xor t of converged trials
-    int16_t *iters;             // rows x n_trials
     long long cap;              // queue entries (= rows)
 };
+constexpr int kSelKeyBits = 28;  // weight (16 bits, N <= 65535) above a 12-bit list index (n_trials <= 4096)
 
 struct JobDev {
     const uint32_t *synd;
@@ -146,6 +154,8 @@ struct StreamDev {
     int chunk;       // team iterations between refills of finished slots (>= 1)
 };
 
+static_assert(sizeof(StreamDev) % 8 == 0, "the block copies the descriptor in 4-byte words");
+
 // Launch: the team shape is set per stream (StreamDev::S, W, teams); each
 // block has one manager warp besides; Q ready-queue entries.
 struct LaunchArgs {
@@ -161,7 +171,10 @@ struct LaunchArgs {
 
 __host__ __device__ inline int align_up(int x, int a) { return (x + a - 1) / a * a; }
 
-constexpr int kBlockHeaderBytes = 64;
+// Block header: 64 bytes of control words, then the block's copy of the
+// descriptor of the code it serves (StreamDev), read by every warp in its
+// loops from shared memory rather than from the kernel parameters.
+constexpr int kBlockHeaderBytes = 64 + ((int)sizeof(StreamDev) + 15) / 16 * 16;
 
 struct LayoutOffsets {
     int row_deg, vpos, lch, lch_pos, total;

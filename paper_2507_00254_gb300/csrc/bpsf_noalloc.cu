@@ -47,19 +47,15 @@ size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 // Bytes of scratch a batch of n shots needs for this code (counters first).
 size_t noalloc_bytes(const bpsf_ctx *c, long long n) {
-    const size_t cap = (size_t)(n > 0 ? n : 1);
-    const size_t w = (size_t)(c->p.w > 0 ? c->p.w : 1), T = (size_t)(c->n_trials > 0 ? c->n_trials : 1);
-    return align256(sizeof(StreamCounters)) + align256(8 * cap) + align256(8 * cap) + align256(4 * cap) +
-           align256(8 * cap) + align256(4 * cap * w) + align256(4 * cap * c->Ws) + align256(4 * cap * T * c->Wn) +
-           align256(2 * cap * T);
+    return align256(sizeof(StreamCounters)) + bpsf_records_bytes(n, c->p.w, c->Ws, c->Wn, 256);
 }
 
 }  // namespace
 
 extern "C" int64_t bpsf_noalloc_max_shots(const bpsf_ctx *c) {
     if (!c) return -1;
-    // Every shot takes at least 24 bytes of records, so the answer is below
-    // 2^21 and the doubling stops long before any product could wrap.
+    // Every shot takes at least 44 bytes of records, so the answer is below
+    // 2^20 and the doubling stops long before any product could wrap.
     long long lo = 0, hi = 1;
     while (noalloc_bytes(c, hi) <= kNoallocScratchBytes) hi *= 2;
     while (hi - lo > 1) {
@@ -100,27 +96,8 @@ extern "C" bpsf_status bpsf_decode_noalloc(bpsf_ctx *c, int64_t n, const uint32_
     if (st != BPSF_OK) return st;
     // Carve the counters and the records out of the array.
     const size_t cap = (size_t)n;
-    const size_t w = (size_t)(c->p.w > 0 ? c->p.w : 1), T = (size_t)(c->n_trials > 0 ? c->n_trials : 1);
-    unsigned char *p = base;
-    StreamCounters *ctr = reinterpret_cast<StreamCounters *>(p);
-    p += align256(sizeof(StreamCounters));
-    Records rec;
-    rec.qseq = reinterpret_cast<unsigned long long *>(p);
-    p += align256(8 * cap);
-    rec.qshot = reinterpret_cast<long long *>(p);
-    p += align256(8 * cap);
-    rec.done = reinterpret_cast<unsigned *>(p);
-    p += align256(4 * cap);
-    rec.best = reinterpret_cast<unsigned long long *>(p);
-    p += align256(8 * cap);
-    rec.phi = reinterpret_cast<int32_t *>(p);
-    p += align256(4 * cap * w);
-    rec.synd = reinterpret_cast<uint32_t *>(p);
-    p += align256(4 * cap * c->Ws);
-    rec.corr = reinterpret_cast<uint32_t *>(p);
-    p += align256(4 * cap * T * c->Wn);
-    rec.iters = reinterpret_cast<int16_t *>(p);
-    rec.cap = (long long)cap;
+    StreamCounters *ctr = reinterpret_cast<StreamCounters *>(base);
+    Records rec = bpsf_records_carve(base + align256(sizeof(StreamCounters)), n, c->p.w, c->Ws, c->Wn, 256);
     // The array keeps the previous call's contents: the counters and the
     // publication queue must start at zero.  Every other record field is
     // written before it is read.

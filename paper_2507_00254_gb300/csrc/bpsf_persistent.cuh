@@ -986,15 +986,18 @@ __device__ void team_loop(const StreamDev &sd, const LayoutMem &L, const TeamMem
     unsigned long long idle_since = 0;
     unsigned last_beat = 0;
     unsigned run = 0u, initm = 0u;
+    constexpr int VMAX = (kVec4 || kLayV4) ? 4 : 2;  // most slots a lane serves in this instance
     int tt = 0;                   // team iterations run (the same in every warp)
-    int start[4] = {0, 0, 0, 0};  // team iteration of the first iteration of the lane's slots' runs
+    int start[VMAX];              // team iteration of the first iteration of the lane's slots' runs
+#pragma unroll
+    for (int c = 0; c < VMAX; ++c) start[c] = 0;
     // Every warp, lane l < S: slot l's first team iteration and iteration cap.
     int l_start = 0, l_lim = 0;
     // Warp 0, lane s < S: slot s's stop key (first-success rule).
     long long w_key = 0;
     // Warp 0, lane 0: iterations run and slot-iterations offered since the
     // last service (added to the control block at the next service).
-    unsigned long long n_iters = 0, n_cap = 0;
+    unsigned n_iters = 0, n_cap = 0;
     const bool first_rule = cd.select == 1;
     bool svc = true;
     const int chunk = sd.chunk > 1 ? sd.chunk : 1;  // iterations between refills of finished slots
@@ -1056,7 +1059,9 @@ __device__ void team_loop(const StreamDev &sd, const LayoutMem &L, const TeamMem
             const int ex = T.ctl->exit;
             if (ex) break;
             if (run == 0u) continue;
-            for (int c = 0; c < vs; ++c) start[c] = T.st[s0 + c].start;
+#pragma unroll
+            for (int c = 0; c < VMAX; ++c)
+                if (c < vs) start[c] = T.st[s0 + c].start;
             if (lane < S) {
                 l_start = T.st[lane].start;
                 l_lim = T.st[lane].limit;
@@ -1075,7 +1080,7 @@ __device__ void team_loop(const StreamDev &sd, const LayoutMem &L, const TeamMem
         // Damping of iteration it = tt - start + 1 of each of the lane's slots.
         float al[4];
 #pragma unroll
-        for (int c = 0; c < 4; ++c) al[c] = damping(cd, tt - start[c] + 1);
+        for (int c = 0; c < 4; ++c) al[c] = c < VMAX ? damping(cd, tt - start[c < VMAX ? c : 0] + 1) : 0.f;
         if (lay) {
             if (kLayV4 && vs == 4) {
                 float a4[4] = {al[0], al[1], al[2], al[3]};
@@ -1199,12 +1204,13 @@ __device__ __forceinline__ void trial_done(const StreamDev &sd, long long row, l
         __threadfence();
         const unsigned long long best = atomicAdd(&sd.rec.best[row], 0ull);
         if (best != ~0ull) {
-            const int kw = (int)(best & 0xffffffffu);
+            // Every converged trial merged its words before it counted itself
+            // done, so each word now holds the winner's (smallest key's) word.
             uint32_t *out = job.corr + row * job.corr_stride;
-            const uint32_t *src = sd.rec.corr + ((long long)row * C + kw) * Wn;
-            for (int w = 0; w < Wn; ++w) out[w] = __ldcg(src + w);
+            const unsigned long long *src = sd.rec.win + row * Wn;
+            for (int w = 0; w < Wn; ++w) out[w] = (uint32_t)(__ldcg(src + w) & 0xffffffffull);
             job.conv[row] = 1;
-            job.iters[row] = __ldcg(sd.rec.iters + (long long)row * C + kw);
+            job.iters[row] = (int16_t)(best & 0xffffull);
             if (job.stage) job.stage[row] = 1;
         }
         shot_complete(sd, row, shot);
@@ -1216,7 +1222,7 @@ __device__ __forceinline__ void trial_done(const StreamDev &sd, long long row, l
 __device__ __forceinline__ bool trial_cannot_win(const StreamDev &sd, long long row, int kidx) {
     if (sd.code.select != 1) return false;
     const unsigned long long best = __ldcg(sd.rec.best + row);
-    return best != ~0ull && (long long)(best & 0xffffffffu) < (long long)kidx;
+    return best != ~0ull && (long long)(best >> 32) < (long long)kidx;
 }
 
 // Lane-parallel write-out of outboxes that need no warp cooperation:
@@ -1244,22 +1250,29 @@ __device__ __forceinline__ void finalize_simple(const StreamDev &sd, TeamMem T, 
     // Trial run: undo the flip (Algorithm 1) and take part in the selection.
     const int C = cd.n_trials, kidx = ss->kidx;
     if (conv) {
-        // e' xor t: t flips the record's Phi[j] for the bits j of the trial's mask.
-        uint32_t *dst = sd.rec.corr + ((long long)row * C + kidx) * Wn;
-        for (int w = 0; w < Wn; ++w) dst[w] = slot_word(T.ebits, Wn, s, w);
+        // e' xor t, in the slot's packed decision (the outbox is this lane's
+        // until it is released): t flips the record's Phi[j] for the bits j
+        // of the trial's mask.
+        uint32_t *ew = T.ebits + s * Wn;
         const unsigned long long mask = __ldg(cd.trial_mask + kidx);
         for (int j = 0; j < cd.w; ++j) {
             if (!((mask >> j) & 1ull)) continue;
             const int b = __ldcg(sd.rec.phi + row * cd.w + j);
-            dst[b >> 5] ^= 1u << (b & 31);
+            ew[b >> 5] ^= 1u << (b & 31);
         }
         unsigned wsum = 0;
-        for (int w = 0; w < Wn; ++w) wsum += __popc(dst[w]);
-        sd.rec.iters[(long long)row * C + kidx] = (int16_t)iter;
-        __threadfence();
-        const unsigned long long key =
-            cd.select == 0 ? (((unsigned long long)wsum << 32) | (unsigned)kidx) : (unsigned long long)kidx;
-        atomicMin(&sd.rec.best[row], key);
+        for (int w = 0; w < Wn; ++w) wsum += __popc(ew[w]);
+        // Selection key (unique per trial): weight, then list index; or the
+        // list index alone under the first-success rule.
+        const unsigned long long key = cd.select == 0 ? (((unsigned long long)wsum << 12) | (unsigned)kidx)
+                                                      : (unsigned long long)kidx;
+        const unsigned long long old = atomicMin(&sd.rec.best[row], (key << 32) | (unsigned)iter);
+        // Only a trial that held the smallest key so far merges its words: the
+        // final winner always does, and merges of others cannot beat it.
+        if ((old >> 32) > key) {
+            unsigned long long *win = sd.rec.win + row * Wn;
+            for (int w = 0; w < Wn; ++w) atomicMin(win + w, (key << 32) | ew[w]);
+        }
     }
     if (DEBUG) {
         if (sd.dbg.trial_conv) sd.dbg.trial_conv[shot * C + kidx] = conv ? 1 : 0;
@@ -1292,6 +1305,7 @@ __device__ __forceinline__ void finalize_failed(const StreamDev &sd, TeamMem T, 
         sd.rec.done[row] = 0u;
         sd.rec.best[row] = ~0ull;
     }
+    for (int w = lane; w < Wn; w += 32) sd.rec.win[row * Wn + w] = ~0ull;
     const uint32_t *syn = job.synd + row * job.synd_stride;
     for (int w = lane; w < Ws; w += 32) sd.rec.synd[row * Ws + w] = __ldcg(syn + w);
     __threadfence();
@@ -1699,7 +1713,17 @@ __global__ void __launch_bounds__(512, MINB) bpsf_persistent(const __grid_consta
             continue;
         }
         waiting = false;
-        const StreamDev &sd = kp.streams[sid];
+        // The block's copy of the stream's descriptor (shared memory): the
+        // parameters are indexed by a run-time stream number, and such loads
+        // from the parameter space are slow.
+        StreamDev *sdc = reinterpret_cast<StreamDev *>(smem + 64);
+        if (sid != cur) {
+            const int *src = reinterpret_cast<const int *>(&kp.streams[sid]);
+            int *dst = reinterpret_cast<int *>(sdc);
+            for (int k = tid; k < (int)(sizeof(StreamDev) / 4); k += blockDim.x) dst[k] = src[k];
+            __syncthreads();
+        }
+        const StreamDev &sd = *sdc;
         const CodeDev &cd = sd.code;
         const int S = sd.S, W = sd.W, teams = sd.teams;
         const LayoutOffsets lo = layout_offsets(cd.M, cd.N, DVS, cd.P);

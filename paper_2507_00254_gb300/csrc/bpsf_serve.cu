@@ -238,30 +238,9 @@ extern "C" bpsf_status bpsf_serve_start(bpsf_server **out, bpsf_ctx *const *code
         if (e != cudaSuccess) break;
         // Records at each arena row; the publication queue is a ring of R
         // entries (pending failed shots never outnumber admitted shots).
-        const int w = std::max(x->p.w, 1), T = std::max(x->n_trials, 1);
-        const size_t sz[8] = {a16(8 * R), a16(8 * R), a16(4 * R), a16(8 * R), a16(4 * R * w), a16(4 * R * x->Ws),
-                              a16(4 * R * T * x->Wn), a16(2 * R * T)};
-        size_t tot = 0;
-        for (size_t v : sz) tot += v;
-        e = cudaMalloc(&sc.d_rec, tot);
+        e = cudaMalloc(&sc.d_rec, bpsf_records_bytes((long long)R, x->p.w, x->Ws, x->Wn, 16));
         if (e != cudaSuccess) break;
-        unsigned char *p = (unsigned char *)sc.d_rec;
-        sc.rec.qseq = (unsigned long long *)p;
-        p += sz[0];
-        sc.rec.qshot = (long long *)p;
-        p += sz[1];
-        sc.rec.done = (unsigned *)p;
-        p += sz[2];
-        sc.rec.best = (unsigned long long *)p;
-        p += sz[3];
-        sc.rec.phi = (int32_t *)p;
-        p += sz[4];
-        sc.rec.synd = (uint32_t *)p;
-        p += sz[5];
-        sc.rec.corr = (uint32_t *)p;
-        p += sz[6];
-        sc.rec.iters = (int16_t *)p;
-        sc.rec.cap = (long long)R;
+        sc.rec = bpsf_records_carve(sc.d_rec, (long long)R, x->p.w, x->Ws, x->Wn, 16);
         e = cudaMemset(sc.rec.qseq, 0, 8 * R);
         // The serving stream of this code.
         JobDev job{sc.m_synd, sc.m_corr, sc.m_conv, sc.m_iters, sc.m_stage8, 0, x->Ws, x->Wn};

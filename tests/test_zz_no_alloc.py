@@ -56,9 +56,9 @@ def decoder():
 def test_noalloc_matches_decode_on_two_calls_in_a_row(decoder):
     c, dec = decoder
     cap = B.bpsf_noalloc_max_shots(dec.handle)
-    assert cap >= 10000
+    assert cap >= 200000  # about 100 bytes of records per shot of [[144]]
     # A larger batch, then a smaller one over the scratch the first one left behind.
-    for n, seed in ((min(cap, 12000), 901), (3000, 902)):
+    for n, seed in ((min(cap, 50000), 901), (3000, 902)):
         synd = _inputs(dec, c, 0.07, n, seed)
         ref = dec.decode(synd)
         got = _noalloc(dec, synd)
@@ -96,12 +96,13 @@ def test_noalloc_leaves_free_memory_unchanged_and_handles_a_trial_list(decoder):
     call()
     torch.cuda.synchronize()
     assert torch.cuda.mem_get_info()[0] == free0
-    # A trial list of a few masks changes the record layout (T != 2^w - 1).
+    # A trial list of a few masks (T != 2^w - 1): a failed shot's record keeps
+    # only the winning trial's correction, so the batch limit does not move.
     masks = [0b1, 0b10, 0b11, 0b100101, 0b111111]
     cap63 = B.bpsf_noalloc_max_shots(dec.handle)
     dec.set_trials(masks)
     try:
-        assert B.bpsf_noalloc_max_shots(dec.handle) > cap63  # five trials' records instead of 63
+        assert B.bpsf_noalloc_max_shots(dec.handle) == cap63
         ref = dec.decode(synd)
         got = _noalloc(dec, synd)
         _same(got, ref)
