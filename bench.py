@@ -149,6 +149,61 @@ def oracle_sample(n_per_p, shot0=0):
                        % (n_per_p, threads), seconds=dt)
 
 
+def _lat_stats(shot_s):
+    ms = np.asarray(shot_s) * 1e3
+    return {"mean_ms": float(ms.mean()), "p50_ms": float(np.percentile(ms, 50)), "p99_ms": float(np.percentile(ms, 99))}
+
+
+def oracle_plan():
+    """The CPU-baseline plan: the FP32 oracle, one host thread and all host
+    threads, on bounded samples of configs 1-4 (shots/s, and each shot's own
+    decode time as mean / p50 / p99).  Runs in the spawned pool process."""
+    import oracle
+    import synth
+    threads = oracle.max_threads()
+    out = {"cores_all": threads}
+
+    def case(oc, synd, p, P, n1, nall):
+        r = {}
+        for label, th, n in (("1_thread", 1, n1), ("all_threads", threads, nall)):
+            s = np.ascontiguousarray(synd[:n])
+            t = np.zeros(s.shape[0], dtype=np.float64)
+            t0 = time.perf_counter()
+            oc.bpsf_batch(s, p, P, fp32=True, threads=th, shot_s=t)
+            dt = time.perf_counter() - t0
+            r[label] = dict(shots=int(s.shape[0]), threads=th, shots_per_s=s.shape[0] / dt, **_lat_stats(t))
+        return r
+
+    def op(prm):
+        return oracle.Params(prm["max_iter"], prm["alpha"], prm["w"], prm["w_max"], prm["short_iter"], prm["select"])
+
+    # Config 1: [[72,12,6]], p = 0.05, max_iter 50, w 4 x short_iter 10.
+    hx, _ = oracle.named_code("bb72")
+    oc = oracle.Code(hx)
+    e = synth.bernoulli_bits(synth.SEEDS["bb72_cc"], 0, 0, 10000, 72, 0.05)
+    out["config1_bb72_p0.05"] = case(oc, oc.syndrome(e), 0.05,
+                                     op(dict(max_iter=50, alpha=0.625, w=4, w_max=0, short_iter=10, select=0)),
+                                     2000, 10000)
+    # Config 2: [[144,12,12]] at the four p (the headline workload's settings).
+    hx, _ = oracle.named_code(CODE)
+    oc = oracle.Code(hx)
+    for k, p in enumerate(P_LIST):
+        e = synth.bernoulli_bits(synth.SEEDS["bb144_cc"][k], 0, 0, 8000, N_BITS, p)
+        out["config2_bb144_p%g" % p] = case(oc, oc.syndrome(e), p, op(PARAMS), 500, 8000)
+    # Config 3: 12-round phenomenological [[144]], p = q = 0.002, 0.004.
+    oc = oracle.Code(oracle.phenom_code(hx, 12))
+    for k, p in enumerate((0.002, 0.004)):
+        e = synth.phenom_error_bits(synth.SEEDS["bb144_phenom"][k], 0, 0, 4000, 144, 72, 12, p, p)
+        out["config3_phenom_p%g" % p] = case(oc, oc.syndrome(e), p, op(PHENOM_PARAMS), 300, 4000)
+    # Config 4: the five BB codes of the mixed batch at p = 0.05 (config-2 parameters).
+    for k, name in enumerate(SERVE_BB):
+        hx, _ = oracle.named_code(name)
+        oc = oracle.Code(hx)
+        e = synth.bernoulli_bits(synth.SEEDS["mixed"][k], 0, 0, 4000, oc.N, 0.05)
+        out["config4_%s_p0.05" % name] = case(oc, oc.syndrome(e), 0.05, op(PARAMS), 300, 4000)
+    return out
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
@@ -299,14 +354,14 @@ def run_gpu(args, rank, world, pool):
         dt = time.perf_counter() - t0
         same = all(bool((po[key] == outs[k][key][:n_plain]).all()) for key in ("corr", "conv", "iters", "stage"))
         plain[str(p)] = {"shots": n_plain, "shots_per_s": n_plain / dt, "identical_to_batched": same}
-    # Per-shot latency of the plain form (launch to flag readback), all p pooled, on a small sample.
+    # Per-shot latency of the plain form (host syndrome in -> host result out, one
+    # single-shot request at a time, timed by the library on the host's monotonic
+    # clock), all p pooled, on the first 200 shots of each p.
+    h_sy = [synds[k][:200].cpu().numpy().view(np.uint32) for k in range(len(P_LIST))]
     lat = []
     for k in range(len(P_LIST)):
-        po = decs[k].outputs(1)
-        for i in range(min(200, n_plain)):
-            t0 = time.perf_counter()
-            decs[k].decode(synds[k][i:i + 1].contiguous(), out=po, plain=True)
-            lat.append(time.perf_counter() - t0)
+        lk, _ = B.plain_replay([decs[k]], None, [0] * 200, [h_sy[k][i:i + 1] for i in range(200)])
+        lat.extend(lk[10:].tolist())
     lat_ms = np.array(lat) * 1e3
     plain_total = sum(v["shots"] for v in plain.values())
     plain_time = sum(v["shots"] / v["shots_per_s"] for v in plain.values())
@@ -323,7 +378,7 @@ def run_gpu(args, rank, world, pool):
     h_jobs = [B.bpsf_job(decs[k].handle, n, h_synd[k].data_ptr(), 3, h_out[k][0].data_ptr(), 5,
                          h_out[k][1].data_ptr(), h_out[k][2].data_ptr(), h_out[k][3].data_ptr())
               for k in range(len(P_LIST))]
-    e2e_steps = max(1, min(args.steps, 3))
+    e2e_steps = args.steps  # the same number of steps as the device-timed value
     B.bpsf_decode_multi_host(h_jobs, stream.cuda_stream)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -350,6 +405,8 @@ def run_gpu(args, rank, world, pool):
     if rank == 0 and not args.no_cpu_baseline:
         cpu = pool.apply(oracle_sample, (args.cpu_shots,)) if pool else oracle_sample(args.cpu_shots)
         cpu.pop("seconds", None)
+        if not args.no_extras:
+            extras["cpu_baseline_plan"] = pool.apply(oracle_plan) if pool else oracle_plan()
 
     if rank == 0:
         # DRAM bytes per launch of the persistent kernel: ncu's dram__bytes_read + write of one
@@ -364,9 +421,12 @@ def run_gpu(args, rank, world, pool):
                        "launch": "one CUDA-graph replay per step: one persistent decode_multi launch over the 4 batches",
                        "tuning": list(tuned), "l2": "flushed between steps (512 MB write)",
                        "parallelism": "replicas" if world > 1 else "single"},
-            "roofline": {"bound": "alu", "achieved": achieved / 1e9, "peak": peak / 1e9, "unit": "Gedge-updates/s",
+            "roofline": {"bound": "smem", "achieved": achieved / 1e9, "peak": peak / 1e9, "unit": "Gedge-updates/s",
                          "frac": achieved / peak, "traffic": traffic, "traffic_unit": "bytes per launch",
-                         "note": "peak = SMs x 128 B/clk shared memory / 16 B per edge-update at the max SM clock"},
+                         "note": ("peak = SMs x 128 B/clk shared memory / 16 B per edge-update at the max SM clock "
+                                  "(nominal shared-memory bandwidth, no measured figure exists for it); the ncu "
+                                  "counters read the kernel as latency-bound (issue and shared-memory wavefronts "
+                                  "both near half of peak), not bandwidth-bound")},
             "cpu_baseline": cpu,
             "e2e": {"value": shots_step / e2e_dt, "unit": "shots/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
@@ -603,25 +663,51 @@ def run_mixed(B, codes, torch):
         e = synth.bernoulli_bits(synth.SEEDS["mixed"][k], 0, 0, int(counts[k]), c.N, 0.05)
         synds.append(d.syndrome(_packed_errors_dev(torch, e, d.Wn)))
         decs.append(d)
+    # Each code's launch shape from the autotuner (threads per shot, shots per
+    # block, iteration chunk), then all five in one launch with those shapes.
+    untuned = [d.tuning for d in decs]
     outs = B.decode_multi(decs, synds)  # warm-up
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     B.decode_multi(decs, synds, outs=outs)
+    dt0 = time.perf_counter() - t0
+    ref = [{k: v.clone() for k, v in o.items()} for o in outs]
+    tuned = [d.autotune(p_sample=0.05, n_sample=1 << 14) for d in decs]
+    B.decode_multi(decs, synds, outs=outs)  # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    B.decode_multi(decs, synds, outs=outs)
     dt = time.perf_counter() - t0
+    same = all(torch.equal(o[k], r[k]) for o, r in zip(outs, ref) for k in r)
     total = int(counts.sum())
-    res = {"codes": list(SERVE_BB), "shots": [int(x) for x in counts], "shots_per_s": total / dt, "ms": dt * 1e3}
+    res = {"codes": list(SERVE_BB), "shots": [int(x) for x in counts], "shots_per_s": total / dt, "ms": dt * 1e3,
+           "tunings": {n: list(t) for n, t in zip(SERVE_BB, tuned)},
+           "default_shapes": {"tunings": {n: list(t) for n, t in zip(SERVE_BB, untuned)}, "shots_per_s": total / dt0},
+           "identical_to_default_shapes": same}
     for d in decs:
         d.close()
     return res
 
 
-def run_served(B, codes, torch, loads, seconds=2.0, pool_shots=8192, tuning=None):
+def _pct(lat_s):
+    ms = np.asarray(lat_s) * 1e3
+    return {"p50_ms": float(np.percentile(ms, 50)), "p99_ms": float(np.percentile(ms, 99)),
+            "p999_ms": float(np.percentile(ms, 99.9)), "mean_ms": float(ms.mean())}
+
+
+def run_served(B, codes, torch, loads, seconds=2.0, pool_shots=8192, tuning=None, plain_cap_shots=20000):
     """Poisson request stream over the five BB codes (p = 0.05) and the 12-round
-    phenomenological [[144]] model (p = q = 0.003), through bpsf_serve_*.
+    phenomenological [[144]] model (p = q = 0.003), served by bpsf_serve_* and,
+    on the same requests, by the plain per-shot form (bpsf_plain_replay).
     Requests carry b = max(1, load / 10000) shots (at most ~10^4 requests/s);
-    the trace is replayed open loop by the library (bpsf_serve_replay), and
-    latency is scheduled arrival -> results ready in host memory."""
+    both traces are replayed by the library on the host's monotonic clock, and
+    latency is scheduled arrival -> results in host memory.  Closed loop: one
+    single-shot request in flight at a time, per code and over the whole mix.
+    The plain form decodes one shot at a time, so above its own rate its
+    open-loop latency grows with the trace; its traces are cut to the first
+    plain_cap_shots shots (the span is reported)."""
     import synth
+    names = list(SERVE_BB) + ["bb144_phenom12"]
     decs, pools = [], []
     for k, name in enumerate(SERVE_BB):
         c = codes.bb(name)
@@ -636,67 +722,80 @@ def run_served(B, codes, torch, loads, seconds=2.0, pool_shots=8192, tuning=None
     e = synth.phenom_error_bits(synth.SEEDS["serve"], 9, 0, pool_shots // 4, 144, 72, 12, 0.003, 0.003)
     pools.append(d.syndrome(_packed_errors_dev(torch, e, d.Wn)).cpu().numpy().view(np.uint32))
     decs.append(d)
-    # Plain per-shot latency on the same mix (launch -> flag readback per shot).
-    lat_plain = []
-    for k, dk in enumerate(decs):
-        for i in range(40):
-            s = torch.from_numpy(pools[k][i:i + 1].view(np.int32).copy()).cuda()
-            o = dk.outputs(1)
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            dk.decode(s, out=o, plain=True)
-            lat_plain.append(time.perf_counter() - t0)
-    lat_plain = np.array(lat_plain) * 1e3
-    srv = B.Server(decs, max_inflight_shots=1 << 16, idle_exit_us=50000)
-    results = []
-    # Closed loop: one single-shot request at a time (submit -> results in host memory).
-    closed = {}
+
+    # Traces: per load, arrivals, codes and request rows (the same for both forms).
+    traces = []
+    for li, load in enumerate(loads):
+        b = max(1, int(load // 10000))
+        rate = load / b
+        n_req = max(50, int(rate * seconds))
+        arrivals = synth.poisson_arrivals(synth.SEEDS["serve"], 100 + li, n_req, rate)
+        which = synth.uniform_choice(synth.SEEDS["serve"], 200 + li, n_req, len(decs))
+        reqs = []
+        cursor = [0] * len(decs)
+        for i in range(n_req):
+            k = int(which[i])
+            nn = b if k < len(SERVE_BB) else max(1, b // 4)
+            pool = pools[k]
+            a = cursor[k] % (pool.shape[0] - nn)
+            cursor[k] += nn
+            reqs.append(pool[a:a + nn])
+        traces.append((load, b, arrivals, which, reqs))
+    n_cl = 200
+    mix_which = synth.uniform_choice(synth.SEEDS["serve"], 300, 600, len(decs))
+    mix_reqs = [pools[int(k)][i:i + 1] for i, k in enumerate(mix_which)]
+
+    def per_code(lat_s, which):
+        out = {}
+        for k in range(len(decs)):
+            sel = np.asarray(lat_s)[np.asarray(which) == k]
+            if sel.size:
+                out[names[k]] = [float(np.percentile(sel * 1e3, 50)), float(np.percentile(sel * 1e3, 99))]
+        return out
+
+    # The plain form first (no server holds the SMs meanwhile).
+    plain_closed, plain_open = {}, []
     for k in range(len(decs)):
-        ts = []
-        for i in range(200):
-            t1 = time.perf_counter()
-            srv.poll(srv.submit(k, pools[k][i:i + 1]), 1, k)
-            ts.append(time.perf_counter() - t1)
-        ts = np.array(ts[20:]) * 1e3
-        closed[(list(SERVE_BB) + ["bb144_phenom12"])[k]] = [float(np.percentile(ts, 50)), float(np.percentile(ts, 99))]
+        lat, _ = B.plain_replay(decs, None, [k] * n_cl, [pools[k][i:i + 1] for i in range(n_cl)])
+        plain_closed[names[k]] = _pct(lat[20:])
+    lat, _ = B.plain_replay(decs, None, mix_which, mix_reqs)
+    plain_closed["mix"] = _pct(lat[20:])
+    for load, b, arrivals, which, reqs in traces:
+        m, shots = 0, 0
+        while m < len(reqs) and shots + reqs[m].shape[0] <= plain_cap_shots:
+            shots += reqs[m].shape[0]
+            m += 1
+        lat, span = B.plain_replay(decs, arrivals[:m], which[:m], reqs[:m])
+        plain_open.append(dict(offered_shots_per_s=load, shots_per_request=b, requests=m,
+                               trace_s=float(arrivals[m - 1]), achieved_shots_per_s=shots / span,
+                               per_code_p50_p99_ms=per_code(lat, which[:m]), **_pct(lat)))
+
+    srv = B.Server(decs, max_inflight_shots=1 << 16, idle_exit_us=50000)
+    served_closed, served_open = {}, []
     try:
-        for li, load in enumerate(loads):
-            b = max(1, int(load // 10000))
-            rate = load / b
-            n_req = max(50, int(rate * seconds))
-            arrivals = synth.poisson_arrivals(synth.SEEDS["serve"], 100 + li, n_req, rate)
-            which = synth.uniform_choice(synth.SEEDS["serve"], 200 + li, n_req, len(decs))
-            reqs = []
-            cursor = [0] * len(decs)
-            for i in range(n_req):
-                k = int(which[i])
-                nn = b if k < len(SERVE_BB) else max(1, b // 4)
-                pool = pools[k]
-                a = cursor[k] % (pool.shape[0] - nn)
-                cursor[k] += nn
-                reqs.append(pool[a:a + nn])
-            lat_s, span = srv.replay(arrivals, which, reqs)
-            lat = lat_s * 1e3
+        for k in range(len(decs)):
+            lat, _ = srv.replay(None, [k] * n_cl, [pools[k][i:i + 1] for i in range(n_cl)])
+            served_closed[names[k]] = _pct(lat[20:])
+        lat, _ = srv.replay(None, mix_which, mix_reqs)
+        served_closed["mix"] = _pct(lat[20:])
+        for load, b, arrivals, which, reqs in traces:
+            lat, span = srv.replay(arrivals, which, reqs)
             shots = sum(x.shape[0] for x in reqs)
-            errs = []
-            per_code = {}
-            for k in range(len(decs)):
-                sel = lat[which == k]
-                if sel.size:
-                    per_code[(list(SERVE_BB) + ["bb144_phenom12"])[k]] = [float(np.percentile(sel, 50)),
-                                                                        float(np.percentile(sel, 99))]
-            results.append({"offered_shots_per_s": load, "shots_per_request": b, "requests": n_req,
-                            "achieved_shots_per_s": shots / span, "p50_ms": float(np.percentile(lat, 50)),
-                            "p99_ms": float(np.percentile(lat, 99)), "p999_ms": float(np.percentile(lat, 99.9)),
-                            "per_code_p50_p99_ms": per_code, "errors": errs[:3]})
+            served_open.append(dict(offered_shots_per_s=load, shots_per_request=b, requests=len(reqs),
+                                    trace_s=float(arrivals[-1]), achieved_shots_per_s=shots / span,
+                                    per_code_p50_p99_ms=per_code(lat, which), **_pct(lat)))
     finally:
         srv.stop()
+    tunings = {names[k]: list(decs[k].tuning) for k in range(len(decs))}
     for dk in decs:
         dk.close()
-    return {"mix": list(SERVE_BB) + ["bb144_phenom12"], "tuning_bb": list(tuning) if tuning else "default",
-            "loads": results, "closed_loop_p50_p99_ms": closed,
-            "plain_per_shot_ms": {"p50": float(np.percentile(lat_plain, 50)), "p99": float(np.percentile(lat_plain, 99)),
-                                  "p999": float(np.percentile(lat_plain, 99.9))}}
+    cmp = []
+    for so, po in zip(served_open, plain_open):
+        cmp.append({"offered_shots_per_s": so["offered_shots_per_s"], "served_p99_ms": so["p99_ms"],
+                    "plain_p99_ms": po["p99_ms"], "served_p99_below_plain": so["p99_ms"] < po["p99_ms"]})
+    return {"mix": names, "tunings": tunings, "clock": "host steady_clock inside the library (both forms)",
+            "loads": served_open, "plain_loads": plain_open, "p99_served_vs_plain": cmp,
+            "closed_loop": {"served": served_closed, "plain": plain_closed}}
 
 
 def main():
@@ -717,6 +816,8 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="skip the served / phenomenological / mixed lines")
     ap.add_argument("--serve-seconds", type=float, default=2.0)
     ap.add_argument("--only-served", action="store_true", help="run only the served measurement (diagnostics)")
+    ap.add_argument("--only", choices=["phenom", "layered", "mixed", "families", "sampled", "first"], default=None,
+                    help="run only one secondary measurement and print its JSON (diagnostics, profiling)")
     ap.add_argument("--serve-tuning", type=lambda x: tuple(int(v) for v in x.split(",")), default=SERVE_TUNING,
                     help="team shape W,S,B,blocks_per_sm of the served BB codes")
     args = ap.parse_args()
@@ -726,6 +827,18 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.only:
+        import torch
+        from paper_2507_00254_gb300 import build as libbuild
+        libbuild.build()
+        from paper_2507_00254_gb300 import bpsf as B
+        from paper_2507_00254_gb300 import codes, harness
+        fn = {"phenom": lambda: run_phenom(B, codes, torch), "layered": lambda: run_layered(B, codes, torch, harness),
+              "mixed": lambda: run_mixed(B, codes, torch), "families": lambda: run_families(B, codes, torch, harness),
+              "sampled": lambda: run_sampled(B, codes, torch, harness),
+              "first": lambda: run_first_success(B, codes, torch)}[args.only]
+        print(json.dumps(fn()))
         return
     if args.only_served:
         import torch

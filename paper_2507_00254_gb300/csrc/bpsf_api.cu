@@ -736,6 +736,7 @@ static bpsf_status check_io(const bpsf_ctx *c, int64_t n, const void *synd, int3
 
 static bpsf_status decode_impl(bpsf_ctx *c, int64_t n, const uint32_t *synd, int32_t ss, uint32_t *corr, int32_t cs,
                                uint8_t *conv, int16_t *iters, uint8_t *stage, const DebugDev *dbg, void *stream) {
+    BpsfRange range("bpsf_decode");
     bpsf_status st = check_io(c, n, synd, ss, corr, cs, conv, iters);
     if (st != BPSF_OK || n == 0) return st;
     cudaSetDevice(c->device);
@@ -850,6 +851,7 @@ extern "C" bpsf_status bpsf_set_trials(bpsf_ctx *c, int32_t n, const uint64_t *m
 
 extern "C" bpsf_status bpsf_decode_plain(bpsf_ctx *c, int64_t n, const uint32_t *synd, int32_t ss, uint32_t *corr,
                                          int32_t cs, uint8_t *conv, int16_t *iters, uint8_t *stage, void *stream) {
+    BpsfRange range("bpsf_decode_plain");
     bpsf_status st = check_io(c, n, synd, ss, corr, cs, conv, iters);
     if (st != BPSF_OK || n == 0) return st;
     cudaSetDevice(c->device);
@@ -880,6 +882,7 @@ extern "C" bpsf_status bpsf_decode_plain(bpsf_ctx *c, int64_t n, const uint32_t 
         cudaError_t e = cudaMemsetAsync(c->d_ctr, 0, sizeof(StreamCounters), s);
         if (e == cudaSuccess) e = cudaMemsetAsync(c->rec.qseq, 0, 8, s);
         if (e != cudaSuccess) return bpsf_fail(BPSF_ECUDA, "cudaMemsetAsync: %s", cudaGetErrorString(e));
+        BpsfRange shot_range("plain shot");
         StreamDev sdA = bpsf_make_stream(c, job, nullptr, kNoTickets);
         bpsf_launch_plan(plA, false, &sdA, 1, 1, stream);
         e = cudaMemcpyAsync(c->h_flag, conv + i, 1, cudaMemcpyDeviceToHost, s);
@@ -892,6 +895,7 @@ extern "C" bpsf_status bpsf_decode_plain(bpsf_ctx *c, int64_t n, const uint32_t 
             ++failed;
             e = cudaMemcpyAsync(c->d_ctr, c->h_preset, sizeof(StreamCounters), cudaMemcpyHostToDevice, s);
             if (e != cudaSuccess) return bpsf_fail(BPSF_ECUDA, "cudaMemcpyAsync: %s", cudaGetErrorString(e));
+            BpsfRange trial_range("plain trial sweep");
             StreamDev sdB = bpsf_make_stream(c, job, nullptr, 0);
             bpsf_launch_plan(plB, false, &sdB, 1, gridB, stream);
             e = cudaMemcpyAsync(c->h_ctr, c->d_ctr, sizeof(StreamCounters), cudaMemcpyDeviceToHost, s);
@@ -982,6 +986,7 @@ extern "C" bpsf_status bpsf_decode_host(bpsf_ctx *c, int64_t n, const uint32_t *
 }
 
 extern "C" bpsf_status bpsf_decode_multi_host(int32_t n_jobs, const bpsf_job *jobs, void *stream) {
+    BpsfRange range("bpsf_decode_multi_host");
     if (n_jobs < 1 || n_jobs > kMaxStreams || !jobs) return bpsf_fail(BPSF_EINVAL, "n_jobs must be in 1..%d", kMaxStreams);
     for (int k = 0; k < n_jobs; ++k) {
         const bpsf_job &j = jobs[k];
@@ -1034,6 +1039,7 @@ extern "C" bpsf_status bpsf_decode_multi_host(int32_t n_jobs, const bpsf_job *jo
 // ---------------------------------------------------------------------------
 
 extern "C" bpsf_status bpsf_decode_multi(int32_t n_jobs, const bpsf_job *jobs, void *stream) {
+    BpsfRange range("bpsf_decode_multi");
     if (n_jobs < 1 || n_jobs > kMaxStreams || !jobs) return bpsf_fail(BPSF_EINVAL, "n_jobs must be in 1..%d", kMaxStreams);
     std::vector<bpsf_ctx *> codes(n_jobs);
     for (int k = 0; k < n_jobs; ++k) {
@@ -1117,6 +1123,7 @@ bool bpsf_tuning_cache_lookup(const bpsf_ctx *c, bpsf_tuning *out) {
 
 extern "C" bpsf_status bpsf_autotune(bpsf_ctx *c, double p_sample, int64_t n_sample, void *stream,
                                      bpsf_tuning *chosen) {
+    BpsfRange range("bpsf_autotune");
     if (!c) return bpsf_fail(BPSF_EINVAL, "ctx is NULL");
     if (!(p_sample > 0.0 && p_sample < 0.5)) return bpsf_fail(BPSF_EINVAL, "p_sample must be in (0, 0.5)");
     if (n_sample < 1 || n_sample > (1 << 24)) return bpsf_fail(BPSF_EINVAL, "n_sample must be in 1..2^24");

@@ -4,8 +4,19 @@
 #include <cstdint>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "bpsf.h"
 #include "bpsf_internal.h"
+
+// NVTX range over a host entry point or one of its steps (shown by profilers
+// that record NVTX; a no-op otherwise).
+struct BpsfRange {
+    explicit BpsfRange(const char *name) { nvtxRangePushA(name); }
+    ~BpsfRange() { nvtxRangePop(); }
+    BpsfRange(const BpsfRange &) = delete;
+    BpsfRange &operator=(const BpsfRange &) = delete;
+};
 
 struct bpsf_ctx {
     int device = 0, sm_count = 0, smem_optin = 0;

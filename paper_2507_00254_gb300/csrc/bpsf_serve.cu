@@ -273,6 +273,7 @@ extern "C" bpsf_status bpsf_serve_submit(bpsf_server *s, int32_t code, int64_t n
     if (n < 1 || !h_synd || !ticket) return bpsf_fail(BPSF_EINVAL, "need n >= 1, syndromes and a ticket pointer");
     SrvCode &sc = s->codes[code];
     if (n > sc.rows) return bpsf_fail(BPSF_EINVAL, "request of %lld shots exceeds %lld rows", (long long)n, sc.rows);
+    BpsfRange range("bpsf_serve_submit");
     std::unique_lock<std::mutex> lk(s->mu);
     const auto deadline = std::chrono::steady_clock::now() + std::chrono::microseconds(std::max<int64_t>(timeout_us, 0));
     auto fits = [&] { return !s->free_slots.empty() && sc.rows - (sc.next_g - sc.released) >= n; };
@@ -326,6 +327,7 @@ extern "C" bpsf_status bpsf_serve_poll(bpsf_server *s, uint64_t ticket, int64_t 
     }
     SrvCode &sc = s->codes[r.code];
     const volatile unsigned *done = sc.h_done;
+    BpsfRange range("bpsf_serve_poll");
     const auto start = std::chrono::steady_clock::now();
     long long spins = 0, i = r.checked;
     while (i < r.n) {
@@ -557,6 +559,7 @@ extern "C" bpsf_status bpsf_plain_replay(bpsf_ctx *const *codes, int32_t n_codes
             while (clk::now() < a) {
             }
         }
+        BpsfRange req_range("plain replay request");
         bpsf_ctx *c = codes[code[i]];
         Buf &b = bufs[code[i]];
         const int64_t n = n_shots[i];
