@@ -175,6 +175,9 @@ template <int FB> __device__ __forceinline__ unsigned flip_bump(unsigned f) { re
 // the configurations; keeps messages finite when adaptive damping tends to 1.
 constexpr float kMagClamp = 0x1p100f;
 
+// Back-off of an idle team's service loop (ns).
+constexpr unsigned kIdleMinNs = 128, kIdleMaxNs = 2048;
+
 // Damping factor of iteration t (1-based) of a run: the fixed alpha, or the
 // adaptive 1 - 2^-t (alpha == 0), an exactly rounded float subtraction
 // (2^-t is exact; t >= 25 rounds to 1).
@@ -985,6 +988,7 @@ __device__ void team_loop(const StreamDev &sd, const LayoutMem &L, const TeamMem
     const int s0 = vs * (lane & ((S / vs) - 1));
     unsigned long long idle_since = 0;
     unsigned last_beat = 0;
+    unsigned idle_ns = kIdleMinNs;  // back-off of an idle team between looks at its inboxes
     unsigned run = 0u, initm = 0u;
     constexpr int VMAX = (kVec4 || kLayV4) ? 4 : 2;  // most slots a lane serves in this instance
     int tt = 0;                   // team iterations run (the same in every warp)
@@ -1042,10 +1046,14 @@ __device__ void team_loop(const StreamDev &sd, const LayoutMem &L, const TeamMem
                             last_beat = beat;
                         }
                         if (now - idle_since > 2 * wait_ns) ex = 1;
-                        __nanosleep(100);
+                        // Idle teams back off (up to 2 us), so the warps of the
+                        // block that do run keep the issue slots.
+                        __nanosleep(idle_ns);
+                        idle_ns = idle_ns < kIdleMaxNs ? 2 * idle_ns : kIdleMaxNs;
                     }
                 } else {
                     idle_since = 0;
+                    idle_ns = kIdleMinNs;
                 }
                 if (lane == 0) {
                     T.ctl->run_mask = rm;
@@ -1477,6 +1485,7 @@ __device__ void manager_loop(const StreamDev &sd, const LayoutMem &L, unsigned c
     const int qstride = qentry_bytes(cd.Ws);
     const int nslots = teams * S;
     MgrState mg{0, 0, 0u, 0u, 0u};
+    unsigned idle_ns = 32;  // back-off after passes that found nothing to do
     for (;;) {
         bool progress = false;
         bool busy = false;
@@ -1587,7 +1596,14 @@ __device__ void manager_loop(const StreamDev &sd, const LayoutMem &L, unsigned c
             // waits across all codes (serving) or for other blocks' trials.
             if (!any_slot) break;
         }
-        if (!progress) __nanosleep(32);
+        // Passes that find nothing back off, up to 1 us (a finished slot then
+        // waits that long at most for its write-out); any progress resets it.
+        if (progress) {
+            idle_ns = 32;
+        } else {
+            __nanosleep(idle_ns);
+            idle_ns = idle_ns < 1024 ? 2 * idle_ns : 1024;
+        }
     }
     // Flush counters and release the teams.
     const unsigned init_tot = __reduce_add_sync(FULLMASK, mg.init_local);
