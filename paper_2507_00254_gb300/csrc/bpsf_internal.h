@@ -154,8 +154,6 @@ struct StreamDev {
     int chunk;       // team iterations between refills of finished slots (>= 1)
 };
 
-static_assert(sizeof(StreamDev) % 8 == 0, "the block copies the descriptor in 4-byte words");
-
 // Launch: the team shape is set per stream (StreamDev::S, W, teams); each
 // block has one manager warp besides; Q ready-queue entries.
 struct LaunchArgs {
@@ -171,10 +169,7 @@ struct LaunchArgs {
 
 __host__ __device__ inline int align_up(int x, int a) { return (x + a - 1) / a * a; }
 
-// Block header: 64 bytes of control words, then the block's copy of the
-// descriptor of the code it serves (StreamDev), read by every warp in its
-// loops from shared memory rather than from the kernel parameters.
-constexpr int kBlockHeaderBytes = 64 + ((int)sizeof(StreamDev) + 15) / 16 * 16;
+constexpr int kBlockHeaderBytes = 64;
 
 struct LayoutOffsets {
     int row_deg, vpos, lch, lch_pos, total;
@@ -229,7 +224,7 @@ struct OutBox {
 };
 static_assert(sizeof(OutBox) == 32, "outbox is 32 bytes");
 
-// Team control block (48 bytes).  run_mask, init_mask and exit are written
+// Team control block (64 bytes).  run_mask, init_mask and exit are written
 // by the team's warp 0 at a service step and read by the whole team after the
 // barrier that follows; stop_mask[t & 1] holds the slots whose run ends after
 // team iteration t whatever its syndrome (iteration cap, or a trial asked to
@@ -239,11 +234,13 @@ struct TeamCtl {
     unsigned run_mask, init_mask;
     int exit;
     unsigned stop_mask[2];
-    unsigned pad;
+    unsigned last_beat;              // idle team (warp 0): the manager's heartbeat last seen,
+    unsigned long long idle_since;   //   when it started idling (0: it runs),
+    unsigned idle_ns, idle_looks;    //   its current sleep and the looks that found nothing
     unsigned long long iters;  // iterations run by this team (all slots)
     unsigned long long cap;    // team iterations with a running slot, times S
 };
-static_assert(sizeof(TeamCtl) <= 48, "team control block fits its 48 bytes");
+static_assert(sizeof(TeamCtl) <= 64, "team control block fits its 64 bytes");
 
 // Work items of the manager's ready queue and of the slots' inboxes: 16
 // bytes of fields plus Ws syndrome words (a trial's words are s' = s xor t H^T).  kind 1 = initial run of a shot,
@@ -283,7 +280,7 @@ __host__ __device__ inline TeamOffsets team_offsets(int S, int M, int N, int P, 
     TeamOffsets o;
     const int sw = (S * M + 31) / 32;
     int p = 0;
-    o.ctl = p;     p += 48;
+    o.ctl = p;     p += 64;
     o.state = p;   p += (int)sizeof(SlotState) * S;
     o.outbox = p;  p += (int)sizeof(OutBox) * S;
     o.syn = p;     p += 4 * sw;

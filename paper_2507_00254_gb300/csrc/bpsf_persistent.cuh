@@ -175,8 +175,9 @@ template <int FB> __device__ __forceinline__ unsigned flip_bump(unsigned f) { re
 // the configurations; keeps messages finite when adaptive damping tends to 1.
 constexpr float kMagClamp = 0x1p100f;
 
-// Back-off of an idle team's service loop (ns).
-constexpr unsigned kIdleMinNs = 128, kIdleMaxNs = 2048;
+// Back-off of an idle team's service loop (ns), after kIdleLooks looks that
+// found nothing; the manager backs off after kIdleLooks passes without progress.
+constexpr unsigned kIdleMinNs = 100, kIdleMaxNs = 2048, kIdleLooks = 16;
 
 // Damping factor of iteration t (1-based) of a run: the fixed alpha, or the
 // adaptive 1 - 2^-t (alpha == 0), an exactly rounded float subtraction
@@ -986,26 +987,26 @@ __device__ void team_loop(const StreamDev &sd, const LayoutMem &L, const TeamMem
     const int vs = lay ? ((kLayV4 && S >= 4) ? 4 : ((kLayV2 && S >= 2) ? 2 : 1))
                        : ((kVec4 && S >= 4) ? 4 : ((kVec && S >= 2) ? 2 : 1));
     const int s0 = vs * (lane & ((S / vs) - 1));
-    unsigned long long idle_since = 0;
-    unsigned last_beat = 0;
-    unsigned idle_ns = kIdleMinNs;  // back-off of an idle team between looks at its inboxes
     unsigned run = 0u, initm = 0u;
-    constexpr int VMAX = (kVec4 || kLayV4) ? 4 : 2;  // most slots a lane serves in this instance
-    int tt = 0;                   // team iterations run (the same in every warp)
-    int start[VMAX];              // team iteration of the first iteration of the lane's slots' runs
-#pragma unroll
-    for (int c = 0; c < VMAX; ++c) start[c] = 0;
-    // Every warp, lane l < S: slot l's first team iteration and iteration cap.
-    int l_start = 0, l_lim = 0;
-    // Warp 0, lane s < S: slot s's stop key (first-success rule).
-    long long w_key = 0;
-    // Warp 0, lane 0: iterations run and slot-iterations offered since the
-    // last service (added to the control block at the next service).
-    unsigned n_iters = 0, n_cap = 0;
+    int tt = 0;  // team iterations run (the same in every warp)
+    // Every warp, lane l < S: the team iteration after which slot l's run
+    // reaches its iteration cap.
+    int l_end = 0;
+    // Warp 0, lane 0: iterations run since the last service, and the team
+    // iteration of that service (added to the control block at the next one).
+    unsigned n_iters = 0;
+    int tt_flush = 0;
     const bool first_rule = cd.select == 1;
+    const bool adaptive = !(cd.alpha > 0.f);  // alpha_t = 1 - 2^-t needs each run's iteration number
     bool svc = true;
     const int chunk = sd.chunk > 1 ? sd.chunk : 1;  // iterations between refills of finished slots
     int since = 0;                                  // team iterations since the last service
+    // The idle state (warp 0 only, rarely used) lives in the control block.
+    if (wt == 0 && lane == 0) {
+        T.ctl->idle_since = 0;
+        T.ctl->idle_ns = kIdleMinNs;
+        T.ctl->idle_looks = 0;
+    }
     for (;;) {
         if (svc) {
             // Every warp has made the previous decision (read the residual
@@ -1015,10 +1016,11 @@ __device__ void team_loop(const StreamDev &sd, const LayoutMem &L, const TeamMem
             if (wt == 0) {
                 // The work counters first: the manager adds them up once every
                 // slot of the block reads empty, which the service below may make so.
-                if (lane == 0 && n_cap) {
+                if (lane == 0 && tt != tt_flush) {
                     T.ctl->iters += n_iters;
-                    T.ctl->cap += n_cap;
-                    n_iters = n_cap = 0;
+                    T.ctl->cap += (unsigned long long)(tt - tt_flush) * (unsigned)S;
+                    n_iters = 0;
+                    tt_flush = tt;
                 }
                 team_service<DEBUG, FB>(sd, L, T, S, lgS, lane);
                 SlotState *ss = &T.st[lane < S ? lane : 0];
@@ -1027,11 +1029,8 @@ __device__ void team_loop(const StreamDev &sd, const LayoutMem &L, const TeamMem
                 __threadfence_block();
                 const unsigned rm = __ballot_sync(FULLMASK, r);
                 const unsigned im = __ballot_sync(FULLMASK, r && ss->kind == 1);
-                if (r) {
-                    // A run installed at this service starts with the next iteration.
-                    if (ss->start < 0) ss->start = tt;
-                    w_key = ss->kind == 2 ? ss->shot * (long long)cd.n_trials + ss->kidx + 1 : 0;
-                }
+                // A run installed at this service starts with the next iteration.
+                if (r && ss->start < 0) ss->start = tt;
                 int ex = 0;
                 if (rm == 0u) {
                     if (hdr->exit) {
@@ -1041,19 +1040,29 @@ __device__ void team_loop(const StreamDev &sd, const LayoutMem &L, const TeamMem
                         // no pass for twice the bound on any of its own waits.
                         const unsigned long long now = globaltimer_ns();
                         const unsigned beat = hdr->heartbeat;
-                        if (idle_since == 0 || beat != last_beat) {
-                            idle_since = now;
-                            last_beat = beat;
+                        unsigned long long since_ns = T.ctl->idle_since;
+                        if (since_ns == 0 || beat != T.ctl->last_beat) since_ns = now;
+                        if (now - since_ns > 2 * wait_ns) ex = 1;
+                        // A team idle for more than a few looks backs off (up
+                        // to 2 us), so the warps of the block that do run keep
+                        // the issue slots; short gaps between runs keep the
+                        // short sleep.
+                        unsigned ns = T.ctl->idle_ns;
+                        const unsigned looks = T.ctl->idle_looks + 1;
+                        __nanosleep(ns);
+                        if (looks > kIdleLooks) ns = ns < kIdleMaxNs ? 2 * ns : kIdleMaxNs;
+                        __syncwarp();
+                        if (lane == 0) {
+                            T.ctl->idle_since = since_ns;
+                            T.ctl->last_beat = beat;
+                            T.ctl->idle_ns = ns;
+                            T.ctl->idle_looks = looks;
                         }
-                        if (now - idle_since > 2 * wait_ns) ex = 1;
-                        // Idle teams back off (up to 2 us), so the warps of the
-                        // block that do run keep the issue slots.
-                        __nanosleep(idle_ns);
-                        idle_ns = idle_ns < kIdleMaxNs ? 2 * idle_ns : kIdleMaxNs;
                     }
-                } else {
-                    idle_since = 0;
-                    idle_ns = kIdleMinNs;
+                } else if (lane == 0) {
+                    T.ctl->idle_since = 0;
+                    T.ctl->idle_ns = kIdleMinNs;
+                    T.ctl->idle_looks = 0;
                 }
                 if (lane == 0) {
                     T.ctl->run_mask = rm;
@@ -1067,28 +1076,26 @@ __device__ void team_loop(const StreamDev &sd, const LayoutMem &L, const TeamMem
             const int ex = T.ctl->exit;
             if (ex) break;
             if (run == 0u) continue;
-#pragma unroll
-            for (int c = 0; c < VMAX; ++c)
-                if (c < vs) start[c] = T.st[s0 + c].start;
-            if (lane < S) {
-                l_start = T.st[lane].start;
-                l_lim = T.st[lane].limit;
-            }
+            if (lane < S) l_end = T.st[lane].start + T.st[lane].limit - 1;
             svc = false;
             since = 0;
         }
         // First-success rule: warp 0 publishes the trials the manager asked to
         // stop (they cannot win), read by every warp after this iteration.
         if (first_rule && wt == 0) {
-            const bool cancel = lane < S && ((run >> lane) & 1u) && w_key != 0 &&
-                                *reinterpret_cast<volatile long long *>(&T.st[lane].cancel) == w_key;
+            bool cancel = false;
+            if (lane < S && ((run >> lane) & 1u) && T.st[lane].kind == 2)
+                cancel = *reinterpret_cast<volatile long long *>(&T.st[lane].cancel) ==
+                         T.st[lane].shot * (long long)cd.n_trials + T.st[lane].kidx + 1;
             const unsigned cm = __ballot_sync(FULLMASK, cancel);
             if (lane == 0) T.ctl->stop_mask[tt & 1] = cm;
         }
-        // Damping of iteration it = tt - start + 1 of each of the lane's slots.
+        // Damping of iteration it = tt - start + 1 of each of the lane's slots
+        // (the start is read only under adaptive damping).
         float al[4];
 #pragma unroll
-        for (int c = 0; c < 4; ++c) al[c] = c < VMAX ? damping(cd, tt - start[c < VMAX ? c : 0] + 1) : 0.f;
+        for (int c = 0; c < 4; ++c)
+            al[c] = adaptive && c < vs ? damping(cd, tt - T.st[s0 + c].start + 1) : cd.alpha;
         if (lay) {
             if (kLayV4 && vs == 4) {
                 float a4[4] = {al[0], al[1], al[2], al[3]};
@@ -1135,20 +1142,18 @@ __device__ void team_loop(const StreamDev &sd, const LayoutMem &L, const TeamMem
         const unsigned nconv = acc & full;
         // Runs at their iteration cap (every warp knows every slot's cap), and
         // trials asked to stop.
-        const int it = tt - l_start + 1;  // lane l: this iteration's number in slot l's run
-        const unsigned capped = __ballot_sync(FULLMASK, lane < S && it >= l_lim);
+        const unsigned capped = __ballot_sync(FULLMASK, lane < S && tt >= l_end);
         const unsigned cancelled = first_rule ? T.ctl->stop_mask[tt & 1] : 0u;
         const unsigned done = run & (~nconv | capped | cancelled);
         if (wt == 0) {
             if ((done >> lane) & 1u) {
                 SlotState *ss = &T.st[lane];
-                ss->iter = it;
+                ss->iter = tt - ss->start + 1;
                 ss->outcome = !((nconv >> lane) & 1u) ? 1 : (((cancelled >> lane) & 1u) ? 3 : 2);
                 // Finished slots are packed by the next service step.
                 *vstate(ss) = kSlotPending;
             }
-            n_iters += (unsigned long long)__popc(run);
-            n_cap += (unsigned long long)S;
+            n_iters += __popc(run);
         }
         // Finished slots leave the run mask at once (their decisions and flip
         // counts stay as they were) and wait for the next service, which comes
@@ -1485,7 +1490,8 @@ __device__ void manager_loop(const StreamDev &sd, const LayoutMem &L, unsigned c
     const int qstride = qentry_bytes(cd.Ws);
     const int nslots = teams * S;
     MgrState mg{0, 0, 0u, 0u, 0u};
-    unsigned idle_ns = 32;  // back-off after passes that found nothing to do
+    unsigned idle_ns = 32;     // back-off after passes that found nothing to do
+    unsigned idle_passes = 0;  // consecutive passes without progress
     for (;;) {
         bool progress = false;
         bool busy = false;
@@ -1596,13 +1602,15 @@ __device__ void manager_loop(const StreamDev &sd, const LayoutMem &L, unsigned c
             // waits across all codes (serving) or for other blocks' trials.
             if (!any_slot) break;
         }
-        // Passes that find nothing back off, up to 1 us (a finished slot then
-        // waits that long at most for its write-out); any progress resets it.
+        // A run of passes that find nothing backs off, up to 1 us (a finished
+        // slot then waits that long at most for its write-out); any progress
+        // resets it.
         if (progress) {
             idle_ns = 32;
+            idle_passes = 0;
         } else {
             __nanosleep(idle_ns);
-            idle_ns = idle_ns < 1024 ? 2 * idle_ns : 1024;
+            if (++idle_passes > kIdleLooks) idle_ns = idle_ns < 1024 ? 2 * idle_ns : 1024;
         }
     }
     // Flush counters and release the teams.
@@ -1729,17 +1737,7 @@ __global__ void __launch_bounds__(512, MINB) bpsf_persistent(const __grid_consta
             continue;
         }
         waiting = false;
-        // The block's copy of the stream's descriptor (shared memory): the
-        // parameters are indexed by a run-time stream number, and such loads
-        // from the parameter space are slow.
-        StreamDev *sdc = reinterpret_cast<StreamDev *>(smem + 64);
-        if (sid != cur) {
-            const int *src = reinterpret_cast<const int *>(&kp.streams[sid]);
-            int *dst = reinterpret_cast<int *>(sdc);
-            for (int k = tid; k < (int)(sizeof(StreamDev) / 4); k += blockDim.x) dst[k] = src[k];
-            __syncthreads();
-        }
-        const StreamDev &sd = *sdc;
+        const StreamDev &sd = kp.streams[sid];
         const CodeDev &cd = sd.code;
         const int S = sd.S, W = sd.W, teams = sd.teams;
         const LayoutOffsets lo = layout_offsets(cd.M, cd.N, DVS, cd.P);
