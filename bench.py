@@ -28,8 +28,9 @@ sys.path.insert(0, ROOT)
 
 P_LIST = (0.02, 0.04, 0.06, 0.08)
 SHOTS_PER_P = 1_000_000
-# ncu, one launch of 4 x 200k shots: 109.2 MB read + 76.1 MB written.
-DRAM_BYTES_PER_SHOT = 185.3e6 / 800_000
+# ncu, one launch of 4 x 400k shots (failed-shot records in failure order):
+# 23.96 MB read + 28.63 MB written.
+DRAM_BYTES_PER_SHOT = 52.59e6 / 1_600_000
 CODE = "bb144"
 N_BITS, M_CHECKS, NNZ = 144, 72, 432
 PARAMS = dict(max_iter=100, alpha=0.625, w=6, w_max=0, short_iter=20, select=0)
@@ -410,7 +411,7 @@ def run_gpu(args, rank, world, pool):
 
     if rank == 0:
         # DRAM bytes per launch of the persistent kernel: ncu's dram__bytes_read + write of one
-        # 800k-shot launch of this kernel over the same p mix, scaled by shots (the traffic is
+        # 1.6M-shot launch of this kernel over the same p mix, scaled by shots (the traffic is
         # the shots' I/O and the failed shots' records).
         traffic = args.traffic_bytes if args.traffic_bytes > 0 else DRAM_BYTES_PER_SHOT * shots_step
         line = {

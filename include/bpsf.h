@@ -136,8 +136,10 @@ void bpsf_destroy(bpsf_ctx *ctx);
  *   d_stage      n_shots bytes (nullable): 0 initial run converged, 1 a
  *                trial converged, 2 failure (the initial run's e is returned).
  * Results depend only on the inputs (not on timing or launch shape).  The
- * first call with a larger n_shots than before allocates device workspace,
- * so capture such calls in a CUDA graph only after a warm-up call.
+ * workspace holds one record per failed shot, in failure order (a power of
+ * two >= n_shots records, about 100 bytes each for [[144,12,12]] at w = 6);
+ * a call with a larger n_shots than before grows it, so capture such calls
+ * in a CUDA graph only after a warm-up call.
  */
 bpsf_status bpsf_decode(bpsf_ctx *ctx, int64_t n_shots, const uint32_t *d_synd, int32_t synd_stride_words,
                         uint32_t *d_corr, int32_t corr_stride_words, uint8_t *d_converged, int16_t *d_iters,
@@ -203,10 +205,13 @@ bpsf_status bpsf_decode_multi_host(int32_t n_jobs, const bpsf_job *jobs, void *s
  * allocator, or a runtime whose own allocator owns the whole device heap).
  * It runs the same kernel as bpsf_decode with the same
  * arguments and results, but the kernel's scratch (launch counters and the
- * records of failed shots) lives in one static 32 MiB device array that
- * every GPU loading this library holds until the process exits.
- *   - At most bpsf_noalloc_max_shots(ctx) shots per call (this depends on the
- *     code and on w); larger batches get BPSF_EINVAL and nothing runs.
+ * ring of records of failed shots in flight) lives in one static 32 MiB
+ * device array that every GPU loading this library holds until the process
+ * exits.
+ *   - At most bpsf_noalloc_max_shots(ctx) shots per call (the records the
+ *     array holds for this code: 262144 for [[144,12,12]] at w = 6, 32768 for
+ *     its 12-round phenomenological code); larger batches get BPSF_EINVAL and
+ *     nothing runs.
  *   - The first call on a device looks up the array's device address
  *     (cudaGetSymbolAddress) with that device current; make that first call
  *     before any stream capture.
@@ -224,7 +229,8 @@ bpsf_status bpsf_decode_noalloc(bpsf_ctx *ctx, int64_t n_shots, const uint32_t *
                                 uint32_t *d_corr, int32_t corr_stride_words, uint8_t *d_converged, int16_t *d_iters,
                                 uint8_t *d_stage, void *stream);
 
-/* Largest n_shots bpsf_decode_noalloc accepts for this context (-1 for NULL). */
+/* Largest n_shots bpsf_decode_noalloc accepts for this context (-1 for NULL,
+ * 0 if not even one record of this code fits the static array). */
 int64_t bpsf_noalloc_max_shots(const bpsf_ctx *ctx);
 
 /* Wait for `stream` and report device-side errors of ctx's last launches

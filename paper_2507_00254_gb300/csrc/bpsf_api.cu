@@ -677,8 +677,8 @@ extern "C" bpsf_status bpsf_create(bpsf_ctx **out, int32_t M, int32_t N, int64_t
 // ---------------------------------------------------------------------------
 
 bpsf_status bpsf_ensure_workspace(bpsf_ctx *c, long long n) {
-    if (n <= c->rec_cap) return BPSF_OK;
-    const long long cap = std::max<long long>(n, 1);
+    const long long cap = bpsf_record_ring(std::max<long long>(n, 1));
+    if (cap <= c->rec_cap) return BPSF_OK;
     const size_t total = bpsf_records_bytes(cap, c->p.w, c->Ws, c->Wn, 16);
     free_workspace(c);
     void *mem = nullptr;
@@ -690,9 +690,9 @@ bpsf_status bpsf_ensure_workspace(bpsf_ctx *c, long long n) {
     return BPSF_OK;
 }
 
-// Queue entries must read "not written" before a launch.
-static bpsf_status clear_queue(bpsf_ctx *c, long long n, cudaStream_t s) {
-    cudaError_t e = cudaMemsetAsync(c->rec.qseq, 0, 8 * (size_t)std::max<long long>(n, 1), s);
+// Every record of the ring reads free before a launch.
+static bpsf_status clear_queue(bpsf_ctx *c, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(c->rec.qseq, 0, 8 * (size_t)c->rec.cap, s);
     if (e != cudaSuccess) return bpsf_fail(BPSF_ECUDA, "cudaMemsetAsync: %s", cudaGetErrorString(e));
     return BPSF_OK;
 }
@@ -749,7 +749,7 @@ static bpsf_status decode_impl(bpsf_ctx *c, int64_t n, const uint32_t *synd, int
     cudaStream_t s = (cudaStream_t)stream;
     cudaError_t e = cudaMemsetAsync(c->d_ctr, 0, sizeof(StreamCounters), s);
     if (e != cudaSuccess) return bpsf_fail(BPSF_ECUDA, "cudaMemsetAsync: %s", cudaGetErrorString(e));
-    st = clear_queue(c, n, s);
+    st = clear_queue(c, s);
     if (st != BPSF_OK) return st;
     JobDev job{synd, corr, conv, iters, stage, n, ss, cs};
     StreamDev sd = bpsf_make_stream(c, job, dbg, 0);
@@ -1069,7 +1069,7 @@ extern "C" bpsf_status bpsf_decode_multi(int32_t n_jobs, const bpsf_job *jobs, v
         if (st != BPSF_OK) return st;
         cudaError_t e = cudaMemsetAsync(c->d_ctr, 0, sizeof(StreamCounters), s);
         if (e != cudaSuccess) return bpsf_fail(BPSF_ECUDA, "cudaMemsetAsync: %s", cudaGetErrorString(e));
-        st = clear_queue(c, j.n_shots, s);
+        st = clear_queue(c, s);
         if (st != BPSF_OK) return st;
         JobDev job{j.d_synd, j.d_corr, j.d_converged, j.d_iters, j.d_stage, j.n_shots, j.synd_stride_words,
                    j.corr_stride_words};

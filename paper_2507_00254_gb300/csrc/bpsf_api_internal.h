@@ -57,7 +57,15 @@ struct bpsf_plan {
 
 bpsf_status bpsf_fail(bpsf_status s, const char *fmt, ...);
 
-// Failed-shot records of `rows` rows in one block of memory, each array
+// Records for n shots: the smallest power of two >= n (a batch has at most n
+// failed shots, a server at most its admitted shots in flight).
+inline long long bpsf_record_ring(long long n) {
+    long long r = 1;
+    while (r < n) r <<= 1;
+    return r;
+}
+
+// A ring of `rows` failed-shot records in one block of memory, each array
 // aligned to `al` bytes: bytes needed, and the arrays carved from `base`.
 inline size_t bpsf_records_bytes(long long rows, int w, int Ws, int Wn, size_t al) {
     const size_t r = (size_t)(rows > 0 ? rows : 1), ww = (size_t)(w > 0 ? w : 1);

@@ -86,9 +86,16 @@ struct StreamCounters {
 };
 static_assert(sizeof(StreamCounters) == 128, "counter block is two 64-byte lines");
 
-// Failed-shot records.  A record lives at the shot's row (its index in the
-// job, or its arena row when serving); the publication queue lists failed
-// shots in the order they failed, and trial tickets walk that queue.
+// Failed-shot records: a ring of `cap` records (a power of two) in failure
+// order.  The team whose initial run fails claims the next failure number q
+// (rec_count), checks that record q % cap is free, writes Phi, the syndrome,
+// an empty selection and the shot's provisional output, and then publishes
+// it (qseq = q + 1); trial tickets walk the failure numbers, and the last
+// trial of a shot frees its record (qseq = 0).  A batch's ring has at least
+// as many records as the batch has shots, so it never wraps within a launch
+// and the records are written densely in failure order; a server's ring has
+// at least its admitted shots (so it wraps only over freed records).  A
+// record found busy is waited for (bounded) and reported (kDevRecordOverflow).
 //
 // Only the winning trial's correction is kept.  A converged trial's
 // selection key (kSelKeyBits bits: weight << 12 | list index, or the list
@@ -98,15 +105,16 @@ static_assert(sizeof(StreamCounters) == 128, "counter block is two 64-byte lines
 // minimum is then the smallest key's own word, whatever order the trials
 // finish in, with no lock.
 struct Records {
-    unsigned long long *qseq;   // cap, (queue index + 1) once the entry is written
-    long long *qshot;           // cap, shot of the queue entry
-    unsigned int *done;         // rows, trials finished
-    unsigned long long *best;   // rows, min over converged trials of key << 32 | iterations
-    unsigned long long *win;    // rows x Wn, min over converged trials of key << 32 | correction word
-    int32_t *phi;               // rows x w
-    uint32_t *synd;             // rows x Ws, the shot's syndrome
-    long long cap;              // queue entries (= rows)
+    unsigned long long *qseq;   // cap: q + 1 while the record holds failure q, 0 when free
+    long long *qshot;           // cap: the failed shot
+    unsigned int *done;         // cap: its trials finished
+    unsigned long long *best;   // cap: min over converged trials of key << 32 | iterations
+    unsigned long long *win;    // cap x Wn: min over converged trials of key << 32 | correction word
+    int32_t *phi;               // cap x w
+    uint32_t *synd;             // cap x Ws: the shot's syndrome
+    long long cap;              // records in the ring (a power of two)
 };
+
 constexpr int kSelKeyBits = 28;  // weight (16 bits, N <= 65535) above a 12-bit list index (n_trials <= 4096)
 
 struct JobDev {
@@ -200,7 +208,7 @@ struct SlotState {
     int iter;        // iterations completed
     int limit;       // iteration cap of this run
     int kidx;        // trial index (trial runs)
-    int pad;
+    int rec;         // record of the shot (trial runs)
     long long shot;  // shot index in the job (global sequence number when serving)
     long long cancel;  // manager -> team: shot * n_trials + kidx + 1 of a trial run that cannot win
 };
@@ -219,7 +227,7 @@ struct OutBox {
     int kidx;
     int outcome;
     int iter;
-    int pad;
+    int rec;  // record of the shot (trial runs)
     long long shot;
 };
 static_assert(sizeof(OutBox) == 32, "outbox is 32 bytes");
@@ -246,8 +254,9 @@ static_assert(sizeof(TeamCtl) <= 64, "team control block fits its 64 bytes");
 // bytes of fields plus Ws syndrome words (a trial's words are s' = s xor t H^T).  kind 1 = initial run of a shot,
 // 2 = trial run, 0 = nothing to run (an item dropped after a timed-out wait).
 struct QEntry {
-    int kind;
-    int kidx;
+    int16_t kind;
+    int16_t kidx;  // < 4096
+    int rec;       // record of the shot (trial runs)
     long long shot;
 };
 static_assert(sizeof(QEntry) == 16, "queue entry header is 16 bytes");

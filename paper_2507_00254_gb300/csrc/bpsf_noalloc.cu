@@ -8,6 +8,7 @@
 // every GPU that loads the library holds until the process exits.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstring>
 #include <mutex>
 
@@ -45,35 +46,33 @@ bpsf_status noalloc_scratch(int device, unsigned char **out) {
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
-// Bytes of scratch a batch of n shots needs for this code (counters first).
-size_t noalloc_bytes(const bpsf_ctx *c, long long n) {
-    return align256(sizeof(StreamCounters)) + bpsf_records_bytes(n, c->p.w, c->Ws, c->Wn, 256);
+// Bytes of scratch for a ring of `ring` failed-shot records (counters first).
+size_t noalloc_bytes(const bpsf_ctx *c, long long ring) {
+    return align256(sizeof(StreamCounters)) + bpsf_records_bytes(ring, c->p.w, c->Ws, c->Wn, 256);
+}
+
+// The largest record ring (a power of two) that fits the static scratch for
+// this code; 0 if not even one record fits.  Every record is at least 44
+// bytes, so the search starts below 2^20 and no product can wrap.
+long long noalloc_ring(const bpsf_ctx *c) {
+    long long r = 1ll << 20;
+    while (r >= 1 && noalloc_bytes(c, r) > kNoallocScratchBytes) r >>= 1;
+    return r;
 }
 
 }  // namespace
 
+// A batch of n shots needs a ring of at least n records.
 extern "C" int64_t bpsf_noalloc_max_shots(const bpsf_ctx *c) {
     if (!c) return -1;
-    // Every shot takes at least 44 bytes of records, so the answer is below
-    // 2^20 and the doubling stops long before any product could wrap.
-    long long lo = 0, hi = 1;
-    while (noalloc_bytes(c, hi) <= kNoallocScratchBytes) hi *= 2;
-    while (hi - lo > 1) {
-        const long long mid = (lo + hi) / 2;
-        if (noalloc_bytes(c, mid) <= kNoallocScratchBytes)
-            lo = mid;
-        else
-            hi = mid;
-    }
-    return lo;
+    return noalloc_ring(c);
 }
 
 extern "C" bpsf_status bpsf_decode_noalloc(bpsf_ctx *c, int64_t n, const uint32_t *synd, int32_t ss, uint32_t *corr,
                                            int32_t cs, uint8_t *conv, int16_t *iters, uint8_t *stage, void *stream) {
     if (!c) return bpsf_fail(BPSF_EINVAL, "ctx is NULL");
     if (n < 0) return bpsf_fail(BPSF_EINVAL, "n_shots must be >= 0");
-    // The bound comes first: the size arithmetic below is only done for
-    // batches known to fit, so no product can wrap.
+    // The bound comes first (no size arithmetic depends on n beyond it).
     const long long max_n = bpsf_noalloc_max_shots(c);
     if (n > max_n)
         return bpsf_fail(BPSF_EINVAL,
@@ -94,16 +93,16 @@ extern "C" bpsf_status bpsf_decode_noalloc(bpsf_ctx *c, int64_t n, const uint32_
     bpsf_ctx *cs1[1] = {c};
     st = bpsf_make_plan(cs1, 1, &c->tune, false, &pl);
     if (st != BPSF_OK) return st;
-    // Carve the counters and the records out of the array.
-    const size_t cap = (size_t)n;
+    // Carve the counters and the record ring out of the array.
+    const long long ring = bpsf_record_ring(n);
     StreamCounters *ctr = reinterpret_cast<StreamCounters *>(base);
-    Records rec = bpsf_records_carve(base + align256(sizeof(StreamCounters)), n, c->p.w, c->Ws, c->Wn, 256);
-    // The array keeps the previous call's contents: the counters and the
-    // publication queue must start at zero.  Every other record field is
-    // written before it is read.
+    Records rec = bpsf_records_carve(base + align256(sizeof(StreamCounters)), ring, c->p.w, c->Ws, c->Wn, 256);
+    // The array keeps the previous call's contents: the counters must start
+    // at zero and every record free.  Every other record field is written
+    // before it is read.
     cudaStream_t s = (cudaStream_t)stream;
     e = cudaMemsetAsync(ctr, 0, sizeof(StreamCounters), s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(rec.qseq, 0, 8 * cap, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(rec.qseq, 0, 8 * (size_t)ring, s);
     if (e != cudaSuccess) return bpsf_fail(BPSF_ECUDA, "cudaMemsetAsync: %s", cudaGetErrorString(e));
     JobDev job{synd, corr, conv, iters, stage, n, ss, cs};
     StreamDev sd = bpsf_make_stream(c, job, nullptr, 0);

@@ -33,18 +33,20 @@
 // the C and V phases are replaced by layer-by-layer row updates against a
 // running posterior (vector lanes for six-wide rows, else one slot per lane).
 //
-// Service (the team's warp 0, at the top of each iteration): a finished
-// slot packs its decision into words, its run's facts into its outbox and,
-// for a failed initial run, Phi = top(flip_count, w) into the shot's record;
-// then it installs the item the manager staged in its inbox and runs again
-// at once.
+// Service (the team's warp 0, after an iteration in which a slot finished or
+// while a slot is empty): a finished slot packs its decision into words and
+// its run's facts into its outbox; a failed initial run also fills a record
+// of the failure ring (Phi = top(flip_count, w), the syndrome, the shot's
+// provisional output) and publishes its trials; then the slot installs the
+// item the manager staged in its inbox and runs again at once.
 //
 // The manager warp does the rest of the global-memory work: it writes the
-// outboxes out, publishes failed shots' trials, resolves the winner of each
-// failed shot (minimum over converged trials of (weight, index), held in a
-// per-shot atomicMin), claims new shots and trial tickets ahead of time into
-// a small ready queue and fills the inboxes from it.  Compute warps never
-// wait on HBM.
+// outboxes out, resolves the winner of each failed shot (minimum over
+// converged trials of (weight, index), merged into the shot's record by
+// atomicMin), claims new shots and trial tickets ahead of time into a small
+// ready queue and fills the inboxes from it.  Compute warps touch global
+// memory only when a run fails (its record) or changes a decision (the
+// column's check list, in L1).
 #pragma once
 #include <cuda_runtime.h>
 
@@ -816,12 +818,16 @@ __device__ __forceinline__ void layered_iteration_vec(const StreamDev &sd, const
 // without a round trip through the manager.
 // ---------------------------------------------------------------------------
 
-// Pack finished slot s into its outbox: the hard decision into words, the
-// run's facts, and for a failed initial run Phi = top(flip_count, w) (keys
-// (count << 16 | 0xffff - i) are distinct, so each round takes the largest
-// key below the previous one: count descending, index ascending).
+// Pack finished slot s into its outbox: the hard decision into words and the
+// run's facts.  A failed initial run (with trials) also gets its record
+// here: Phi = top(flip_count, w) (keys (count << 16 | 0xffff - i) are
+// distinct, so each round takes the largest key below the previous one:
+// count descending, index ascending), the shot's syndrome, an empty
+// selection and the provisional output (the initial run's e, not
+// converged), and only then is the record published for the trials.
 template <bool DEBUG, int FB>
-__device__ __forceinline__ void team_pack(const StreamDev &sd, const TeamMem &T, int lgS, int s, int lane) {
+__device__ __forceinline__ void team_pack(const StreamDev &sd, const TeamMem &T, int lgS, int s, int lane,
+                                          unsigned long long wait_ns) {
     const CodeDev &cd = sd.code;
     const int N = cd.N, Wn = cd.Wn;
     const SlotState *ss = &T.st[s];
@@ -834,10 +840,11 @@ __device__ __forceinline__ void team_pack(const StreamDev &sd, const TeamMem &T,
     }
     const int kind = ss->kind, outcome = ss->outcome;
     if (kind == 1 && outcome == 2 && cd.w > 0) {
-        // Phi goes straight to the shot's record (up to 64 entries); the
-        // manager publishes the record after this outbox, and the fence
-        // below orders these stores before the outbox flag.
-        const long long row = (sd.flags & kServe) ? (ss->shot % sd.serve.rows) : ss->shot;
+        const JobDev &job = sd.job;
+        const long long shot = ss->shot;
+        const long long row = (sd.flags & kServe) ? (shot % sd.serve.rows) : shot;
+        // Phi into lane registers: lane r % 32 holds Phi[r] (r < 32 in phi0, else phi1).
+        int phi0 = -1, phi1 = -1;
         unsigned thr = 0xffffffffu;
         for (int r = 0; r < cd.w; ++r) {
             unsigned best = 0;
@@ -848,13 +855,61 @@ __device__ __forceinline__ void team_pack(const StreamDev &sd, const TeamMem &T,
             }
             best = __reduce_max_sync(FULLMASK, best);
             const int phi_r = (int)(0xffffu - (best & 0xffffu));
-            if (lane == 0) {
-                sd.rec.phi[row * cd.w + r] = phi_r;
-                if (DEBUG && sd.dbg.phi) sd.dbg.phi[ss->shot * cd.w + r] = phi_r;
+            if (lane == (r & 31)) {
+                if (r < 32)
+                    phi0 = phi_r;
+                else
+                    phi1 = phi_r;
             }
+            if (DEBUG && lane == 0 && sd.dbg.phi) sd.dbg.phi[shot * cd.w + r] = phi_r;
             thr = best;
         }
+        // The next failure number and its record, once free (a bounded wait;
+        // more failed shots in flight than records is reported).
+        unsigned long long q = 0;
+        if (lane == 0) {
+            q = atomicAdd(&sd.ctr->rec_count, 1ull);
+            const unsigned long long *qs = sd.rec.qseq + (q & (unsigned long long)(sd.rec.cap - 1));
+            if (ld_acquire_u64(qs) != 0ull) {
+                const unsigned long long t0 = globaltimer_ns();
+                while (ld_acquire_u64(qs) != 0ull) {
+                    if (globaltimer_ns() - t0 > wait_ns) {
+                        atomicOr(&sd.ctr->status, kDevRecordOverflow);
+                        break;
+                    }
+                    __nanosleep(256);
+                }
+            }
+        }
+        q = __shfl_sync(FULLMASK, q, 0);
+        const long long rs = (long long)(q & (unsigned long long)(sd.rec.cap - 1));
+        if (lane < cd.w) sd.rec.phi[rs * cd.w + lane] = phi0;
+        if (lane + 32 < cd.w) sd.rec.phi[rs * cd.w + lane + 32] = phi1;
+        // The slot's syndrome (check j sits at bit j*S + s of the team's words).
+        for (int w = 0; w < cd.Ws; ++w) {
+            const int j = 32 * w + lane;
+            const int b = (j << lgS) + s;
+            const unsigned bit = j < cd.M ? (T.syn[b >> 5] >> (b & 31)) & 1u : 0u;
+            const unsigned word = __ballot_sync(FULLMASK, bit != 0u);
+            if (lane == 0) sd.rec.synd[rs * cd.Ws + w] = word;
+        }
+        __syncwarp();  // lane 0's decision words are visible to the warp
+        uint32_t *out = job.corr + row * job.corr_stride;
+        for (int w = lane; w < Wn; w += 32) {
+            sd.rec.win[rs * Wn + w] = ~0ull;
+            out[w] = T.ebits[s * Wn + w];
+        }
+        if (lane == 0) {
+            job.conv[row] = 0;
+            job.iters[row] = (int16_t)cd.max_iter;
+            if (job.stage) job.stage[row] = 2;
+            sd.rec.done[rs] = 0u;
+            sd.rec.best[rs] = ~0ull;
+            sd.rec.qshot[rs] = shot;
+        }
         __threadfence();
+        __syncwarp();
+        if (lane == 0) st_release_u64(sd.rec.qseq + rs, q + 1ull);
     }
     if (DEBUG && kind == 1 && sd.dbg.flips)
         for (int i = lane; i < N; i += 32)
@@ -862,6 +917,7 @@ __device__ __forceinline__ void team_pack(const StreamDev &sd, const TeamMem &T,
     if (lane == 0) {
         ob->kind = kind;
         ob->kidx = ss->kidx;
+        ob->rec = ss->rec;
         ob->outcome = outcome;
         ob->iter = ss->iter;
         ob->shot = ss->shot;
@@ -904,6 +960,7 @@ __device__ __forceinline__ void team_install(const StreamDev &sd, const LayoutMe
     if (lane == 0) {
         ss->kind = e->kind;
         ss->kidx = e->kidx;
+        ss->rec = e->rec;
         ss->shot = e->shot;
         ss->iter = 0;
         ss->start = -1;  // set by the team at the service that starts the run
@@ -916,7 +973,7 @@ __device__ __forceinline__ void team_install(const StreamDev &sd, const LayoutMe
 
 template <bool DEBUG, int FB>
 __device__ __forceinline__ void team_service(const StreamDev &sd, const LayoutMem &L, const TeamMem &T, int S, int lgS,
-                                             int lane) {
+                                             int lane, unsigned long long wait_ns) {
     const int stv = lane < S ? *vstate(&T.st[lane]) : kSlotRunning;
     const bool obf = lane < S && *vflag(&T.ob[lane].full) != 0;
     unsigned pm = __ballot_sync(FULLMASK, stv == kSlotPending && !obf);
@@ -924,7 +981,7 @@ __device__ __forceinline__ void team_service(const StreamDev &sd, const LayoutMe
     while (pm) {
         const int s = __ffs(pm) - 1;
         pm &= pm - 1u;
-        team_pack<DEBUG, FB>(sd, T, lgS, s, lane);
+        team_pack<DEBUG, FB>(sd, T, lgS, s, lane, wait_ns);
         // team_pack set the outbox flag before the slot reads EMPTY (the
         // manager's exit test reads the state first, then the outbox flag).
         if (lane == 0) {
@@ -1022,7 +1079,7 @@ __device__ void team_loop(const StreamDev &sd, const LayoutMem &L, const TeamMem
                     n_iters = 0;
                     tt_flush = tt;
                 }
-                team_service<DEBUG, FB>(sd, L, T, S, lgS, lane);
+                team_service<DEBUG, FB>(sd, L, T, S, lgS, lane, wait_ns);
                 SlotState *ss = &T.st[lane < S ? lane : 0];
                 const int stv = lane < S ? *vstate(ss) : kSlotEmpty;
                 const bool r = stv == kSlotRunning;
@@ -1207,34 +1264,37 @@ __device__ __forceinline__ void shot_complete(const StreamDev &sd, long long row
 // One trial of a failed shot is over (run, or cancelled because it cannot
 // win): count it; the last one settles the winner (the minimum key of the
 // shot's converged trials) and completes the shot.
-__device__ __forceinline__ void trial_done(const StreamDev &sd, long long row, long long shot) {
+__device__ __forceinline__ void trial_done(const StreamDev &sd, long long rs, long long row, long long shot) {
     const CodeDev &cd = sd.code;
     const JobDev &job = sd.job;
     const int C = cd.n_trials, Wn = cd.Wn;
     __threadfence();
-    const unsigned d = atomicAdd(&sd.rec.done[row], 1u) + 1u;
+    const unsigned d = atomicAdd(&sd.rec.done[rs], 1u) + 1u;
     if (d == (unsigned)C) {
         __threadfence();
-        const unsigned long long best = atomicAdd(&sd.rec.best[row], 0ull);
+        const unsigned long long best = atomicAdd(&sd.rec.best[rs], 0ull);
         if (best != ~0ull) {
             // Every converged trial merged its words before it counted itself
             // done, so each word now holds the winner's (smallest key's) word.
             uint32_t *out = job.corr + row * job.corr_stride;
-            const unsigned long long *src = sd.rec.win + row * Wn;
+            const unsigned long long *src = sd.rec.win + rs * Wn;
             for (int w = 0; w < Wn; ++w) out[w] = (uint32_t)(__ldcg(src + w) & 0xffffffffull);
             job.conv[row] = 1;
             job.iters[row] = (int16_t)(best & 0xffffull);
             if (job.stage) job.stage[row] = 1;
         }
+        // The record is free for a later failure once its reads are done.
+        __threadfence();
+        st_release_u64(sd.rec.qseq + rs, 0ull);
         shot_complete(sd, row, shot);
     }
 }
 
 // Under the first-success rule (select = 1) the winner is the earliest
 // converged trial: once trial k* has converged, no later trial can win.
-__device__ __forceinline__ bool trial_cannot_win(const StreamDev &sd, long long row, int kidx) {
+__device__ __forceinline__ bool trial_cannot_win(const StreamDev &sd, long long rs, int kidx) {
     if (sd.code.select != 1) return false;
-    const unsigned long long best = __ldcg(sd.rec.best + row);
+    const unsigned long long best = __ldcg(sd.rec.best + rs);
     return best != ~0ull && (long long)(best >> 32) < (long long)kidx;
 }
 
@@ -1251,17 +1311,21 @@ __device__ __forceinline__ void finalize_simple(const StreamDev &sd, TeamMem T, 
     const long long row = row_of(sd, shot);
     const int Wn = cd.Wn;
     if (kind == 1) {
+        mg.init_local += 1;
+        // A failed run with trials already has its record and provisional
+        // output (written by its team before it published the trials).
+        if (!conv && cd.w > 0) return;
         uint32_t *out = job.corr + row * job.corr_stride;
         for (int w = 0; w < Wn; ++w) out[w] = slot_word(T.ebits, Wn, s, w);
         job.conv[row] = conv ? 1 : 0;
         job.iters[row] = (int16_t)(conv ? iter : cd.max_iter);
         if (job.stage) job.stage[row] = conv ? 0 : 2;
-        mg.init_local += 1;
         shot_complete(sd, row, shot);
         return;
     }
     // Trial run: undo the flip (Algorithm 1) and take part in the selection.
     const int C = cd.n_trials, kidx = ss->kidx;
+    const long long rs = ss->rec;
     if (conv) {
         // e' xor t, in the slot's packed decision (the outbox is this lane's
         // until it is released): t flips the record's Phi[j] for the bits j
@@ -1270,7 +1334,7 @@ __device__ __forceinline__ void finalize_simple(const StreamDev &sd, TeamMem T, 
         const unsigned long long mask = __ldg(cd.trial_mask + kidx);
         for (int j = 0; j < cd.w; ++j) {
             if (!((mask >> j) & 1ull)) continue;
-            const int b = __ldcg(sd.rec.phi + row * cd.w + j);
+            const int b = __ldcg(sd.rec.phi + rs * cd.w + j);
             ew[b >> 5] ^= 1u << (b & 31);
         }
         unsigned wsum = 0;
@@ -1279,11 +1343,11 @@ __device__ __forceinline__ void finalize_simple(const StreamDev &sd, TeamMem T, 
         // list index alone under the first-success rule.
         const unsigned long long key = cd.select == 0 ? (((unsigned long long)wsum << 12) | (unsigned)kidx)
                                                       : (unsigned long long)kidx;
-        const unsigned long long old = atomicMin(&sd.rec.best[row], (key << 32) | (unsigned)iter);
+        const unsigned long long old = atomicMin(&sd.rec.best[rs], (key << 32) | (unsigned)iter);
         // Only a trial that held the smallest key so far merges its words: the
         // final winner always does, and merges of others cannot beat it.
         if ((old >> 32) > key) {
-            unsigned long long *win = sd.rec.win + row * Wn;
+            unsigned long long *win = sd.rec.win + rs * Wn;
             for (int w = 0; w < Wn; ++w) atomicMin(win + w, (key << 32) | ew[w]);
         }
     }
@@ -1295,42 +1359,7 @@ __device__ __forceinline__ void finalize_simple(const StreamDev &sd, TeamMem T, 
         mg.trials_cancelled += 1;  // stopped: it could not win
     else
         mg.trials_local += 1;
-    trial_done(sd, row, shot);
-}
-
-// Failed initial run with trials (whole manager warp): provisional output,
-// record (its Phi written by the team, the shot's syndrome copied from its
-// input row) and publication of its trials.
-template <bool DEBUG>
-__device__ __forceinline__ void finalize_failed(const StreamDev &sd, TeamMem T, int s, int lane, MgrState &mg) {
-    const CodeDev &cd = sd.code;
-    const JobDev &job = sd.job;
-    const OutBox *ob = &T.ob[s];
-    const long long shot = ob->shot;
-    const long long row = row_of(sd, shot);
-    const int Wn = cd.Wn, Ws = cd.Ws;
-    uint32_t *out = job.corr + row * job.corr_stride;
-    for (int w = lane; w < Wn; w += 32) out[w] = slot_word(T.ebits, Wn, s, w);
-    if (lane == 0) {
-        job.conv[row] = 0;
-        job.iters[row] = (int16_t)cd.max_iter;
-        if (job.stage) job.stage[row] = 2;
-        sd.rec.done[row] = 0u;
-        sd.rec.best[row] = ~0ull;
-    }
-    for (int w = lane; w < Wn; w += 32) sd.rec.win[row * Wn + w] = ~0ull;
-    const uint32_t *syn = job.synd + row * job.synd_stride;
-    for (int w = lane; w < Ws; w += 32) sd.rec.synd[row * Ws + w] = __ldcg(syn + w);
-    __threadfence();
-    __syncwarp();
-    if (lane == 0) {
-        const unsigned long long q = atomicAdd(&sd.ctr->rec_count, 1ull);
-        const long long qi = (long long)(q % (unsigned long long)sd.rec.cap);
-        sd.rec.qshot[qi] = shot;
-        st_release_u64(sd.rec.qseq + qi, q + 1ull);
-        mg.init_local += 1;
-    }
-    __syncwarp();
+    trial_done(sd, rs, row, shot);
 }
 
 // Shots that may be claimed now.
@@ -1390,25 +1419,21 @@ __device__ __forceinline__ bool prefetch(const StreamDev &sd, unsigned char *qba
                 }
             }
             QEntry *e = qentry(qbase, (mg.tail + lane) % Q, qstride);
+            if (ok && trial_cannot_win(sd, slot_q, kidx)) ok = false;  // early cancel: counted, not run
             if (ok) {
                 const long long shot = __ldcg(sd.rec.qshot + slot_q);
-                const long long row = row_of(sd, shot);
-                if (trial_cannot_win(sd, row, kidx)) ok = false;  // early cancel: counted, not run
-            }
-            if (ok) {
-                const long long shot = __ldcg(sd.rec.qshot + slot_q);
-                const long long row = row_of(sd, shot);
                 e->kind = 2;
-                e->kidx = kidx;
+                e->kidx = (int16_t)kidx;
+                e->rec = (int)slot_q;
                 e->shot = shot;
                 // The trial vector t: the bits Phi[j] its mask selects.
                 const unsigned long long mask = __ldg(cd.trial_mask + kidx);
                 uint32_t *sy = qsyn(e);
-                for (int w = 0; w < Ws; ++w) sy[w] = __ldcg(sd.rec.synd + row * Ws + w);
+                for (int w = 0; w < Ws; ++w) sy[w] = __ldcg(sd.rec.synd + slot_q * Ws + w);
                 // s' = s xor t H^T (Algorithm 1): flip the checks of every selected bit.
                 for (int j = 0; j < cd.w; ++j) {
                     if (!((mask >> j) & 1ull)) continue;
-                    const int v = __ldcg(sd.rec.phi + row * cd.w + j);
+                    const int v = __ldcg(sd.rec.phi + slot_q * cd.w + j);
                     for (int k = 0; k < cd.vstride; ++k) {
                         const int c = __ldg(cd.vchk + v * cd.vstride + k);
                         if (c == 0xffff) break;
@@ -1423,7 +1448,7 @@ __device__ __forceinline__ bool prefetch(const StreamDev &sd, unsigned char *qba
                 // timed-out wait the record never settles and the status reports it.
                 if (!timed_out) {
                     const long long shot = __ldcg(sd.rec.qshot + slot_q);
-                    trial_done(sd, row_of(sd, shot), shot);
+                    trial_done(sd, slot_q, row_of(sd, shot), shot);
                     ++mg.trials_cancelled;
                 }
                 e->kind = 0;
@@ -1470,6 +1495,7 @@ __device__ __forceinline__ bool prefetch(const StreamDev &sd, unsigned char *qba
             QEntry *e = qentry(qbase, (mg.tail + lane) % Q, qstride);
             e->kind = 1;
             e->kidx = 0;
+            e->rec = -1;
             e->shot = shot;
             const uint32_t *src = sd.job.synd + row * sd.job.synd_stride;
             uint32_t *sy = qsyn(e);
@@ -1506,25 +1532,16 @@ __device__ void manager_loop(const StreamDev &sd, const LayoutMem &L, unsigned c
             const int stv = inr ? *vstate(&T.st[s]) : kSlotEmpty;
             const bool fin = inr && *vflag(&T.ob[s].full) != 0;
             __threadfence_block();
-            const bool coop = fin && T.ob[s].kind == 1 && T.ob[s].outcome == 2 && cd.w > 0;
             if (__any_sync(FULLMASK, stv != kSlotEmpty)) busy = true;
             // First-success rule: ask running trials that can no longer win to stop.
             if (cd.select == 1 && stv == kSlotRunning && T.st[s].kind == 2) {
                 const long long shot = T.st[s].shot;
                 const int kidx = T.st[s].kidx;
                 const long long key = shot * (long long)cd.n_trials + kidx + 1;
-                if (T.st[s].cancel != key && trial_cannot_win(sd, row_of(sd, shot), kidx))
+                if (T.st[s].cancel != key && trial_cannot_win(sd, T.st[s].rec, kidx))
                     *reinterpret_cast<volatile long long *>(&T.st[s].cancel) = key;
             }
-            if (fin && !coop) finalize_simple<DEBUG>(sd, T, s, mg);
-            unsigned cm = __ballot_sync(FULLMASK, coop);
-            while (cm) {
-                const int l = __ffs(cm) - 1;
-                cm &= cm - 1u;
-                const int gg = g0 + l;
-                const int tt = gg / S, s2 = gg - tt * S;
-                finalize_failed<DEBUG>(sd, team_mem(team_base + tt * team_bytes, to), s2, lane, mg);
-            }
+            if (fin) finalize_simple<DEBUG>(sd, T, s, mg);
             __syncwarp();
             if (fin) {
                 __threadfence_block();

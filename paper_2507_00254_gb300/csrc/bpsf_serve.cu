@@ -236,12 +236,13 @@ extern "C" bpsf_status bpsf_serve_start(bpsf_server **out, bpsf_ctx *const *code
         e = cudaMalloc((void **)&sc.d_ctr, sizeof(StreamCounters));
         if (e == cudaSuccess) e = cudaMemset(sc.d_ctr, 0, sizeof(StreamCounters));
         if (e != cudaSuccess) break;
-        // Records at each arena row; the publication queue is a ring of R
-        // entries (pending failed shots never outnumber admitted shots).
-        e = cudaMalloc(&sc.d_rec, bpsf_records_bytes((long long)R, x->p.w, x->Ws, x->Wn, 16));
+        // A ring of failed-shot records (failed shots in flight never
+        // outnumber admitted shots), all free.
+        const long long RR = bpsf_record_ring((long long)R);
+        e = cudaMalloc(&sc.d_rec, bpsf_records_bytes(RR, x->p.w, x->Ws, x->Wn, 16));
         if (e != cudaSuccess) break;
-        sc.rec = bpsf_records_carve(sc.d_rec, (long long)R, x->p.w, x->Ws, x->Wn, 16);
-        e = cudaMemset(sc.rec.qseq, 0, 8 * R);
+        sc.rec = bpsf_records_carve(sc.d_rec, RR, x->p.w, x->Ws, x->Wn, 16);
+        e = cudaMemset(sc.rec.qseq, 0, 8 * (size_t)RR);
         // The serving stream of this code.
         JobDev job{sc.m_synd, sc.m_corr, sc.m_conv, sc.m_iters, sc.m_stage8, 0, x->Ws, x->Wn};
         StreamDev sd = bpsf_make_stream(x, job, nullptr, kServe);
