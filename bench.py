@@ -393,6 +393,7 @@ def run_gpu(args, rank, world, pool):
 
     extras = {}
     if rank == 0 and not args.no_extras:
+        extras["long_runs_same_kernel"] = run_long_runs(B, codes, torch, tuned, peak)
         extras["phenomenological"] = run_phenom(B, codes, torch)
         extras["mixed_one_launch"] = run_mixed(B, codes, torch)
         extras["code_capacity_paper_setting"] = run_families(B, codes, torch, harness)
@@ -501,7 +502,8 @@ FAMILY_SETTINGS = (("bb72", 4), ("bb144", 7), ("cbb126", 6), ("gb254", 13), ("cb
 
 
 def run_families(B, codes, torch, harness, n=100_000, p_list=(0.04, 0.06)):
-    """Code families under the paper's code-capacity setting, batched: shots/s and LER."""
+    """Code families under the paper's code-capacity setting, batched: shots/s and LER
+    (each code's launch shape autotuned once, on a sample at the larger p)."""
     import synth
     out = {}
     for k, (name, w) in enumerate(FAMILY_SETTINGS):
@@ -512,6 +514,8 @@ def run_families(B, codes, torch, harness, n=100_000, p_list=(0.04, 0.06)):
         for j, p in enumerate(p_list):
             d = B.Decoder(c.ptr, c.idx, c.M, c.N, np.full(c.N, p),
                           B.Params(max_iter=50, alpha=0.0, w=w, w_max=1, short_iter=50))
+            if j == 0:
+                d.autotune(p_sample=p_list[-1], n_sample=1 << 15)  # per code; the cache serves the next p
             e = synth.bernoulli_bits(6100 + k, j, 0, n, c.N, p)
             synd = d.syndrome(_packed_errors_dev(torch, e, d.Wn))
             o = d.outputs(n)
@@ -534,6 +538,47 @@ def run_families(B, codes, torch, harness, n=100_000, p_list=(0.04, 0.06)):
                            "tuning": list(d.tuning)}
             d.close()
         out[name] = res
+    return out
+
+
+def run_long_runs(B, codes, torch, tuning, peak, n=100_000):
+    """The benchmark's kernel and launch shape on runs that are all max_iter long:
+    random syndromes (each bit 1/2, almost never satisfied within 100 iterations),
+    no trials, four [[144]] streams at the benchmark's priors in one launch.  Shows
+    what the BP iteration loop itself reaches against the same roofline, apart
+    from the cost of starting and ending the benchmark's short runs."""
+    import synth
+    c = codes.bb(CODE)
+    P = B.Params(max_iter=100, alpha=0.625, w=0, short_iter=1)
+    decs, synds = [], []
+    for k, p in enumerate(P_LIST):
+        d = B.Decoder(c.ptr, c.idx, c.M, c.N, np.full(c.N, p), P)
+        d.tuning = tuning
+        s = synth.bernoulli_bits(synth.SEEDS["serve"], 40 + k, 0, n, c.M, 0.5)
+        synds.append(_packed_errors_dev(torch, s, d.Ws))
+        decs.append(d)
+    stream = torch.cuda.current_stream()
+    B.decode_multi(decs, synds)  # warm-up
+    best = None
+    for _ in range(3):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        B.decode_multi(decs, synds, sync=False)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b)
+        best = ms if best is None else min(best, ms)
+    for d in decs:
+        B.bpsf_sync(d.handle, stream.cuda_stream)
+    w = [d.last_work() for d in decs]
+    eu = sum(x["edge_updates"] for x in w)
+    it = sum(x["iterations"] for x in w)
+    achieved = eu / (best / 1e3)
+    out = {"shots": n * len(P_LIST), "ms": best, "iterations_per_run": it / (n * len(P_LIST)),
+           "edge_updates_per_s": achieved, "roofline_frac": achieved / peak,
+           "slot_occupancy": it / max(1, sum(x["slot_capacity"] for x in w)), "tuning": list(tuning)}
+    for d in decs:
+        d.close()
     return out
 
 
@@ -817,7 +862,8 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="skip the served / phenomenological / mixed lines")
     ap.add_argument("--serve-seconds", type=float, default=2.0)
     ap.add_argument("--only-served", action="store_true", help="run only the served measurement (diagnostics)")
-    ap.add_argument("--only", choices=["phenom", "layered", "mixed", "families", "sampled", "first"], default=None,
+    ap.add_argument("--only", choices=["phenom", "layered", "mixed", "families", "sampled", "first", "long"],
+                    default=None,
                     help="run only one secondary measurement and print its JSON (diagnostics, profiling)")
     ap.add_argument("--serve-tuning", type=lambda x: tuple(int(v) for v in x.split(",")), default=SERVE_TUNING,
                     help="team shape W,S,B,blocks_per_sm of the served BB codes")
@@ -838,7 +884,12 @@ def main():
         fn = {"phenom": lambda: run_phenom(B, codes, torch), "layered": lambda: run_layered(B, codes, torch, harness),
               "mixed": lambda: run_mixed(B, codes, torch), "families": lambda: run_families(B, codes, torch, harness),
               "sampled": lambda: run_sampled(B, codes, torch, harness),
-              "first": lambda: run_first_success(B, codes, torch)}[args.only]
+              "first": lambda: run_first_success(B, codes, torch),
+              "long": lambda: run_long_runs(B, codes, torch, args.tuning or (1, 8, 13, 0, 1),
+                                            roofline_peak_edge_updates(torch.cuda.get_device_properties(0)
+                                                                       .multi_processor_count,
+                                                                       float(measured_peaks().get("sm_max_mhz",
+                                                                                                  2070.0))))}[args.only]
         print(json.dumps(fn()))
         return
     if args.only_served:
