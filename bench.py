@@ -582,6 +582,36 @@ def run_long_runs(B, codes, torch, tuning, peak, n=100_000):
     return out
 
 
+def run_single_slot(B, codes, torch, reps=5):
+    """One failing [[144]] shot (p = 0.05, w = 0) through the plain form: each
+    decode is one launch of one block whose single one-warp team runs the shot's
+    100 iterations on one slot, the chain that sets the served and plain forms'
+    tail latency.  Device time per decode, CUDA events."""
+    import synth
+    c = codes.bb(CODE)
+    P0 = B.Params(max_iter=100, alpha=0.625, w=0, short_iter=20)
+    d = B.Decoder(c.ptr, c.idx, c.M, c.N, np.full(c.N, 0.05), P0)
+    d.tuning = (1, 1, 1, 0)
+    e = synth.bernoulli_bits(synth.SEEDS["serve"], 4, 0, 4096, c.N, 0.05)
+    synd = d.syndrome(_packed_errors_dev(torch, e, d.Wn))
+    st = d.decode(synd)["stage"].cpu().numpy()
+    fail = np.nonzero(st != 0)[0]
+    s = synd[int(fail[0]):int(fail[0]) + 1].clone()
+    o = d.outputs(1)
+    ms = []
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        d.decode(s, out=o, plain=True)
+        b.record()
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+    out = {"iters": int(o["iters"][0]), "converged": int(o["conv"][0]), "ms_per_decode": ms,
+           "us_per_iteration_median": float(np.median(ms)) * 1e3 / max(1, int(o["iters"][0]))}
+    d.close()
+    return out
+
+
 def run_sampled(B, codes, torch, harness, n=100_000, p=0.003):
     """The paper's complexity study (Section V: |Phi| = 50, n_s trial vectors sampled per
     weight 1..w_max, 100 iterations per BP instance, adaptive damping), on the 12-round
@@ -862,7 +892,8 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="skip the served / phenomenological / mixed lines")
     ap.add_argument("--serve-seconds", type=float, default=2.0)
     ap.add_argument("--only-served", action="store_true", help="run only the served measurement (diagnostics)")
-    ap.add_argument("--only", choices=["phenom", "layered", "mixed", "families", "sampled", "first", "long"],
+    ap.add_argument("--only", choices=["phenom", "layered", "mixed", "families", "sampled", "first", "long",
+                                       "single"],
                     default=None,
                     help="run only one secondary measurement and print its JSON (diagnostics, profiling)")
     ap.add_argument("--serve-tuning", type=lambda x: tuple(int(v) for v in x.split(",")), default=SERVE_TUNING,
@@ -885,6 +916,7 @@ def main():
               "mixed": lambda: run_mixed(B, codes, torch), "families": lambda: run_families(B, codes, torch, harness),
               "sampled": lambda: run_sampled(B, codes, torch, harness),
               "first": lambda: run_first_success(B, codes, torch),
+              "single": lambda: run_single_slot(B, codes, torch),
               "long": lambda: run_long_runs(B, codes, torch, args.tuning or (1, 8, 13, 0, 1),
                                             roofline_peak_edge_updates(torch.cuda.get_device_properties(0)
                                                                        .multi_processor_count,
