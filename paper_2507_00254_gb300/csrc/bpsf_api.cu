@@ -655,16 +655,16 @@ extern "C" bpsf_status bpsf_create(bpsf_ctx **out, int32_t M, int32_t N, int64_t
             bpsf_activate_layout(cd, 1);
         }
     }
-    if (e == cudaSuccess) e = cudaMalloc((void **)&c->d_ctr, sizeof(StreamCounters));
-    if (e == cudaSuccess) e = cudaMemset(c->d_ctr, 0, sizeof(StreamCounters));
-    if (e == cudaSuccess) e = cudaMallocHost((void **)&c->h_ctr, sizeof(StreamCounters));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&c->d_ctr, kMaxStreams * sizeof(StreamCounters));
+    if (e == cudaSuccess) e = cudaMemset(c->d_ctr, 0, kMaxStreams * sizeof(StreamCounters));
+    if (e == cudaSuccess) e = cudaMallocHost((void **)&c->h_ctr, kMaxStreams * sizeof(StreamCounters));
     if (e == cudaSuccess) e = cudaMallocHost((void **)&c->h_flag, 64);
     if (e == cudaSuccess) e = cudaMallocHost((void **)&c->h_preset, sizeof(StreamCounters));
     if (e != cudaSuccess) {
         bpsf_destroy(c);
         return bpsf_fail(BPSF_ECUDA, "context allocation: %s", cudaGetErrorString(e));
     }
-    std::memset(c->h_ctr, 0, sizeof(StreamCounters));
+    std::memset(c->h_ctr, 0, kMaxStreams * sizeof(StreamCounters));
     c->tune = default_tuning(c);
     bpsf_tuning cached;
     if (bpsf_tuning_cache_lookup(c, &cached)) c->tune = cached;
@@ -677,7 +677,27 @@ extern "C" bpsf_status bpsf_create(bpsf_ctx **out, int32_t M, int32_t N, int64_t
 // ---------------------------------------------------------------------------
 
 bpsf_status bpsf_ensure_workspace(bpsf_ctx *c, long long n) {
-    const long long cap = bpsf_record_ring(std::max<long long>(n, 1));
+    long long cap_s = 0;
+    return bpsf_ensure_workspace_sharded(c, n, 1, &cap_s);
+}
+
+// Shards of a batch of n shots in a launch of n_jobs jobs: a power of two, at
+// most kMaxShards, with no more than kMaxStreams streams in the launch and at
+// least kMinShardShots shots per shard; codes of more than kMaxShardNnz edges
+// are not sharded (their blocks claim work rarely, and a block that moves to
+// another stream reloads the code's tables).
+int bpsf_batch_shards(const bpsf_ctx *c, long long n, int n_jobs) {
+    int k = 1;
+    if (c->nnz > kMaxShardNnz) return 1;
+    while (2 * k <= kMaxShards && (long long)n_jobs * 2 * k <= kMaxStreams && n / (2 * k) >= kMinShardShots) k *= 2;
+    return k;
+}
+
+bpsf_status bpsf_ensure_workspace_sharded(bpsf_ctx *c, long long n, int shards, long long *shard_cap) {
+    const long long per = (std::max<long long>(n, 1) + shards - 1) / shards;
+    const long long cap_s = bpsf_record_ring(per);
+    *shard_cap = cap_s;
+    const long long cap = cap_s * shards;  // a power of two: shards is one
     if (cap <= c->rec_cap) return BPSF_OK;
     const size_t total = bpsf_records_bytes(cap, c->p.w, c->Ws, c->Wn, 16);
     free_workspace(c);
@@ -695,6 +715,35 @@ static bpsf_status clear_queue(bpsf_ctx *c, cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(c->rec.qseq, 0, 8 * (size_t)c->rec.cap, s);
     if (e != cudaSuccess) return bpsf_fail(BPSF_ECUDA, "cudaMemsetAsync: %s", cudaGetErrorString(e));
     return BPSF_OK;
+}
+
+void bpsf_shard_streams(const bpsf_ctx *c, const JobDev &job, int shards, long long shard_cap, const DebugDev *dbg,
+                        StreamDev *out) {
+    const long long n = job.n_shots;
+    const long long ww = c->p.w > 0 ? c->p.w : 1;
+    for (int j = 0; j < shards; ++j) {
+        const long long a = n * j / shards, b = n * (j + 1) / shards;
+        JobDev jj = job;
+        jj.synd = job.synd + a * job.synd_stride;
+        jj.corr = job.corr + a * job.corr_stride;
+        jj.conv = job.conv + a;
+        jj.iters = job.iters + a;
+        jj.stage = job.stage ? job.stage + a : nullptr;
+        jj.n_shots = b - a;
+        StreamDev sd = bpsf_make_stream(c, jj, dbg, 0);
+        sd.ctr = c->d_ctr + j;
+        const long long r0 = (long long)j * shard_cap;
+        Records &r = sd.rec;
+        r.qseq = c->rec.qseq + r0;
+        r.qshot = c->rec.qshot + r0;
+        r.done = c->rec.done + r0;
+        r.best = c->rec.best + r0;
+        r.win = c->rec.win + r0 * c->Wn;
+        r.phi = c->rec.phi + r0 * ww;
+        r.synd = c->rec.synd + r0 * c->Ws;
+        r.cap = shard_cap;
+        out[j] = sd;
+    }
 }
 
 StreamDev bpsf_make_stream(const bpsf_ctx *c, const JobDev &job, const DebugDev *dbg, unsigned flags) {
@@ -744,19 +793,34 @@ static bpsf_status decode_impl(bpsf_ctx *c, int64_t n, const uint32_t *synd, int
     bpsf_ctx *cs1[1] = {c};
     st = bpsf_make_plan(cs1, 1, &c->tune, dbg != nullptr, &pl);
     if (st != BPSF_OK) return st;
-    st = bpsf_ensure_workspace(c, n);
+    // Shards (the debug dump indexes its arrays by shot, so it keeps one).
+    const int K = dbg ? 1 : bpsf_batch_shards(c, n, 1);
+    if (K > 1) {
+        bpsf_ctx *ck[kMaxShards];
+        bpsf_tuning tk[kMaxShards];
+        for (int j = 0; j < K; ++j) {
+            ck[j] = c;
+            tk[j] = c->tune;
+        }
+        st = bpsf_make_plan(ck, K, tk, false, &pl);
+        if (st != BPSF_OK) return st;
+    }
+    long long cap_s = 0;
+    st = bpsf_ensure_workspace_sharded(c, n, K, &cap_s);
     if (st != BPSF_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
-    cudaError_t e = cudaMemsetAsync(c->d_ctr, 0, sizeof(StreamCounters), s);
+    cudaError_t e = cudaMemsetAsync(c->d_ctr, 0, K * sizeof(StreamCounters), s);
     if (e != cudaSuccess) return bpsf_fail(BPSF_ECUDA, "cudaMemsetAsync: %s", cudaGetErrorString(e));
     st = clear_queue(c, s);
     if (st != BPSF_OK) return st;
     JobDev job{synd, corr, conv, iters, stage, n, ss, cs};
-    StreamDev sd = bpsf_make_stream(c, job, dbg, 0);
-    bpsf_launch_plan(pl, dbg != nullptr, &sd, 1, pl.grid, stream);
+    StreamDev sds[kMaxShards];
+    bpsf_shard_streams(c, job, K, cap_s, dbg, sds);
+    bpsf_launch_plan(pl, dbg != nullptr, sds, K, pl.grid, stream);
     e = cudaGetLastError();
     if (e != cudaSuccess) return bpsf_fail(BPSF_ECUDA, "kernel launch: %s", cudaGetErrorString(e));
     c->d_ctr_last = c->d_ctr;
+    c->last_shards = K;
     c->last_launch_n = n;
     return BPSF_OK;
 }
@@ -779,19 +843,27 @@ extern "C" bpsf_status bpsf_sync(bpsf_ctx *c, void *stream) {
     cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
     if (e != cudaSuccess) return bpsf_fail(BPSF_ECUDA, "cudaStreamSynchronize: %s", cudaGetErrorString(e));
     StreamCounters *dc = c->d_ctr_last ? c->d_ctr_last : c->d_ctr;
-    e = cudaMemcpy(c->h_ctr, dc, sizeof(StreamCounters), cudaMemcpyDeviceToHost);
+    const int K = std::max(1, c->last_shards);
+    e = cudaMemcpy(c->h_ctr, dc, K * sizeof(StreamCounters), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return bpsf_fail(BPSF_ECUDA, "cudaMemcpy: %s", cudaGetErrorString(e));
-    const StreamCounters &k = *c->h_ctr;
-    c->last.initial_runs = (int64_t)k.init_done;
-    c->last.failed_shots = (int64_t)k.rec_count;
-    c->last.trial_runs = (int64_t)k.trial_runs;
-    c->last.iterations = (int64_t)k.iters_total;
-    c->last.edge_updates = (int64_t)k.iters_total * c->nnz;
-    c->last.slot_capacity = (int64_t)k.slot_capacity;
-    c->last.trials_cancelled = (int64_t)k.trials_cancelled;
-    if (k.status) {
-        const unsigned stv = k.status;
-        cudaMemsetAsync(&dc->status, 0, sizeof(unsigned), (cudaStream_t)stream);
+    // The launch's shards add up.
+    bpsf_work w{};
+    unsigned stv = 0;
+    for (int j = 0; j < K; ++j) {
+        const StreamCounters &k = c->h_ctr[j];
+        w.initial_runs += (int64_t)k.init_done;
+        w.failed_shots += (int64_t)k.rec_count;
+        w.trial_runs += (int64_t)k.trial_runs;
+        w.iterations += (int64_t)k.iters_total;
+        w.slot_capacity += (int64_t)k.slot_capacity;
+        w.trials_cancelled += (int64_t)k.trials_cancelled;
+        stv |= k.status;
+    }
+    w.edge_updates = w.iterations * c->nnz;
+    c->last = w;
+    if (stv) {
+        for (int j = 0; j < K; ++j)
+            if (c->h_ctr[j].status) cudaMemsetAsync(&dc[j].status, 0, sizeof(unsigned), (cudaStream_t)stream);
         cudaStreamSynchronize((cudaStream_t)stream);
         if (stv & (kDevReadyTimeout | kDevIdleTimeout))
             return bpsf_fail(BPSF_ETIMEOUT, "a bounded device wait ran out (status 0x%x)", stv);
@@ -911,6 +983,7 @@ extern "C" bpsf_status bpsf_decode_plain(bpsf_ctx *c, int64_t n, const uint32_t 
     }
     c->last = bpsf_work{n, failed, trial_runs, iters_total, iters_total * c->nnz, cap, cancelled};
     c->d_ctr_last = c->d_ctr;
+    c->last_shards = 1;
     return BPSF_OK;
 }
 
@@ -1054,30 +1127,45 @@ extern "C" bpsf_status bpsf_decode_multi(int32_t n_jobs, const bpsf_job *jobs, v
     }
     bpsf_ctx *c0 = codes[0];
     cudaSetDevice(c0->device);
-    // Each code keeps its own team shape (shrunk if its block does not fit).
-    std::vector<bpsf_tuning> tunes(n_jobs);
-    for (int k = 0; k < n_jobs; ++k) tunes[k] = codes[k]->tune;
+    // Each code keeps its own team shape (shrunk if its block does not fit);
+    // each job is split into shards (streams of the launch with their own
+    // counters and ring slices).
+    std::vector<int> shards(n_jobs);
+    std::vector<bpsf_ctx *> scodes;
+    std::vector<bpsf_tuning> tunes;
+    for (int k = 0; k < n_jobs; ++k) {
+        shards[k] = bpsf_batch_shards(codes[k], std::max<int64_t>(jobs[k].n_shots, 1), n_jobs);
+        for (int q = 0; q < shards[k]; ++q) {
+            scodes.push_back(codes[k]);
+            tunes.push_back(codes[k]->tune);
+        }
+    }
+    const int n_streams = (int)scodes.size();
     bpsf_plan pl;
-    bpsf_status st = bpsf_make_plan(codes.data(), n_jobs, tunes.data(), false, &pl, true);
+    bpsf_status st = bpsf_make_plan(scodes.data(), n_streams, tunes.data(), false, &pl, true);
     if (st != BPSF_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
-    std::vector<StreamDev> sds(n_jobs);
+    std::vector<StreamDev> sds(n_streams);
+    int at = 0;
     for (int k = 0; k < n_jobs; ++k) {
         bpsf_ctx *c = codes[k];
         const bpsf_job &j = jobs[k];
-        st = bpsf_ensure_workspace(c, std::max<int64_t>(j.n_shots, 1));
+        long long cap_s = 0;
+        st = bpsf_ensure_workspace_sharded(c, std::max<int64_t>(j.n_shots, 1), shards[k], &cap_s);
         if (st != BPSF_OK) return st;
-        cudaError_t e = cudaMemsetAsync(c->d_ctr, 0, sizeof(StreamCounters), s);
+        cudaError_t e = cudaMemsetAsync(c->d_ctr, 0, shards[k] * sizeof(StreamCounters), s);
         if (e != cudaSuccess) return bpsf_fail(BPSF_ECUDA, "cudaMemsetAsync: %s", cudaGetErrorString(e));
         st = clear_queue(c, s);
         if (st != BPSF_OK) return st;
         JobDev job{j.d_synd, j.d_corr, j.d_converged, j.d_iters, j.d_stage, j.n_shots, j.synd_stride_words,
                    j.corr_stride_words};
-        sds[k] = bpsf_make_stream(c, job, nullptr, 0);
+        bpsf_shard_streams(c, job, shards[k], cap_s, nullptr, sds.data() + at);
+        at += shards[k];
         c->last_launch_n = j.n_shots;
         c->d_ctr_last = c->d_ctr;
+        c->last_shards = shards[k];
     }
-    bpsf_launch_plan(pl, false, sds.data(), n_jobs, pl.grid, stream);
+    bpsf_launch_plan(pl, false, sds.data(), n_streams, pl.grid, stream);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return bpsf_fail(BPSF_ECUDA, "kernel launch: %s", cudaGetErrorString(e));
     return BPSF_OK;
@@ -1254,6 +1342,7 @@ extern "C" bpsf_status bpsf_selftest_wait(bpsf_ctx *c, int64_t wait_us, void *st
     e = cudaGetLastError();
     if (e != cudaSuccess) return bpsf_fail(BPSF_ECUDA, "kernel launch: %s", cudaGetErrorString(e));
     c->d_ctr_last = c->d_ctr;
+    c->last_shards = 1;
     return bpsf_sync(c, stream);
 }
 

@@ -30,7 +30,7 @@ struct bpsf_ctx {
     const unsigned long long *default_masks = nullptr;
     int default_n_trials = 0;
     bpsf::CodeDev code{};
-    bpsf::StreamCounters *d_ctr = nullptr;  // per-launch counters
+    bpsf::StreamCounters *d_ctr = nullptr;  // per-launch counters, one block per shard (kMaxStreams)
     bpsf::StreamCounters *d_ctr_last = nullptr;  // counters of the most recent launch (read by bpsf_sync)
     bpsf::StreamCounters *h_ctr = nullptr;  // pinned copy read by bpsf_sync
     bpsf::StreamCounters *h_preset = nullptr;
@@ -43,7 +43,21 @@ struct bpsf_ctx {
     bpsf_tuning tune{};
     bpsf_work last{};
     long long last_launch_n = 0;
+    int last_shards = 1;                    // shards of the last launch (counter blocks bpsf_sync adds up)
 };
+
+// A batch is decoded as up to kMaxShards shards: contiguous shot ranges, each
+// its own stream of the launch with its own counters and its own slice of the
+// record ring (so the blocks' claims spread over several sets of counters).
+constexpr int kMaxShards = 4;
+constexpr long long kMinShardShots = 8192;
+constexpr int kMaxShardNnz = 2048;  // larger codes: few, long runs per block, and a costly table reload per stream
+int bpsf_batch_shards(const bpsf_ctx *c, long long n, int n_jobs);
+// Workspace for n shots in `shards` shards; *shard_cap = records per shard.
+bpsf_status bpsf_ensure_workspace_sharded(bpsf_ctx *c, long long n, int shards, long long *shard_cap);
+// The streams of one job's shards (counters and ring slices of ctx c).
+void bpsf_shard_streams(const bpsf_ctx *c, const bpsf::JobDev &job, int shards, long long shard_cap,
+                        const bpsf::DebugDev *dbg, bpsf::StreamDev *out);
 
 // Launch plan of the persistent kernel for one or several codes.
 struct bpsf_plan {

@@ -118,6 +118,7 @@ extern "C" bpsf_status bpsf_decode_noalloc(bpsf_ctx *c, int64_t n, const uint32_
     e = cudaMemcpyAsync(c->d_ctr, ctr, sizeof(StreamCounters), cudaMemcpyDeviceToDevice, s);
     if (e != cudaSuccess) return bpsf_fail(BPSF_ECUDA, "counter copy: %s", cudaGetErrorString(e));
     c->d_ctr_last = c->d_ctr;
+    c->last_shards = 1;
     c->last_launch_n = n;
     return BPSF_OK;
 }

@@ -392,6 +392,32 @@ def test_one_byte_flip_words():
     assert ei.value.status == B.BPSF_EINVAL
 
 
+def test_sharded_batch_equals_its_pieces_decoded_alone():
+    """A batch large enough to be decoded as four shards (streams of one launch
+    with their own counters and record-ring slices) gives exactly the outputs
+    and work of its four quarters decoded one by one (too small to shard)."""
+    P = B.Params(max_iter=100, alpha=0.625, w=6, short_iter=20)
+    q = 9000
+    oc, e, s = make_inputs("bb144", 0.07, 4 * q, 21)
+    dec = decoder("bb144", 0.07, P)
+    whole = gpu_decode(dec, s)
+    ww = dec.last_work()
+    parts, works = [], []
+    for k in range(4):
+        parts.append(gpu_decode(dec, s[k * q:(k + 1) * q]))
+        works.append(dec.last_work())
+    for key in ("corr", "conv", "iters", "stage"):
+        assert (whole[key] == np.concatenate([p_[key] for p_ in parts])).all(), key
+    for key in ("initial_runs", "failed_shots", "trial_runs", "iterations", "edge_updates"):
+        assert ww[key] == sum(w_[key] for w_ in works), key
+    assert ww["initial_runs"] == 4 * q and (whole["stage"] == 1).sum() > 0
+    # And the oracle on a sample of each quarter.
+    idx = np.concatenate([k * q + np.arange(0, q, 37) for k in range(4)])
+    eo, co, io, so = oc.bpsf_batch(s[idx], 0.07, oparams(P), threads=THREADS)
+    assert (unpack(whole["corr"][idx], oc.N) == eo).all(axis=1).mean() >= CORR_MATCH
+    assert (whole["stage"][idx] == so).all()
+
+
 def test_launch_shape_irregular_code():
     """Every slot count has its own message layout (rank stride and edge order);
     for the irregular-row [[254,28]] code the strides differ from M at some slot
