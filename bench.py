@@ -28,9 +28,9 @@ sys.path.insert(0, ROOT)
 
 P_LIST = (0.02, 0.04, 0.06, 0.08)
 SHOTS_PER_P = 1_000_000
-# ncu, one launch of 4 x 400k shots (failed-shot records in failure order):
-# 23.96 MB read + 28.63 MB written.
-DRAM_BYTES_PER_SHOT = 52.59e6 / 1_600_000
+# ncu, one launch of 4 x 400k shots (each batch in four shards):
+# 23.24 MB read + 24.54 MB written.
+DRAM_BYTES_PER_SHOT = 47.78e6 / 1_600_000
 CODE = "bb144"
 N_BITS, M_CHECKS, NNZ = 144, 72, 432
 PARAMS = dict(max_iter=100, alpha=0.625, w=6, w_max=0, short_iter=20, select=0)
