@@ -139,7 +139,10 @@ void bpsf_destroy(bpsf_ctx *ctx);
  * workspace holds one record per failed shot, in failure order (a power of
  * two >= n_shots records, about 100 bytes each for [[144,12,12]] at w = 6);
  * a call with a larger n_shots than before grows it, so capture such calls
- * in a CUDA graph only after a warm-up call.
+ * in a CUDA graph only after a warm-up call.  A batch of at least 16384
+ * shots of a code with at most 2048 edges runs as 2 or 4 shards (contiguous
+ * shot ranges with their own claim counters and record slices, one launch);
+ * this changes no result, and bpsf_last_work reports their sums.
  */
 bpsf_status bpsf_decode(bpsf_ctx *ctx, int64_t n_shots, const uint32_t *d_synd, int32_t synd_stride_words,
                         uint32_t *d_corr, int32_t corr_stride_words, uint8_t *d_converged, int16_t *d_iters,
